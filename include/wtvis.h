@@ -1,0 +1,189 @@
+/*
+ * wtvis.h -- C ABI of libwtvis: GB300 (sm_103a) model-visibility prediction
+ * for the major cycle of CLEAN, after Skipper, Scaife & McEwen,
+ * "Cleaning radio interferometric images using a spherical wavelet
+ * decomposition" (arXiv:1909.03956).
+ *
+ * Two routes compute the model visibilities of a clean-component list:
+ *   - the direct sum over components (Sec. 3.3, Eq. 12): dft_predict_vis;
+ *   - the spherical Haar wavelet route (Sec. 3.2-3.5, Eqs. 9, 10, 16, 17):
+ *     wt_build_tree maps the components onto a nested pixelisation of the
+ *     celestial sphere and keeps the nonzero scaling/wavelet coefficients in
+ *     a tree; wt_predict_vis evaluates, per visibility, the plane wave's
+ *     coefficients on that tree and the multiresolution sum.
+ * subtract_model forms the residual visibilities (Sec. 2.2, major-cycle
+ * step 2).
+ *
+ * Conventions (all entry points):
+ *   - Pointers are DEVICE pointers unless the comment says host. The caller
+ *     owns every input and output buffer; the library owns only wt_tree
+ *     handles (and their device memory) and the scratch it allocates inside
+ *     a call.
+ *   - uvw is an array of n_vis baselines [u, v, w] in wavelengths, row-major
+ *     (24 bytes per visibility), float64. The exponent of Eq. 1 is then
+ *     dimensionless.
+ *   - Components are (l, m, flux): float64 direction cosines relative to the
+ *     phase centre (Sec. 2.2; l east, m north) and float64 fluxes.
+ *   - Visibilities are interleaved complex: complex128 ([re, im] float64
+ *     pairs) in WT_FP64 mode, complex64 ([re, im] float32 pairs) in the
+ *     other modes.
+ *   - sign = +1 evaluates exp(+i 2 pi B.(s - P)) as printed in Eqs. 1, 12
+ *     and 14; sign = -1 the conjugate convention.
+ *   - stream is a cudaStream_t (NULL = legacy default stream). Every call is
+ *     asynchronous on that stream unless its comment says otherwise.
+ *   - Return value: WT_OK or a negative wt_status. Argument errors are
+ *     detected on the host and returned at once, before anything is
+ *     enqueued. Errors found by a kernel (a component with l^2 + m^2 >= 1, a
+ *     non-finite input, a wait that ran out of time) are recorded in a
+ *     per-device status word that wt_device_status() reads and clears.
+ *   - wt_last_error() gives a text message for the calling thread's last
+ *     failing call.
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     entry point returns WT_ERR_CUDA.
+ */
+#ifndef WTVIS_H
+#define WTVIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wt_tree_s* wt_tree;     /* opaque, owned by the library */
+
+typedef enum {
+    WT_OK = 0,
+    WT_ERR_ARG = -1,          /* null pointer, negative size, bad mode/sign */
+    WT_ERR_RANGE = -2,        /* J outside 1..30, l^2 + m^2 >= 1, non-finite input */
+    WT_ERR_CUDA = -3,         /* a CUDA call failed (message in wt_last_error) */
+    WT_ERR_NOMEM = -4,        /* device allocation failed */
+    WT_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out */
+    WT_ERR_CORRUPT = -6,      /* a tree handle failed validation */
+    WT_ERR_UNSUPPORTED = -7   /* mode not available for this entry point */
+} wt_status;
+
+typedef enum {
+    WT_FP64 = 0,     /* float64 throughout, complex128 output */
+    WT_MIXED = 1,    /* float64-accurate phase (double-float), float32 sincos and
+                        compensated float32 accumulation, complex64 output */
+    WT_LEARNED = 2   /* wavelet route only: learned per-level response (MLP) */
+} wt_mode;
+
+typedef enum {
+    WT_SUM_EQ17 = 0, /* multiresolution sum over all tree nodes (Eq. 17) */
+    WT_SUM_EQ16 = 1  /* level-J sum over the leaves only (Eq. 16) */
+} wt_sum;
+
+/* ---------------------------------------------------------------------------
+ * wt_build_tree -- Sec. 3.5 (the algorithm) with Sec. 3.3 (SIN projection),
+ * Sec. 3.4 / Eq. 18 (uvw -> xyz rotation) and Eqs. 9, 10 (coefficients).
+ *
+ * Maps the n_comp components to pixels of level J of the HEALPix-nested
+ * pixelisation of Sec. 3.2 (N_j = 12 * 4^(j-1) pixels at level j; the pole
+ * axis is the NCP and the longitude the RA), merges components that share a
+ * level-J pixel (Phi_k = summed flux, in input order), builds every ancestor
+ * k_j = k_J >> 2(J - j), and computes the image coefficients:
+ *   lambda_J,k = Phi_k / A_J,   A_j = 4 pi / N_j,
+ *   lambda_j,k = (1/4) sum of the four children (absent child = 0)   (Eq. 9)
+ *   gamma^m_j,k = (sqrt(A_j)/4) (H_m . children)                      (Eq. 10)
+ * in the same rounding order as the paper's formulas read left to right, so
+ * that keys, topology and coefficients are reproducible bit for bit.
+ *
+ *   l, m, flux  device float64 [n_comp]; l^2 + m^2 < 1 required.
+ *   n_comp      >= 0 (0 gives an empty tree whose visibilities are 0).
+ *   ra0, dec0   phase centre (radians).
+ *   J           level, 1 <= J <= 30.
+ *   out         host pointer receiving the new handle (freed by wt_free_tree).
+ * The call allocates the tree's device memory, enqueues the build on
+ * `stream` and returns without waiting. Input buffers may be reused once
+ * the stream has passed the build.
+ * ------------------------------------------------------------------------- */
+int wt_build_tree(const double* l, const double* m, const double* flux, int64_t n_comp,
+                  double ra0, double dec0, int J, wt_tree* out, void* stream);
+
+/* Sizes of a built tree (host outputs; any may be NULL). Waits for the
+ * build's stream. nodes_per_level has J entries, level 1 first. */
+int wt_tree_info(wt_tree t, int* J, int64_t* n_leaves, int64_t* n_nodes, int64_t* nodes_per_level);
+
+/* Copy a built tree to HOST buffers in breadth-first order: nodes sorted by
+ * (level ascending, pixel key ascending). Waits for the build's stream.
+ *   key [n_nodes]            nested pixel index k_j of each node
+ *   child_mask [n_nodes]     bit c set when child 4k + c exists (0 for leaves)
+ *   first_child [n_nodes]    breadth-first index of the first child, -1 for leaves
+ *   lambda [n_nodes]         scaling coefficient (Eq. 9; level J: Phi / A_J)
+ *   gamma [n_nodes][3]       wavelet coefficients (Eq. 10; 0 for leaves)
+ *   leaf_dir [n_leaves][3]   pixel centre in the uvw frame as (s_u, s_v, s_w - 1)
+ *   leaf_flux [n_leaves]     Phi_k, the merged flux of each leaf
+ * Any pointer may be NULL to skip that array. */
+int wt_tree_export(wt_tree t, int64_t* key, uint8_t* child_mask, int32_t* first_child,
+                   double* lambda, double* gamma, double* leaf_dir, double* leaf_flux);
+
+/* Release a tree handle and its device memory (synchronises with the
+ * stream the tree was built on). NULL is ignored. */
+void wt_free_tree(wt_tree t);
+
+/* ---------------------------------------------------------------------------
+ * wt_predict_vis -- Sec. 3.3 (Eqs. 13-17) and Sec. 3.6.1 (per-visibility
+ * steps): for each baseline B_n,
+ *   1. the plane wave F^P (Eq. 14) at every leaf pixel centre: eta_J,k;
+ *   2. the plane wave's coefficients for j = J-1 .. 1, bottom-up:
+ *      eta_j,k = (1/4) sum of children, sigma^m_j,k = (sqrt(A_j)/4) H_m . children
+ *      (absent child = 0; Sec. 3.5: empty branches are skipped);
+ *   3. the multiresolution sum (Eq. 17 with the area factor of level 1):
+ *      V = A_1 sum_k lambda_1,k eta_1,k + sum_j sum_k sum_m gamma^m sigma^m.
+ * With which = WT_SUM_EQ16 the level-J sum V = sum_k Phi_k eta_J,k (Eq. 16)
+ * is evaluated instead; the two agree up to rounding.
+ *
+ *   t        a built tree (the build must precede this call in stream order)
+ *   uvw      device float64 [n_vis][3], wavelengths
+ *   vis_out  device complex128 [n_vis] (WT_FP64) or complex64 [n_vis] (WT_MIXED)
+ *   mode     WT_FP64 or WT_MIXED (WT_LEARNED: see wt_predict_vis_learned)
+ *   which    wt_sum
+ * ------------------------------------------------------------------------- */
+int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
+                   int mode, int sign, int which, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * dft_predict_vis -- Sec. 3.3, Eq. 12: the direct sum over the component list
+ *   V_n = sum_m C_m exp(sign i 2 pi [u_n l_m + v_n m_m + w_n (n_m - 1)]),
+ *   n_m = sqrt(1 - l_m^2 - m_m^2),
+ * the "more accurate alternative" of Sec. 2.2. Components are staged through
+ * a device scratch buffer the call allocates and releases on `stream`.
+ *   l, m, flux  device float64 [n_comp]
+ *   uvw         device float64 [n_vis][3]
+ *   vis_out     device complex128 (WT_FP64) or complex64 (WT_MIXED) [n_vis]
+ * ------------------------------------------------------------------------- */
+int dft_predict_vis(const double* l, const double* m, const double* flux, int64_t n_comp,
+                    const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign,
+                    void* stream);
+
+/* ---------------------------------------------------------------------------
+ * subtract_model -- Sec. 2.2, major-cycle step 2: V_resid = V - V_M,
+ * element by element. vis_resid may alias vis_obs (in place).
+ *   mode WT_FP64: complex128 arrays; any other mode: complex64 arrays.
+ * ------------------------------------------------------------------------- */
+int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid,
+                   int64_t n_vis, int mode, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Helpers
+ * ------------------------------------------------------------------------- */
+
+/* Sec. 3.3 and Table 1: the smallest J whose pixel size
+ * Delta theta_J = 2^(1-J) sqrt(pi/3) is at most half of dtheta (radians),
+ * i.e. the sphere oversamples the image pixel by two. Host only. Returns
+ * WT_ERR_ARG for dtheta <= 0 and WT_ERR_RANGE when J would exceed 30. */
+int wt_recommended_J(double dtheta_rad);
+
+/* Read and clear the device status word of the current device after
+ * synchronising `stream`: WT_OK, or the first error a kernel recorded. */
+int wt_device_status(void* stream);
+
+/* Text of the calling thread's last error (never NULL). */
+const char* wt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WTVIS_H */

@@ -1,0 +1,223 @@
+"""GB300-native model-visibility prediction (arXiv:1909.03956).
+
+A thin ctypes binding over ``libwtvis.so``, the C-ABI library declared in
+``include/wtvis.h``. The functions here carry the same names as the C entry
+points and only marshal arguments: torch tensors supply device memory and
+the current CUDA stream; every step of the computation runs in the library's
+CUDA kernels. There is no CPU fallback: if the library cannot be loaded, or
+a call fails, an exception is raised.
+
+Entry points (see include/wtvis.h for the contract of each):
+    wt_build_tree     components -> sphere pixels -> coefficient tree (Sec. 3.5)
+    wt_tree_info      tree sizes
+    wt_tree_export    tree arrays, breadth-first, on the host
+    wt_free_tree      release a tree
+    wt_predict_vis    Eq. 17 (or Eq. 16) per visibility on the tree
+    dft_predict_vis   Eq. 12, direct sum over the components
+    subtract_model    V_resid = V - V_M (Sec. 2.2)
+    wt_recommended_J  Table 1 rule (Sec. 3.3)
+    wt_device_status  read and clear the device-side status word
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+WT_OK, WT_ERR_ARG, WT_ERR_RANGE, WT_ERR_CUDA, WT_ERR_NOMEM, WT_ERR_TIMEOUT, WT_ERR_CORRUPT, WT_ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+WT_FP64, WT_MIXED, WT_LEARNED = 0, 1, 2
+WT_SUM_EQ17, WT_SUM_EQ16 = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwtvis.so")
+
+# Every symbol include/wtvis.h declares.
+EXPORTS = [
+    "wt_build_tree", "wt_tree_info", "wt_tree_export", "wt_free_tree", "wt_predict_vis",
+    "dft_predict_vis", "subtract_model", "wt_recommended_J", "wt_device_status", "wt_last_error",
+]
+
+
+class WtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Load libwtvis.so (building it with nvcc when absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libwtvis.so is not built (%s); run paper_1909_03956_gb300/build.py" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    _declare(L)
+    _lib = L
+    return L
+
+
+def _declare(L):
+    vp, d, i64 = C.c_void_p, C.c_double, C.c_int64
+    L.wt_build_tree.argtypes = [vp, vp, vp, i64, d, d, C.c_int, C.POINTER(vp), vp]
+    L.wt_tree_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(i64), vp]
+    L.wt_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.wt_free_tree.argtypes = [vp]
+    L.wt_free_tree.restype = None
+    L.wt_predict_vis.argtypes = [vp, vp, i64, vp, C.c_int, C.c_int, C.c_int, vp]
+    L.dft_predict_vis.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int, C.c_int, vp]
+    L.subtract_model.argtypes = [vp, vp, vp, i64, C.c_int, vp]
+    L.wt_recommended_J.argtypes = [d]
+    L.wt_device_status.argtypes = [vp]
+    L.wt_last_error.restype = C.c_char_p
+
+
+def _check(rc):
+    if rc != WT_OK:
+        raise WtError(rc, load().wt_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _vis_dtype(mode):
+    import torch
+    return torch.complex128 if mode == WT_FP64 else torch.complex64
+
+
+# ---------------------------------------------------------------- tree
+
+class Tree:
+    """Owns a wt_tree handle (freed on close / garbage collection)."""
+
+    def __init__(self, handle, J):
+        self.h = handle
+        self.J = J
+
+    def close(self):
+        if self.h:
+            load().wt_free_tree(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return wt_tree_info(self)
+
+    def export(self):
+        return wt_tree_export(self)
+
+
+def wt_build_tree(l, m, flux, ra0, dec0, J, stream=None):
+    """Build the coefficient tree of Sec. 3.5 from float64 CUDA tensors."""
+    import torch
+    n = l.numel()
+    h = C.c_void_p()
+    _check(load().wt_build_tree(_dev(l, torch.float64), _dev(m, torch.float64), _dev(flux, torch.float64), n,
+                                float(ra0), float(dec0), int(J), C.byref(h), _stream(stream)))
+    return Tree(h, int(J))
+
+
+def wt_tree_info(tree):
+    J = C.c_int()
+    nl, nn = C.c_int64(), C.c_int64()
+    per = np.zeros(tree.J, dtype=np.int64)
+    _check(load().wt_tree_info(tree.h, C.byref(J), C.byref(nl), C.byref(nn), per.ctypes.data_as(C.c_void_p)))
+    return dict(J=J.value, n_leaves=nl.value, n_nodes=nn.value, per_level=per)
+
+
+def wt_tree_export(tree):
+    inf = wt_tree_info(tree)
+    T, NL = inf["n_nodes"], inf["n_leaves"]
+    key = np.zeros(T, dtype=np.int64)
+    mask = np.zeros(T, dtype=np.uint8)
+    first = np.zeros(T, dtype=np.int32)
+    lam = np.zeros(T)
+    gam = np.zeros((T, 3))
+    ldir = np.zeros((NL, 3))
+    lflux = np.zeros(NL)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(load().wt_tree_export(tree.h, p(key), p(mask), p(first), p(lam), p(gam), p(ldir), p(lflux)))
+    offs = np.concatenate([[0], np.cumsum(inf["per_level"])])
+    return dict(key=key, child_mask=mask, first_child=first, lam=lam, gamma=gam, leaf_dir=ldir,
+                leaf_flux=lflux, level_offsets=offs, **inf)
+
+
+def wt_free_tree(tree):
+    tree.close()
+
+
+def wt_predict_vis(tree, uvw, mode=WT_FP64, sign=1, which=WT_SUM_EQ17, out=None, stream=None):
+    """Model visibilities on the tree (Eq. 17, or Eq. 16 with which=WT_SUM_EQ16)."""
+    import torch
+    n = uvw.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=_vis_dtype(mode), device=uvw.device)
+    _check(load().wt_predict_vis(tree.h, _dev(uvw, torch.float64), n, _dev(out, _vis_dtype(mode)), int(mode),
+                                 int(sign), int(which), _stream(stream)))
+    return out
+
+
+def dft_predict_vis(l, m, flux, uvw, mode=WT_FP64, sign=1, out=None, stream=None):
+    """Direct sum over the components (Eq. 12)."""
+    import torch
+    n = uvw.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=_vis_dtype(mode), device=uvw.device)
+    _check(load().dft_predict_vis(_dev(l, torch.float64), _dev(m, torch.float64), _dev(flux, torch.float64),
+                                  l.numel(), _dev(uvw, torch.float64), n, _dev(out, _vis_dtype(mode)), int(mode),
+                                  int(sign), _stream(stream)))
+    return out
+
+
+def subtract_model(vis_obs, vis_model, mode=WT_FP64, out=None, stream=None):
+    """V_resid = V - V_M (Sec. 2.2). out may be vis_obs (in place)."""
+    dt = _vis_dtype(mode)
+    if out is None:
+        out = vis_obs.new_empty(vis_obs.shape)
+    _check(load().subtract_model(_dev(vis_obs, dt), _dev(vis_model, dt), _dev(out, dt), vis_obs.numel(),
+                                 int(mode), _stream(stream)))
+    return out
+
+
+def wt_recommended_J(dtheta_rad):
+    rc = load().wt_recommended_J(float(dtheta_rad))
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def wt_device_status(stream=None):
+    return _check(load().wt_device_status(_stream(stream)))
+
+
+def wt_last_error():
+    return load().wt_last_error().decode()

@@ -1,0 +1,194 @@
+// dft.cu -- dft_predict_vis: the direct sum over the clean-component list
+// (Sec. 3.3, Eq. 12; the "more accurate alternative" of Sec. 2.2):
+//   V_n = sum_m C_m exp(sign i 2 pi [u_n l_m + v_n m_m + w_n (n_m - 1)]).
+//
+// A prologue kernel packs each component once into a 32-byte record in a
+// scratch buffer: (l, m, n - 1, C) in float64 for WT_FP64, or double-float
+// halves of l, m, n - 1 plus C in float32 for WT_MIXED. The main kernel gives
+// each thread one visibility and streams the records through shared memory
+// (bulk copies, double-buffered, broadcast reads), like the wavelet kernels.
+#include "staging.cuh"
+#include "wt_internal.cuh"
+
+namespace wt {
+namespace {
+
+constexpr int kChunk = 512;
+
+struct CompD {
+    double l, m, nm1, flux;
+};
+struct CompF {
+    float lh, ll, mh, ml, nh, nl, flux, pad;
+};
+static_assert(sizeof(CompD) == 32 && sizeof(CompF) == 32, "component record layout");
+
+// n - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)), free of cancellation.
+__global__ void k_pack_components(const double* __restrict__ l, const double* __restrict__ m,
+                                  const double* __restrict__ flux, int64_t n, CompD* __restrict__ outd,
+                                  CompF* __restrict__ outf, int* status)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double li = l[i], mi = m[i], fi = flux[i];
+    const double r2 = li * li + mi * mi;
+    double nm1 = 0.0;
+    if (!(r2 < 1.0) || !isfinite(li) || !isfinite(mi) || !isfinite(fi)) {
+        record_status(status, WT_ERR_RANGE);
+    } else {
+        nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+    }
+    if (outd) outd[i] = CompD{li, mi, nm1, fi};
+    if (outf) {
+        const F2 a = split_f64(li), b = split_f64(mi), c = split_f64(nm1);
+        outf[i] = CompF{a.hi, a.lo, b.hi, b.lo, c.hi, c.lo, static_cast<float>(fi), 0.0f};
+    }
+}
+
+struct BodyD {
+    double u, v, w, sgn, vr, vi;
+    __device__ void operator()(const CompD& c)
+    {
+        double t = fma(w, c.nm1, fma(v, c.m, u * c.l));
+        t -= rint(t);
+        double s, co;
+        sincospi(2.0 * t, &s, &co);
+        vr = fma(c.flux, co, vr);
+        vi = fma(c.flux, sgn * s, vi);
+    }
+};
+
+struct BodyF {
+    F2 u, v, w;
+    float sgn, vr, vi, cr, ci;
+    __device__ void operator()(const CompF& c)
+    {
+        float th, tl;
+        phase_turns_df(u, v, w, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, th, tl);
+        float s, co;
+        sincos_turns_f32(th, tl, s, co);
+        kahan_add(vr, cr, c.flux * co);
+        kahan_add(vi, ci, c.flux * (sgn * s));
+    }
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dft_fp64(const CompD* __restrict__ comps, int64_t n_comp,
+                                                 const double* __restrict__ uvw, int64_t n_vis,
+                                                 double2* __restrict__ vis, double sgn, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stager<CompD> st;
+    stager_setup(st, smem, comps, n_comp, kChunk);
+    const int64_t ntiles = (n_vis + NT - 1) / NT;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t n = tile * NT + threadIdx.x;
+        const bool valid = n < n_vis;
+        BodyD b{valid ? uvw[3 * n] : 0.0, valid ? uvw[3 * n + 1] : 0.0, valid ? uvw[3 * n + 2] : 0.0, sgn, 0.0, 0.0};
+        if (!st.sweep(b)) {
+            if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
+            return;
+        }
+        if (valid) vis[n] = make_double2(b.vr, b.vi);
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comps, int64_t n_comp,
+                                                  const double* __restrict__ uvw, int64_t n_vis,
+                                                  float2* __restrict__ vis, float sgn, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stager<CompF> st;
+    stager_setup(st, smem, comps, n_comp, kChunk);
+    const int64_t ntiles = (n_vis + NT - 1) / NT;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t n = tile * NT + threadIdx.x;
+        const bool valid = n < n_vis;
+        BodyF b{split_f64(valid ? uvw[3 * n] : 0.0), split_f64(valid ? uvw[3 * n + 1] : 0.0),
+                split_f64(valid ? uvw[3 * n + 2] : 0.0), sgn, 0.f, 0.f, 0.f, 0.f};
+        if (!st.sweep(b)) {
+            if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
+            return;
+        }
+        if (valid) vis[n] = make_float2(b.vr - b.cr, b.vi - b.ci);
+    }
+}
+
+template <class K>
+int grid_for(K kernel, int nt, size_t smem, int64_t n_vis, dim3& grid)
+{
+    WT_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int per_sm = 0;
+    WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem));
+    if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "dft kernel does not fit on an SM");
+    const int64_t ntiles = (n_vis + nt - 1) / nt;
+    int64_t g = static_cast<int64_t>(num_sms()) * per_sm;
+    grid = dim3(static_cast<unsigned>(g < ntiles ? g : ntiles));
+    return WT_OK;
+}
+
+}  // namespace
+
+// Launch the DFT on component records already packed in `scratch`
+// (n_comp records of 32 bytes, 256-byte aligned).
+int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, int64_t n_vis, void* vis, int mode,
+                      int sign, cudaStream_t s)
+{
+    int* status = device_status_word();
+    dim3 grid;
+    if (mode == WT_FP64) {
+        constexpr int NT = 128;
+        const size_t smem = static_cast<size_t>(stager_bytes<CompD>(kChunk));
+        auto k = k_dft_fp64<NT>;
+        int rc = grid_for(k, NT, smem, n_vis, grid);
+        if (rc) return rc;
+        k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(scratch), n_comp, uvw, n_vis, static_cast<double2*>(vis),
+                                 static_cast<double>(sign), status);
+    } else {
+        constexpr int NT = 256;
+        const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
+        auto k = k_dft_mixed<NT>;
+        int rc = grid_for(k, NT, smem, n_vis, grid);
+        if (rc) return rc;
+        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(scratch), n_comp, uvw, n_vis, static_cast<float2*>(vis),
+                                 static_cast<float>(sign), status);
+    }
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+int dft_pack(const double* l, const double* m, const double* flux, int64_t n_comp, void* scratch, int mode,
+             cudaStream_t s)
+{
+    if (n_comp == 0) return WT_OK;
+    const int tb = 256;
+    k_pack_components<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(
+        l, m, flux, n_comp, mode == WT_FP64 ? static_cast<CompD*>(scratch) : nullptr,
+        mode == WT_FP64 ? nullptr : static_cast<CompF*>(scratch), device_status_word());
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+int predict_dft(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
+                int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s)
+{
+    if (n_vis == 0) return WT_OK;
+    // 32-byte records, padded to a 16-byte multiple for the bulk copies
+    const size_t bytes = static_cast<size_t>((n_comp > 0 ? n_comp : 1) * 32 + 256);
+    void* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "dft_predict_vis: scratch allocation of %zu bytes failed: %s", bytes,
+                         cudaGetErrorString(e));
+    }
+    int rc = dft_pack(l, m, flux, n_comp, scratch, mode, s);
+    if (rc == WT_OK) rc = dft_launch_packed(scratch, n_comp, uvw, n_vis, vis, mode, sign, s);
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (rc != WT_OK) return rc;
+    if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync");
+    return WT_OK;
+}
+
+}  // namespace wt

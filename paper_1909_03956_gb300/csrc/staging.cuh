@@ -1,0 +1,106 @@
+// staging.cuh -- per-CTA streaming of a read-only record list through shared
+// memory with bulk (TMA, non-tensor, non-multicast) copies and mbarriers.
+//
+// Every thread of the CTA walks the same records in the same order (each
+// thread owns a different visibility), so a record is read from shared
+// memory as a broadcast. Two buffers of `chunk` records alternate: while the
+// CTA works on one, the next chunk is in flight into the other. A list that
+// fits in the two buffers is loaded once and stays resident for every tile
+// the (persistent) CTA processes.
+#pragma once
+
+#include "wt_internal.cuh"
+
+namespace wt {
+
+template <class Rec>
+struct Stager {
+    const Rec* recs;      // global, 16-byte aligned, readable up to a 16-byte multiple
+    int64_t count;        // records in the list
+    Rec* buf;             // shared, 2 * chunk records
+    uint64_t* bars;       // shared, 2 mbarriers
+    int chunk;            // records per buffer (even, so chunk * sizeof(Rec) % 16 == 0)
+    uint32_t phase0, phase1;  // expected parity per buffer
+    bool resident;        // whole list fits in the two buffers
+    bool loaded;          // resident list already in shared memory
+
+    __device__ int64_t nchunks() const { return (count + chunk - 1) / chunk; }
+
+    __device__ void issue(int64_t c, int b)
+    {
+        const int64_t first = c * chunk;
+        const int64_t n = (count - first < chunk) ? (count - first) : chunk;
+        const uint32_t bytes = static_cast<uint32_t>(((n * static_cast<int64_t>(sizeof(Rec))) + 15) & ~int64_t(15));
+        mbar_arrive_expect_tx(&bars[b], bytes);
+        bulk_copy_g2s(buf + static_cast<int64_t>(b) * chunk, recs + first, bytes, &bars[b]);
+    }
+
+    // Called by all threads once, after the barriers are initialised.
+    __device__ void init_state()
+    {
+        phase0 = phase1 = 0;
+        resident = nchunks() <= 2;
+        loaded = false;
+    }
+
+    // Run body(rec) for every record, in order. Returns false (uniformly
+    // across the CTA) if a copy did not arrive within the spin limit.
+    template <class Body>
+    __device__ bool sweep(Body& body)
+    {
+        const int64_t nc = nchunks();
+        if (nc == 0) return true;
+        const bool need_load = !(resident && loaded);
+        if (need_load && threadIdx.x == 0) {
+            issue(0, 0);
+            if (nc > 1) issue(1, 1);
+        }
+        for (int64_t c = 0; c < nc; ++c) {
+            const int b = static_cast<int>(c & 1);
+            if (need_load) {
+                const bool ok = mbar_wait_parity(&bars[b], b ? phase1 : phase0);
+                if (!__syncthreads_and(ok ? 1 : 0)) return false;
+                if (b) phase1 ^= 1u;
+                else phase0 ^= 1u;
+            }
+            const int64_t first = c * chunk;
+            const int n = static_cast<int>((count - first < chunk) ? (count - first) : chunk);
+            const Rec* cb = buf + static_cast<int64_t>(b) * chunk;
+            for (int r = 0; r < n; ++r) body(cb[r]);
+            if (!resident) {
+                __syncthreads();                           // buffer b fully consumed
+                if (threadIdx.x == 0 && c + 2 < nc) issue(c + 2, b);
+            }
+        }
+        if (resident) loaded = true;
+        return true;
+    }
+};
+
+// Shared-memory layout helper: bytes for the two record buffers plus the two
+// mbarriers, rounded to 16.
+template <class Rec>
+__host__ __device__ constexpr int64_t stager_bytes(int chunk)
+{
+    return ((2 * static_cast<int64_t>(chunk) * static_cast<int64_t>(sizeof(Rec)) + 16 + 15) / 16) * 16;
+}
+
+template <class Rec>
+__device__ __forceinline__ void stager_setup(Stager<Rec>& st, unsigned char* smem, const Rec* recs, int64_t count,
+                                             int chunk)
+{
+    st.recs = recs;
+    st.count = count;
+    st.chunk = chunk;
+    st.buf = reinterpret_cast<Rec*>(smem);
+    st.bars = reinterpret_cast<uint64_t*>(smem + 2 * static_cast<int64_t>(chunk) * sizeof(Rec));
+    if (threadIdx.x == 0) {
+        mbar_init(&st.bars[0], 1);
+        mbar_init(&st.bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    st.init_state();
+}
+
+}  // namespace wt

@@ -1,0 +1,355 @@
+// wt_api.cu -- the extern "C" boundary of libwtvis: argument checks, handle
+// lifetime, error reporting, and dispatch to the kernels. No computation of
+// the method happens here; every step runs in the kernels of the other files.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "wt_internal.cuh"
+
+namespace wt {
+
+namespace {
+thread_local char g_msg[512] = "no error";
+std::mutex g_mu;
+int* g_status[64] = {nullptr};
+int g_sms[64] = {0};
+
+// cuMemGetAddressRange from the driver, looked up at run time so that the
+// library loads on machines without a driver (every call then fails cleanly).
+typedef int (*AddrRangeFn)(unsigned long long*, size_t*, unsigned long long);
+AddrRangeFn g_addr_range = nullptr;
+bool g_addr_range_tried = false;
+
+AddrRangeFn addr_range_fn()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr_range_tried) {
+        g_addr_range_tried = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_addr_range = reinterpret_cast<AddrRangeFn>(fn);
+        else
+            cudaGetLastError();
+    }
+    return g_addr_range;
+}
+
+int current_device(int* dev)
+{
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (*dev < 0 || *dev >= 64) return set_error(WT_ERR_CUDA, "device ordinal %d out of range", *dev);
+    return WT_OK;
+}
+}  // namespace
+
+int set_error(int status, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_error(cudaError_t e, const char* what)
+{
+    cudaGetLastError();
+    return set_error(WT_ERR_CUDA, "%s: %s (%d)", what, cudaGetErrorString(e), static_cast<int>(e));
+}
+
+int* device_status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(p);
+            return nullptr;
+        }
+        g_status[dev] = p;
+        // Keep stream-ordered allocations cached in the pool between calls.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    }
+    return g_status[dev];
+}
+
+int num_sms()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (g_sms[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = n > 0 ? n : 1;
+    }
+    return g_sms[dev];
+}
+
+// A pointer the kernels will dereference must be device (or managed) memory
+// of the current device, and [p, p + bytes) must lie inside its allocation.
+int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name)
+{
+    if (bytes == 0) return WT_OK;
+    if (!p) return set_error(WT_ERR_ARG, "%s: %s is NULL", fn, name);
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_ARG, "%s: %s is not a CUDA pointer (%s)", fn, name, cudaGetErrorString(e));
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return set_error(WT_ERR_ARG, "%s: %s must be device memory", fn, name);
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return set_error(WT_ERR_ARG, "%s: %s lives on device %d, current device is %d", fn, name, a.device, dev);
+    AddrRangeFn f = addr_range_fn();
+    if (f) {
+        unsigned long long base = 0;
+        size_t size = 0;
+        if (f(&base, &size, reinterpret_cast<unsigned long long>(p)) == 0) {
+            const unsigned long long end = base + size;
+            const unsigned long long q = reinterpret_cast<unsigned long long>(p);
+            if (q + bytes > end)
+                return set_error(WT_ERR_ARG, "%s: %s holds %llu bytes from this address, %zu needed", fn, name,
+                                 end - q, bytes);
+        }
+    }
+    return WT_OK;
+}
+
+}  // namespace wt
+
+using namespace wt;
+
+static int check_tree(wt_tree t, const char* fn)
+{
+    if (!t) return set_error(WT_ERR_ARG, "%s: tree is NULL", fn);
+    if (t->magic != kTreeMagic) return set_error(WT_ERR_CORRUPT, "%s: not a live tree handle", fn);
+    int dev = 0;
+    int rc = wt::current_device(&dev);
+    if (rc) return rc;
+    if (dev != t->device)
+        return set_error(WT_ERR_ARG, "%s: tree was built on device %d, current device is %d", fn, t->device, dev);
+    return WT_OK;
+}
+
+extern "C" {
+
+int wt_build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
+                  int J, wt_tree* out, void* stream)
+{
+    const char* fn = "wt_build_tree";
+    if (!out) return set_error(WT_ERR_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    if (n_comp < 0) return set_error(WT_ERR_ARG, "%s: n_comp < 0", fn);
+    if (n_comp > (int64_t(1) << 30)) return set_error(WT_ERR_RANGE, "%s: n_comp too large", fn);
+    if (J < 1 || J > kMaxJ) return set_error(WT_ERR_RANGE, "%s: J = %d outside 1..%d", fn, J, kMaxJ);
+    if (!isfinite(ra0) || !isfinite(dec0)) return set_error(WT_ERR_RANGE, "%s: non-finite phase centre", fn);
+    const size_t nb = static_cast<size_t>(n_comp) * sizeof(double);
+    int rc;
+    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux")))
+        return rc;
+    int dev = 0;
+    if ((rc = wt::current_device(&dev))) return rc;
+    wt_tree t = new (std::nothrow) wt_tree_s();
+    if (!t) return set_error(WT_ERR_NOMEM, "%s: host allocation failed", fn);
+    memset(static_cast<void*>(t), 0, sizeof(*t));
+    t->magic = kTreeMagic;
+    t->device = dev;
+    t->J = J;
+    t->ra0 = ra0;
+    t->dec0 = dec0;
+    t->n_comp = n_comp;
+    t->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&t->host_hdr), sizeof(TreeHeader));
+    if (e != cudaSuccess) {
+        t->magic = 0;
+        delete t;
+        return cuda_error(e, "cudaMallocHost");
+    }
+    rc = wt::build_tree(l, m, flux, n_comp, ra0, dec0, J, t, t->stream);
+    if (rc != WT_OK) {
+        if (t->block) cudaFreeAsync(t->block, t->stream);
+        cudaStreamSynchronize(t->stream);
+        cudaFreeHost(t->host_hdr);
+        t->magic = 0;
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return WT_OK;
+}
+
+int wt_tree_info(wt_tree t, int* J, int64_t* n_leaves, int64_t* n_nodes, int64_t* nodes_per_level)
+{
+    int rc = check_tree(t, "wt_tree_info");
+    if (rc) return rc;
+    if ((rc = wt::tree_sync_header(t))) return rc;
+    const TreeHeader* h = t->host_hdr;
+    if (J) *J = t->J;
+    if (n_leaves) *n_leaves = h->n_leaves;
+    if (n_nodes) *n_nodes = h->n_nodes;
+    if (nodes_per_level)
+        for (int j = 1; j <= t->J; ++j) nodes_per_level[j - 1] = h->per_level[j];
+    return WT_OK;
+}
+
+int wt_tree_export(wt_tree t, int64_t* key, uint8_t* child_mask, int32_t* first_child, double* lambda, double* gamma,
+                   double* leaf_dir, double* leaf_flux)
+{
+    int rc = check_tree(t, "wt_tree_export");
+    if (rc) return rc;
+    if ((rc = wt::tree_sync_header(t))) return rc;
+    const TreeHeader h = *t->host_hdr;
+    const int64_t T = h.n_nodes, NL = h.n_leaves;
+    if (T == 0) return WT_OK;
+    const TreeDev& d = t->d;
+    std::vector<int64_t> k(T);
+    std::vector<uint8_t> mk(T);
+    std::vector<int32_t> fc(T);
+    std::vector<double> lam(T), gam(3 * T);
+    WT_CUDA_TRY(cudaMemcpy(k.data(), d.key, T * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    WT_CUDA_TRY(cudaMemcpy(mk.data(), d.mask, T, cudaMemcpyDeviceToHost));
+    WT_CUDA_TRY(cudaMemcpy(fc.data(), d.first_child, T * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    WT_CUDA_TRY(cudaMemcpy(lam.data(), d.lambda, T * sizeof(double), cudaMemcpyDeviceToHost));
+    WT_CUDA_TRY(cudaMemcpy(gam.data(), d.gamma, 3 * T * sizeof(double), cudaMemcpyDeviceToHost));
+    // level-J-first layout -> breadth-first (level ascending)
+    int64_t bfs_off[kMaxJ + 2];
+    bfs_off[1] = 0;
+    for (int j = 1; j <= t->J; ++j) bfs_off[j + 1] = bfs_off[j] + h.per_level[j];
+    for (int j = 1; j <= t->J; ++j) {
+        for (int64_t i = 0; i < h.per_level[j]; ++i) {
+            const int64_t src = h.rev_offset[j] + i, dst = bfs_off[j] + i;
+            if (key) key[dst] = k[src];
+            if (child_mask) child_mask[dst] = mk[src];
+            if (first_child) first_child[dst] = (j < t->J) ? static_cast<int32_t>(bfs_off[j + 1] + fc[src]) : -1;
+            if (lambda) lambda[dst] = lam[src];
+            if (gamma)
+                for (int q = 0; q < 3; ++q) gamma[3 * dst + q] = gam[3 * src + q];
+        }
+    }
+    if (leaf_dir) WT_CUDA_TRY(cudaMemcpy(leaf_dir, d.leaf_dir, 3 * NL * sizeof(double), cudaMemcpyDeviceToHost));
+    if (leaf_flux) WT_CUDA_TRY(cudaMemcpy(leaf_flux, d.leaf_flux, NL * sizeof(double), cudaMemcpyDeviceToHost));
+    return WT_OK;
+}
+
+void wt_free_tree(wt_tree t)
+{
+    if (!t || t->magic != kTreeMagic) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != t->device) cudaSetDevice(t->device);
+    cudaStreamSynchronize(t->stream);
+    if (t->block) cudaFreeAsync(t->block, t->stream);
+    cudaStreamSynchronize(t->stream);
+    if (t->host_hdr) cudaFreeHost(t->host_hdr);
+    cudaGetLastError();
+    if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+    t->magic = 0;
+    delete t;
+}
+
+int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign, int which,
+                   void* stream)
+{
+    const char* fn = "wt_predict_vis";
+    int rc = check_tree(t, fn);
+    if (rc) return rc;
+    if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
+    if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
+    if (which != WT_SUM_EQ17 && which != WT_SUM_EQ16) return set_error(WT_ERR_ARG, "%s: bad sum selector", fn);
+    if (mode == WT_LEARNED)
+        return set_error(WT_ERR_UNSUPPORTED, "%s: the learned response has its own entry point", fn);
+    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    const size_t ob = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
+        return rc;
+    return wt::predict_wavelet(t, uvw, n_vis, vis_out, mode, sign, which, static_cast<cudaStream_t>(stream));
+}
+
+int dft_predict_vis(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
+                    int64_t n_vis, void* vis_out, int mode, int sign, void* stream)
+{
+    const char* fn = "dft_predict_vis";
+    if (n_comp < 0 || n_vis < 0) return set_error(WT_ERR_ARG, "%s: negative size", fn);
+    if (n_comp > (int64_t(1) << 30)) return set_error(WT_ERR_RANGE, "%s: n_comp too large", fn);
+    if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
+    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    const size_t nb = static_cast<size_t>(n_comp) * 8;
+    const size_t ob = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
+    int rc;
+    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux")) ||
+        (rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
+        return rc;
+    if (!device_status_word()) return set_error(WT_ERR_CUDA, "%s: no usable CUDA device", fn);
+    return wt::predict_dft(l, m, flux, n_comp, uvw, n_vis, vis_out, mode, sign, static_cast<cudaStream_t>(stream));
+}
+
+int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid, int64_t n_vis, int mode, void* stream)
+{
+    const char* fn = "subtract_model";
+    if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_LEARNED) return set_error(WT_ERR_ARG, "%s: bad mode", fn);
+    const size_t b = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
+    int rc;
+    if ((rc = check_device_buffer(vis_obs, b, fn, "vis_obs")) || (rc = check_device_buffer(vis_model, b, fn, "vis_model")) ||
+        (rc = check_device_buffer(vis_resid, b, fn, "vis_resid")))
+        return rc;
+    if (!device_status_word()) return set_error(WT_ERR_CUDA, "%s: no usable CUDA device", fn);
+    return wt::subtract(vis_obs, vis_model, vis_resid, n_vis, mode, static_cast<cudaStream_t>(stream));
+}
+
+int wt_recommended_J(double dtheta_rad)
+{
+    if (!(dtheta_rad > 0.0) || !isfinite(dtheta_rad)) return set_error(WT_ERR_ARG, "wt_recommended_J: dtheta <= 0");
+    for (int J = 1; J <= kMaxJ; ++J) {
+        const double pix = ldexp(sqrt(kPi / 3.0), 1 - J);   // Delta theta_J
+        if (pix <= 0.5 * dtheta_rad) return J;
+    }
+    return set_error(WT_ERR_RANGE, "wt_recommended_J: needs J > %d", kMaxJ);
+}
+
+int wt_device_status(void* stream)
+{
+    int* w = device_status_word();
+    if (!w) return set_error(WT_ERR_CUDA, "wt_device_status: no usable CUDA device");
+    WT_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int v = 0;
+    WT_CUDA_TRY(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        WT_CUDA_TRY(cudaMemset(w, 0, sizeof(int)));
+        return set_error(v, "a kernel reported status %d", v);
+    }
+    return WT_OK;
+}
+
+const char* wt_last_error(void) { return g_msg; }
+
+}  // extern "C"

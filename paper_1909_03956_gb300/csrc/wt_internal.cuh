@@ -1,0 +1,282 @@
+// wt_internal.cuh -- shared declarations of libwtvis (sm_103a).
+//
+// Device helpers used by more than one kernel file: PTX wrappers for the
+// mbarrier / bulk-copy staging path, double-float arithmetic for the mixed
+// precision forms, a float32 sin/cos of 2*pi*t written from the Taylor series,
+// the per-device status word, and the host-side error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wtvis.h"
+
+namespace wt {
+
+// ---------------------------------------------------------------- constants
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxJ = 30;
+
+// Upper bound on the spins of any bounded wait (mbarrier parity waits).
+// A healthy wait finishes in microseconds; this limit is seconds.
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+// ---------------------------------------------------------------- host side
+// Thread-local error message + status helpers (wt_api.cu).
+int set_error(int status, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+int* device_status_word();          // per-device int, zero-initialised
+
+#define WT_CUDA_TRY(expr)                                             \
+    do {                                                              \
+        cudaError_t _e = (expr);                                      \
+        if (_e != cudaSuccess) return ::wt::cuda_error(_e, #expr);    \
+    } while (0)
+
+// ---------------------------------------------------------------- device side
+__device__ __forceinline__ void record_status(int* status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+// ---- mbarrier + bulk copy (non-tensor TMA), one CTA, no multicast ----------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Returns true once the phase with parity `parity` has completed; false if
+// the bounded number of polls ran out.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Bulk copy global -> shared of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completion signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- double-float helpers (mixed precision forms) --------------------------
+// A float64 value x is carried as hi + lo, hi = fl32(x), lo = fl32(x - hi):
+// 48 significant bits, enough for phases of many thousand turns.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 split_f64(double x)
+{
+    F2 r;
+    r.hi = __double2float_rn(x);
+    r.lo = __double2float_rn(x - static_cast<double>(r.hi));
+    return r;
+}
+
+// Error-free sum (Knuth): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// Fractional part (in turns) of x * y, for x = xh + xl and y = yh + yl
+// double-floats: returns an exact integer-free head in [-1/2, 1/2] and a
+// small tail. The head is xh*yh reduced by its nearest integer (exact: both
+// operands share the float's ulp); the tail holds the rounding error of xh*yh
+// (exact via FMA) plus the cross terms xh*yl + xl*yh (xl*yl is below 2^-48 of
+// the product and dropped).
+__device__ __forceinline__ void frac_product(F2 x, F2 y, float& head, float& tail)
+{
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+    head = __fsub_rn(p, rintf(p));
+    tail = __fadd_rn(e, c);
+}
+
+// Phase in turns of B.(s - P) = u*su + v*sv + w*sw1, reduced to [-1/2, 1/2],
+// returned as a head and a small tail (double-float). Float64-accurate: the
+// three heads are added with error-free sums, their errors join the tails.
+__device__ __forceinline__ void phase_turns_df(F2 u, F2 v, F2 w, F2 su, F2 sv, F2 sw1, float& th, float& tl)
+{
+    float h1, t1, h2, t2, h3, t3;
+    frac_product(u, su, h1, t1);
+    frac_product(v, sv, h2, t2);
+    frac_product(w, sw1, h3, t3);
+    float s, e1, s2, e2;
+    two_sum(h1, h2, s, e1);
+    two_sum(s, h3, s2, e2);
+    s2 = __fsub_rn(s2, rintf(s2));           // exact, back to [-1/2, 1/2]
+    float tail = __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), __fadd_rn(t3, e1)), e2);
+    two_sum(s2, tail, th, tl);
+}
+
+// sin and cos of 2*pi*(th + tl) for |th| <= 1/2 (turns), float32.
+// Quadrant reduction q = rint(4 th), f = 4 th - q (exact) in [-1/2, 1/2],
+// angle x = (f + 4 tl) * pi/2 in [-pi/4, pi/4] with a two-float pi/2; then
+// the Taylor series of sin (to x^9) and cos (to x^10), whose truncation
+// errors (< 2e-9 and < 2e-10 on this interval) are below float32 rounding.
+__device__ __forceinline__ void sincos_turns_f32(float th, float tl, float& s, float& c)
+{
+    const float q = rintf(4.0f * th);
+    const float f = __fadd_rn(__fsub_rn(4.0f * th, q), 4.0f * tl);
+    const float PIO2_HI = 1.57079637050628662109375f;          // fl32(pi/2)
+    const float PIO2_LO = -4.37113900018624283e-8f;            // pi/2 - PIO2_HI
+    const float x = __fmaf_rn(f, PIO2_HI, __fmul_rn(f, PIO2_LO));
+    const float x2 = __fmul_rn(x, x);
+    // sin x = x (1 - x^2/3! + x^4/5! - x^6/7! + x^8/9!)
+    float ps = __fmaf_rn(x2, 2.7557319223985893e-6f, -1.9841269841269841e-4f);
+    ps = __fmaf_rn(x2, ps, 8.3333333333333333e-3f);
+    ps = __fmaf_rn(x2, ps, -1.6666666666666667e-1f);
+    const float sx = __fmaf_rn(__fmul_rn(x, x2), ps, x);
+    // cos x = 1 - x^2/2! + x^4/4! - x^6/6! + x^8/8! - x^10/10!
+    float pc = __fmaf_rn(x2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
+    pc = __fmaf_rn(x2, pc, -1.3888888888888889e-3f);
+    pc = __fmaf_rn(x2, pc, 4.1666666666666667e-2f);
+    pc = __fmaf_rn(x2, pc, -0.5f);
+    const float cx = __fmaf_rn(x2, pc, 1.0f);
+    const int qi = static_cast<int>(q) & 3;
+    // angle = q * pi/2 + x
+    const float ss = (qi & 1) ? cx : sx;
+    const float cc = (qi & 1) ? sx : cx;
+    s = (qi & 2) ? -ss : ss;
+    c = ((qi + 1) & 2) ? -cc : cc;
+}
+
+// Kahan-compensated float32 accumulation: sum + comp carries the total.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
+{
+    const float y = __fsub_rn(x, comp);
+    const float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+// ---------------------------------------------------------------- tree handle
+// Post-order record of one tree node for the float64 predictor (40 bytes):
+// meta bits 0-4 level j, 5-6 child slot (key & 3), 7-10 child mask,
+// 11 leaf flag. Payload: leaf -> (s_u, s_v, s_w - 1, Phi); internal ->
+// (gamma^0, gamma^1, gamma^2, A_1 lambda_1 for level 1 else 0).
+struct RecD {
+    uint32_t meta;
+    uint32_t pad;
+    double a, b, c, d;
+};
+static_assert(sizeof(RecD) == 40, "RecD layout");
+
+// Same for the mixed predictor (32 bytes): leaf -> (s_u, s_v, s_w - 1) as
+// double-float pairs and Phi; internal -> (gamma^0, gamma^1, gamma^2, 0, 0, 0,
+// A_1 lambda_1 for level 1 else 0) in float32.
+struct RecF {
+    uint32_t meta;
+    float a, b, c, d, e, f, g;
+};
+static_assert(sizeof(RecF) == 32, "RecF layout");
+
+__host__ __device__ __forceinline__ uint32_t rec_level(uint32_t meta) { return meta & 31u; }
+__host__ __device__ __forceinline__ uint32_t rec_slot(uint32_t meta) { return (meta >> 5) & 3u; }
+__host__ __device__ __forceinline__ uint32_t rec_mask(uint32_t meta) { return (meta >> 7) & 15u; }
+__host__ __device__ __forceinline__ uint32_t rec_leaf(uint32_t meta) { return (meta >> 11) & 1u; }
+
+// Device-side header of a tree (written by the build kernels).
+struct TreeHeader {
+    int64_t n_leaves;
+    int64_t n_nodes;
+    int64_t per_level[kMaxJ + 1];   // [j] = nodes at level j (index 0 unused)
+    int64_t rev_offset[kMaxJ + 2];  // start of level j in the level-J-first layout
+};
+
+struct TreeDev {
+    // capacity-sized arrays in "level J first" layout (level J, J-1, ..., 1)
+    int64_t* key;
+    double* lambda;
+    double* gamma;        // [cap][3]
+    int32_t* first_child; // index within the child level, -1 for leaves
+    uint8_t* mask;
+    int32_t* leaf_lo;     // first leaf index of the subtree
+    int32_t* leaf_hi;     // one past the last leaf index
+    int32_t* size;        // nodes in the subtree
+    int32_t* parent;      // index of the parent within its level
+    double* leaf_dir;     // [n_leaves cap][3]
+    double* leaf_flux;    // [n_leaves cap]
+    int64_t* anc_sum;     // per leaf: sum over levels of the ancestor's index
+    int32_t* anc;         // per leaf: current ancestor index
+    RecD* recd;           // post-order records [cap]
+    RecF* recf;
+    RecD* leafd;          // leaf records in key order [n_leaves cap] (Eq. 16)
+    RecF* leaff;
+    TreeHeader* hdr;
+};
+
+}  // namespace wt
+
+// The opaque handle behind wt_tree.
+struct wt_tree_s {
+    uint64_t magic;
+    int device;
+    int J;
+    double ra0, dec0;
+    int64_t n_comp;
+    int64_t cap_nodes;
+    int64_t cap_leaves;
+    cudaStream_t stream;          // stream of the build
+    void* block;                  // single device allocation holding everything
+    wt::TreeDev d;
+    wt::TreeHeader* host_hdr;     // pinned copy of the header
+    bool host_valid;
+};
+
+constexpr uint64_t kTreeMagic = 0x57545645455f3031ull;   // "WTVEE_01"
+
+namespace wt {
+// tree_build.cu
+int build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
+               int J, wt_tree t, cudaStream_t s);
+int tree_sync_header(wt_tree t);
+// wavelet.cu
+int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int mode, int sign, int which,
+                    cudaStream_t s);
+// dft.cu
+int predict_dft(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
+                int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s);
+// subtract.cu
+int subtract(const void* obs, const void* model, void* resid, int64_t n_vis, int mode, cudaStream_t s);
+// utilities
+int num_sms();
+void rotation_matrix(double ra0, double dec0, double* R);
+}  // namespace wt

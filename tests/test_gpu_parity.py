@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars (see the oracle's readings R1-R9):
+  * tree keys, topology, lambda, gamma, merged fluxes: bit-exact;
+    leaf pixel centres: within a few ulp (they go through sin/cos);
+  * WT_FP64 visibilities: max |dV| <= 1e-10 * sum |C| (relative to the peak
+    amplitude, the zero-spacing visibility);
+  * WT_MIXED visibilities: max |dV| <= 1e-6 * sum |C|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+wt = pytest.importorskip("paper_1909_03956_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-6
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def peak(flux):
+    return float(np.abs(flux).sum())
+
+
+def gpu_tree(w, J):
+    return wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, J)
+
+
+def assert_margins_clear(w, J, thresh=1e-9):
+    # Every component must sit clearly inside its pixel for a bit-exact key
+    # comparison (the GPU's atan2 may differ from libm's in the last ulp).
+    _, mg = O.map_components(w.l, w.m, w.ra0, w.dec0, J)
+    assert mg.min() > thresh, "component within %g of a pixel edge; choose another seed" % thresh
+
+
+def compare_trees(w, J):
+    assert_margins_clear(w, J)
+    t = gpu_tree(w, J)
+    g = t.export()
+    o = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J).export()
+    assert g["n_nodes"] == len(o["key"])
+    assert np.array_equal(g["level_offsets"], o["level_offsets"])
+    assert np.array_equal(g["key"], o["key"])
+    assert np.array_equal(g["child_mask"], o["child_mask"])
+    assert np.array_equal(g["first_child"], o["first_child"])
+    assert np.array_equal(g["leaf_flux"], o["leaf_flux"])
+    assert np.array_equal(g["lam"], o["lam"])
+    assert np.array_equal(g["gamma"], o["gamma"])
+    # pixel centres go through sin/cos: a few ulp of the unit vector
+    assert np.max(np.abs(g["leaf_dir"] - o["leaf_dir"])) < 1e-15
+    rel = np.abs(g["leaf_dir"][:, 2] - o["leaf_dir"][:, 2]) / np.maximum(np.abs(o["leaf_dir"][:, 2]), 1e-300)
+    assert rel.max() < 1e-12
+    return t
+
+
+# ---------------------------------------------------------------- tree build
+
+@pytest.mark.parametrize("J", [1, 2, 5, 8, 12, 16, 20, 25])
+def test_tree_bit_exact_small(J):
+    compare_trees(synth.small(), J)
+
+
+@pytest.mark.parametrize("J", [8, 10, 12, 14])
+def test_tree_bit_exact_medium(J):
+    compare_trees(synth.medium(n_t=2), J)
+
+
+def test_tree_bit_exact_mixed_sign_and_duplicates():
+    w = synth.small()
+    rng = np.random.default_rng(21)
+    f = w.flux * np.where(rng.random(len(w.flux)) < 0.5, -1.0, 1.0)
+    l = np.concatenate([w.l, w.l[:30]])          # exact duplicates: same pixel
+    m = np.concatenate([w.m, w.m[:30]])
+    f = np.concatenate([f, -f[:30]])             # some pixels cancel to zero
+    w2 = synth.Workload("dup", w.uvw, l, m, f, 10)
+    compare_trees(w2, 10)
+
+
+def test_tree_large_component_list():
+    # 50 000 components (the learned-response workload's list), several sort
+    # tiles and many chunks of records.
+    w = synth.learned(n_t=2)
+    compare_trees(w, 12)
+
+
+def test_tree_empty():
+    t = wt.wt_build_tree(dev(np.zeros(0)), dev(np.zeros(0)), dev(np.zeros(0)), 1.0, 0.5, 8)
+    inf = t.info()
+    assert inf["n_nodes"] == 0 and inf["n_leaves"] == 0
+    v = wt.wt_predict_vis(t, dev(np.ones((5, 3))))
+    assert torch.all(v == 0)
+
+
+# ---------------------------------------------------------------- wavelet
+
+def _wavelet_case(w, J, uvw, mode, which=wt.WT_SUM_EQ17, sign=1):
+    t = gpu_tree(w, J)
+    v = wt.wt_predict_vis(t, dev(uvw), mode=mode, which=which, sign=sign).cpu().numpy()
+    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+    ref = ot.vis_eq16(uvw, sign) if which == wt.WT_SUM_EQ16 else ot.vis_eq17(uvw, sign)
+    return np.max(np.abs(v - ref)) / peak(w.flux)
+
+
+@pytest.mark.parametrize("J", [1, 3, 8, 12, 20])
+def test_wavelet_fp64_small_all_vis(J):
+    w = synth.small()
+    assert _wavelet_case(w, J, w.uvw, wt.WT_FP64) <= TOL64
+
+
+@pytest.mark.parametrize("J", [8, 12, 14])
+def test_wavelet_fp64_medium(J):
+    # J = 14 has thousands of nodes: the records stream through shared
+    # memory in many chunks.
+    w = synth.medium(n_t=6)
+    uvw = w.uvw[::3]
+    assert _wavelet_case(w, J, uvw, wt.WT_FP64) <= TOL64
+
+
+@pytest.mark.parametrize("J", [8, 12, 14])
+def test_wavelet_mixed_medium(J):
+    w = synth.medium(n_t=6)
+    uvw = w.uvw[::3]
+    assert _wavelet_case(w, J, uvw, wt.WT_MIXED) <= TOLMIX
+
+
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_wavelet_eq16(mode, tol):
+    w = synth.medium(n_t=6)
+    assert _wavelet_case(w, 12, w.uvw[::5], mode, which=wt.WT_SUM_EQ16) <= tol
+
+
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_wavelet_sign_minus(mode, tol):
+    w = synth.small()
+    assert _wavelet_case(w, 10, w.uvw[:777], mode, sign=-1) <= tol
+
+
+@pytest.mark.parametrize("n", [1, 31, 255, 257, 1000])
+def test_wavelet_ragged_tiles(n):
+    w = synth.small()
+    assert _wavelet_case(w, 12, w.uvw[:n], wt.WT_FP64) <= TOL64
+    assert _wavelet_case(w, 12, w.uvw[:n], wt.WT_MIXED) <= TOLMIX
+
+
+def test_wavelet_zero_vis():
+    w = synth.small()
+    t = gpu_tree(w, 8)
+    out = wt.wt_predict_vis(t, dev(np.zeros((0, 3))))
+    assert out.numel() == 0
+
+
+def test_wavelet_deep_tree_spaced_components():
+    # Distinct components far apart: every leaf has its own chain of
+    # ancestors (the tree of the paper's run-time study, Sec. 3.6.1).
+    w = synth.medium_fixed(40, n_t=4)
+    for J in (16, 25):
+        assert _wavelet_case(w, J, w.uvw[::4], wt.WT_FP64) <= TOL64
+        assert _wavelet_case(w, J, w.uvw[::4], wt.WT_MIXED) <= TOLMIX
+
+
+# ---------------------------------------------------------------- direct sum
+
+def _dft_case(w, uvw, mode, sign=1):
+    v = wt.dft_predict_vis(dev(w.l), dev(w.m), dev(w.flux), dev(uvw), mode=mode, sign=sign).cpu().numpy()
+    ref = O.dft(w.l, w.m, w.flux, uvw, sign)
+    return np.max(np.abs(v - ref)) / peak(w.flux)
+
+
+def test_dft_fp64_small_all_vis():
+    w = synth.small()
+    assert _dft_case(w, w.uvw, wt.WT_FP64) <= TOL64
+
+
+def test_dft_mixed_small_all_vis():
+    w = synth.small()
+    assert _dft_case(w, w.uvw, wt.WT_MIXED) <= TOLMIX
+
+
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_dft_medium_many_chunks(mode, tol):
+    # 5 000 components: ten shared-memory chunks per sweep.
+    w = synth.medium(n_t=2)
+    assert _dft_case(w, w.uvw[::4], mode) <= tol
+
+
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_dft_sign_and_ragged(mode, tol):
+    w = synth.small()
+    assert _dft_case(w, w.uvw[:333], mode, sign=-1) <= tol
+
+
+def test_dft_empty_components():
+    v = wt.dft_predict_vis(dev(np.zeros(0)), dev(np.zeros(0)), dev(np.zeros(0)), dev(np.ones((7, 3))))
+    assert torch.all(v == 0)
+
+
+def test_dft_point_source_phase_centre_exact():
+    rng = np.random.default_rng(3)
+    uvw = rng.uniform(-3e4, 3e4, (1000, 3))
+    v = wt.dft_predict_vis(dev([0.0]), dev([0.0]), dev([0.37]), dev(uvw)).cpu().numpy()
+    assert np.all(v.real == 0.37) and np.all(v.imag == 0.0)
+
+
+# ---------------------------------------------------------------- subtract
+
+@pytest.mark.parametrize("mode", [wt.WT_FP64, wt.WT_MIXED])
+@pytest.mark.parametrize("n", [1, 2, 3, 1001, 100000])
+def test_subtract(mode, n):
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ct = np.complex128 if mode == wt.WT_FP64 else np.complex64
+    a, b = a.astype(ct), b.astype(ct)
+    r = wt.subtract_model(dev(a), dev(b), mode=mode).cpu().numpy()
+    assert np.array_equal(r, a - b)
+    x = dev(a)
+    wt.subtract_model(x, dev(b), mode=mode, out=x)          # in place
+    assert np.array_equal(x.cpu().numpy(), a - b)
+
+
+def test_subtract_unaligned_complex64_view():
+    n = 1001
+    a = (np.arange(n + 1) + 1j).astype(np.complex64)
+    b = (np.arange(n + 1) * 0.5).astype(np.complex64)
+    A, B = dev(a)[1:], dev(b)[1:]
+    r = wt.subtract_model(A, B, mode=wt.WT_MIXED).cpu().numpy()
+    assert np.array_equal(r, a[1:] - b[1:])
+
+
+# ---------------------------------------------------------------- errors
+
+def test_component_outside_unit_disc_is_reported():
+    l = np.array([0.1, 1.2])
+    m = np.array([0.0, 0.0])
+    f = np.array([1.0, 1.0])
+    wt.wt_device_status()
+    t = wt.wt_build_tree(dev(l), dev(m), dev(f), 1.0, 0.5, 8)
+    with pytest.raises(wt.WtError) as e:
+        wt.wt_device_status()
+    assert e.value.status == wt.WT_ERR_RANGE
+    t.close()
+    wt.wt_device_status()   # cleared
+
+
+def test_host_pointer_rejected_before_launch():
+    import ctypes as C
+    L = wt.load()
+    host = np.zeros(3 * 10)
+    out = torch.empty(10, dtype=torch.complex128, device="cuda")
+    rc = L.dft_predict_vis(C.c_void_p(out.data_ptr()), C.c_void_p(out.data_ptr()), C.c_void_p(out.data_ptr()), 1,
+                           host.ctypes.data_as(C.c_void_p), 10, C.c_void_p(out.data_ptr()), 0, 1, None)
+    assert rc == wt.WT_ERR_ARG
+
+
+def test_buffer_too_small_rejected_before_launch():
+    uvw = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
+    out = torch.empty(5, dtype=torch.complex128, device="cuda")
+    import ctypes as C
+    L = wt.load()
+    z = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # claim 10**9 visibilities: far beyond the allocations
+    rc = L.dft_predict_vis(C.c_void_p(z.data_ptr()), C.c_void_p(z.data_ptr()), C.c_void_p(z.data_ptr()), 1,
+                           C.c_void_p(uvw.data_ptr()), 10 ** 9, C.c_void_p(out.data_ptr()), 0, 1, None)
+    assert rc == wt.WT_ERR_ARG
+
+
+def test_tree_on_wrong_mode_rejected():
+    w = synth.small()
+    t = gpu_tree(w, 8)
+    with pytest.raises(wt.WtError):
+        wt.wt_predict_vis(t, dev(w.uvw[:4]), mode=7)

@@ -1,0 +1,432 @@
+"""Benchmark: model visibilities per second for one major cycle's prediction.
+
+Workload (default): the medium array -- 64 antennas in a 5 km disc, 500 hour
+angles, 1 008 000 visibilities at 1.4 GHz -- with 5 000 clean components in
+20 Gaussian blobs inside a 2 deg field, wavelet level J = 12 (synthetic,
+seeded; see synth/).
+
+One step = the whole hot path over that batch:
+  wt_build_tree (components -> sphere pixels -> coefficient tree, Sec. 3.5)
+  -> wt_predict_vis (Eq. 17 per visibility, the chosen form)
+  -> subtract_model (V_resid = V - V_M, Sec. 2.2).
+The chosen form is WT_MIXED (float64-accurate phase, float32 sin/cos and
+compensated accumulation), whose error against the FP64 oracle is measured
+in the same run and must stay <= 1e-6 of the peak amplitude sum |C|.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream; the L2 cache is flushed (a 512 MB write) before
+every timed step, outside the events. Inputs are resident in HBM. Under
+torchrun each rank runs its own batch (weak scaling) and the max time over
+ranks is reported. The e2e figure repeats the step through the public API
+from pinned host buffers, host<->device copies inside the timed region.
+
+--impl reference times the CPU oracle (as it stands, single thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+MEDIUM_J = 12
+METRIC = "model visibilities/s"
+UNIT = "vis/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--J", type=int, default=MEDIUM_J)
+    p.add_argument("--no-extras", action="store_true", help="skip the per-form side measurements")
+    p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- native
+
+def native(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1909_03956_gb300 as wt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wt.load()
+
+    J = args.J
+    w = synth.medium(seed=1910 + rank, J=J)
+    n_vis = w.n_vis
+    S = float(np.abs(w.flux).sum())
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    l, m, fl, uvw = d(w.l), d(w.m), d(w.flux), d(w.uvw)
+    rng = np.random.default_rng(7 + rank)
+    obs = d((rng.standard_normal(n_vis) + 1j * rng.standard_normal(n_vis)).astype(np.complex64))
+    model = torch.empty(n_vis, dtype=torch.complex64, device=dev)
+    resid = torch.empty_like(model)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = wt.WT_MIXED
+
+    def step():
+        tree = wt.wt_build_tree(l, m, fl, w.ra0, w.dec0, J)
+        wt.wt_predict_vis(tree, uvw, mode=mode, out=model)
+        wt.subtract_model(obs, model, mode=mode, out=resid)
+        return tree
+
+    for _ in range(args.warmup):
+        t = step()
+        t.close()
+    torch.cuda.synchronize()
+    wt.wt_device_status()
+
+    # per-kernel timing of the dominant kernel (the predictor) on the same stream
+    tree_keep = step()
+    info = tree_keep.info()
+    times, pred_times = [], []
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree = wt.wt_build_tree(l, m, fl, w.ra0, w.dec0, J)
+        p0.record(stream)
+        wt.wt_predict_vis(tree, uvw, mode=mode, out=model)
+        p1.record(stream)
+        wt.subtract_model(obs, model, mode=mode, out=resid)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        pred_times.append(p0.elapsed_time(p1) / 1e3)
+        tree.close()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    wt.wt_device_status()
+    t_step = statistics.mean(times)
+    t_pred = statistics.mean(pred_times)
+    if world > 1:
+        tt = torch.tensor([t_step, t_pred], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_pred = float(tt[0]), float(tt[1])
+
+    # accuracy of the chosen form against the FP64 oracle on a strided sample
+    err = None
+    if rank == 0:
+        import oracle as O
+        idx = np.arange(0, n_vis, max(1, n_vis // 4000))
+        ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+        ref = ot.vis_eq17(w.uvw[idx])
+        got = model.cpu().numpy()[idx]
+        err = float(np.max(np.abs(got - ref)) / S)
+
+    # e2e through the public API from pinned host buffers
+    hl, hm, hf = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (w.l, w.m, w.flux))
+    huvw = torch.from_numpy(np.ascontiguousarray(w.uvw)).pin_memory()
+    hobs = obs.cpu().pin_memory()
+    hres = torch.empty_like(hobs).pin_memory()
+    dl, dm, df = torch.empty_like(l), torch.empty_like(m), torch.empty_like(fl)
+    duvw, dobs = torch.empty_like(uvw), torch.empty_like(obs)
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dl.copy_(hl, non_blocking=True)
+        dm.copy_(hm, non_blocking=True)
+        df.copy_(hf, non_blocking=True)
+        duvw.copy_(huvw, non_blocking=True)
+        dobs.copy_(hobs, non_blocking=True)
+        tree = wt.wt_build_tree(dl, dm, df, w.ra0, w.dec0, J)
+        wt.wt_predict_vis(tree, duvw, mode=mode, out=model)
+        wt.subtract_model(dobs, model, mode=mode, out=resid)
+        hres.copy_(resid, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        tree.close()
+        if it >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1) / 1e3)
+    t_e2e = statistics.mean(e2e_times)
+    if world > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt[0])
+    h2d = sum(x.numel() * x.element_size() for x in (hl, hm, hf, huvw, hobs))
+    d2h = hres.numel() * hres.element_size()
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = side_measurements(wt, torch, w, l, m, fl, uvw, tree_keep, stream, flush, S)
+    tree_keep.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the mixed Eq. 17 predictor)
+    n_leaves, n_nodes = info["n_leaves"], info["n_nodes"]
+    ops = n_vis * (OPS_LEAF * n_leaves + OPS_NODE * (n_nodes - n_leaves))
+    achieved = ops / t_pred / 1e12
+    peak = FP32_PEAK_TOPS
+    passes = (2 * J + 2 + 7) // 8
+    launches = (4 + 3 * passes) + 1 + 1
+    line = {
+        "metric": METRIC,
+        "value": world * n_vis / t_step,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64 (double-float phase, f32 sincos, Kahan f32 sum)",
+        "data": "synthetic (seeded; medium array stand-in for the paper's simulated VLA data)",
+        "config": {
+            "workload": w.name,
+            "n_vis": n_vis,
+            "n_comp": w.n_comp,
+            "J": J,
+            "n_leaves": n_leaves,
+            "n_nodes": n_nodes,
+            "form": "wavelet Eq.17, WT_MIXED",
+            "step": "wt_build_tree + wt_predict_vis + subtract_model",
+            "parallelism": "dp%d (replicated tree, sharded visibilities)" % world,
+            "l2": "flushed (512 MB write) before every timed step",
+        },
+        "vis_terms_per_s": world * n_vis * n_leaves / t_step,
+        "vis_nodes_per_s": world * n_vis * n_nodes / t_step,
+        "max_rel_err_vs_fp64_oracle": err,
+        "predict_ms": t_pred * 1e3,
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TOP/s (FP32 pipe ops)",
+            "frac": achieved / peak,
+            "traffic": None,
+            "kernel": "k_wavelet_mixed (Eq. 17)",
+        },
+        "e2e": {"value": world * n_vis / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    line.update(extras)
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, J, budget_s=15.0)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# FP32 pipe operations of the mixed Eq. 17 form, counted from the method's
+# arithmetic (double-float phase, quadrant-reduced Taylor sin/cos, eta/sigma
+# recursion, compensated sum); instruction overhead (record decode, loads,
+# branches) is not counted.
+OPS_LEAF = 68
+OPS_NODE = 38
+# 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
+def _time_call(fn, stream, flush, reps=3):
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return statistics.median(ts)
+
+
+def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
+    n = w.n_vis
+    out64 = torch.empty(n, dtype=torch.complex128, device=uvw.device)
+    out32 = torch.empty(n, dtype=torch.complex64, device=uvw.device)
+    r = {}
+    t = _time_call(lambda: wt.wt_build_tree(l, m, fl, w.ra0, w.dec0, w.J), stream, flush)
+    r["build_tree_ms"] = t * 1e3
+    for name, mode, which, out in [("wavelet_fp64_eq17", wt.WT_FP64, wt.WT_SUM_EQ17, out64),
+                                   ("wavelet_mixed_eq17", wt.WT_MIXED, wt.WT_SUM_EQ17, out32),
+                                   ("wavelet_fp64_eq16", wt.WT_FP64, wt.WT_SUM_EQ16, out64),
+                                   ("wavelet_mixed_eq16", wt.WT_MIXED, wt.WT_SUM_EQ16, out32)]:
+        t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out), stream, flush)
+        r[name + "_vis_per_s"] = n / t
+    t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_FP64, out=out64), stream, flush, reps=1)
+    r["dft_fp64_vis_per_s"] = n / t
+    t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED, out=out32), stream, flush)
+    r["dft_mixed_vis_per_s"] = n / t
+    r["dft_terms"] = w.n_comp
+    t = _time_call(lambda: wt.subtract_model(out32, out32, mode=wt.WT_MIXED, out=out32), stream, flush)
+    r["subtract_c64_GBps"] = 24 * n / t / 1e9
+    return {"forms": r}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+
+def _oracle_step_rate(w, J, n_sample):
+    """Seconds for one oracle step extrapolated from a strided sample:
+    oracle tree build + Eq. 17 on n_sample visibilities + subtract."""
+    import oracle as O
+    idx = np.arange(0, w.n_vis, max(1, w.n_vis // n_sample))[:n_sample]
+    t0 = time.perf_counter()
+    tr = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+    t1 = time.perf_counter()
+    v = tr.vis_eq17(w.uvw[idx])
+    t2 = time.perf_counter()
+    O.subtract(v, v)
+    t3 = time.perf_counter()
+    per_vis = (t2 - t1 + t3 - t2) / len(idx)
+    step_s = (t1 - t0) + per_vis * w.n_vis
+    return step_s, len(idx), (t3 - t0)
+
+
+def cpu_baseline(w, J, budget_s=15.0):
+    # size the sample so that the oracle work takes about budget_s seconds
+    step_s, n_s, wall = _oracle_step_rate(w, J, 256)
+    per_vis = max((step_s) / w.n_vis, 1e-9)
+    n_sample = int(min(w.n_vis, max(256, budget_s / per_vis)))
+    step_s, n_s, wall = _oracle_step_rate(w, J, n_sample)
+    return {"value": w.n_vis / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle tree build + Eq. 17 on %d strided visibilities of %d (+ subtract), "
+                      "extrapolated to the full batch; %.1f s of CPU work" % (n_s, w.n_vis, wall)}
+
+
+def reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    J = args.J
+    w = synth.medium(J=J)
+    # each step: a bounded sample (about 3 s of CPU work), extrapolated
+    step_s, n_s, wall = _oracle_step_rate(w, J, 256)
+    per_vis = step_s / w.n_vis
+    n_sample = int(min(w.n_vis, max(256, 3.0 / max(per_vis, 1e-9))))
+    for _ in range(args.warmup):
+        _oracle_step_rate(w, J, min(n_sample, 512))
+    steps = []
+    for _ in range(args.steps):
+        s, n_s, wall = _oracle_step_rate(w, J, n_sample)
+        steps.append(s)
+    t = statistics.mean(steps)
+    val = w.n_vis / t
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_vis": w.n_vis, "n_comp": w.n_comp, "J": J,
+                   "form": "CPU oracle, Eq. 17, f64", "step": "oracle tree build + Eq. 17 + subtract"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d strided visibilities per step of %d, extrapolated" % (n_s, w.n_vis)},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

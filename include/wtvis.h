@@ -159,6 +159,36 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
                     void* stream);
 
 /* ---------------------------------------------------------------------------
+ * dft_predict_vis_noalloc -- the same direct sum as dft_predict_vis, for
+ * callers that cannot allocate device memory while they run: an application
+ * that reserves its whole device-memory budget at start-up and forbids
+ * allocation afterwards (an allocation could fail, or stall behind the
+ * allocator's synchronisation), or a host framework that owns every device
+ * allocation. The paper has no counterpart; this is plumbing.
+ *
+ * Nothing is allocated: the packed component records go to a fixed array in
+ * the library's device image, WT_NOALLOC_MAX_COMPONENTS records of 32 bytes
+ * (2 MiB), which every GPU that loads the library holds until the process
+ * exits. n_comp above that limit returns WT_ERR_RANGE before anything is
+ * enqueued.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     records. Calls whose work overlaps on the GPU (e.g. on two streams with
+ *     no ordering between them) race on it and give wrong results; order
+ *     them on one stream.
+ *   - status: optional caller-owned device int; kernels record the first
+ *     device-side error there (WT_ERR_RANGE for a component with
+ *     l^2 + m^2 >= 1 or a non-finite input) and leave it untouched otherwise.
+ *     With status = NULL such errors are not reported.
+ * Arguments otherwise as dft_predict_vis.
+ * ------------------------------------------------------------------------- */
+#define WT_NOALLOC_MAX_COMPONENTS 65536
+int dft_predict_vis_noalloc(const double* l, const double* m, const double* flux, int64_t n_comp,
+                            const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign,
+                            int* status, void* stream);
+
+/* ---------------------------------------------------------------------------
  * subtract_model -- Sec. 2.2, major-cycle step 2: V_resid = V - V_M,
  * element by element. vis_resid may alias vis_obs (in place).
  *   mode WT_FP64: complex128 arrays; any other mode: complex64 arrays.

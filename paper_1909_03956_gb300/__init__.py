@@ -37,7 +37,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libwtvis.so")
 EXPORTS = [
     "wt_build_tree", "wt_tree_info", "wt_tree_export", "wt_free_tree", "wt_predict_vis",
     "dft_predict_vis", "subtract_model", "wt_recommended_J", "wt_device_status", "wt_last_error",
+    "dft_predict_vis_noalloc",
 ]
+WT_NOALLOC_MAX_COMPONENTS = 65536
 
 
 class WtError(RuntimeError):
@@ -74,6 +76,7 @@ def _declare(L):
     L.wt_free_tree.restype = None
     L.wt_predict_vis.argtypes = [vp, vp, i64, vp, C.c_int, C.c_int, C.c_int, vp]
     L.dft_predict_vis.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int, C.c_int, vp]
+    L.dft_predict_vis_noalloc.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int, C.c_int, vp, vp]
     L.subtract_model.argtypes = [vp, vp, vp, i64, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
     L.wt_device_status.argtypes = [vp]

@@ -192,3 +192,124 @@ int predict_dft(const double* l, const double* m, const double* flux, int64_t n_
 }
 
 }  // namespace wt
+
+#include <mutex>
+
+// ===========================================================================
+// dft_predict_vis_noalloc -- the direct sum without any device allocation.
+//
+// For callers that must not allocate device memory once they are running:
+// an application that reserves its whole device-memory budget up front and
+// forbids allocation in its steady state (an allocation there could fail, or
+// stall behind the allocator's synchronisation), or a host framework that
+// owns every device allocation itself. dft_predict_vis allocates a scratch
+// buffer for the packed component records on each call; this variant packs
+// them instead into the fixed array below, which lives in the library's
+// device image. The paper has no counterpart: it is plumbing, not method.
+//
+// Every GPU that loads the library holds the array (2 MiB) until the
+// process exits. All calls on a device share it and it keeps the previous
+// call's records, so two calls whose work overlaps on the GPU (different
+// streams, no ordering between them) race on it and give wrong results.
+// Nothing in it has to start at zero: each call overwrites the records it
+// reads.
+// ===========================================================================
+namespace wt {
+namespace {
+
+constexpr int64_t kNoAllocMaxComponents = 65536;   // 32-byte records: 2 MiB
+static_assert(sizeof(CompD) == 32 && sizeof(CompF) == 32, "record size assumed below");
+
+static __device__ __align__(256) unsigned char g_noalloc_records[kNoAllocMaxComponents * 32];
+// Where the kernels record errors when the caller passes no status word.
+static __device__ int g_noalloc_status_sink;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};
+int* g_noalloc_sink[64] = {nullptr};
+
+// Device addresses of the two arrays above on the current device. The first
+// call on a device looks them up (cudaGetSymbolAddress, with that device
+// current); in host code the names are only host-side stand-ins and must
+// never be handed to a kernel.
+int noalloc_addresses(void** records, int** sink)
+{
+    int dev = 0;
+    WT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(WT_ERR_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_records);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_records)");
+        void* q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_noalloc_status_sink);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_status_sink)");
+        if (!p || !q) return set_error(WT_ERR_CUDA, "cudaGetSymbolAddress returned a null address");
+        g_noalloc_addr[dev] = p;
+        g_noalloc_sink[dev] = static_cast<int*>(q);
+    }
+    *records = g_noalloc_addr[dev];
+    *sink = g_noalloc_sink[dev];
+    return WT_OK;
+}
+
+}  // namespace
+
+int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name);
+
+}  // namespace wt
+
+extern "C" int dft_predict_vis_noalloc(const double* l, const double* m, const double* flux, int64_t n_comp,
+                                       const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign,
+                                       int* status, void* stream)
+{
+    using namespace wt;
+    const char* fn = "dft_predict_vis_noalloc";
+    if (n_comp < 0 || n_vis < 0) return set_error(WT_ERR_ARG, "%s: negative size", fn);
+    if (n_comp > kNoAllocMaxComponents)
+        return set_error(WT_ERR_RANGE, "%s: %lld components exceed the fixed capacity of %lld", fn,
+                         static_cast<long long>(n_comp), static_cast<long long>(kNoAllocMaxComponents));
+    if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
+    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    const size_t nb = static_cast<size_t>(n_comp) * 8;
+    const size_t ob = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
+    int rc;
+    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux")) ||
+        (rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")) ||
+        (status && (rc = check_device_buffer(status, sizeof(int), fn, "status"))))
+        return rc;
+    void* records = nullptr;
+    int* sink = nullptr;
+    if ((rc = noalloc_addresses(&records, &sink))) return rc;
+    if (!status) status = sink;
+    if (n_vis == 0) return WT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_comp > 0) {
+        const int tb = 256;
+        k_pack_components<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(
+            l, m, flux, n_comp, mode == WT_FP64 ? static_cast<CompD*>(records) : nullptr,
+            mode == WT_FP64 ? nullptr : static_cast<CompF*>(records), status);
+        WT_CUDA_TRY(cudaGetLastError());
+    }
+    dim3 grid;
+    if (mode == WT_FP64) {
+        constexpr int NT = 128;
+        const size_t smem = static_cast<size_t>(stager_bytes<CompD>(kChunk));
+        auto k = k_dft_fp64<NT>;
+        if ((rc = grid_for(k, NT, smem, n_vis, grid))) return rc;
+        k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(records), n_comp, uvw, n_vis, static_cast<double2*>(vis_out),
+                                 static_cast<double>(sign), status);
+    } else {
+        constexpr int NT = 256;
+        const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
+        auto k = k_dft_mixed<NT>;
+        if ((rc = grid_for(k, NT, smem, n_vis, grid))) return rc;
+        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<float2*>(vis_out),
+                                 static_cast<float>(sign), status);
+    }
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}

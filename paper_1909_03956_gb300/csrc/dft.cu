@@ -52,9 +52,9 @@ struct BodyD {
         double t = fma(w, c.nm1, fma(v, c.m, u * c.l));
         t -= rint(t);
         double s, co;
-        sincospi(2.0 * t, &s, &co);
+        sincos_turns_f64(t, s, co);
         vr = fma(c.flux, co, vr);
-        vi = fma(c.flux, sgn * s, vi);
+        vi = fma(c.flux, s, vi);
     }
 };
 
@@ -68,7 +68,7 @@ struct BodyF {
         float s, co;
         sincos_turns_f32(th, tl, s, co);
         kahan_add(vr, cr, c.flux * co);
-        kahan_add(vi, ci, c.flux * (sgn * s));
+        kahan_add(vi, ci, c.flux * s);
     }
 };
 
@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(NT) k_dft_fp64(const CompD* __restrict__ comps
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t n = tile * NT + threadIdx.x;
         const bool valid = n < n_vis;
-        BodyD b{valid ? uvw[3 * n] : 0.0, valid ? uvw[3 * n + 1] : 0.0, valid ? uvw[3 * n + 2] : 0.0, sgn, 0.0, 0.0};
+        // the sign is folded into the baseline: exp(-i 2 pi t) = exp(i 2 pi (-t)), exact
+        BodyD b{valid ? sgn * uvw[3 * n] : 0.0, valid ? sgn * uvw[3 * n + 1] : 0.0,
+                valid ? sgn * uvw[3 * n + 2] : 0.0, sgn, 0.0, 0.0};
         if (!st.sweep(b)) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
             return;
@@ -105,8 +107,9 @@ __global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comp
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t n = tile * NT + threadIdx.x;
         const bool valid = n < n_vis;
-        BodyF b{split_f64(valid ? uvw[3 * n] : 0.0), split_f64(valid ? uvw[3 * n + 1] : 0.0),
-                split_f64(valid ? uvw[3 * n + 2] : 0.0), sgn, 0.f, 0.f, 0.f, 0.f};
+        const double sg = static_cast<double>(sgn);   // sign folded into the baseline (exact)
+        BodyF b{split_f64(valid ? sg * uvw[3 * n] : 0.0), split_f64(valid ? sg * uvw[3 * n + 1] : 0.0),
+                split_f64(valid ? sg * uvw[3 * n + 2] : 0.0), sgn, 0.f, 0.f, 0.f, 0.f};
         if (!st.sweep(b)) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
             return;

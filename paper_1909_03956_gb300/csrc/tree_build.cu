@@ -451,7 +451,13 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         const bool leaf = (j == J);
         const uint32_t mask = d.mask[n];
         const uint32_t slot = static_cast<uint32_t>(d.key[n] & 3);
-        const uint32_t meta = static_cast<uint32_t>(j) | (slot << 5) | (mask << 7) | ((leaf ? 1u : 0u) << 11);
+        const bool single = !leaf && (__popc(mask) == 1);
+        const uint32_t cslot = single ? static_cast<uint32_t>(__ffs(mask) - 1) : 0u;
+        const uint32_t store_row = (j >= 2) ? static_cast<uint32_t>(4 * (j - 2)) + slot : 0u;
+        const uint32_t child_row = leaf ? 0u : static_cast<uint32_t>(4 * (j - 1)) + cslot;
+        const uint32_t meta = store_row | (child_row << 7) | (mask << 14) | (leaf ? kRecLeaf : 0u) |
+                              (j == 1 ? kRecRoot : 0u) | (single ? kRecSingle : 0u) |
+                              (static_cast<uint32_t>(j) << 21);
         RecD rd;
         RecF rf;
         rd.meta = meta;
@@ -465,6 +471,7 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
             rd.b = sv;
             rd.c = sw1;
             rd.d = phi_k;
+            rd.e = 0.0;
             const F2 a = split_f64(su), b = split_f64(sv), c = split_f64(sw1);
             rf.a = a.hi;
             rf.b = a.lo;
@@ -473,21 +480,27 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
             rf.e = c.hi;
             rf.f = c.lo;
             rf.g = static_cast<float>(phi_k);
-            RecD ld = rd;
-            RecF lf = rf;
-            d.leafd[li] = ld;
-            d.leaff[li] = lf;
+            d.leafd[li] = rd;
+            d.leaff[li] = rf;
         } else {
-            const double g0 = d.gamma[3 * n], g1 = d.gamma[3 * n + 1], g2 = d.gamma[3 * n + 2];
+            double g0 = d.gamma[3 * n], g1 = d.gamma[3 * n + 1], g2 = d.gamma[3 * n + 2];
+            if (single) {
+                // Hadamard signs of the only child: rows (+-+-), (++--), (+--+)
+                if (cslot & 1u) g0 = -g0;
+                if (cslot & 2u) g1 = -g1;
+                if (((cslot & 1u) ^ ((cslot >> 1) & 1u)) != 0u) g2 = -g2;
+            }
+            const double q = quarter_sqrt_area(j);
             const double root = (j == 1) ? A1 * d.lambda[n] : 0.0;
             rd.a = g0;
             rd.b = g1;
             rd.c = g2;
-            rd.d = root;
+            rd.d = q;
+            rd.e = root;
             rf.a = static_cast<float>(g0);
             rf.b = static_cast<float>(g1);
             rf.c = static_cast<float>(g2);
-            rf.d = 0.0f;
+            rf.d = static_cast<float>(q);
             rf.e = 0.0f;
             rf.f = 0.0f;
             rf.g = static_cast<float>(root);
@@ -511,8 +524,8 @@ int64_t carve_bytes(int64_t cap_nodes, int64_t cap_leaves)
     auto b = [](int64_t x) { return (x + 255) & ~int64_t(255); };
     return b(cap_nodes * 8) + b(cap_nodes * 8) + b(cap_nodes * 24) + b(cap_nodes * 4) + b(cap_nodes) +
            4 * b(cap_nodes * 4) + b(cap_leaves * 24) + b(cap_leaves * 8) + b(cap_leaves * 8) +
-           b(cap_leaves * 4) + b(cap_nodes * 40) + b(cap_nodes * 32) + b(cap_leaves * 40) + b(cap_leaves * 32) +
-           b(sizeof(TreeHeader));
+           b(cap_leaves * 4) + b(cap_nodes * int64_t(sizeof(RecD))) + b(cap_nodes * int64_t(sizeof(RecF))) +
+           b(cap_leaves * int64_t(sizeof(RecD))) + b(cap_leaves * int64_t(sizeof(RecF))) + b(sizeof(TreeHeader));
 }
 
 }  // namespace

@@ -129,9 +129,11 @@ __device__ __forceinline__ void frac_product(F2 x, F2 y, float& head, float& tai
     tail = __fadd_rn(e, c);
 }
 
-// Phase in turns of B.(s - P) = u*su + v*sv + w*sw1, reduced to [-1/2, 1/2],
-// returned as a head and a small tail (double-float). Float64-accurate: the
-// three heads are added with error-free sums, their errors join the tails.
+// Phase in turns of B.(s - P) = u*su + v*sv + w*sw1 modulo 1, returned as
+// an unevaluated sum th + tl: th in [-1/2, 1/2], tl small (|tl| < 1e-2 for
+// products below 2^16 turns). Float64-accurate: the three heads are added
+// with error-free sums and their errors join the tails. Valid while each
+// product |x * y| stays below 2^22 turns.
 __device__ __forceinline__ void phase_turns_df(F2 u, F2 v, F2 w, F2 su, F2 sv, F2 sw1, float& th, float& tl)
 {
     float h1, t1, h2, t2, h3, t3;
@@ -141,23 +143,22 @@ __device__ __forceinline__ void phase_turns_df(F2 u, F2 v, F2 w, F2 su, F2 sv, F
     float s, e1, s2, e2;
     two_sum(h1, h2, s, e1);
     two_sum(s, h3, s2, e2);
-    s2 = __fsub_rn(s2, rintf(s2));           // exact, back to [-1/2, 1/2]
-    float tail = __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), __fadd_rn(t3, e1)), e2);
-    two_sum(s2, tail, th, tl);
+    th = __fsub_rn(s2, rintf(s2));           // exact, back to [-1/2, 1/2]
+    tl = __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), __fadd_rn(t3, e1)), e2);
 }
 
-// sin and cos of 2*pi*(th + tl) for |th| <= 1/2 (turns), float32.
-// Quadrant reduction q = rint(4 th), f = 4 th - q (exact) in [-1/2, 1/2],
-// angle x = (f + 4 tl) * pi/2 in [-pi/4, pi/4] with a two-float pi/2; then
-// the Taylor series of sin (to x^9) and cos (to x^10), whose truncation
-// errors (< 2e-9 and < 2e-10 on this interval) are below float32 rounding.
+// sin and cos of 2*pi*(th + tl) for |th| <= 1/2 and small tl (turns),
+// float32. Quadrant reduction q = rint(4 th), f = (4 th - q) + 4 tl, the
+// first difference exact, so |f| <= 1/2 + 4|tl|; angle x = f * pi/2 (pi/2
+// rounded to float32: relative error 3e-8, below the float32 result's own
+// rounding); then the Taylor series of sin (to x^9) and cos (to x^10),
+// whose truncation errors on |x| <= 0.8 (< 4e-9 and < 5e-10) are below
+// float32 rounding.
 __device__ __forceinline__ void sincos_turns_f32(float th, float tl, float& s, float& c)
 {
     const float q = rintf(4.0f * th);
-    const float f = __fadd_rn(__fsub_rn(4.0f * th, q), 4.0f * tl);
-    const float PIO2_HI = 1.57079637050628662109375f;          // fl32(pi/2)
-    const float PIO2_LO = -4.37113900018624283e-8f;            // pi/2 - PIO2_HI
-    const float x = __fmaf_rn(f, PIO2_HI, __fmul_rn(f, PIO2_LO));
+    const float f = __fmaf_rn(4.0f, tl, __fsub_rn(4.0f * th, q));
+    const float x = __fmul_rn(f, 1.57079637050628662109375f);
     const float x2 = __fmul_rn(x, x);
     // sin x = x (1 - x^2/3! + x^4/5! - x^6/7! + x^8/9!)
     float ps = __fmaf_rn(x2, 2.7557319223985893e-6f, -1.9841269841269841e-4f);
@@ -178,6 +179,32 @@ __device__ __forceinline__ void sincos_turns_f32(float th, float tl, float& s, f
     c = ((qi + 1) & 2) ? -cc : cc;
 }
 
+// ---- float64 sin/cos of 2 pi t, |t| <= 1/2 (turns) --------------------------
+// Table-driven reduction (the table-lookup method of P. T. P. Tang, ACM TOMS
+// 15(2), 1989): k = rint(256 t), f = t - k/256 (exact, |f| <= 1/512), and
+// exp(i 2 pi t) = exp(i 2 pi k/256) exp(i 2 pi f). The table holds the first
+// factor correctly rounded (gen_sincos_table.py); the second comes from the
+// Taylor series of sin (to x^7) and cos (to x^6) at x = 2 pi f, |x| <= 0.0123,
+// whose truncation errors (< 2e-20 and < 8e-21) are far below float64
+// rounding. About 18 float64 operations instead of a general sin/cos.
+static __device__ const double2 kSinCos256[257] =
+#include "sincos_table.inc"
+    ;
+
+__device__ __forceinline__ void sincos_turns_f64(double t, double& s, double& c)
+{
+    const double k = rint(t * 256.0);
+    const double f = fma(k, -0.00390625, t);                       // t - k/256, exact
+    const double x = f * 6.283185307179586476925286766559;          // 2 pi f
+    const double x2 = x * x;
+    const double ps = fma(x2, fma(x2, -1.9841269841269841e-4, 8.3333333333333333e-3), -1.6666666666666667e-1);
+    const double sx = fma(x * x2, ps, x);
+    const double pc = fma(x2, fma(x2, fma(x2, -1.3888888888888889e-3, 4.1666666666666667e-2), -0.5), 1.0);
+    const double2 tk = __ldg(&kSinCos256[static_cast<int>(k) + 128]);
+    c = fma(tk.x, pc, -tk.y * sx);
+    s = fma(tk.y, pc, tk.x * sx);
+}
+
 // Kahan-compensated float32 accumulation: sum + comp carries the total.
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
 {
@@ -188,30 +215,48 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
 }
 
 // ---------------------------------------------------------------- tree handle
-// Post-order record of one tree node for the float64 predictor (40 bytes):
-// meta bits 0-4 level j, 5-6 child slot (key & 3), 7-10 child mask,
-// 11 leaf flag. Payload: leaf -> (s_u, s_v, s_w - 1, Phi); internal ->
-// (gamma^0, gamma^1, gamma^2, A_1 lambda_1 for level 1 else 0).
+// Node records for the predictors, in post-order, pre-decoded at build time.
+// A thread keeps one column of a shared-memory "stack" of 4 (J - 1) rows:
+// row 4 (j - 2) + c holds the plane-wave coefficient eta of the open level-j
+// node in child slot c (j = 2 .. J). meta bits:
+//    0-6   store row: where this node's eta goes (unused at level 1)
+//    7-13  child row: first of the node's four child rows, or, for a node
+//          with a single child, that child's row
+//   14-17  child mask (bit c: child 4k + c exists)
+//   18     leaf (level J)
+//   19     level 1 (adds A_1 lambda_1 eta_1, or Phi eta for a level-1 leaf)
+//   20     single child
+//   21-25  level j
+constexpr uint32_t kRecLeaf = 1u << 18;
+constexpr uint32_t kRecRoot = 1u << 19;
+constexpr uint32_t kRecSingle = 1u << 20;
+__host__ __device__ __forceinline__ uint32_t rec_store_row(uint32_t meta) { return meta & 127u; }
+__host__ __device__ __forceinline__ uint32_t rec_child_row(uint32_t meta) { return (meta >> 7) & 127u; }
+__host__ __device__ __forceinline__ uint32_t rec_mask(uint32_t meta) { return (meta >> 14) & 15u; }
+__host__ __device__ __forceinline__ uint32_t rec_level(uint32_t meta) { return (meta >> 21) & 31u; }
+
+// float64 record (48 bytes).
+//   leaf:     a, b, c = s_u, s_v, s_w - 1 (pixel centre, uvw frame); d = Phi
+//   internal: a, b, c = gamma^0, gamma^1, gamma^2 -- for a single-child node
+//             each multiplied by that child's sign in the Hadamard row
+//             (exact), so that gamma^m sigma^m = a_m (q eta_c);
+//             d = q = sqrt(A_j) / 4; e = A_1 lambda_1 at level 1, else 0
 struct RecD {
     uint32_t meta;
     uint32_t pad;
-    double a, b, c, d;
+    double a, b, c, d, e;
 };
-static_assert(sizeof(RecD) == 40, "RecD layout");
+static_assert(sizeof(RecD) == 48, "RecD layout");
 
-// Same for the mixed predictor (32 bytes): leaf -> (s_u, s_v, s_w - 1) as
-// double-float pairs and Phi; internal -> (gamma^0, gamma^1, gamma^2, 0, 0, 0,
-// A_1 lambda_1 for level 1 else 0) in float32.
+// float32 record of the mixed form (32 bytes).
+//   leaf:     (a, b), (c, d), (e, f) = s_u, s_v, s_w - 1 as double-float
+//             pairs; g = Phi
+//   internal: a, b, c = gamma as above; d = q; g = A_1 lambda_1 at level 1
 struct RecF {
     uint32_t meta;
     float a, b, c, d, e, f, g;
 };
 static_assert(sizeof(RecF) == 32, "RecF layout");
-
-__host__ __device__ __forceinline__ uint32_t rec_level(uint32_t meta) { return meta & 31u; }
-__host__ __device__ __forceinline__ uint32_t rec_slot(uint32_t meta) { return (meta >> 5) & 3u; }
-__host__ __device__ __forceinline__ uint32_t rec_mask(uint32_t meta) { return (meta >> 7) & 15u; }
-__host__ __device__ __forceinline__ uint32_t rec_leaf(uint32_t meta) { return (meta >> 11) & 1u; }
 
 // Device-side header of a tree (written by the build kernels).
 struct TreeHeader {
@@ -264,6 +309,20 @@ struct wt_tree_s {
 constexpr uint64_t kTreeMagic = 0x57545645455f3031ull;   // "WTVEE_01"
 
 namespace wt {
+// One wavelet-predictor launch, independent of the launch shape.
+struct WaveletJob {
+    const RecD* recd;        // post-order records (Eq. 17)
+    const RecF* recf;
+    const RecD* recd_leaf;   // leaf records (Eq. 16)
+    const RecF* recf_leaf;
+    const TreeHeader* hdr;
+    const double* uvw;
+    int64_t n_vis;
+    void* vis;
+    int mode, sign, which, J;
+    int* status;
+};
+
 // tree_build.cu
 int build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
                int J, wt_tree t, cudaStream_t s);
@@ -271,6 +330,13 @@ int tree_sync_header(wt_tree t);
 // wavelet.cu
 int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int mode, int sign, int which,
                     cudaStream_t s);
+extern const int kNumWaveletVariants;
+int wavelet_variant_shape(int v, int* nt, int* vpt);
+bool wavelet_variant_fits(int v, int mode, int which, int J);
+int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s);
+int default_wavelet_variant(int mode, int which, int J);
+// autotune.cu
+int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s);
 // dft.cu
 int predict_dft(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
                 int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s);

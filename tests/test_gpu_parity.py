@@ -279,3 +279,17 @@ def test_tree_on_wrong_mode_rejected():
     t = gpu_tree(w, 8)
     with pytest.raises(wt.WtError):
         wt.wt_predict_vis(t, dev(w.uvw[:4]), mode=7)
+
+
+# ---------------------------------------------------------------- launch shapes
+
+@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_wavelet_every_launch_shape(variant, mode, tol, monkeypatch):
+    # Each (threads per CTA, visibilities per thread) shape the autotuner may
+    # pick gives the oracle's answer, on a ragged count of visibilities.
+    monkeypatch.setenv("WT_WAVELET_VARIANT", str(variant))
+    w = synth.medium(n_t=4)
+    uvw = w.uvw[::7][:1111]
+    assert _wavelet_case(w, 13, uvw, mode) <= tol
+    assert _wavelet_case(w, 13, uvw, mode, which=wt.WT_SUM_EQ16) <= tol

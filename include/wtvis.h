@@ -145,6 +145,29 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
                    int mode, int sign, int which, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * wt_predict_vis_batched -- wt_predict_vis (Eq. 17) for many channels (or
+ * major cycles) at once: channel c has its own tree trees[c] and frequency
+ * freq_hz[c]; the baselines are shared, in metres, and scaled per channel to
+ * wavelengths, u_lambda = u_m f_c / c (c = 299 792 458 m/s).
+ *
+ *   trees    HOST array [n_ch] of built trees (any mix of J and sizes)
+ *   freq_hz  HOST array [n_ch], > 0
+ *   uvw_m    device float64 [n_vis][3], metres
+ *   vis_out  device [n_ch][n_vis], complex128 (WT_FP64) or complex64 (WT_MIXED)
+ *   mode     WT_FP64 or WT_MIXED; sign +1 / -1
+ * All channels run in one persistent kernel that takes (channel, tile) work
+ * items, largest trees first, from a device-side counter. The first call for
+ * a given (trees, freq_hz, mode, sign) builds a plan: it reads the trees'
+ * sizes (waiting for their build streams), times the fitting launch shapes
+ * on the caller's stream (skipped under WT_AUTOTUNE=0 or when the stream is
+ * being captured) and captures [counter reset + kernel] into a CUDA graph;
+ * later calls with the same buffers replay that graph. Freeing any of the
+ * trees drops the plans that use it.
+ * ------------------------------------------------------------------------- */
+int wt_predict_vis_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const double* uvw_m,
+                           int64_t n_vis, void* vis_out, int mode, int sign, void* stream);
+
+/* ---------------------------------------------------------------------------
  * dft_predict_vis -- Sec. 3.3, Eq. 12: the direct sum over the component list
  *   V_n = sum_m C_m exp(sign i 2 pi [u_n l_m + v_n m_m + w_n (n_m - 1)]),
  *   n_m = sqrt(1 - l_m^2 - m_m^2),

@@ -37,7 +37,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libwtvis.so")
 EXPORTS = [
     "wt_build_tree", "wt_tree_info", "wt_tree_export", "wt_free_tree", "wt_predict_vis",
     "dft_predict_vis", "subtract_model", "wt_recommended_J", "wt_device_status", "wt_last_error",
-    "dft_predict_vis_noalloc",
+    "dft_predict_vis_noalloc", "wt_predict_vis_batched",
 ]
 WT_NOALLOC_MAX_COMPONENTS = 65536
 
@@ -78,6 +78,7 @@ def _declare(L):
     L.dft_predict_vis.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int, C.c_int, vp]
     L.dft_predict_vis_noalloc.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int, C.c_int, vp, vp]
     L.subtract_model.argtypes = [vp, vp, vp, i64, C.c_int, vp]
+    L.wt_predict_vis_batched.argtypes = [vp, vp, C.c_int, vp, i64, vp, C.c_int, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
     L.wt_device_status.argtypes = [vp]
     L.wt_last_error.restype = C.c_char_p
@@ -186,6 +187,24 @@ def wt_predict_vis(tree, uvw, mode=WT_FP64, sign=1, which=WT_SUM_EQ17, out=None,
         out = torch.empty(n, dtype=_vis_dtype(mode), device=uvw.device)
     _check(load().wt_predict_vis(tree.h, _dev(uvw, torch.float64), n, _dev(out, _vis_dtype(mode)), int(mode),
                                  int(sign), int(which), _stream(stream)))
+    return out
+
+
+def wt_predict_vis_batched(trees, freq_hz, uvw_m, mode=WT_MIXED, sign=1, out=None, stream=None):
+    """Eq. 17 for many channels in one persistent, graph-captured launch.
+    trees: list of Tree; freq_hz: per-channel frequencies; uvw_m: [n_vis, 3]
+    metres (CUDA float64). Returns [n_ch, n_vis] visibilities."""
+    import torch
+    n_ch, n = len(trees), uvw_m.shape[0]
+    if out is None:
+        out = torch.empty((n_ch, n), dtype=_vis_dtype(mode), device=uvw_m.device)
+    handles = (C.c_void_p * n_ch)(*[t.h.value if isinstance(t.h, C.c_void_p) else t.h for t in trees])
+    freqs = np.ascontiguousarray(np.asarray(freq_hz, dtype=np.float64))
+    if freqs.shape != (n_ch,):
+        raise ValueError("freq_hz must have one entry per tree")
+    _check(load().wt_predict_vis_batched(C.cast(handles, C.c_void_p), freqs.ctypes.data_as(C.c_void_p), n_ch,
+                                         _dev(uvw_m, torch.float64), n, _dev(out, _vis_dtype(mode)), int(mode),
+                                         int(sign), _stream(stream)))
     return out
 
 

@@ -1,0 +1,470 @@
+// batched.cu -- wt_predict_vis_batched: many frequency channels (or major
+// cycles), each with its own coefficient tree, in one persistent launch.
+//
+// Work items are (channel, tile of NT * VPT visibilities). Channels are
+// ordered by decreasing tree size (largest work first), items numbered
+// channel-major in that order, and CTAs (one or two per SM, persistent) take
+// the next item from a device-wide atomic counter, so channels of very
+// uneven size keep every SM busy to the end. Items depend on nothing but
+// their own inputs: no CTA ever waits for another. A CTA re-targets its
+// shared-memory record staging only when the channel changes. Baselines are
+// shared in metres and scaled per channel, u_lambda = u_m f_c / c.
+//
+// The memset of the counter plus the kernel are captured once into a CUDA
+// graph per plan (tree set, frequencies, form, sign, buffers, launch shape)
+// and replayed on the caller's stream; the launch shape is picked by timing
+// the fitting shapes on the plan's first use (WT_AUTOTUNE=0: default shape).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "staging.cuh"
+#include "wavelet_bodies.cuh"
+#include "wt_internal.cuh"
+
+namespace wt {
+namespace {
+
+constexpr double kLightSpeed = 299792458.0;   // m/s
+
+struct BatchChan {
+    const RecD* recd;
+    const RecF* recf;
+    const TreeHeader* hdr;
+    double scale;          // f_c / c: metres -> wavelengths
+    int64_t out_offset;    // channel * n_vis
+    int64_t tile_base;     // first work item of this channel
+    int32_t J;
+    int32_t pad;
+};
+static_assert(sizeof(BatchChan) == 56, "BatchChan layout");
+
+__device__ __forceinline__ int find_channel(const BatchChan* __restrict__ ch, int n_ch, int64_t item)
+{
+    int a = 0, b = n_ch - 1;   // last channel whose tile_base <= item
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (__ldg(&ch[mid].tile_base) <= item) a = mid;
+        else b = mid - 1;
+    }
+    return a;
+}
+
+template <int NT, int VPT, bool MIXED>
+__global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ chans, int n_ch, int64_t total_items,
+                                                const double* __restrict__ uvw_m, int64_t n_vis, void* vis, double sgn,
+                                                int rows_max, unsigned long long* queue, int* status)
+{
+    using Rec = typename std::conditional<MIXED, RecF, RecD>::type;
+    constexpr int kChunk = MIXED ? kChunkF : kChunkD;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    Stager<Rec> st;
+    stager_setup(st, smem, static_cast<const Rec*>(nullptr), 0, kChunk);
+    unsigned char* stk_base = smem + stager_bytes<Rec>(kChunk);
+    int cur = -1;
+    int maxrow = 0;
+    constexpr int64_t per_tile = static_cast<int64_t>(NT) * VPT;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = static_cast<long long>(atomicAdd(queue, 1ull));
+        __syncthreads();
+        const int64_t item = s_item;
+        __syncthreads();
+        if (item >= total_items) break;
+        const int c = find_channel(chans, n_ch, item);
+        const BatchChan ch = chans[c];
+        if (c != cur) {
+            const Rec* recs;
+            if constexpr (MIXED) recs = ch.recf;
+            else recs = ch.recd;
+            st.retarget(recs, ch.hdr->n_nodes);
+            cur = c;
+            maxrow = min(4 * (ch.J > 1 ? ch.J - 1 : 1), rows_max) - 1;
+        }
+        const int64_t n0 = (item - ch.tile_base) * per_tile + threadIdx.x;
+        bool good;
+        if constexpr (MIXED) {
+            Eq17F<NT, VPT> b;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+                const bool ok = n < n_vis;
+                const double s = sgn * ch.scale;   // sign folded into B (exact negation)
+                b.u[k] = split_f64(ok ? uvw_m[3 * n] * s : 0.0);
+                b.v[k] = split_f64(ok ? uvw_m[3 * n + 1] * s : 0.0);
+                b.w[k] = split_f64(ok ? uvw_m[3 * n + 2] * s : 0.0);
+                b.vr[k] = 0.f; b.vi[k] = 0.f; b.cr[k] = 0.f; b.ci[k] = 0.f;
+            }
+            b.sgn = 1.0f;
+            b.stk = reinterpret_cast<float2*>(stk_base) + threadIdx.x;
+            b.maxrow = maxrow;
+            good = st.sweep(b);
+            float2* out = static_cast<float2*>(vis) + ch.out_offset;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+                if (good && n < n_vis) out[n] = make_float2(b.vr[k] - b.cr[k], b.vi[k] - b.ci[k]);
+            }
+        } else {
+            Eq17D<NT, VPT> b;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+                const bool ok = n < n_vis;
+                const double s = sgn * ch.scale;
+                b.u[k] = ok ? uvw_m[3 * n] * s : 0.0;
+                b.v[k] = ok ? uvw_m[3 * n + 1] * s : 0.0;
+                b.w[k] = ok ? uvw_m[3 * n + 2] * s : 0.0;
+                b.vr[k] = 0.0; b.vi[k] = 0.0;
+            }
+            b.sgn = 1.0;
+            b.stk = reinterpret_cast<double2*>(stk_base) + threadIdx.x;
+            b.maxrow = maxrow;
+            good = st.sweep(b);
+            double2* out = static_cast<double2*>(vis) + ch.out_offset;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+                if (good && n < n_vis) out[n] = make_double2(b.vr[k], b.vi[k]);
+            }
+        }
+        if (!good) {
+            if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host
+struct Shape {
+    int nt, vpt;
+};
+constexpr int kNumBatchShapes = 5;
+const Shape kBatchShapes[kNumBatchShapes] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}, {32, 1}};
+
+size_t batch_smem(int mode, int shape, int rows_max)
+{
+    const size_t cplx = mode == WT_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t stage = mode == WT_FP64 ? stager_bytes<RecD>(kChunkD) : stager_bytes<RecF>(kChunkF);
+    return stage + static_cast<size_t>(rows_max) * kBatchShapes[shape].nt * kBatchShapes[shape].vpt * cplx;
+}
+
+bool batch_fits(int mode, int shape, int rows_max) { return batch_smem(mode, shape, rows_max) <= 220 * 1024; }
+
+template <int NT, int VPT, bool MIXED>
+int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
+                 int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
+{
+    auto k = k_batched<NT, VPT, MIXED>;
+    int per_sm = 0;
+    WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+    if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
+    int64_t grid = static_cast<int64_t>(num_sms()) * per_sm;
+    if (grid > total) grid = total > 0 ? total : 1;
+    k<<<static_cast<unsigned>(grid), NT, smem, s>>>(chans, n_ch, total, uvw_m, n_vis, vis, static_cast<double>(sign),
+                                                    rows_max, queue, status);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+template <bool MIXED>
+int set_attr(int shape, size_t smem)
+{
+    const void* fn;
+    switch (shape) {
+        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, MIXED>); break;
+        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, MIXED>); break;
+        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, MIXED>); break;
+        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, MIXED>); break;
+        default: fn = reinterpret_cast<const void*>(k_batched<32, 1, MIXED>); break;
+    }
+    WT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    return WT_OK;
+}
+
+int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m,
+                 int64_t n_vis, void* vis, int sign, int rows_max, unsigned long long* queue, int* status,
+                 cudaStream_t s)
+{
+    const size_t smem = batch_smem(mode, shape, rows_max);
+    if (mode == WT_FP64) {
+        switch (shape) {
+            case 0: return launch_shape<256, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 1: return launch_shape<128, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 2: return launch_shape<128, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 3: return launch_shape<64, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            default: return launch_shape<32, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        }
+    }
+    switch (shape) {
+        case 0: return launch_shape<256, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 1: return launch_shape<128, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 2: return launch_shape<128, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 3: return launch_shape<64, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        default: return launch_shape<32, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+    }
+}
+
+// A plan: one set of trees and frequencies in one form, its device-side
+// channel table and counter, its launch shape and its captured graph.
+struct Plan {
+    int device = 0, mode = 0, sign = 1, n_ch = 0;
+    std::vector<wt_tree> trees;
+    std::vector<double> freqs;
+    std::vector<int> order;          // channels by decreasing node count
+    std::vector<int64_t> nodes;
+    int rows_max = 4;
+    int shape = -1;
+    void* dmem = nullptr;            // [n_ch] BatchChan + counter
+    BatchChan* d_chan = nullptr;
+    unsigned long long* d_queue = nullptr;
+    int64_t table_nvis = -1;
+    int table_shape = -1;
+    int64_t total = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const double* g_uvw = nullptr;
+    int64_t g_nvis = -1;
+    void* g_vis = nullptr;
+    int g_shape = -1;
+
+    ~Plan()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+        if (dmem) cudaFree(dmem);
+        cudaGetLastError();
+    }
+};
+
+std::mutex g_mu;
+std::vector<std::unique_ptr<Plan>> g_plans;
+
+Plan* find_plan(const wt_tree* trees, const double* freqs, int n_ch, int mode, int sign, int dev)
+{
+    for (auto& p : g_plans) {
+        if (p->device != dev || p->mode != mode || p->sign != sign || p->n_ch != n_ch) continue;
+        bool same = true;
+        for (int c = 0; c < n_ch && same; ++c) same = p->trees[c] == trees[c] && p->freqs[c] == freqs[c];
+        if (same) return p.get();
+    }
+    return nullptr;
+}
+
+// Fill and upload the channel table for n_vis and the plan's shape.
+int write_table(Plan& p, int64_t n_vis, int shape, cudaStream_t s)
+{
+    if (p.table_nvis == n_vis && p.table_shape == shape) return WT_OK;
+    const int64_t per_tile = static_cast<int64_t>(kBatchShapes[shape].nt) * kBatchShapes[shape].vpt;
+    const int64_t tiles = (n_vis + per_tile - 1) / per_tile;
+    std::vector<BatchChan> h(p.n_ch);
+    int64_t base = 0;
+    for (int i = 0; i < p.n_ch; ++i) {
+        const int c = p.order[i];
+        wt_tree t = p.trees[c];
+        BatchChan& b = h[i];
+        b.recd = t->d.recd;
+        b.recf = t->d.recf;
+        b.hdr = t->d.hdr;
+        b.scale = p.freqs[c] / kLightSpeed;
+        b.out_offset = static_cast<int64_t>(c) * n_vis;
+        b.tile_base = base;
+        b.J = t->J;
+        b.pad = 0;
+        base += tiles;
+    }
+    // The table is read by kernels already enqueued on `s`; order the copy
+    // after them and keep the host buffer alive until it is done.
+    WT_CUDA_TRY(cudaMemcpyAsync(p.d_chan, h.data(), sizeof(BatchChan) * p.n_ch, cudaMemcpyHostToDevice, s));
+    WT_CUDA_TRY(cudaStreamSynchronize(s));
+    p.table_nvis = n_vis;
+    p.table_shape = shape;
+    p.total = base;
+    return WT_OK;
+}
+
+int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cudaStream_t s)
+{
+    int first = -1;
+    for (int sh = 0; sh < kNumBatchShapes; ++sh)
+        if (batch_fits(p.mode, sh, p.rows_max)) {
+            first = sh;
+            break;
+        }
+    if (first < 0) return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis_batched: no launch shape fits J");
+    const char* e = getenv("WT_AUTOTUNE");
+    if (e && e[0] == '0') return first;
+    const int64_t sample = n_vis < 16384 ? n_vis : 16384;
+    cudaEvent_t e0, e1;
+    WT_CUDA_TRY(cudaEventCreate(&e0));
+    WT_CUDA_TRY(cudaEventCreate(&e1));
+    int best = first;
+    float best_ms = 1e30f;
+    for (int sh = 0; sh < kNumBatchShapes; ++sh) {
+        if (!batch_fits(p.mode, sh, p.rows_max)) continue;
+        int rc = (p.mode == WT_FP64) ? set_attr<false>(sh, batch_smem(p.mode, sh, p.rows_max))
+                                     : set_attr<true>(sh, batch_smem(p.mode, sh, p.rows_max));
+        if (rc) continue;
+        if (write_table(p, sample, sh, s)) continue;
+        float ms_best_rep = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaMemsetAsync(p.d_queue, 0, sizeof(unsigned long long), s);
+            cudaEventRecord(e0, s);
+            rc = launch_batch(p.mode, sh, p.d_chan, p.n_ch, p.total, uvw_m, sample, vis, p.sign, p.rows_max,
+                              p.d_queue, status, s);
+            cudaEventRecord(e1, s);
+            if (rc || cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < ms_best_rep) ms_best_rep = ms;
+        }
+        cudaGetLastError();
+        const char* v = getenv("WT_AUTOTUNE_VERBOSE");
+        if (v && v[0] == '1')
+            fprintf(stderr, "[wt autotune] batched n_ch=%d mode%d shape %d (%d threads x %d vis): %.4f ms for %lld vis/ch\n",
+                    p.n_ch, p.mode, sh, kBatchShapes[sh].nt, kBatchShapes[sh].vpt, ms_best_rep,
+                    static_cast<long long>(sample));
+        if (ms_best_rep < best_ms) {
+            best_ms = ms_best_rep;
+            best = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+}  // namespace
+
+void batch_forget_tree(wt_tree t)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = 0; i < g_plans.size();) {
+        bool uses = false;
+        for (wt_tree x : g_plans[i]->trees) uses = uses || x == t;
+        if (uses) g_plans.erase(g_plans.begin() + static_cast<long>(i));
+        else ++i;
+    }
+}
+
+int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const double* uvw_m, int64_t n_vis,
+                    void* vis, int mode, int sign, cudaStream_t s)
+{
+    int dev = 0;
+    WT_CUDA_TRY(cudaGetDevice(&dev));
+    int* status = device_status_word();
+    if (!status) return set_error(WT_ERR_CUDA, "wt_predict_vis_batched: no device status word");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Plan* p = find_plan(trees, freq_hz, n_ch, mode, sign, dev);
+    if (!p) {
+        std::unique_ptr<Plan> np(new Plan());
+        np->device = dev;
+        np->mode = mode;
+        np->sign = sign;
+        np->n_ch = n_ch;
+        np->trees.assign(trees, trees + n_ch);
+        np->freqs.assign(freq_hz, freq_hz + n_ch);
+        np->nodes.resize(n_ch);
+        int jmax = 1;
+        for (int c = 0; c < n_ch; ++c) {
+            int rc = tree_sync_header(trees[c]);
+            if (rc) return rc;
+            np->nodes[c] = trees[c]->host_hdr->n_nodes;
+            if (trees[c]->J > jmax) jmax = trees[c]->J;
+        }
+        np->rows_max = jmax > 1 ? 4 * (jmax - 1) : 4;
+        np->order.resize(n_ch);
+        for (int c = 0; c < n_ch; ++c) np->order[c] = c;
+        std::stable_sort(np->order.begin(), np->order.end(),
+                         [&](int a, int b) { return np->nodes[a] > np->nodes[b]; });
+        const size_t bytes = sizeof(BatchChan) * static_cast<size_t>(n_ch) + 256;
+        cudaError_t e = cudaMalloc(&np->dmem, bytes);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (batch plan)");
+        np->d_chan = static_cast<BatchChan*>(np->dmem);
+        np->d_queue = reinterpret_cast<unsigned long long*>(static_cast<char*>(np->dmem) +
+                                                            ((sizeof(BatchChan) * n_ch + 127) & ~size_t(127)));
+        WT_CUDA_TRY(cudaStreamCreateWithFlags(&np->cap, cudaStreamNonBlocking));
+        p = np.get();
+        g_plans.push_back(std::move(np));
+    }
+    if (p->shape < 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        WT_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            for (int sh = 0; sh < kNumBatchShapes && p->shape < 0; ++sh)
+                if (batch_fits(mode, sh, p->rows_max)) p->shape = sh;
+        } else {
+            const int best = tune(*p, uvw_m, n_vis, vis, status, s);
+            if (best < 0) return best;
+            p->shape = best;
+        }
+    }
+    const size_t smem = batch_smem(mode, p->shape, p->rows_max);
+    int rc = (mode == WT_FP64) ? set_attr<false>(p->shape, smem) : set_attr<true>(p->shape, smem);
+    if (rc) return rc;
+    if ((rc = write_table(*p, n_vis, p->shape, s))) return rc;
+    if (!p->exec || p->g_uvw != uvw_m || p->g_nvis != n_vis || p->g_vis != vis || p->g_shape != p->shape) {
+        // capture [counter reset, persistent kernel] once for these buffers
+        cudaGraph_t g = nullptr;
+        WT_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned long long), p->cap);
+        rc = launch_batch(mode, p->shape, p->d_chan, n_ch, p->total, uvw_m, n_vis, vis, sign, p->rows_max,
+                          p->d_queue, status, p->cap);
+        cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+        e = cudaGraphInstantiate(&p->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        p->g_uvw = uvw_m;
+        p->g_nvis = n_vis;
+        p->g_vis = vis;
+        p->g_shape = p->shape;
+    }
+    WT_CUDA_TRY(cudaGraphLaunch(p->exec, s));
+    return WT_OK;
+}
+
+}  // namespace wt
+
+// ---------------------------------------------------------------------------
+extern "C" int wt_predict_vis_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const double* uvw_m,
+                                      int64_t n_vis, void* vis_out, int mode, int sign, void* stream)
+{
+    using namespace wt;
+    const char* fn = "wt_predict_vis_batched";
+    if (!trees || !freq_hz) return set_error(WT_ERR_ARG, "%s: trees and freq_hz are host arrays, not NULL", fn);
+    if (n_ch < 1 || n_ch > 65536) return set_error(WT_ERR_ARG, "%s: n_ch = %d outside 1..65536", fn, n_ch);
+    if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
+    if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
+    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    int dev = 0;
+    WT_CUDA_TRY(cudaGetDevice(&dev));
+    for (int c = 0; c < n_ch; ++c) {
+        wt_tree t = trees[c];
+        if (!t) return set_error(WT_ERR_ARG, "%s: tree %d is NULL", fn, c);
+        if (t->magic != kTreeMagic) return set_error(WT_ERR_CORRUPT, "%s: tree %d is not a live handle", fn, c);
+        if (t->device != dev) return set_error(WT_ERR_ARG, "%s: tree %d lives on another device", fn, c);
+        if (!(freq_hz[c] > 0.0) || !isfinite(freq_hz[c]))
+            return set_error(WT_ERR_RANGE, "%s: frequency %d must be positive and finite", fn, c);
+    }
+    const size_t ob = static_cast<size_t>(n_vis) * n_ch * (mode == WT_FP64 ? 16 : 8);
+    int rc;
+    if ((rc = check_device_buffer(uvw_m, static_cast<size_t>(n_vis) * 24, fn, "uvw_m")) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
+        return rc;
+    if (n_vis == 0) return WT_OK;
+    return predict_batched(trees, freq_hz, n_ch, uvw_m, n_vis, vis_out, mode, sign, static_cast<cudaStream_t>(stream));
+}

@@ -43,6 +43,17 @@ struct Stager {
         loaded = false;
     }
 
+    // Point the stager at another record list (same chunking). Call only
+    // when no copy is in flight (after a completed sweep) and after a CTA
+    // barrier, so that no thread still reads the buffers.
+    __device__ void retarget(const Rec* r, int64_t n)
+    {
+        recs = r;
+        count = n;
+        resident = nchunks() <= 2;
+        loaded = false;
+    }
+
     // Run body(rec) for every record, in order. Returns false (uniformly
     // across the CTA) if a copy did not arrive within the spin limit.
     template <class Body>

@@ -263,6 +263,7 @@ void wt_free_tree(wt_tree t)
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != t->device) cudaSetDevice(t->device);
+    wt::batch_forget_tree(t);
     cudaStreamSynchronize(t->stream);
     if (t->block) cudaFreeAsync(t->block, t->stream);
     cudaStreamSynchronize(t->stream);

@@ -337,6 +337,11 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s);
 int default_wavelet_variant(int mode, int which, int J);
 // autotune.cu
 int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s);
+// batched.cu
+int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const double* uvw_m, int64_t n_vis,
+                    void* vis, int mode, int sign, cudaStream_t s);
+void batch_forget_tree(wt_tree t);
+int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name);
 // dft.cu
 int predict_dft(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
                 int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s);

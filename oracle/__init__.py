@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp",
            "-Wall", "-o", tmp] + srcs + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
@@ -87,7 +87,12 @@ def _declare(L):
 
 
 def _declare_mlp(L):
-    pass
+    L.orc_pixel_response.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int64, _d, C.c_int, _d]
+    L.orc_level_pixel_size.argtypes = [C.c_int]
+    L.orc_level_pixel_size.restype = C.c_double
+    L.orc_mlp_n_params.restype = C.c_int
+    L.orc_mlp_forward.argtypes = [_d, C.c_int, C.c_int64, _d, _d]
+    L.orc_mlp_loss_grad.argtypes = [_d, C.c_int, C.c_int64, _d, _d, _d, _d]
 
 
 def _p(a, t=_d):
@@ -252,6 +257,61 @@ def dense_vis_eq17(l, m, flux, ra0, dec0, J, uvw, sign=1):
     _check(lib().orc_dense_vis_eq17(J, len(l), _p(l), _p(m), _p(flux), ra0, dec0,
                                     uvw.shape[0], _p(uvw), sign, _p(out)), "dense_eq17")
     return _as_complex(out)
+
+
+# ---------------------------------------------------------------------------
+# Learned response (an addition, not in the paper): readings R10, R11 of
+# oracle_mlp.c
+# ---------------------------------------------------------------------------
+
+MLP_HIDDEN = 64
+
+
+def pixel_response(j, D, ra0, dec0, uvw, sign=1):
+    """Exact R_j(B): mean of exp(sign i 2 pi B.(s_i - c_j)) over the 4^D
+    level-(j+D) sub-pixel centres of the level-j pixel holding the phase
+    centre (float64, OpenMP over samples)."""
+    uvw = _f64(uvw).reshape(-1, 3)
+    out = np.zeros(2 * uvw.shape[0])
+    _check(lib().orc_pixel_response(j, D, ra0, dec0, uvw.shape[0], _p(uvw), sign, _p(out)), "pixel_response")
+    return _as_complex(out)
+
+
+def level_pixel_size(j):
+    return float(lib().orc_level_pixel_size(j))
+
+
+def mlp_n_params():
+    return int(lib().orc_mlp_n_params())
+
+
+def mlp_split(params):
+    """Views W1[64,3], b1, W2[64,64], b2, W3[2,64], b3 of a flat vector."""
+    h = MLP_HIDDEN
+    o = np.cumsum([0, 3 * h, h, h * h, h, 2 * h, 2])
+    p = np.asarray(params)
+    return (p[o[0]:o[1]].reshape(h, 3), p[o[1]:o[2]], p[o[2]:o[3]].reshape(h, h), p[o[3]:o[4]],
+            p[o[4]:o[5]].reshape(2, h), p[o[5]:o[6]])
+
+
+def mlp_forward(params, level, uvw):
+    params = _f64(params)
+    uvw = _f64(uvw).reshape(-1, 3)
+    y = np.zeros(2 * uvw.shape[0])
+    _check(lib().orc_mlp_forward(_p(params), level, uvw.shape[0], _p(uvw), _p(y)), "mlp_forward")
+    return y.reshape(-1, 2)
+
+
+def mlp_loss_grad(params, level, uvw, target):
+    """Mean squared error (both outputs) and its gradient (float64)."""
+    params = _f64(params)
+    uvw = _f64(uvw).reshape(-1, 3)
+    target = _f64(target).reshape(-1, 2)
+    g = np.zeros_like(params)
+    loss = C.c_double()
+    _check(lib().orc_mlp_loss_grad(_p(params), level, uvw.shape[0], _p(uvw), _p(target), C.byref(loss), _p(g)),
+           "mlp_loss_grad")
+    return loss.value, g
 
 
 def recommended_J(dtheta_rad):

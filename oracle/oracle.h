@@ -82,6 +82,17 @@ int orc_dense_vis_eq17(int J, int64_t n, const double* l, const double* m, const
                        double ra0, double dec0, int64_t n_vis, const double* uvw, int sign,
                        double* vis);
 
+/* ---- Learned response (oracle_mlp.c; an addition, not in the paper) -------- */
+/* Exact per-level pixel response R_j(B) over the 4^D descendants of the
+ * level-j pixel holding the phase centre (see oracle_mlp.c). out: [n][2]. */
+int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
+                       double* out);
+double orc_level_pixel_size(int j);
+int orc_mlp_n_params(void);
+int orc_mlp_forward(const double* params, int level, int64_t n, const double* uvw, double* y);
+int orc_mlp_loss_grad(const double* params, int level, int64_t n, const double* uvw, const double* target,
+                      double* loss, double* grad);
+
 /* ---- Helpers ---------------------------------------------------------------- */
 /* Sec. 3.3: smallest J with Delta theta_J <= dtheta / 2 (Table 1 rule). */
 int orc_recommended_J(double dtheta_rad);

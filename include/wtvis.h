@@ -220,6 +220,55 @@ int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid,
                    int64_t n_vis, int mode, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned response (an addition to the paper's method).
+ *
+ * For level j, R_j(B) = 4^-D sum_i exp(i 2 pi B.(s_i - c_j)) over the 4^D
+ * descendants s_i, D levels down, of the level-j pixel c_j holding the phase
+ * centre: the plane wave's level-j scaling coefficient on a fully populated
+ * sub-tree (the Eq. 9 recursion), demodulated by the plane wave at c_j. A
+ * per-level network 3 -> 64 -> 64 -> 2 (SiLU; BF16 weights, FP32
+ * accumulation on the tensor cores) maps x = B Delta theta_j
+ * (Delta theta_j = 2^(1-j) sqrt(pi/3), Sec. 3.3) to (Re R, Im R). Where
+ * |x|_inf > x_max (outside the trained domain) the exact sum is used.
+ * Parameters: 4546 float32 in the order W1[64][3], b1[64], W2[64][64],
+ * b2[64], W3[2][64], b3[2]. All entry points below synchronise with the
+ * device where they say so; uvw is device float64 [n][3] in wavelengths.
+ * ------------------------------------------------------------------------- */
+typedef struct wt_mlp_s* wt_mlp;
+
+/* New network for `level`, seeded random weights; depth = D (0..8) of the
+ * exact response used as fallback; x_max bounds the trained domain.
+ * Synchronises the device. */
+int wt_mlp_create(int level, double ra0, double dec0, int depth, float x_max, uint64_t seed, wt_mlp* out);
+void wt_mlp_free(wt_mlp m);
+/* Host copies of the 4546 float32 parameters (both synchronise). */
+int wt_mlp_get_params(wt_mlp m, float* host_params);
+int wt_mlp_set_params(wt_mlp m, const float* host_params);
+/* Exact R_j(B) in float64 (the fallback and the judge); out: device
+ * complex128 [n]. sign = -1 gives the conjugate. */
+int wt_response_exact(int level, int depth, double ra0, double dec0, const double* uvw, int64_t n, int sign,
+                      void* out, void* stream);
+/* Mean squared error of both outputs against target (device float32
+ * [n][2]) and its gradient (HOST float32 [4546]); synchronises `stream`.
+ * The forward pass rounds W2 and the hidden activations to BF16 exactly as
+ * inference does. */
+int wt_mlp_loss_grad(wt_mlp m, const double* uvw, const float* target, int64_t n, float* loss, float* grad,
+                     void* stream);
+/* `steps` Adam steps (cosine-decayed rate from lr) on contiguous minibatches
+ * of `batch` samples taken cyclically from (uvw, target); final_loss (host,
+ * may be NULL) receives the last minibatch's loss (synchronises). */
+int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, int steps, int batch, float lr,
+                 float* final_loss, void* stream);
+/* R(B) by the network (exact sum beyond x_max); out: device complex64 [n]. */
+int wt_mlp_eval(wt_mlp m, const double* uvw, int64_t n, int sign, void* out, void* stream);
+/* Learned form of the tree prediction: V = R_J(B) sum_k Phi_k exp(sign i 2 pi
+ * B.(c_k - P)) -- the level-J sum (Eq. 16) with each leaf's centre-snapped
+ * plane wave replaced by the pixel's full response. The network's level must
+ * equal the tree's J and the phase centres must match. Output complex64. */
+int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis, void* vis_out, int sign,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------
  * Helpers
  * ------------------------------------------------------------------------- */
 

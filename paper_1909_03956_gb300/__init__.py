@@ -38,7 +38,10 @@ EXPORTS = [
     "wt_build_tree", "wt_tree_info", "wt_tree_export", "wt_free_tree", "wt_predict_vis",
     "dft_predict_vis", "subtract_model", "wt_recommended_J", "wt_device_status", "wt_last_error",
     "dft_predict_vis_noalloc", "wt_predict_vis_batched",
+    "wt_mlp_create", "wt_mlp_free", "wt_mlp_get_params", "wt_mlp_set_params", "wt_response_exact",
+    "wt_mlp_loss_grad", "wt_mlp_train", "wt_mlp_eval", "wt_predict_vis_learned",
 ]
+MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
 
 
@@ -79,6 +82,17 @@ def _declare(L):
     L.dft_predict_vis_noalloc.argtypes = [vp, vp, vp, i64, vp, i64, vp, C.c_int, C.c_int, vp, vp]
     L.subtract_model.argtypes = [vp, vp, vp, i64, C.c_int, vp]
     L.wt_predict_vis_batched.argtypes = [vp, vp, C.c_int, vp, i64, vp, C.c_int, C.c_int, vp]
+    f = C.c_float
+    L.wt_mlp_create.argtypes = [C.c_int, d, d, C.c_int, f, C.c_uint64, C.POINTER(vp)]
+    L.wt_mlp_free.argtypes = [vp]
+    L.wt_mlp_free.restype = None
+    L.wt_mlp_get_params.argtypes = [vp, vp]
+    L.wt_mlp_set_params.argtypes = [vp, vp]
+    L.wt_response_exact.argtypes = [C.c_int, C.c_int, d, d, vp, i64, C.c_int, vp, vp]
+    L.wt_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    L.wt_mlp_train.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, f, vp, vp]
+    L.wt_mlp_eval.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+    L.wt_predict_vis_learned.argtypes = [vp, vp, vp, i64, vp, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
     L.wt_device_status.argtypes = [vp]
     L.wt_last_error.restype = C.c_char_p
@@ -205,6 +219,83 @@ def wt_predict_vis_batched(trees, freq_hz, uvw_m, mode=WT_MIXED, sign=1, out=Non
     _check(load().wt_predict_vis_batched(C.cast(handles, C.c_void_p), freqs.ctypes.data_as(C.c_void_p), n_ch,
                                          _dev(uvw_m, torch.float64), n, _dev(out, _vis_dtype(mode)), int(mode),
                                          int(sign), _stream(stream)))
+    return out
+
+
+# ---------------------------------------------------------------- learned response
+
+class Mlp:
+    """Owns a wt_mlp handle: the per-level response network."""
+
+    def __init__(self, level, ra0, dec0, depth=4, x_max=8.0, seed=0):
+        h = C.c_void_p()
+        _check(load().wt_mlp_create(int(level), float(ra0), float(dec0), int(depth), float(x_max), int(seed),
+                                    C.byref(h)))
+        self.h, self.level, self.depth, self.x_max = h, level, depth, x_max
+
+    def close(self):
+        if self.h:
+            load().wt_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(MLP_N_PARAMS, dtype=np.float32)
+        _check(load().wt_mlp_get_params(self.h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().wt_mlp_set_params(self.h, p.ctypes.data_as(C.c_void_p)))
+
+    def loss_grad(self, uvw, target, stream=None):
+        import torch
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(MLP_N_PARAMS, dtype=np.float32)
+        _check(load().wt_mlp_loss_grad(self.h, _dev(uvw, torch.float64), _dev(target, torch.float32), uvw.shape[0],
+                                       loss.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p),
+                                       _stream(stream)))
+        return float(loss[0]), g
+
+    def train(self, uvw, target, steps, batch=8192, lr=3e-3, stream=None):
+        import torch
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().wt_mlp_train(self.h, _dev(uvw, torch.float64), _dev(target, torch.float32), uvw.shape[0],
+                                   int(steps), int(batch), float(lr), loss.ctypes.data_as(C.c_void_p),
+                                   _stream(stream)))
+        return float(loss[0])
+
+    def eval(self, uvw, sign=1, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(uvw.shape[0], dtype=torch.complex64, device=uvw.device)
+        _check(load().wt_mlp_eval(self.h, _dev(uvw, torch.float64), uvw.shape[0], int(sign),
+                                  _dev(out, torch.complex64), _stream(stream)))
+        return out
+
+
+def wt_response_exact(level, depth, ra0, dec0, uvw, sign=1, out=None, stream=None):
+    """Exact per-level pixel response R_j(B) (float64)."""
+    import torch
+    if out is None:
+        out = torch.empty(uvw.shape[0], dtype=torch.complex128, device=uvw.device)
+    _check(load().wt_response_exact(int(level), int(depth), float(ra0), float(dec0), _dev(uvw, torch.float64),
+                                    uvw.shape[0], int(sign), _dev(out, torch.complex128), _stream(stream)))
+    return out
+
+
+def wt_predict_vis_learned(tree, mlp, uvw, sign=1, out=None, stream=None):
+    """Learned form: the level-J sum with each leaf's full pixel response."""
+    import torch
+    if out is None:
+        out = torch.empty(uvw.shape[0], dtype=torch.complex64, device=uvw.device)
+    _check(load().wt_predict_vis_learned(tree.h, mlp.h, _dev(uvw, torch.float64), uvw.shape[0],
+                                         _dev(out, torch.complex64), int(sign), _stream(stream)))
     return out
 
 

@@ -1,0 +1,742 @@
+// mlp.cu -- the learned per-level visibility response (an addition to the
+// paper's method, not in arXiv:1909.03956).
+//
+// What is learned. For level j, let P_j be the level-j pixel holding the
+// phase centre, c_j its centre and s_i its 4^D descendants D levels down.
+// The pixel response R_j(B) = 4^-D sum_i exp(i 2 pi B.(s_i - c_j)) is the
+// plane wave's level-j scaling coefficient on a fully populated sub-tree
+// (the Eq. 9 recursion), demodulated by the plane wave at the centre. A
+// pixel whose flux fills it uniformly contributes
+// Phi exp(i 2 pi B.(c - P)) R_j(B) instead of the centre-snapped term of
+// Eq. 16, so the learned form of the tree prediction is
+//     V_learned(B) = R_j(B) sum_k Phi_k exp(i 2 pi B.(c_k - P))      (j = J).
+// A network 3 -> 64 -> 64 -> 2 (SiLU) maps x = B Delta theta_j to
+// (Re R, Im R). Outside |x|_inf <= x_max (the trained domain) the exact sum
+// is evaluated instead: exact evaluation is the fallback and the judge.
+//
+// Kernels:
+//   k_response_offsets  s_i - c_j for the 4^D sub-pixels (float64)
+//   k_response_exact    R_j(B) by the exact sum (float64, table sin/cos)
+//   k_mlp_apply         inference on the tensor cores: mma.sync m16n8k16
+//                       BF16 x BF16 -> FP32 for the 64 x 64 layer, FP32 for
+//                       the 3 -> 64 and 64 -> 2 layers; writes R or
+//                       multiplies visibilities by it in place
+//   k_mlp_train_grad    forward + backward over a batch (FP32, with the
+//                       hidden activations and W2 rounded to BF16 in the
+//                       forward pass exactly as the inference kernel sees
+//                       them), gradients reduced per CTA then atomically
+//   k_mlp_adam          Adam update of the FP32 master parameters
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cuda_bf16.h>
+
+#include <random>
+#include <vector>
+
+#include "sphere.cuh"
+#include "wt_internal.cuh"
+
+namespace wt {
+namespace {
+
+constexpr int kH = 64;                                   // hidden width
+constexpr int kNumParams = kH * 3 + kH + kH * kH + kH + 2 * kH + 2;   // 4546
+// offsets into the flat parameter vector (same order as the CPU oracle)
+constexpr int oW1 = 0, ob1 = oW1 + kH * 3, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH, ob3 = oW3 + 2 * kH;
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z)
+{
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// D = A (16x16 bf16, row) * B (16x8 bf16, col) + C (16x8 f32)
+__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+struct Rot {
+    double r[9];
+};
+
+// ---------------------------------------------------------------- exact response
+// Unit vector of nested pixel `pix` at `level` in the uvw frame, (s_u, s_v, s_w - 1).
+__device__ void pixel_dir(int level, int64_t pix, const Rot& R, double* d)
+{
+    double z, st, ph, sph, cph;
+    pixel_centre(level - 1, pix, z, st, ph);
+    sincos(ph, &sph, &cph);
+    const double x = st * sph, y = z, zc = st * cph;
+    const double su = R.r[0] * x + R.r[3] * y + R.r[6] * zc;
+    const double sv = R.r[1] * x + R.r[4] * y + R.r[7] * zc;
+    const double sw = R.r[2] * x + R.r[5] * y + R.r[8] * zc;
+    d[0] = su;
+    d[1] = sv;
+    d[2] = (sw > 0.0) ? -(su * su + sv * sv) / (1.0 + sw) : sw - 1.0;
+}
+
+// Level-j pixel holding the phase centre: the image point l = m = 0, mapped
+// exactly as the tree build maps a component.
+__device__ int64_t phase_centre_pixel(int level, const Rot& R)
+{
+    double phi = atan2(R.r[2], R.r[8]);
+    if (phi < 0.0) phi = __dadd_rn(phi, 2.0 * kPi);
+    if (phi >= 2.0 * kPi) phi = __dsub_rn(phi, 2.0 * kPi);
+    return pixel_of(level - 1, R.r[5], phi);
+}
+
+__global__ void k_response_offsets(int level, int depth, Rot R, double* __restrict__ offs)
+{
+    const int64_t nsub = int64_t(1) << (2 * depth);
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nsub) return;
+    const int64_t kref = phase_centre_pixel(level, R);
+    double c[3], s[3];
+    pixel_dir(level, kref, R, c);
+    pixel_dir(level + depth, (kref << (2 * depth)) + i, R, s);
+    offs[3 * i + 0] = s[0] - c[0];
+    offs[3 * i + 1] = s[1] - c[1];
+    offs[3 * i + 2] = s[2] - c[2];
+}
+
+__device__ double2 response_exact_one(double u, double v, double w, const double* __restrict__ offs, int n_off)
+{
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < n_off; ++i) {
+        double t = fma(w, __ldg(&offs[3 * i + 2]), fma(v, __ldg(&offs[3 * i + 1]), u * __ldg(&offs[3 * i])));
+        t -= rint(t);
+        double s, c;
+        sincos_turns_f64(t, s, c);
+        re += c;
+        im += s;
+    }
+    const double inv = 1.0 / static_cast<double>(n_off);
+    return make_double2(re * inv, im * inv);
+}
+
+__global__ void k_response_exact(const double* __restrict__ uvw, int64_t n, const double* __restrict__ offs, int n_off,
+                                 double sgn, double2* __restrict__ out)
+{
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double2 r = response_exact_one(uvw[3 * q], uvw[3 * q + 1], uvw[3 * q + 2], offs, n_off);
+        out[q] = make_double2(r.x, sgn * r.y);
+    }
+}
+
+// ---------------------------------------------------------------- inference
+struct MlpDev {
+    const float* params;        // FP32 master, oracle layout
+    const uint32_t* w2_bf16x2;  // W2 as bf16 pairs, row n: W2[n][2p], W2[n][2p+1] -> [n * 32 + p]
+};
+
+constexpr int kApplyThreads = 128;
+
+// One warp evaluates 16 samples per step: layer 1 straight into the A
+// fragments, layer 2 as 4 x 8 mma.sync tiles (K = 64, N = 64), layer 3 by
+// quad reductions of the accumulator fragments.
+template <bool APPLY>
+__global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const double* __restrict__ uvw, int64_t n,
+                                                             float2* __restrict__ io, float scale, int sign,
+                                                             float x_max, const double* __restrict__ offs, int n_off)
+{
+    __shared__ float sW1[kH * 3], sb1[kH], sb2[kH], sW3[2 * kH], sb3[2];
+    for (int i = threadIdx.x; i < kH * 3; i += blockDim.x) sW1[i] = p.params[oW1 + i];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        sb1[i] = p.params[ob1 + i];
+        sb2[i] = p.params[ob2 + i];
+    }
+    for (int i = threadIdx.x; i < 2 * kH; i += blockDim.x) sW3[i] = p.params[oW3 + i];
+    if (threadIdx.x < 2) sb3[threadIdx.x] = p.params[ob3 + threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    // B fragments of W2^T (k = input unit, n = output unit) for every tile
+    uint32_t bfr[4][8][2];
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int nn = 8 * nt + g, k0 = 16 * kt + 2 * tq;
+            bfr[kt][nt][0] = __ldg(&p.w2_bf16x2[nn * 32 + k0 / 2]);
+            bfr[kt][nt][1] = __ldg(&p.w2_bf16x2[nn * 32 + (k0 + 8) / 2]);
+        }
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t tile = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n;
+         tile += warps) {
+        const int64_t s0 = tile * 16 + g, s1 = s0 + 8;
+        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
+        if (s0 < n)
+            for (int d = 0; d < 3; ++d) x0[d] = static_cast<float>(uvw[3 * s0 + d]) * scale;
+        if (s1 < n)
+            for (int d = 0; d < 3; ++d) x1[d] = static_cast<float>(uvw[3 * s1 + d]) * scale;
+        // layer 1 -> A fragments (rows g, g + 8; columns 16 kt + 2 tq + {0, 1, 8, 9})
+        uint32_t a[4][4];
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            float h0[4], h1[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = 16 * kt + 2 * tq + (e & 1) + 8 * (e >> 1);
+                const float w0 = sW1[3 * col], w1 = sW1[3 * col + 1], w2 = sW1[3 * col + 2], b = sb1[col];
+                h0[e] = silu_f(fmaf(w2, x0[2], fmaf(w1, x0[1], fmaf(w0, x0[0], b))));
+                h1[e] = silu_f(fmaf(w2, x1[2], fmaf(w1, x1[1], fmaf(w0, x1[0], b))));
+            }
+            a[kt][0] = pack_bf16x2(h0[0], h0[1]);
+            a[kt][1] = pack_bf16x2(h1[0], h1[1]);
+            a[kt][2] = pack_bf16x2(h0[2], h0[3]);
+            a[kt][3] = pack_bf16x2(h1[2], h1[3]);
+        }
+        // layer 2 (tensor cores), SiLU, layer 3
+        float y00 = 0.f, y01 = 0.f, y10 = 0.f, y11 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int col = 8 * nt + 2 * tq;
+            float acc[4] = {sb2[col], sb2[col + 1], sb2[col], sb2[col + 1]};
+#pragma unroll
+            for (int kt = 0; kt < 4; ++kt) mma_bf16_16816(acc, a[kt], bfr[kt][nt]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float hr0 = silu_f(acc[j]), hr1 = silu_f(acc[2 + j]);
+                y00 = fmaf(sW3[col + j], hr0, y00);
+                y01 = fmaf(sW3[kH + col + j], hr0, y01);
+                y10 = fmaf(sW3[col + j], hr1, y10);
+                y11 = fmaf(sW3[kH + col + j], hr1, y11);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            y00 += __shfl_xor_sync(0xffffffffu, y00, o);
+            y01 += __shfl_xor_sync(0xffffffffu, y01, o);
+            y10 += __shfl_xor_sync(0xffffffffu, y10, o);
+            y11 += __shfl_xor_sync(0xffffffffu, y11, o);
+        }
+        // lane tq = 0 finishes row g, lane tq = 1 row g + 8
+        if (tq < 2) {
+            const int64_t s = tq ? s1 : s0;
+            if (s < n) {
+                const float* x = tq ? x1 : x0;
+                float rr = (tq ? y10 : y00) + sb3[0];
+                float ri = (tq ? y11 : y01) + sb3[1];
+                if (fmaxf(fabsf(x[0]), fmaxf(fabsf(x[1]), fabsf(x[2]))) > x_max) {
+                    const double2 e = response_exact_one(uvw[3 * s], uvw[3 * s + 1], uvw[3 * s + 2], offs, n_off);
+                    rr = static_cast<float>(e.x);
+                    ri = static_cast<float>(e.y);
+                }
+                if (sign < 0) ri = -ri;
+                if (APPLY) {
+                    const float2 v = io[s];
+                    io[s] = make_float2(v.x * rr - v.y * ri, v.x * ri + v.y * rr);
+                } else {
+                    io[s] = make_float2(rr, ri);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_w2_to_bf16(const float* __restrict__ params, uint32_t* __restrict__ w2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // pair index
+    if (i >= kH * kH / 2) return;
+    const int nrow = i / 32, pcol = i % 32;
+    w2[i] = pack_bf16x2(params[oW2 + nrow * kH + 2 * pcol], params[oW2 + nrow * kH + 2 * pcol + 1]);
+}
+
+// ---------------------------------------------------------------- training
+constexpr int kTrainThreads = 256;
+constexpr int kS = 64;   // samples per CTA tile
+
+struct TrainSmem {
+    float x[kS][3];
+    float t[kS][2];
+    float dy[kS][2];
+    float valid[kS];
+    float z1[kS][kH];    // pre-activation, later dz1
+    float h1[kS][kH];    // bf16-rounded activation
+    float z2[kS][kH];
+    float h2[kS][kH];
+    float dz2[kS][kH];
+    float W2q[kH][kH];   // bf16-rounded W2
+    float W1[kH * 3], b1[kH], b2[kH], W3[2 * kH], b3[2];
+    float gW1[kH * 3], gb1[kH], gb2[kH], gW3[2 * kH], gb3[2];
+    float loss;
+};
+
+__global__ void __launch_bounds__(kTrainThreads) k_mlp_train_grad(const float* __restrict__ params,
+                                                                  const double* __restrict__ uvw,
+                                                                  const float* __restrict__ target, int64_t first,
+                                                                  int64_t count, int64_t n_total, int64_t n_data,
+                                                                  float scale, float* __restrict__ grad,
+                                                                  float* __restrict__ loss_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kH * kH; i += blockDim.x) sm.W2q[i / kH][i % kH] = bf16_round(params[oW2 + i]);
+    for (int i = tid; i < kH * 3; i += blockDim.x) {
+        sm.W1[i] = params[oW1 + i];
+        sm.gW1[i] = 0.f;
+    }
+    for (int i = tid; i < kH; i += blockDim.x) {
+        sm.b1[i] = params[ob1 + i];
+        sm.b2[i] = params[ob2 + i];
+        sm.gb1[i] = 0.f;
+        sm.gb2[i] = 0.f;
+    }
+    for (int i = tid; i < 2 * kH; i += blockDim.x) {
+        sm.W3[i] = params[oW3 + i];
+        sm.gW3[i] = 0.f;
+    }
+    if (tid < 2) {
+        sm.b3[tid] = params[ob3 + tid];
+        sm.gb3[tid] = 0.f;
+    }
+    if (tid == 0) sm.loss = 0.f;
+    float gW2[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) gW2[i] = 0.f;
+    __syncthreads();
+    const float inv_n = 1.0f / static_cast<float>(n_total);
+    for (int64_t base = first + static_cast<int64_t>(blockIdx.x) * kS; base < first + count;
+         base += static_cast<int64_t>(gridDim.x) * kS) {
+        // samples wrap around the data set (minibatches are contiguous slices)
+        if (tid < kS) {
+            const int64_t q = base + tid;
+            const bool ok = q < first + count;
+            const int64_t qq = ok ? (q % n_data) : 0;
+            for (int d = 0; d < 3; ++d) sm.x[tid][d] = ok ? static_cast<float>(uvw[3 * qq + d]) * scale : 0.f;
+            sm.t[tid][0] = ok ? target[2 * qq] : 0.f;
+            sm.t[tid][1] = ok ? target[2 * qq + 1] : 0.f;
+            sm.valid[tid] = ok ? 1.f : 0.f;
+        }
+        __syncthreads();
+        for (int e = tid; e < kS * kH; e += blockDim.x) {
+            const int s = e / kH, k = e % kH;
+            const float z = fmaf(sm.W1[3 * k + 2], sm.x[s][2], fmaf(sm.W1[3 * k + 1], sm.x[s][1],
+                                                                    fmaf(sm.W1[3 * k], sm.x[s][0], sm.b1[k])));
+            sm.z1[s][k] = z;
+            sm.h1[s][k] = bf16_round(silu_f(z));
+        }
+        __syncthreads();
+        for (int e = tid; e < kS * kH; e += blockDim.x) {
+            const int s = e / kH, o = e % kH;
+            float z = sm.b2[o];
+#pragma unroll 16
+            for (int k = 0; k < kH; ++k) z = fmaf(sm.W2q[o][k], sm.h1[s][k], z);
+            sm.z2[s][o] = z;
+            sm.h2[s][o] = silu_f(z);
+        }
+        __syncthreads();
+        if (tid < 2 * kS) {
+            const int s = tid >> 1, o = tid & 1;
+            float y = sm.b3[o];
+            for (int k = 0; k < kH; ++k) y = fmaf(sm.W3[o * kH + k], sm.h2[s][k], y);
+            const float err = (sm.valid[s] != 0.f) ? y - sm.t[s][o] : 0.f;
+            atomicAdd(&sm.loss, err * err);
+            sm.dy[s][o] = 2.f * err * inv_n;
+        }
+        __syncthreads();
+        for (int e = tid; e < kS * kH; e += blockDim.x) {
+            const int s = e / kH, o = e % kH;
+            const float dh = sm.dy[s][0] * sm.W3[o] + sm.dy[s][1] * sm.W3[kH + o];
+            sm.dz2[s][o] = dh * dsilu_f(sm.z2[s][o]);
+        }
+        if (tid < 2 * kH) {
+            const int o2 = tid / kH, k = tid % kH;
+            float a = 0.f;
+            for (int s = 0; s < kS; ++s) a = fmaf(sm.dy[s][o2], sm.h2[s][k], a);
+            sm.gW3[tid] += a;
+        }
+        if (tid < 2) {
+            float a = 0.f;
+            for (int s = 0; s < kS; ++s) a += sm.dy[s][tid];
+            sm.gb3[tid] += a;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + kTrainThreads * i, o = e / kH, k = e % kH;
+            float a = 0.f;
+            for (int s = 0; s < kS; ++s) a = fmaf(sm.dz2[s][o], sm.h1[s][k], a);
+            gW2[i] += a;
+        }
+        if (tid < kH) {
+            float a = 0.f;
+            for (int s = 0; s < kS; ++s) a += sm.dz2[s][tid];
+            sm.gb2[tid] += a;
+        }
+        for (int e = tid; e < kS * kH; e += blockDim.x) {
+            const int s = e / kH, k = e % kH;
+            float dh = 0.f;
+#pragma unroll 16
+            for (int o = 0; o < kH; ++o) dh = fmaf(sm.dz2[s][o], sm.W2q[o][k], dh);
+            sm.z1[s][k] = dh * dsilu_f(sm.z1[s][k]);   // dz1, in place
+        }
+        __syncthreads();
+        if (tid < kH) {
+            float a = 0.f;
+            for (int s = 0; s < kS; ++s) a += sm.z1[s][tid];
+            sm.gb1[tid] += a;
+        }
+        if (tid < kH * 3) {
+            const int k = tid / 3, d = tid % 3;
+            float a = 0.f;
+            for (int s = 0; s < kS; ++s) a = fmaf(sm.z1[s][k], sm.x[s][d], a);
+            sm.gW1[tid] += a;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) atomicAdd(&grad[oW2 + tid + kTrainThreads * i], gW2[i]);
+    for (int i = tid; i < kH * 3; i += blockDim.x) atomicAdd(&grad[oW1 + i], sm.gW1[i]);
+    for (int i = tid; i < kH; i += blockDim.x) {
+        atomicAdd(&grad[ob1 + i], sm.gb1[i]);
+        atomicAdd(&grad[ob2 + i], sm.gb2[i]);
+    }
+    for (int i = tid; i < 2 * kH; i += blockDim.x) atomicAdd(&grad[oW3 + i], sm.gW3[i]);
+    if (tid < 2) atomicAdd(&grad[ob3 + tid], sm.gb3[tid]);
+    if (tid == 0) atomicAdd(loss_out, sm.loss * inv_n);
+}
+
+__global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m, float* __restrict__ v,
+                           float* __restrict__ grad, float lr, float b1c, float b2c)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNumParams) return;
+    const float g = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * g;
+    const float vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    params[i] -= lr * (mi / b1c) / (sqrtf(vi / b2c) + 1e-8f);
+    grad[i] = 0.f;
+}
+
+}  // namespace
+}  // namespace wt
+
+// ===========================================================================
+// Host side: the wt_mlp handle and the C entry points.
+// ===========================================================================
+struct wt_mlp_s {
+    uint64_t magic;
+    int device;
+    int level, depth;
+    float x_max;
+    double ra0, dec0;
+    void* block;                 // params, m, v, grad, loss, w2 bf16, offsets
+    float* params;
+    float* m;
+    float* v;
+    float* grad;
+    float* loss;
+    uint32_t* w2;
+    double* offs;
+    int n_off;
+    int adam_t;
+};
+
+namespace {
+constexpr uint64_t kMlpMagic = 0x4d4c505f57543031ull;   // "MLP_WT01"
+
+int check_mlp(wt_mlp m, const char* fn)
+{
+    using namespace wt;
+    if (!m) return set_error(WT_ERR_ARG, "%s: mlp is NULL", fn);
+    if (m->magic != kMlpMagic) return set_error(WT_ERR_CORRUPT, "%s: not a live mlp handle", fn);
+    int dev = 0;
+    WT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != m->device) return set_error(WT_ERR_ARG, "%s: mlp lives on device %d", fn, m->device);
+    return WT_OK;
+}
+
+int refresh_bf16(wt_mlp m, cudaStream_t s)
+{
+    wt::k_w2_to_bf16<<<(wt::kH * wt::kH / 2 + 255) / 256, 256, 0, s>>>(m->params, m->w2);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+int launch_apply(wt_mlp m, const double* uvw, int64_t n, void* io, int sign, bool apply, cudaStream_t s)
+{
+    using namespace wt;
+    const float scale = static_cast<float>(ldexp(sqrt(kPi / 3.0), 1 - m->level));   // Delta theta_j
+    MlpDev p{m->params, m->w2};
+    const int64_t tiles = (n + 15) / 16;
+    int64_t blocks = (tiles + (kApplyThreads / 32) - 1) / (kApplyThreads / 32);
+    const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (apply)
+        k_mlp_apply<true><<<static_cast<unsigned>(blocks), kApplyThreads, 0, s>>>(
+            p, uvw, n, static_cast<float2*>(io), scale, sign, m->x_max, m->offs, m->n_off);
+    else
+        k_mlp_apply<false><<<static_cast<unsigned>(blocks), kApplyThreads, 0, s>>>(
+            p, uvw, n, static_cast<float2*>(io), scale, sign, m->x_max, m->offs, m->n_off);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+int run_grad(wt_mlp m, const double* uvw, const float* target, int64_t first, int64_t count, int64_t n_data,
+             cudaStream_t s)
+{
+    using namespace wt;
+    const size_t smem = sizeof(TrainSmem);
+    WT_CUDA_TRY(cudaFuncSetAttribute(k_mlp_train_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem)));
+    const float scale = static_cast<float>(ldexp(sqrt(kPi / 3.0), 1 - m->level));
+    int64_t blocks = (count + kS - 1) / kS;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * 2;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_mlp_train_grad<<<static_cast<unsigned>(blocks), kTrainThreads, smem, s>>>(
+        m->params, uvw, target, first, count, count, n_data, scale, m->grad, m->loss);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+}  // namespace
+
+using namespace wt;
+
+extern "C" {
+
+int wt_mlp_create(int level, double ra0, double dec0, int depth, float x_max, uint64_t seed, wt_mlp* out)
+{
+    const char* fn = "wt_mlp_create";
+    if (!out) return set_error(WT_ERR_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    if (level < 1 || depth < 0 || depth > 8 || level + depth > kMaxJ)
+        return set_error(WT_ERR_RANGE, "%s: need 1 <= level, 0 <= depth <= 8, level + depth <= %d", fn, kMaxJ);
+    if (!(x_max >= 0.0f) || !isfinite(ra0) || !isfinite(dec0)) return set_error(WT_ERR_RANGE, "%s: bad x_max or centre", fn);
+    int dev = 0;
+    WT_CUDA_TRY(cudaGetDevice(&dev));
+    wt_mlp m = new (std::nothrow) wt_mlp_s();
+    if (!m) return set_error(WT_ERR_NOMEM, "%s: host allocation failed", fn);
+    memset(static_cast<void*>(m), 0, sizeof(*m));
+    m->device = dev;
+    m->level = level;
+    m->depth = depth;
+    m->x_max = x_max;
+    m->ra0 = ra0;
+    m->dec0 = dec0;
+    m->n_off = 1 << (2 * depth);
+    const size_t fbytes = sizeof(float) * kNumParams;
+    const size_t bytes = 4 * ((fbytes + 255) & ~size_t(255)) + 256 + (kH * kH / 2) * 4 + 256 +
+                         sizeof(double) * 3 * static_cast<size_t>(m->n_off) + 256;
+    cudaError_t e = cudaMalloc(&m->block, bytes);
+    if (e != cudaSuccess) {
+        delete m;
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "%s: device allocation failed", fn);
+    }
+    char* p = static_cast<char*>(m->block);
+    auto take = [&](size_t b) {
+        char* r = p;
+        p += (b + 255) & ~size_t(255);
+        return r;
+    };
+    m->params = reinterpret_cast<float*>(take(fbytes));
+    m->m = reinterpret_cast<float*>(take(fbytes));
+    m->v = reinterpret_cast<float*>(take(fbytes));
+    m->grad = reinterpret_cast<float*>(take(fbytes));
+    m->loss = reinterpret_cast<float*>(take(sizeof(float)));
+    m->w2 = reinterpret_cast<uint32_t*>(take((kH * kH / 2) * 4));
+    m->offs = reinterpret_cast<double*>(take(sizeof(double) * 3 * static_cast<size_t>(m->n_off)));
+    // He-style initial weights, zero biases, from a seeded host generator
+    std::vector<float> h(kNumParams, 0.0f);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.0f, 1.0f);
+    for (int i = 0; i < kH * 3; ++i) h[oW1 + i] = nd(rng) * 1.0f;
+    for (int i = 0; i < kH * kH; ++i) h[oW2 + i] = nd(rng) * sqrtf(2.0f / kH);
+    for (int i = 0; i < 2 * kH; ++i) h[oW3 + i] = nd(rng) * sqrtf(1.0f / kH);
+    int rc = WT_OK;
+    if (cudaMemcpy(m->params, h.data(), fbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->m, 0, fbytes) != cudaSuccess || cudaMemset(m->v, 0, fbytes) != cudaSuccess ||
+        cudaMemset(m->grad, 0, fbytes) != cudaSuccess || cudaMemset(m->loss, 0, sizeof(float)) != cudaSuccess)
+        rc = cuda_error(cudaGetLastError(), "wt_mlp_create initialisation");
+    if (rc == WT_OK) {
+        Rot R;
+        rotation_matrix(ra0, dec0, R.r);
+        k_response_offsets<<<(m->n_off + 127) / 128, 128>>>(level, depth, R, m->offs);
+        rc = refresh_bf16(m, nullptr);
+        if (rc == WT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = cuda_error(cudaGetLastError(), "wt_mlp_create");
+    }
+    if (rc != WT_OK) {
+        cudaFree(m->block);
+        delete m;
+        return rc;
+    }
+    m->magic = kMlpMagic;
+    *out = m;
+    return WT_OK;
+}
+
+void wt_mlp_free(wt_mlp m)
+{
+    if (!m || m->magic != kMlpMagic) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != m->device) cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    cudaFree(m->block);
+    cudaGetLastError();
+    if (prev >= 0 && prev != m->device) cudaSetDevice(prev);
+    m->magic = 0;
+    delete m;
+}
+
+int wt_mlp_get_params(wt_mlp m, float* host_params)
+{
+    int rc = check_mlp(m, "wt_mlp_get_params");
+    if (rc) return rc;
+    if (!host_params) return set_error(WT_ERR_ARG, "wt_mlp_get_params: NULL buffer");
+    WT_CUDA_TRY(cudaDeviceSynchronize());
+    WT_CUDA_TRY(cudaMemcpy(host_params, m->params, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
+    return WT_OK;
+}
+
+int wt_mlp_set_params(wt_mlp m, const float* host_params)
+{
+    int rc = check_mlp(m, "wt_mlp_set_params");
+    if (rc) return rc;
+    if (!host_params) return set_error(WT_ERR_ARG, "wt_mlp_set_params: NULL buffer");
+    WT_CUDA_TRY(cudaDeviceSynchronize());
+    WT_CUDA_TRY(cudaMemcpy(m->params, host_params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+    WT_CUDA_TRY(cudaMemset(m->m, 0, sizeof(float) * kNumParams));
+    WT_CUDA_TRY(cudaMemset(m->v, 0, sizeof(float) * kNumParams));
+    m->adam_t = 0;
+    if ((rc = refresh_bf16(m, nullptr))) return rc;
+    WT_CUDA_TRY(cudaDeviceSynchronize());
+    return WT_OK;
+}
+
+int wt_response_exact(int level, int depth, double ra0, double dec0, const double* uvw, int64_t n, int sign,
+                      void* out, void* stream)
+{
+    const char* fn = "wt_response_exact";
+    if (level < 1 || depth < 0 || depth > 8 || level + depth > kMaxJ)
+        return set_error(WT_ERR_RANGE, "%s: need 1 <= level, 0 <= depth <= 8, level + depth <= %d", fn, kMaxJ);
+    if (n < 0 || (sign != 1 && sign != -1)) return set_error(WT_ERR_ARG, "%s: bad n or sign", fn);
+    int rc;
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(out, static_cast<size_t>(n) * 16, fn, "out")))
+        return rc;
+    if (n == 0) return WT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n_off = 1 << (2 * depth);
+    double* offs = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&offs), sizeof(double) * 3 * n_off, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+    Rot R;
+    rotation_matrix(ra0, dec0, R.r);
+    k_response_offsets<<<(n_off + 127) / 128, 128, 0, s>>>(level, depth, R, offs);
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
+    if (blocks > cap) blocks = cap;
+    k_response_exact<<<static_cast<unsigned>(blocks), 256, 0, s>>>(uvw, n, offs, n_off, static_cast<double>(sign),
+                                                                   static_cast<double2*>(out));
+    cudaError_t le = cudaGetLastError();
+    cudaFreeAsync(offs, s);
+    if (le != cudaSuccess) return cuda_error(le, fn);
+    return WT_OK;
+}
+
+int wt_mlp_loss_grad(wt_mlp m, const double* uvw, const float* target, int64_t n, float* loss, float* grad,
+                     void* stream)
+{
+    const char* fn = "wt_mlp_loss_grad";
+    int rc = check_mlp(m, fn);
+    if (rc) return rc;
+    if (n <= 0 || !loss || !grad) return set_error(WT_ERR_ARG, "%s: need n > 0 and host outputs", fn);
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target")))
+        return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WT_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNumParams, s));
+    WT_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+    if ((rc = run_grad(m, uvw, target, 0, n, n, s))) return rc;
+    WT_CUDA_TRY(cudaMemcpyAsync(grad, m->grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, s));
+    WT_CUDA_TRY(cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    WT_CUDA_TRY(cudaStreamSynchronize(s));
+    WT_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNumParams, s));
+    return WT_OK;
+}
+
+int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, int steps, int batch, float lr,
+                 float* final_loss, void* stream)
+{
+    const char* fn = "wt_mlp_train";
+    int rc = check_mlp(m, fn);
+    if (rc) return rc;
+    if (n <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0f)) return set_error(WT_ERR_ARG, "%s: bad sizes or lr", fn);
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target")))
+        return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WT_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNumParams, s));
+    int64_t first = 0;
+    for (int it = 0; it < steps; ++it) {
+        WT_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+        if ((rc = run_grad(m, uvw, target, first, batch, n, s))) return rc;
+        m->adam_t += 1;
+        // cosine decay of the learning rate over the run
+        const float lr_t = 0.5f * lr * (1.0f + cosf(3.14159265f * static_cast<float>(it) / static_cast<float>(steps)));
+        const float b1c = 1.0f - powf(0.9f, static_cast<float>(m->adam_t));
+        const float b2c = 1.0f - powf(0.999f, static_cast<float>(m->adam_t));
+        k_mlp_adam<<<(kNumParams + 255) / 256, 256, 0, s>>>(m->params, m->m, m->v, m->grad, lr_t, b1c, b2c);
+        WT_CUDA_TRY(cudaGetLastError());
+        first = (first + batch) % n;
+    }
+    if ((rc = refresh_bf16(m, s))) return rc;
+    if (final_loss) {
+        WT_CUDA_TRY(cudaMemcpyAsync(final_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        WT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return WT_OK;
+}
+
+int wt_mlp_eval(wt_mlp m, const double* uvw, int64_t n, int sign, void* out, void* stream)
+{
+    const char* fn = "wt_mlp_eval";
+    int rc = check_mlp(m, fn);
+    if (rc) return rc;
+    if (n < 0 || (sign != 1 && sign != -1)) return set_error(WT_ERR_ARG, "%s: bad n or sign", fn);
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
+        (rc = check_device_buffer(out, static_cast<size_t>(n) * 8, fn, "out")))
+        return rc;
+    if (n == 0) return WT_OK;
+    return launch_apply(m, uvw, n, out, sign, false, static_cast<cudaStream_t>(stream));
+}
+
+int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis, void* vis_out, int sign,
+                           void* stream)
+{
+    const char* fn = "wt_predict_vis_learned";
+    int rc = check_mlp(m, fn);
+    if (rc) return rc;
+    if (!t || t->magic != kTreeMagic) return set_error(WT_ERR_ARG, "%s: bad tree handle", fn);
+    if (t->J != m->level) return set_error(WT_ERR_ARG, "%s: the network is for level %d, the tree has J = %d", fn,
+                                           m->level, t->J);
+    if (t->ra0 != m->ra0 || t->dec0 != m->dec0)
+        return set_error(WT_ERR_ARG, "%s: tree and network have different phase centres", fn);
+    if ((rc = wt_predict_vis(t, uvw, n_vis, vis_out, WT_MIXED, sign, WT_SUM_EQ16, stream))) return rc;
+    if (n_vis == 0) return WT_OK;
+    return launch_apply(m, uvw, n_vis, vis_out, sign, true, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -56,6 +56,12 @@ def parse():
     p.add_argument("--J", type=int, default=MEDIUM_J)
     p.add_argument("--no-extras", action="store_true", help="skip the per-form side measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    p.add_argument("--forms-once", action="store_true",
+                   help="run each predictor once on the medium workload after one warm-up (a bounded "
+                        "command for profilers); prints nothing but a short summary")
+    p.add_argument("--sweep", action="store_true",
+                   help="print the run-time scaling study (J and distinct-component sweeps, paper-context "
+                        "workload) as one JSON line instead of the benchmark line")
     return p.parse_args()
 
 
@@ -245,6 +251,8 @@ def native(args):
     tree_keep.close()
     if rank == 0 and not args.no_extras:
         extras["batched"] = batched_measurement(wt, torch, dev, stream, flush)
+        extras["mixed_config"] = mixed_measurement(wt, torch, dev, stream, flush)
+        extras["learned"] = learned_measurement(wt, torch, dev, stream, flush)
 
     if rank != 0:
         if world > 1:
@@ -294,7 +302,10 @@ def native(args):
             "peak": peak,
             "unit": "TOP/s (FP32 pipe ops)",
             "frac": achieved / peak,
-            "traffic": None,
+            "traffic": TRAFFIC_BYTES_MEDIUM_J12 if (J == MEDIUM_J and n_vis == 1008000) else None,
+            "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
+                            "(profiles/k_wavelet_mixed_medium_1008000vis_J12.md); output still in L2 at exit",
+            "algorithmic_bytes": 32 * n_vis,
             "kernel": "k_wavelet_mixed (Eq. 17)",
         },
         "e2e": {"value": world * n_vis / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -317,6 +328,9 @@ def native(args):
 # branches) is not counted.
 OPS_LEAF = 68
 OPS_NODE = 38
+# DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
+# from ncu (dram__bytes_read.sum 24 265 472 + dram__bytes_write.sum 0).
+TRAFFIC_BYTES_MEDIUM_J12 = 24265472
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
@@ -406,6 +420,107 @@ def batched_measurement(wt, torch, dev, stream, flush):
             "form": "WT_MIXED Eq. 17"}
 
 
+def mixed_measurement(wt, torch, dev, stream, flush):
+    """Config X: 128 antennas, 2 032 000 visibilities per channel at 1.3 and
+    1.5 GHz, 20 000 clustered components, J = 12; the mixed form against the
+    FP64 oracle, for the wavelet route and the direct sum."""
+    import oracle as O
+    w = synth.mixed()
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    l, m, f = d(w.l), d(w.m), d(w.flux)
+    S = float(np.abs(w.flux).sum())
+    out = {"workload": w.name, "n_vis_per_ch": int(w.extra["uvw_m"].shape[0]), "n_comp": w.n_comp, "J": w.J}
+    tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, w.J)
+    info = tree.info()
+    out["n_leaves"], out["n_nodes"] = info["n_leaves"], info["n_nodes"]
+    errs_w, errs_d, tw, td = [], [], 0.0, 0.0
+    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J)
+    for fr in w.extra["freqs"]:
+        uvw_np = w.extra["uvw_m"] * (fr / synth.C_LIGHT)
+        uvw = d(uvw_np)
+        vw = torch.empty(uvw.shape[0], dtype=torch.complex64, device=dev)
+        vd = torch.empty_like(vw)
+        wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=vw)
+        wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd)
+        tw += _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=vw), stream, flush)
+        td += _time_call(lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd), stream, flush, reps=1)
+        idx = np.arange(0, uvw_np.shape[0], uvw_np.shape[0] // 400)
+        errs_w.append(float(np.max(np.abs(vw.cpu().numpy()[idx] - ot.vis_eq17(uvw_np[idx]))) / S))
+        errs_d.append(float(np.max(np.abs(vd.cpu().numpy()[idx] - O.dft(w.l, w.m, w.flux, uvw_np[idx]))) / S))
+    n_tot = 2 * out["n_vis_per_ch"]
+    tree.close()
+    out.update({"wavelet_mixed_vis_per_s": n_tot / tw, "wavelet_max_rel_err": max(errs_w),
+                "dft_mixed_vis_per_s": n_tot / td, "dft_mixed_vis_terms_per_s": n_tot * w.n_comp / td,
+                "dft_max_rel_err": max(errs_d)})
+    return out
+
+
+def learned_measurement(wt, torch, dev, stream, flush, n_train=10_000_000, depth=4):
+    """Config L: 256 antennas, 15 993 600 visibilities, 50 000 components,
+    J = 12; the level-12 response network trained on n_train responses the
+    oracle generates (baselines drawn from the array), then the learned form
+    timed on every visibility and judged on a sample: against the exact
+    response (its fallback and judge) and, for the gain, against the true
+    visibilities (Eq. 12 at the true positions) next to the centre-snapped
+    level-J sum."""
+    import oracle as O
+    w = synth.learned()
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    J = w.J
+    rng = np.random.default_rng(21)
+    t0 = time.perf_counter()
+    idx = rng.integers(0, w.n_vis, n_train)
+    tr_uvw = w.uvw[idx] * np.where(rng.random((n_train, 1)) < 0.5, -1.0, 1.0)
+    tgt = O.pixel_response(J, depth, w.ra0, w.dec0, tr_uvw)
+    t_gen = time.perf_counter() - t0
+    dt = O.level_pixel_size(J)
+    x_max = float(np.max(np.abs(tr_uvw * dt))) * 1.0001
+    mlp = wt.Mlp(J, w.ra0, w.dec0, depth=depth, x_max=x_max, seed=5)
+    tu = d(tr_uvw)
+    tt = d(np.stack([tgt.real, tgt.imag], axis=1).astype(np.float32))
+    del tr_uvw, tgt
+    steps = 2 * (n_train // 8192)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = mlp.train(tu, tt, steps=steps, batch=8192, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del tu, tt
+    uvw = d(w.uvw)
+    l, m, f = d(w.l), d(w.m), d(w.flux)
+    tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, J)
+    info = tree.info()
+    out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+    wt.wt_predict_vis_learned(tree, mlp, uvw, out=out)
+    t_l = _time_call(lambda: wt.wt_predict_vis_learned(tree, mlp, uvw, out=out), stream, flush)
+    o17 = torch.empty_like(out)
+    wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o17)
+    t_17 = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o17), stream, flush)
+    # judge on a strided sample
+    S = float(np.abs(w.flux).sum())
+    sidx = np.arange(0, w.n_vis, w.n_vis // 600)[:600]
+    su = w.uvw[sidx]
+    got = out.cpu().numpy()[sidx]
+    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+    v_centre = ot.vis_eq16(su)
+    r_exact = O.pixel_response(J, depth, w.ra0, w.dec0, su)
+    v_exact_resp = v_centre * r_exact
+    v_true = O.dft(w.l, w.m, w.flux, su)
+    rms = lambda a, b: float(np.sqrt(np.mean(np.abs(a - b) ** 2)) / S)
+    y = mlp.eval(d(su)).cpu().numpy()
+    res = {"workload": w.name, "J": J, "n_vis": w.n_vis, "n_comp": w.n_comp, "n_leaves": info["n_leaves"],
+           "n_nodes": info["n_nodes"], "train_samples": n_train, "train_steps": steps, "depth": depth,
+           "x_max": x_max, "oracle_target_gen_s": t_gen, "train_s": t_train, "final_minibatch_loss": loss,
+           "response_rms_err_vs_exact": float(np.sqrt(np.mean(np.abs(y - r_exact) ** 2))),
+           "learned_vis_per_s": w.n_vis / t_l, "wavelet_mixed_eq17_vis_per_s": w.n_vis / t_17,
+           "learned_max_rel_err_vs_exact_response_form": float(np.max(np.abs(got - v_exact_resp)) / S),
+           "rms_err_vs_true_learned": rms(got, v_true), "rms_err_vs_true_exact_response": rms(v_exact_resp, v_true),
+           "rms_err_vs_true_centre_snapped": rms(v_centre, v_true)}
+    tree.close()
+    mlp.close()
+    return res
+
+
 # ---------------------------------------------------------------- oracle (CPU)
 
 def _oracle_step_rate(w, J, n_sample):
@@ -469,8 +584,94 @@ def reference(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep(args):
+    """Run-time scaling as in Sec. 3.6.1: per-visibility time of the Eq. 17
+    predictor (both forms) against J on the medium workload and on a fixed
+    set of distinct components, against the number of distinct components at
+    fixed J, and the paper-context workload (27 antennas, 1 263 600
+    visibilities, J = 20, 15 and 140 distinct components) beside the paper's
+    own 146 s and 1000 s per major cycle on its unstated CPU."""
+    import torch
+
+    import paper_1909_03956_gb300 as wt
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wt.load()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+
+    def measure(w, J, forms=("mixed", "fp64")):
+        l, m, f, uvw = d(w.l), d(w.m), d(w.flux), d(w.uvw)
+        tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, J)
+        info = tree.info()
+        r = {"J": J, "n_leaves": info["n_leaves"], "n_nodes": info["n_nodes"]}
+        for name in forms:
+            mode = wt.WT_MIXED if name == "mixed" else wt.WT_FP64
+            out = torch.empty(w.n_vis, dtype=torch.complex64 if name == "mixed" else torch.complex128, device=dev)
+            wt.wt_predict_vis(tree, uvw, mode=mode, out=out)
+            t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, out=out), stream, flush,
+                           reps=3 if name == "mixed" else 1)
+            r[name + "_ns_per_vis"] = t / w.n_vis * 1e9
+        tree.close()
+        return r
+
+    res = {"kind": "scaling sweep (Sec. 3.6.1)", "unit": "ns per visibility, one GB300"}
+    med = synth.medium()
+    res["medium_J_sweep"] = [measure(med, J) for J in range(8, 15)]
+    fixed = {}
+    for nd in (10, 20, 40, 80, 140):
+        w = synth.medium_fixed(nd)
+        fixed[str(nd)] = [measure(w, J, forms=("mixed",)) for J in (12, 15, 20, 25)]
+    res["fixed_distinct_J_sweep"] = fixed
+    res["paper_context"] = []
+    for nd, paper_s in ((15, 146.0), (140, 1000.0)):
+        w = synth.paper_context(n_distinct=nd)
+        r = measure(w, 20)
+        r.update({"n_vis": w.n_vis, "n_distinct": nd, "paper_s_per_major_cycle": paper_s,
+                  "gpu_fp64_s_per_major_cycle": r["fp64_ns_per_vis"] * w.n_vis / 1e9,
+                  "gpu_mixed_s_per_major_cycle": r["mixed_ns_per_vis"] * w.n_vis / 1e9})
+        res["paper_context"].append(r)
+    print(json.dumps(res), flush=True)
+
+
+def forms_once(args):
+    import torch
+
+    import paper_1909_03956_gb300 as wt
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wt.load()
+    w = synth.medium(J=args.J)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    l, m, f, uvw = d(w.l), d(w.m), d(w.flux), d(w.uvw)
+    tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, w.J)
+    o64 = torch.empty(w.n_vis, dtype=torch.complex128, device=dev)
+    o32 = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+    sub = uvw[:131072].contiguous()
+    runs = [("wavelet_mixed", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o32)),
+            ("wavelet_fp64", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_FP64, out=o64)),
+            ("dft_mixed", lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=o32)),
+            ("dft_fp64_131072", lambda: wt.dft_predict_vis(l, m, f, sub, mode=wt.WT_FP64, out=o64[:131072])),
+            ("subtract_c64", lambda: wt.subtract_model(o32, o32, mode=wt.WT_MIXED, out=o32))]
+    for name, fn in runs:
+        fn()
+        torch.cuda.synchronize()
+        fn()
+        torch.cuda.synchronize()
+    wt.wt_device_status()
+    tree.close()
+    print("forms-once ok: " + ", ".join(n for n, _ in runs), flush=True)
+
+
 def main():
     args = parse()
+    if args.forms_once:
+        forms_once(args)
+        return
+    if args.sweep:
+        sweep(args)
+        return
     if args.impl == "reference":
         reference(args)
     else:

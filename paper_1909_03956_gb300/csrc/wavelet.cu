@@ -285,7 +285,7 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
 // Default when nothing is tuned: the widest variant whose stack fits.
 int default_wavelet_variant(int mode, int which, int J)
 {
-    static const int order_mixed[kNumWaveletVariants] = {2, 0, 1, 3, 4, 5, 6, 7};
+    static const int order_mixed[kNumWaveletVariants] = {0, 2, 1, 3, 4, 5, 6, 7};
     static const int order_fp64[kNumWaveletVariants] = {1, 0, 2, 3, 4, 5, 6, 7};
     const int* order = (mode == WT_FP64) ? order_fp64 : order_mixed;
     for (int i = 0; i < kNumWaveletVariants; ++i)

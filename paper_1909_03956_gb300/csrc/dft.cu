@@ -50,7 +50,6 @@ struct BodyD {
     __device__ void operator()(const CompD& c)
     {
         double t = fma(w, c.nm1, fma(v, c.m, u * c.l));
-        t -= rint(t);
         double s, co;
         sincos_turns_f64(t, s, co);
         vr = fma(c.flux, co, vr);

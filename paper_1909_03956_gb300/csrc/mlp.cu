@@ -119,7 +119,6 @@ __device__ double2 response_exact_one(double u, double v, double w, const double
     double re = 0.0, im = 0.0;
     for (int i = 0; i < n_off; ++i) {
         double t = fma(w, __ldg(&offs[3 * i + 2]), fma(v, __ldg(&offs[3 * i + 1]), u * __ldg(&offs[3 * i])));
-        t -= rint(t);
         double s, c;
         sincos_turns_f64(t, s, c);
         re += c;

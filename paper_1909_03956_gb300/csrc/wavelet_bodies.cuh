@@ -35,7 +35,6 @@ struct Eq17D {
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 double t = fma(w[k], r.c, fma(v[k], r.b, u[k] * r.a));
-                t -= rint(t);
                 double s, c;
                 sincos_turns_f64(t, s, c);
                 const double ei = s;
@@ -104,7 +103,6 @@ struct Eq16D {
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             double t = fma(w[k], r.c, fma(v[k], r.b, u[k] * r.a));
-            t -= rint(t);
             double s, c;
             sincos_turns_f64(t, s, c);
             vr[k] = fma(r.d, c, vr[k]);

@@ -114,36 +114,34 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-// Fractional part (in turns) of x * y, for x = xh + xl and y = yh + yl
-// double-floats: returns an exact integer-free head in [-1/2, 1/2] and a
-// small tail. The head is xh*yh reduced by its nearest integer (exact: both
-// operands share the float's ulp); the tail holds the rounding error of xh*yh
-// (exact via FMA) plus the cross terms xh*yl + xl*yh (xl*yl is below 2^-48 of
-// the product and dropped).
-__device__ __forceinline__ void frac_product(F2 x, F2 y, float& head, float& tail)
+// Product of two double-floats x = xh + xl, y = yh + yl as an unevaluated
+// sum p + t: p = fl(xh yh) and t = its exact rounding error (FMA) plus the
+// cross terms xh yl + xl yh (xl yl is below 2^-48 of the product: dropped).
+__device__ __forceinline__ void df_product(F2 x, F2 y, float& p, float& t)
 {
-    float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
-    head = __fsub_rn(p, rintf(p));
-    tail = __fadd_rn(e, c);
+    p = __fmul_rn(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.hi, -p);
+    const float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+    t = __fadd_rn(e, c);
 }
 
 // Phase in turns of B.(s - P) = u*su + v*sv + w*sw1 modulo 1, returned as
-// an unevaluated sum th + tl: th in [-1/2, 1/2], tl small (|tl| < 1e-2 for
-// products below 2^16 turns). Float64-accurate: the three heads are added
-// with error-free sums and their errors join the tails. Valid while each
-// product |x * y| stays below 2^22 turns.
+// an unevaluated sum th + tl with th in [-1/2, 1/2] and tl small.
+// Float64-accurate: the three head products are added with error-free sums
+// (exact for any operands), so only their total needs reducing by its
+// nearest integer (exact below 2^22 turns); all rounding errors, of size
+// ulp(head), join the tail, whose own rounding (~1e-11 turns for heads of
+// a thousand turns) is far below float32 resolution of th.
 __device__ __forceinline__ void phase_turns_df(F2 u, F2 v, F2 w, F2 su, F2 sv, F2 sw1, float& th, float& tl)
 {
-    float h1, t1, h2, t2, h3, t3;
-    frac_product(u, su, h1, t1);
-    frac_product(v, sv, h2, t2);
-    frac_product(w, sw1, h3, t3);
+    float p1, t1, p2, t2, p3, t3;
+    df_product(u, su, p1, t1);
+    df_product(v, sv, p2, t2);
+    df_product(w, sw1, p3, t3);
     float s, e1, s2, e2;
-    two_sum(h1, h2, s, e1);
-    two_sum(s, h3, s2, e2);
-    th = __fsub_rn(s2, rintf(s2));           // exact, back to [-1/2, 1/2]
+    two_sum(p1, p2, s, e1);
+    two_sum(s, p3, s2, e2);
+    th = __fsub_rn(s2, rintf(s2));           // exact
     tl = __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), __fadd_rn(t3, e1)), e2);
 }
 
@@ -179,14 +177,16 @@ __device__ __forceinline__ void sincos_turns_f32(float th, float tl, float& s, f
     c = ((qi + 1) & 2) ? -cc : cc;
 }
 
-// ---- float64 sin/cos of 2 pi t, |t| <= 1/2 (turns) --------------------------
+// ---- float64 sin/cos of 2 pi t (t in turns, |t| < 2^40) ---------------------
 // Table-driven reduction (the table-lookup method of P. T. P. Tang, ACM TOMS
 // 15(2), 1989): k = rint(256 t), f = t - k/256 (exact, |f| <= 1/512), and
-// exp(i 2 pi t) = exp(i 2 pi k/256) exp(i 2 pi f). The table holds the first
-// factor correctly rounded (gen_sincos_table.py); the second comes from the
-// Taylor series of sin (to x^7) and cos (to x^6) at x = 2 pi f, |x| <= 0.0123,
-// whose truncation errors (< 2e-20 and < 8e-21) are far below float64
-// rounding. About 18 float64 operations instead of a general sin/cos.
+// exp(i 2 pi t) = exp(i 2 pi (k mod 256)/256) exp(i 2 pi f). The table holds
+// the first factor correctly rounded (gen_sincos_table.py, entries for
+// k = -128 .. 128, of which 0 .. 255 modulo 256 are used); the second comes
+// from the Taylor series of sin (to x^7) and cos (to x^6) at x = 2 pi f,
+// |x| <= 0.0123, whose truncation errors (< 2e-20 and < 8e-21) are far below
+// float64 rounding. No separate reduction of t by its nearest integer is
+// needed: k mod 256 absorbs the whole turns.
 static __device__ const double2 kSinCos256[257] =
 #include "sincos_table.inc"
     ;
@@ -200,7 +200,9 @@ __device__ __forceinline__ void sincos_turns_f64(double t, double& s, double& c)
     const double ps = fma(x2, fma(x2, -1.9841269841269841e-4, 8.3333333333333333e-3), -1.6666666666666667e-1);
     const double sx = fma(x * x2, ps, x);
     const double pc = fma(x2, fma(x2, fma(x2, -1.3888888888888889e-3, 4.1666666666666667e-2), -0.5), 1.0);
-    const double2 tk = __ldg(&kSinCos256[static_cast<int>(k) + 128]);
+    // entry j of the table is k = j - 128; k mod 256 in 0 .. 255 -> j = 128 + (k mod 256) - 256 * (k mod 256 >= 128)
+    const int km = static_cast<int>(static_cast<long long>(k) & 255);
+    const double2 tk = __ldg(&kSinCos256[(km < 128) ? km + 128 : km - 128]);
     c = fma(tk.x, pc, -tk.y * sx);
     s = fma(tk.y, pc, tk.x * sx);
 }

@@ -359,6 +359,8 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
     r["build_tree_ms"] = t * 1e3
     for name, mode, which, out in [("wavelet_fp64_eq17", wt.WT_FP64, wt.WT_SUM_EQ17, out64),
                                    ("wavelet_mixed_eq17", wt.WT_MIXED, wt.WT_SUM_EQ17, out32),
+                                   ("wavelet_fp64_eq17_regrouped", wt.WT_FP64, wt.WT_SUM_EQ17_REGROUPED, out64),
+                                   ("wavelet_mixed_eq17_regrouped", wt.WT_MIXED, wt.WT_SUM_EQ17_REGROUPED, out32),
                                    ("wavelet_fp64_eq16", wt.WT_FP64, wt.WT_SUM_EQ16, out64),
                                    ("wavelet_mixed_eq16", wt.WT_MIXED, wt.WT_SUM_EQ16, out32)]:
         t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out), stream, flush)

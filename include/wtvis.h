@@ -71,8 +71,14 @@ typedef enum {
 } wt_mode;
 
 typedef enum {
-    WT_SUM_EQ17 = 0, /* multiresolution sum over all tree nodes (Eq. 17) */
-    WT_SUM_EQ16 = 1  /* level-J sum over the leaves only (Eq. 16) */
+    WT_SUM_EQ17 = 0,          /* multiresolution sum over all tree nodes (Eq. 17):
+                                 per node eta and sigma^m formed, gamma^m sigma^m added */
+    WT_SUM_EQ16 = 1,          /* level-J sum over the leaves only (Eq. 16) */
+    WT_SUM_EQ17_REGROUPED = 2 /* Eq. 17 with each node's sum_m gamma^m sigma^m
+                                 distributed over its children: per node a weight
+                                 w = (sqrt(A_j)/4) sum_m H_m[c] gamma^m_parent, fixed per
+                                 major cycle, and V = sum_n w_n eta_n (same terms,
+                                 regrouped; the eta recursion is unchanged) */
 } wt_sum;
 
 /* ---------------------------------------------------------------------------
@@ -133,7 +139,8 @@ void wt_free_tree(wt_tree t);
  *   3. the multiresolution sum (Eq. 17 with the area factor of level 1):
  *      V = A_1 sum_k lambda_1,k eta_1,k + sum_j sum_k sum_m gamma^m sigma^m.
  * With which = WT_SUM_EQ16 the level-J sum V = sum_k Phi_k eta_J,k (Eq. 16)
- * is evaluated instead; the two agree up to rounding.
+ * is evaluated instead, and with WT_SUM_EQ17_REGROUPED the regrouped Eq. 17
+ * (see wt_sum); all three agree up to rounding.
  *
  *   t        a built tree (the build must precede this call in stream order)
  *   uvw      device float64 [n_vis][3], wavelengths

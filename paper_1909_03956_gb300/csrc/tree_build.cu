@@ -403,6 +403,45 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         }
         d.recd[post] = rd;
         d.recf[post] = rf;
+        // regrouped Eq. 17: the node's weight from its parent's gammas
+        double wgt;
+        bool first = true;
+        if (j == 1) {
+            wgt = A1 * d.lambda[n];
+        } else {
+            const int64_t P = h->rev_offset[j - 1] + d.parent[n];
+            const double g0 = d.gamma[3 * P], g1 = d.gamma[3 * P + 1], g2 = d.gamma[3 * P + 2];
+            const double h0 = (slot & 1u) ? -1.0 : 1.0;                          // + - + -
+            const double h1 = (slot & 2u) ? -1.0 : 1.0;                          // + + - -
+            const double h2 = (((slot & 1u) ^ ((slot >> 1) & 1u)) != 0u) ? -1.0 : 1.0;   // + - - +
+            wgt = quarter_sqrt_area(j - 1) * ((h0 * g0 + h1 * g1) + h2 * g2);
+            const uint32_t pmask = d.mask[P];
+            first = slot == static_cast<uint32_t>(__ffs(pmask) - 1);
+        }
+        const uint32_t wmeta = static_cast<uint32_t>(j) | (leaf ? kRwLeaf : 0u) | (j == 1 ? kRwRoot : 0u) |
+                               (first ? kRwFirst : 0u);
+        RecWD wd;
+        RecWF wf;
+        wd.meta = wmeta;
+        wd.pad = 0;
+        wd.a = rd.a;
+        wd.b = rd.b;
+        wd.c = rd.c;
+        wd.d = wgt;
+        wd.e = 0.0;
+        wf.meta = wmeta;
+        wf.a = leaf ? rf.a : 0.f;
+        wf.b = leaf ? rf.b : 0.f;
+        wf.c = leaf ? rf.c : 0.f;
+        wf.d = leaf ? rf.d : 0.f;
+        wf.e = leaf ? rf.e : 0.f;
+        wf.f = leaf ? rf.f : 0.f;
+        wf.g = static_cast<float>(wgt);
+        if (!leaf) {
+            wd.a = wd.b = wd.c = 0.0;
+        }
+        d.recwd[post] = wd;
+        d.recwf[post] = wf;
     }
 }
 
@@ -421,7 +460,8 @@ int64_t carve_bytes(int64_t cap_nodes, int64_t cap_leaves)
     return b(cap_nodes * 8) + b(cap_nodes * 8) + b(cap_nodes * 24) + b(cap_nodes * 4) + b(cap_nodes) +
            4 * b(cap_nodes * 4) + b(cap_leaves * 24) + b(cap_leaves * 8) + b(cap_leaves * 8) +
            b(cap_leaves * 4) + b(cap_nodes * int64_t(sizeof(RecD))) + b(cap_nodes * int64_t(sizeof(RecF))) +
-           b(cap_leaves * int64_t(sizeof(RecD))) + b(cap_leaves * int64_t(sizeof(RecF))) + b(sizeof(TreeHeader));
+           b(cap_leaves * int64_t(sizeof(RecD))) + b(cap_leaves * int64_t(sizeof(RecF))) +
+           b(cap_nodes * int64_t(sizeof(RecWD))) + b(cap_nodes * int64_t(sizeof(RecWF))) + b(sizeof(TreeHeader));
 }
 
 }  // namespace
@@ -500,6 +540,8 @@ int build_tree(const double* l, const double* m, const double* flux, int64_t n_c
     d.recf = carve<RecF>(p, cap1);
     d.leafd = carve<RecD>(p, capl);
     d.leaff = carve<RecF>(p, capl);
+    d.recwd = carve<RecWD>(p, cap1);
+    d.recwf = carve<RecWF>(p, cap1);
     d.hdr = carve<TreeHeader>(p, 1);
 
     char* q = scratch;

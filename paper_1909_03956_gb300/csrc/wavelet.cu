@@ -34,16 +34,19 @@ namespace wt {
 namespace {
 
 // ---------------------------------------------------------------- kernels
-template <int NT, int VPT, bool EQ16>
-__global__ void __launch_bounds__(NT) k_wavelet_fp64(const RecD* __restrict__ recs, const TreeHeader* __restrict__ hdr,
+// SUM: 0 = Eq. 17 with explicit sigma (RecD / RecF), 1 = Eq. 16 over the
+// leaf records, 2 = regrouped Eq. 17 (RecWD / RecWF).
+template <int NT, int VPT, int SUM, class Rec>
+__global__ void __launch_bounds__(NT) k_wavelet_fp64(const Rec* __restrict__ recs, const TreeHeader* __restrict__ hdr,
                                                      const double* __restrict__ uvw, int64_t n_vis,
-                                                     double2* __restrict__ vis, double sgn, int rows, int* status)
+                                                     double2* __restrict__ vis, double sgn, int rows, int J,
+                                                     int* status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    Stager<RecD> st;
-    const int64_t count = EQ16 ? hdr->n_leaves : hdr->n_nodes;
+    Stager<Rec> st;
+    const int64_t count = (SUM == 1) ? hdr->n_leaves : hdr->n_nodes;
     stager_setup(st, smem, recs, count, kChunkD);
-    double2* stk = reinterpret_cast<double2*>(smem + stager_bytes<RecD>(kChunkD)) + threadIdx.x;
+    double2* stk = reinterpret_cast<double2*>(smem + stager_bytes<Rec>(kChunkD)) + threadIdx.x;
     const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const RecD* __restrict__ re
         }
         bool good;
         double vr[VPT], vi[VPT];
-        if (EQ16) {
+        if constexpr (SUM == 1) {
             Eq16D<VPT> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const RecD* __restrict__ re
             good = st.sweep(b);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k]; vi[k] = b.vi[k]; }
-        } else {
+        } else if constexpr (SUM == 0) {
             Eq17D<NT, VPT> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -77,6 +80,19 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const RecD* __restrict__ re
             }
             b.sgn = sgn;
             b.stk = stk;
+            b.maxrow = rows - 1;
+            good = st.sweep(b);
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k]; vi[k] = b.vi[k]; }
+        } else {
+            Eq17WD<NT, VPT> b;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k]; b.vr[k] = 0.0; b.vi[k] = 0.0;
+                b.sr[k] = 0.0; b.si[k] = 0.0; b.xr[k] = 0.0; b.xi[k] = 0.0;
+            }
+            b.stk = stk;
+            b.J = J;
             b.maxrow = rows - 1;
             good = st.sweep(b);
 #pragma unroll
@@ -94,16 +110,17 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const RecD* __restrict__ re
     }
 }
 
-template <int NT, int VPT, bool EQ16>
-__global__ void __launch_bounds__(NT) k_wavelet_mixed(const RecF* __restrict__ recs, const TreeHeader* __restrict__ hdr,
+template <int NT, int VPT, int SUM, class Rec>
+__global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ recs, const TreeHeader* __restrict__ hdr,
                                                       const double* __restrict__ uvw, int64_t n_vis,
-                                                      float2* __restrict__ vis, float sgn, int rows, int* status)
+                                                      float2* __restrict__ vis, float sgn, int rows, int J,
+                                                      int* status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    Stager<RecF> st;
-    const int64_t count = EQ16 ? hdr->n_leaves : hdr->n_nodes;
+    Stager<Rec> st;
+    const int64_t count = (SUM == 1) ? hdr->n_leaves : hdr->n_nodes;
     stager_setup(st, smem, recs, count, kChunkF);
-    float2* stk = reinterpret_cast<float2*>(smem + stager_bytes<RecF>(kChunkF)) + threadIdx.x;
+    float2* stk = reinterpret_cast<float2*>(smem + stager_bytes<Rec>(kChunkF)) + threadIdx.x;
     const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -120,7 +137,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const RecF* __restrict__ r
         }
         bool good;
         float vr[VPT], vi[VPT];
-        if (EQ16) {
+        if constexpr (SUM == 1) {
             Eq16F<VPT> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -131,7 +148,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const RecF* __restrict__ r
             good = st.sweep(b);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
-        } else {
+        } else if constexpr (SUM == 0) {
             Eq17F<NT, VPT> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -140,6 +157,20 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const RecF* __restrict__ r
             }
             b.sgn = sgn;
             b.stk = stk;
+            b.maxrow = rows - 1;
+            good = st.sweep(b);
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
+        } else {
+            Eq17WF<NT, VPT> b;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
+                b.vr[k] = 0.f; b.vi[k] = 0.f; b.cr[k] = 0.f; b.ci[k] = 0.f;
+                b.sr[k] = 0.f; b.si[k] = 0.f; b.xr[k] = 0.f; b.xi[k] = 0.f;
+            }
+            b.stk = stk;
+            b.J = J;
             b.maxrow = rows - 1;
             good = st.sweep(b);
 #pragma unroll
@@ -176,27 +207,36 @@ int prepare(K kernel, int nt, size_t smem, int64_t per_tile, int64_t n_vis, dim3
     return WT_OK;
 }
 
-int rows_of(int J) { return J > 1 ? 4 * (J - 1) : 4; }
+// Shared-memory stack rows a form needs for a tree of depth J.
+int stack_rows(int which, int J)
+{
+    if (which == WT_SUM_EQ16) return 0;
+    if (which == WT_SUM_EQ17_REGROUPED) return J > 3 ? 2 * (J - 2) : 2;
+    return J > 1 ? 4 * (J - 1) : 4;
+}
 
 template <int NT, int VPT>
 int run_fp64(const WaveletJob& jb, cudaStream_t s)
 {
-    const bool eq16 = jb.which == WT_SUM_EQ16;
-    const int rows = rows_of(jb.J);
-    const size_t stack = eq16 ? 0 : static_cast<size_t>(rows) * VPT * NT * sizeof(double2);
+    const int rows = stack_rows(jb.which, jb.J);
+    const size_t stack = static_cast<size_t>(rows) * VPT * NT * sizeof(double2);
     const size_t smem = static_cast<size_t>(stager_bytes<RecD>(kChunkD)) + stack;
     dim3 grid;
     int rc;
-    if (eq16) {
-        auto k = k_wavelet_fp64<NT, VPT, true>;
+    double2* out = static_cast<double2*>(jb.vis);
+    const double sg = jb.sign;
+    if (jb.which == WT_SUM_EQ16) {
+        auto k = k_wavelet_fp64<NT, VPT, 1, RecD>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recd_leaf, jb.hdr, jb.uvw, jb.n_vis, static_cast<double2*>(jb.vis), jb.sign, rows,
-                                 jb.status);
+        k<<<grid, NT, smem, s>>>(jb.recd_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+    } else if (jb.which == WT_SUM_EQ17) {
+        auto k = k_wavelet_fp64<NT, VPT, 0, RecD>;
+        if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
+        k<<<grid, NT, smem, s>>>(jb.recd, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else {
-        auto k = k_wavelet_fp64<NT, VPT, false>;
+        auto k = k_wavelet_fp64<NT, VPT, 2, RecWD>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recd, jb.hdr, jb.uvw, jb.n_vis, static_cast<double2*>(jb.vis), jb.sign, rows,
-                                 jb.status);
+        k<<<grid, NT, smem, s>>>(jb.recwd, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     }
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
@@ -205,22 +245,25 @@ int run_fp64(const WaveletJob& jb, cudaStream_t s)
 template <int NT, int VPT>
 int run_mixed(const WaveletJob& jb, cudaStream_t s)
 {
-    const bool eq16 = jb.which == WT_SUM_EQ16;
-    const int rows = rows_of(jb.J);
-    const size_t stack = eq16 ? 0 : static_cast<size_t>(rows) * VPT * NT * sizeof(float2);
+    const int rows = stack_rows(jb.which, jb.J);
+    const size_t stack = static_cast<size_t>(rows) * VPT * NT * sizeof(float2);
     const size_t smem = static_cast<size_t>(stager_bytes<RecF>(kChunkF)) + stack;
     dim3 grid;
     int rc;
-    if (eq16) {
-        auto k = k_wavelet_mixed<NT, VPT, true>;
+    float2* out = static_cast<float2*>(jb.vis);
+    const float sg = static_cast<float>(jb.sign);
+    if (jb.which == WT_SUM_EQ16) {
+        auto k = k_wavelet_mixed<NT, VPT, 1, RecF>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, static_cast<float2*>(jb.vis),
-                                 static_cast<float>(jb.sign), rows, jb.status);
+        k<<<grid, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+    } else if (jb.which == WT_SUM_EQ17) {
+        auto k = k_wavelet_mixed<NT, VPT, 0, RecF>;
+        if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
+        k<<<grid, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else {
-        auto k = k_wavelet_mixed<NT, VPT, false>;
+        auto k = k_wavelet_mixed<NT, VPT, 2, RecWF>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, static_cast<float2*>(jb.vis),
-                                 static_cast<float>(jb.sign), rows, jb.status);
+        k<<<grid, NT, smem, s>>>(jb.recwf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     }
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
@@ -250,7 +293,7 @@ bool wavelet_variant_fits(int v, int mode, int which, int J)
     if (v < 0 || v >= kNumWaveletVariants) return false;
     const size_t cplx = (mode == WT_FP64) ? sizeof(double2) : sizeof(float2);
     const size_t stage = (mode == WT_FP64) ? stager_bytes<RecD>(kChunkD) : stager_bytes<RecF>(kChunkF);
-    const size_t stack = (which == WT_SUM_EQ16) ? 0 : static_cast<size_t>(rows_of(J)) * kVariants[v].nt * kVariants[v].vpt * cplx;
+    const size_t stack = static_cast<size_t>(stack_rows(which, J)) * kVariants[v].nt * kVariants[v].vpt * cplx;
     return stage + stack <= 220 * 1024;
 }
 
@@ -302,6 +345,8 @@ int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int 
     jb.recf = t->d.recf;
     jb.recd_leaf = t->d.leafd;
     jb.recf_leaf = t->d.leaff;
+    jb.recwd = t->d.recwd;
+    jb.recwf = t->d.recwf;
     jb.hdr = t->d.hdr;
     jb.uvw = uvw;
     jb.n_vis = n_vis;

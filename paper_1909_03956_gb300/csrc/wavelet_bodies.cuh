@@ -213,5 +213,157 @@ struct Eq16F {
     }
 };
 
+// ---------------------------------------------------------------- regrouped Eq. 17
+// V = sum_n w_n eta_n (see RecWD in wt_internal.cuh). Per level j = 1 .. J-2
+// a thread keeps two accumulators of the open level-j node in shared memory
+// (row 2(j-1): sum of its children's eta; row 2(j-1)+1: sum of w_c eta_c);
+// those of the open level-(J-1) node live in registers, so a leaf never
+// touches shared memory. A node reads its own accumulators, forms
+// eta = (1/4) sum (the Eq. 9 form), adds the children's weighted sum to V
+// and passes eta and w eta up to its parent (the first child writes, the
+// others add).
+template <int NT, int VPT>
+struct Eq17WD {
+    double u[VPT], v[VPT], w[VPT];
+    double vr[VPT], vi[VPT];
+    double sr[VPT], si[VPT], xr[VPT], xi[VPT];
+    double2* stk;   // shared stack + threadIdx.x; row stride VPT * NT
+    int J;
+    int maxrow;
+
+    __device__ __forceinline__ double2& slot(int row, int k) { return stk[(row * VPT + k) * NT]; }
+
+    __device__ void operator()(const RecWD& r)
+    {
+        const uint32_t meta = r.meta;
+        const int lev = static_cast<int>(meta & 31u);
+        const bool root = meta & kRwRoot, first = meta & kRwFirst;
+        if (meta & kRwLeaf) {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const double t = fma(w[k], r.c, fma(v[k], r.b, u[k] * r.a));
+                double s, c;
+                sincos_turns_f64(t, s, c);
+                if (root) {
+                    vr[k] = fma(r.d, c, vr[k]);
+                    vi[k] = fma(r.d, s, vi[k]);
+                } else if (first) {
+                    sr[k] = c;
+                    si[k] = s;
+                    xr[k] = r.d * c;
+                    xi[k] = r.d * s;
+                } else {
+                    sr[k] += c;
+                    si[k] += s;
+                    xr[k] = fma(r.d, c, xr[k]);
+                    xi[k] = fma(r.d, s, xi[k]);
+                }
+            }
+            return;
+        }
+        const bool in_regs = (lev == J - 1);
+        const int own = clamp_row(static_cast<uint32_t>(2 * (lev - 1)), maxrow - 1);
+        const int par = clamp_row(static_cast<uint32_t>(2 * (lev > 1 ? lev - 2 : 0)), maxrow - 1);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            double2 S, X;
+            if (in_regs) {
+                S = make_double2(sr[k], si[k]);
+                X = make_double2(xr[k], xi[k]);
+            } else {
+                S = slot(own, k);
+                X = slot(own + 1, k);
+            }
+            const double er = 0.25 * S.x, ei = 0.25 * S.y;   // Eq. 9 form
+            vr[k] += X.x;
+            vi[k] += X.y;
+            if (root) {
+                vr[k] = fma(r.d, er, vr[k]);
+                vi[k] = fma(r.d, ei, vi[k]);
+            } else if (first) {
+                slot(par, k) = make_double2(er, ei);
+                slot(par + 1, k) = make_double2(r.d * er, r.d * ei);
+            } else {
+                double2& ps = slot(par, k);
+                double2& px = slot(par + 1, k);
+                ps = make_double2(ps.x + er, ps.y + ei);
+                px = make_double2(fma(r.d, er, px.x), fma(r.d, ei, px.y));
+            }
+        }
+    }
+};
+
+template <int NT, int VPT>
+struct Eq17WF {
+    F2 u[VPT], v[VPT], w[VPT];
+    float vr[VPT], vi[VPT], cr[VPT], ci[VPT];   // Kahan sums and compensations
+    float sr[VPT], si[VPT], xr[VPT], xi[VPT];
+    float2* stk;
+    int J;
+    int maxrow;
+
+    __device__ __forceinline__ float2& slot(int row, int k) { return stk[(row * VPT + k) * NT]; }
+
+    __device__ void operator()(const RecWF& r)
+    {
+        const uint32_t meta = r.meta;
+        const int lev = static_cast<int>(meta & 31u);
+        const bool root = meta & kRwRoot, first = meta & kRwFirst;
+        if (meta & kRwLeaf) {
+            const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                float th, tl, s, c;
+                phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
+                sincos_turns_f32(th, tl, s, c);
+                if (root) {
+                    kahan_add(vr[k], cr[k], r.g * c);
+                    kahan_add(vi[k], ci[k], r.g * s);
+                } else if (first) {
+                    sr[k] = c;
+                    si[k] = s;
+                    xr[k] = r.g * c;
+                    xi[k] = r.g * s;
+                } else {
+                    sr[k] += c;
+                    si[k] += s;
+                    xr[k] = fmaf(r.g, c, xr[k]);
+                    xi[k] = fmaf(r.g, s, xi[k]);
+                }
+            }
+            return;
+        }
+        const bool in_regs = (lev == J - 1);
+        const int own = clamp_row(static_cast<uint32_t>(2 * (lev - 1)), maxrow - 1);
+        const int par = clamp_row(static_cast<uint32_t>(2 * (lev > 1 ? lev - 2 : 0)), maxrow - 1);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            float2 S, X;
+            if (in_regs) {
+                S = make_float2(sr[k], si[k]);
+                X = make_float2(xr[k], xi[k]);
+            } else {
+                S = slot(own, k);
+                X = slot(own + 1, k);
+            }
+            const float er = 0.25f * S.x, ei = 0.25f * S.y;
+            kahan_add(vr[k], cr[k], X.x);
+            kahan_add(vi[k], ci[k], X.y);
+            if (root) {
+                kahan_add(vr[k], cr[k], r.g * er);
+                kahan_add(vi[k], ci[k], r.g * ei);
+            } else if (first) {
+                slot(par, k) = make_float2(er, ei);
+                slot(par + 1, k) = make_float2(r.g * er, r.g * ei);
+            } else {
+                float2& ps = slot(par, k);
+                float2& px = slot(par + 1, k);
+                ps = make_float2(ps.x + er, ps.y + ei);
+                px = make_float2(fmaf(r.g, er, px.x), fmaf(r.g, ei, px.y));
+            }
+        }
+    }
+};
+
 }  // namespace
 }  // namespace wt

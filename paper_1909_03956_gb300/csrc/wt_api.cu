@@ -282,7 +282,8 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out, i
     if (rc) return rc;
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
     if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
-    if (which != WT_SUM_EQ17 && which != WT_SUM_EQ16) return set_error(WT_ERR_ARG, "%s: bad sum selector", fn);
+    if (which != WT_SUM_EQ17 && which != WT_SUM_EQ16 && which != WT_SUM_EQ17_REGROUPED)
+        return set_error(WT_ERR_ARG, "%s: bad sum selector", fn);
     if (mode == WT_LEARNED)
         return set_error(WT_ERR_UNSUPPORTED, "%s: the learned response has its own entry point", fn);
     if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);

@@ -260,6 +260,34 @@ struct RecF {
 };
 static_assert(sizeof(RecF) == 32, "RecF layout");
 
+// Records of the regrouped Eq. 17 (WT_SUM_EQ17_REGROUPED). Per node n one
+// weight w_n: for a node in child slot c of parent p at level j,
+// w_n = q_j sum_m H_m[c] gamma^m_p (q_j = sqrt(A_j)/4, H the Eq. 10 sign
+// rows), and w_n = A_1 lambda_1 at level 1; then, per visibility,
+// V = sum_n w_n eta_n, the same sum as Eq. 17 with each node's
+// sum_m gamma^m sigma^m distributed over its children
+// (gamma^T (H eta) = (H^T gamma)^T eta). meta bits: 0-4 level, 5 leaf,
+// 6 level 1, 7 first child of its parent (in post-order).
+constexpr uint32_t kRwLeaf = 1u << 5;
+constexpr uint32_t kRwRoot = 1u << 6;
+constexpr uint32_t kRwFirst = 1u << 7;
+
+// float64 (48 bytes): a, b, c = leaf pixel centre (s_u, s_v, s_w - 1); d = w.
+struct RecWD {
+    uint32_t meta;
+    uint32_t pad;
+    double a, b, c, d, e;
+};
+static_assert(sizeof(RecWD) == 48, "RecWD layout");
+
+// mixed (32 bytes): (a, b), (c, d), (e, f) = leaf pixel centre as
+// double-float pairs; g = w.
+struct RecWF {
+    uint32_t meta;
+    float a, b, c, d, e, f, g;
+};
+static_assert(sizeof(RecWF) == 32, "RecWF layout");
+
 // Device-side header of a tree (written by the build kernels).
 struct TreeHeader {
     int64_t n_leaves;
@@ -287,6 +315,8 @@ struct TreeDev {
     RecF* recf;
     RecD* leafd;          // leaf records in key order [n_leaves cap] (Eq. 16)
     RecF* leaff;
+    RecWD* recwd;         // post-order records of the regrouped Eq. 17 [cap]
+    RecWF* recwf;
     TreeHeader* hdr;
 };
 
@@ -317,6 +347,8 @@ struct WaveletJob {
     const RecF* recf;
     const RecD* recd_leaf;   // leaf records (Eq. 16)
     const RecF* recf_leaf;
+    const RecWD* recwd;      // regrouped Eq. 17
+    const RecWF* recwf;
     const TreeHeader* hdr;
     const double* uvw;
     int64_t n_vis;

@@ -293,3 +293,35 @@ def test_wavelet_every_launch_shape(variant, mode, tol, monkeypatch):
     uvw = w.uvw[::7][:1111]
     assert _wavelet_case(w, 13, uvw, mode) <= tol
     assert _wavelet_case(w, 13, uvw, mode, which=wt.WT_SUM_EQ16) <= tol
+    assert _wavelet_case(w, 13, uvw, mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
+
+
+# ---------------------------------------------------------------- regrouped Eq. 17
+
+@pytest.mark.parametrize("J", [1, 2, 3, 8, 12, 20])
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_wavelet_regrouped_small(J, mode, tol):
+    # V = sum_n w_n eta_n with w from the parents' gammas: the same terms as
+    # Eq. 17, judged against the oracle's literal Eq. 17.
+    w = synth.small()
+    assert _wavelet_case(w, J, w.uvw[::3], mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
+
+
+@pytest.mark.parametrize("J", [10, 14])
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+def test_wavelet_regrouped_medium_and_sign(J, mode, tol):
+    w = synth.medium(n_t=6)
+    assert _wavelet_case(w, J, w.uvw[::3], mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
+    assert _wavelet_case(w, J, w.uvw[:999], mode, which=wt.WT_SUM_EQ17_REGROUPED, sign=-1) <= tol
+
+
+def test_wavelet_regrouped_deep_and_mixed_sign():
+    w = synth.medium_fixed(40, n_t=4)
+    for J in (16, 25):
+        assert _wavelet_case(w, J, w.uvw[::4], wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED) <= TOL64
+        assert _wavelet_case(w, J, w.uvw[::4], wt.WT_MIXED, which=wt.WT_SUM_EQ17_REGROUPED) <= TOLMIX
+    rng = np.random.default_rng(31)
+    s = synth.small()
+    f = s.flux * np.where(rng.random(len(s.flux)) < 0.5, -1.0, 1.0)
+    w2 = synth.Workload("mixed-sign", s.uvw, s.l, s.m, f, 11)
+    assert _wavelet_case(w2, 11, s.uvw[::5], wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED) <= TOL64

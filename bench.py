@@ -119,6 +119,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    whole job's time)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def rank_workload_seed(rank):
+    """Each rank predicts its own batch (weak scaling): the medium workload
+    drawn with a rank-specific seed."""
+    return 1910 + rank
+
+
 # ---------------------------------------------------------------- native
 
 def native(args):
@@ -137,7 +154,7 @@ def native(args):
     wt.load()
 
     J = args.J
-    w = synth.medium(seed=1910 + rank, J=J)
+    w = synth.medium(seed=rank_workload_seed(rank), J=J)
     n_vis = w.n_vis
     S = float(np.abs(w.flux).sum())
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
@@ -196,9 +213,7 @@ def native(args):
     t_step = statistics.mean(times)
     t_pred = statistics.mean(pred_times)
     if world > 1:
-        tt = torch.tensor([t_step, t_pred], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_pred = float(tt[0]), float(tt[1])
+        t_step, t_pred = max_over_ranks([t_step, t_pred], dist, dev)
 
     # accuracy of the chosen form against the FP64 oracle on a strided sample
     err = None
@@ -239,9 +254,7 @@ def native(args):
             e2e_times.append(e0.elapsed_time(e1) / 1e3)
     t_e2e = statistics.mean(e2e_times)
     if world > 1:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt[0])
+        (t_e2e,) = max_over_ranks([t_e2e], dist, dev)
     h2d = sum(x.numel() * x.element_size() for x in (hl, hm, hf, huvw, hobs))
     d2h = hres.numel() * hres.element_size()
 

@@ -289,6 +289,13 @@ int wt_recommended_J(double dtheta_rad);
  * synchronising `stream`: WT_OK, or the first error a kernel recorded. */
 int wt_device_status(void* stream);
 
+/* Failure-detection self-test: a one-CTA kernel waits, with at most
+ * spin_limit (1..65536) polls, on an mbarrier phase that never completes, gives
+ * up and records WT_ERR_TIMEOUT in the device status word -- the path every
+ * bounded wait of the library takes when a copy does not arrive. The kernel
+ * returns normally; read the outcome with wt_device_status(). */
+int wt_selftest_bounded_wait(uint32_t spin_limit, void* stream);
+
 /* Text of the calling thread's last error (never NULL). */
 const char* wt_last_error(void);
 

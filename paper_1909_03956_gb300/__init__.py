@@ -40,6 +40,7 @@ EXPORTS = [
     "dft_predict_vis_noalloc", "wt_predict_vis_batched",
     "wt_mlp_create", "wt_mlp_free", "wt_mlp_get_params", "wt_mlp_set_params", "wt_response_exact",
     "wt_mlp_loss_grad", "wt_mlp_train", "wt_mlp_eval", "wt_predict_vis_learned",
+    "wt_selftest_bounded_wait",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -95,6 +96,7 @@ def _declare(L):
     L.wt_predict_vis_learned.argtypes = [vp, vp, vp, i64, vp, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
     L.wt_device_status.argtypes = [vp]
+    L.wt_selftest_bounded_wait.argtypes = [C.c_uint32, vp]
     L.wt_last_error.restype = C.c_char_p
 
 
@@ -330,6 +332,12 @@ def wt_recommended_J(dtheta_rad):
 
 def wt_device_status(stream=None):
     return _check(load().wt_device_status(_stream(stream)))
+
+
+def wt_selftest_bounded_wait(spin_limit=1000, stream=None):
+    """Run the bounded-wait self-test kernel; the timeout shows up in
+    wt_device_status() as WT_ERR_TIMEOUT."""
+    return _check(load().wt_selftest_bounded_wait(int(spin_limit), _stream(stream)))
 
 
 def wt_last_error():

@@ -355,3 +355,35 @@ int wt_device_status(void* stream)
 const char* wt_last_error(void) { return g_msg; }
 
 }  // extern "C"
+
+namespace wt {
+// One CTA waits on an mbarrier whose phase never completes (nothing arrives
+// on it), with `limit` polls: the wait must give up and report
+// WT_ERR_TIMEOUT through the status word, and the kernel return normally.
+__global__ void k_selftest_bounded_wait(uint32_t limit, int* status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        wt::mbar_init(&bar, 1);
+        wt::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = wt::mbar_wait_parity(&bar, 0, limit);
+    if (!__syncthreads_and(ok ? 1 : 0) && threadIdx.x == 0) wt::record_status(status, WT_ERR_TIMEOUT);
+}
+}  // namespace wt
+
+extern "C" {
+
+int wt_selftest_bounded_wait(uint32_t spin_limit, void* stream)
+{
+    if (spin_limit == 0 || spin_limit > (1u << 16))
+        return set_error(WT_ERR_ARG, "wt_selftest_bounded_wait: spin_limit must be in 1..65536");
+    int* w = device_status_word();
+    if (!w) return set_error(WT_ERR_CUDA, "wt_selftest_bounded_wait: no usable CUDA device");
+    wt::k_selftest_bounded_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(spin_limit, w);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+}  // extern "C"

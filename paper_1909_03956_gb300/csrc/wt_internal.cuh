@@ -17,9 +17,11 @@ namespace wt {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxJ = 30;
 
-// Upper bound on the spins of any bounded wait (mbarrier parity waits).
-// A healthy wait finishes in microseconds; this limit is seconds.
-constexpr uint32_t kSpinLimit = 1u << 26;
+// Upper bound on the polls of any bounded wait (mbarrier parity waits).
+// A healthy wait finishes in microseconds; each failed poll may suspend the
+// thread for a short hardware time slice, so this limit is of the order of
+// a second.
+constexpr uint32_t kSpinLimit = 1u << 20;
 
 // ---------------------------------------------------------------- host side
 // Thread-local error message + status helpers (wt_api.cu).
@@ -62,11 +64,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Returns true once the phase with parity `parity` has completed; false if
-// the bounded number of polls ran out.
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
+// `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit)
 {
     const uint32_t a = smem_addr(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -325,3 +325,18 @@ def test_wavelet_regrouped_deep_and_mixed_sign():
     f = s.flux * np.where(rng.random(len(s.flux)) < 0.5, -1.0, 1.0)
     w2 = synth.Workload("mixed-sign", s.uvw, s.l, s.m, f, 11)
     assert _wavelet_case(w2, 11, s.uvw[::5], wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED) <= TOL64
+
+
+# ---------------------------------------------------------------- failure detection
+
+def test_bounded_wait_times_out_and_reports():
+    # A wait on a phase nothing completes gives up after its poll limit and
+    # reports WT_ERR_TIMEOUT; the context stays usable afterwards.
+    wt.wt_device_status()
+    wt.wt_selftest_bounded_wait(500)
+    with pytest.raises(wt.WtError) as e:
+        wt.wt_device_status()
+    assert e.value.status == wt.WT_ERR_TIMEOUT
+    wt.wt_device_status()                     # cleared
+    w = synth.small()
+    assert _dft_case(w, w.uvw[:100], wt.WT_FP64) <= TOL64

@@ -344,6 +344,8 @@ OPS_NODE = 38
 # DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
 # from ncu (dram__bytes_read.sum 24 265 472 + dram__bytes_write.sum 0).
 TRAFFIC_BYTES_MEDIUM_J12 = 24265472
+# Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
+HBM_PEAK_GBPS = 6690.1
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
@@ -385,6 +387,15 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
     r["dft_terms"] = w.n_comp
     t = _time_call(lambda: wt.subtract_model(out32, out32, mode=wt.WT_MIXED, out=out32), stream, flush)
     r["subtract_c64_GBps"] = 24 * n / t / 1e9
+    # the subtraction at a size where HBM, not the launch, sets the time:
+    # 64 Mi complex64 visibilities, 1.5 GiB moved per call (two reads, one write)
+    big = 64 * 1024 * 1024
+    a = torch.zeros(big, dtype=torch.complex64, device=uvw.device)
+    b = torch.zeros_like(a)
+    t = _time_call(lambda: wt.subtract_model(a, b, mode=wt.WT_MIXED, out=a), stream, flush)
+    r["subtract_c64_64Mi_GBps"] = 24 * big / t / 1e9
+    r["subtract_c64_64Mi_frac_of_hbm"] = 24 * big / t / 1e9 / HBM_PEAK_GBPS
+    del a, b
     return {"forms": r}
 
 

@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--J", type=int, default=MEDIUM_J)
+    p.add_argument("--form", default="fast", choices=["fast", "mixed"],
+                   help="chosen form of the step: WT_MIXED_FAST (default) or WT_MIXED")
     p.add_argument("--no-extras", action="store_true", help="skip the per-form side measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--forms-once", action="store_true",
@@ -165,7 +167,7 @@ def native(args):
     resid = torch.empty_like(model)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    mode = wt.WT_MIXED
+    mode = wt.WT_MIXED_FAST if args.form == "fast" else wt.WT_MIXED
 
     def step():
         tree = wt.wt_build_tree(l, m, fl, w.ra0, w.dec0, J)
@@ -275,7 +277,8 @@ def native(args):
 
     # roofline of the dominant kernel (the mixed Eq. 17 predictor)
     n_leaves, n_nodes = info["n_leaves"], info["n_nodes"]
-    ops = n_vis * (OPS_LEAF * n_leaves + OPS_NODE * (n_nodes - n_leaves))
+    op_leaf = OPS_LEAF_FAST if args.form == "fast" else OPS_LEAF
+    ops = n_vis * (op_leaf * n_leaves + OPS_NODE * (n_nodes - n_leaves))
     achieved = ops / t_pred / 1e12
     peak = FP32_PEAK_TOPS
     passes = (2 * J + 2 + 7) // 8
@@ -291,7 +294,8 @@ def native(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64 (double-float phase, f32 sincos, Kahan f32 sum)",
+        "dtype": ("f32+f64 (double-float phase, f32 SFU sincos, Kahan f32 sum)" if args.form == "fast"
+                  else "f32+f64 (double-float phase, f32 polynomial sincos, Kahan f32 sum)"),
         "data": "synthetic (seeded; medium array stand-in for the paper's simulated VLA data)",
         "config": {
             "workload": w.name,
@@ -300,7 +304,7 @@ def native(args):
             "J": J,
             "n_leaves": n_leaves,
             "n_nodes": n_nodes,
-            "form": "wavelet Eq.17, WT_MIXED",
+            "form": "wavelet Eq.17, " + ("WT_MIXED_FAST" if args.form == "fast" else "WT_MIXED"),
             "step": "wt_build_tree + wt_predict_vis + subtract_model",
             "parallelism": "dp%d (replicated tree, sharded visibilities)" % world,
             "l2": "flushed (512 MB write) before every timed step",
@@ -313,11 +317,12 @@ def native(args):
             "bound": "alu",
             "achieved": achieved,
             "peak": peak,
-            "unit": "TOP/s (FP32 pipe ops)",
+            "unit": "TOP/s (FP32-pipe ops; an SFU op counts 8, its pipe-time ratio)",
             "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES_MEDIUM_J12 if (J == MEDIUM_J and n_vis == 1008000) else None,
+            "traffic": (TRAFFIC_BYTES_MEDIUM_J12 if (J == MEDIUM_J and n_vis == 1008000 and args.form == "fast")
+                        else None),
             "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
-                            "(profiles/k_wavelet_mixed_medium_1008000vis_J12.md); output still in L2 at exit",
+                            "(profiles/k_wavelet_mixed_fast_medium_1008000vis_J12.md); output still in L2 at exit",
             "algorithmic_bytes": 32 * n_vis,
             "kernel": "k_wavelet_mixed (Eq. 17)",
         },
@@ -341,9 +346,13 @@ def native(args):
 # branches) is not counted.
 OPS_LEAF = 68
 OPS_NODE = 38
-# DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
-# from ncu (dram__bytes_read.sum 24 265 472 + dram__bytes_write.sum 0).
-TRAFFIC_BYTES_MEDIUM_J12 = 24265472
+# Fast form: the same phase (33 ops) and angle (3) on the FP32 pipe, sin and
+# cos on the special-function unit (16 lanes per SM against 128 FP32 lanes:
+# each SFU op occupies its pipe for the time of 8 FP32 ops).
+OPS_LEAF_FAST = 36 + 2 * 8
+# DRAM bytes of one k_wavelet_mixed launch (fast form) on the medium workload
+# at J = 12, from ncu (dram__bytes_read.sum 24 263 680 + dram__bytes_write.sum 0).
+TRAFFIC_BYTES_MEDIUM_J12 = 24263680
 # Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
 HBM_PEAK_GBPS = 6690.1
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
@@ -377,13 +386,17 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
                                    ("wavelet_fp64_eq17_regrouped", wt.WT_FP64, wt.WT_SUM_EQ17_REGROUPED, out64),
                                    ("wavelet_mixed_eq17_regrouped", wt.WT_MIXED, wt.WT_SUM_EQ17_REGROUPED, out32),
                                    ("wavelet_fp64_eq16", wt.WT_FP64, wt.WT_SUM_EQ16, out64),
-                                   ("wavelet_mixed_eq16", wt.WT_MIXED, wt.WT_SUM_EQ16, out32)]:
+                                   ("wavelet_mixed_eq16", wt.WT_MIXED, wt.WT_SUM_EQ16, out32),
+                                   ("wavelet_mixed_fast_eq17", wt.WT_MIXED_FAST, wt.WT_SUM_EQ17, out32),
+                                   ("wavelet_mixed_fast_eq16", wt.WT_MIXED_FAST, wt.WT_SUM_EQ16, out32)]:
         t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out), stream, flush)
         r[name + "_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_FP64, out=out64), stream, flush, reps=1)
     r["dft_fp64_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED, out=out32), stream, flush)
     r["dft_mixed_vis_per_s"] = n / t
+    t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED_FAST, out=out32), stream, flush)
+    r["dft_mixed_fast_vis_per_s"] = n / t
     r["dft_terms"] = w.n_comp
     t = _time_call(lambda: wt.subtract_model(out32, out32, mode=wt.WT_MIXED, out=out32), stream, flush)
     r["subtract_c64_GBps"] = 24 * n / t / 1e9
@@ -675,7 +688,8 @@ def forms_once(args):
     o64 = torch.empty(w.n_vis, dtype=torch.complex128, device=dev)
     o32 = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
     sub = uvw[:131072].contiguous()
-    runs = [("wavelet_mixed", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o32)),
+    runs = [("wavelet_mixed_fast", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED_FAST, out=o32)),
+            ("wavelet_mixed", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o32)),
             ("wavelet_fp64", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_FP64, out=o64)),
             ("dft_mixed", lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=o32)),
             ("dft_fp64_131072", lambda: wt.dft_predict_vis(l, m, f, sub, mode=wt.WT_FP64, out=o64[:131072])),

@@ -67,7 +67,10 @@ typedef enum {
     WT_FP64 = 0,     /* float64 throughout, complex128 output */
     WT_MIXED = 1,    /* float64-accurate phase (double-float), float32 sincos and
                         compensated float32 accumulation, complex64 output */
-    WT_LEARNED = 2   /* wavelet route only: learned per-level response (MLP) */
+    WT_LEARNED = 2,  /* wavelet route only: learned per-level response (MLP) */
+    WT_MIXED_FAST = 3 /* as WT_MIXED, but sin/cos of the reduced phase from the
+                         special-function unit: at most ~7e-7 of a term's flux in
+                         error per term (measured against the oracle); complex64 */
 } wt_mode;
 
 typedef enum {
@@ -144,8 +147,10 @@ void wt_free_tree(wt_tree t);
  *
  *   t        a built tree (the build must precede this call in stream order)
  *   uvw      device float64 [n_vis][3], wavelengths
- *   vis_out  device complex128 [n_vis] (WT_FP64) or complex64 [n_vis] (WT_MIXED)
- *   mode     WT_FP64 or WT_MIXED (WT_LEARNED: see wt_predict_vis_learned)
+ *   vis_out  device complex128 [n_vis] (WT_FP64) or complex64 [n_vis] (WT_MIXED,
+ *            WT_MIXED_FAST)
+ *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST (WT_LEARNED: see
+ *            wt_predict_vis_learned)
  *   which    wt_sum
  * ------------------------------------------------------------------------- */
 int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
@@ -182,7 +187,8 @@ int wt_predict_vis_batched(const wt_tree* trees, const double* freq_hz, int n_ch
  * a device scratch buffer the call allocates and releases on `stream`.
  *   l, m, flux  device float64 [n_comp]
  *   uvw         device float64 [n_vis][3]
- *   vis_out     device complex128 (WT_FP64) or complex64 (WT_MIXED) [n_vis]
+ *   vis_out     device complex128 (WT_FP64) or complex64 (WT_MIXED,
+ *               WT_MIXED_FAST) [n_vis]
  * ------------------------------------------------------------------------- */
 int dft_predict_vis(const double* l, const double* m, const double* flux, int64_t n_comp,
                     const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign,

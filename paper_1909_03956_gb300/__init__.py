@@ -27,7 +27,7 @@ import numpy as np
 
 WT_OK, WT_ERR_ARG, WT_ERR_RANGE, WT_ERR_CUDA, WT_ERR_NOMEM, WT_ERR_TIMEOUT, WT_ERR_CORRUPT, WT_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7
-WT_FP64, WT_MIXED, WT_LEARNED = 0, 1, 2
+WT_FP64, WT_MIXED, WT_LEARNED, WT_MIXED_FAST = 0, 1, 2, 3
 WT_SUM_EQ17, WT_SUM_EQ16, WT_SUM_EQ17_REGROUPED = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

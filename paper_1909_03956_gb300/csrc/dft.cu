@@ -57,6 +57,7 @@ struct BodyD {
     }
 };
 
+template <bool FAST>
 struct BodyF {
     F2 u, v, w;
     float sgn, vr, vi, cr, ci;
@@ -65,7 +66,7 @@ struct BodyF {
         float th, tl;
         phase_turns_df(u, v, w, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, th, tl);
         float s, co;
-        sincos_turns_f32(th, tl, s, co);
+        sincos_mixed<FAST>(th, tl, s, co);
         kahan_add(vr, cr, c.flux * co);
         kahan_add(vi, ci, c.flux * s);
     }
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(NT) k_dft_fp64(const CompD* __restrict__ comps
     }
 }
 
-template <int NT>
+template <int NT, bool FAST>
 __global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comps, int64_t n_comp,
                                                   const double* __restrict__ uvw, int64_t n_vis,
                                                   float2* __restrict__ vis, float sgn, int* status)
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comp
         const int64_t n = tile * NT + threadIdx.x;
         const bool valid = n < n_vis;
         const double sg = static_cast<double>(sgn);   // sign folded into the baseline (exact)
-        BodyF b{split_f64(valid ? sg * uvw[3 * n] : 0.0), split_f64(valid ? sg * uvw[3 * n + 1] : 0.0),
+        BodyF<FAST> b{split_f64(valid ? sg * uvw[3 * n] : 0.0), split_f64(valid ? sg * uvw[3 * n + 1] : 0.0),
                 split_f64(valid ? sg * uvw[3 * n + 2] : 0.0), sgn, 0.f, 0.f, 0.f, 0.f};
         if (!st.sweep(b)) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
@@ -150,7 +151,7 @@ int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, in
     } else {
         constexpr int NT = 256;
         const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
-        auto k = k_dft_mixed<NT>;
+        auto k = (mode == WT_MIXED_FAST) ? k_dft_mixed<NT, true> : k_dft_mixed<NT, false>;
         int rc = grid_for(k, NT, smem, n_vis, grid);
         if (rc) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(scratch), n_comp, uvw, n_vis, static_cast<float2*>(vis),
@@ -307,7 +308,7 @@ extern "C" int dft_predict_vis_noalloc(const double* l, const double* m, const d
     } else {
         constexpr int NT = 256;
         const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
-        auto k = k_dft_mixed<NT>;
+        auto k = k_dft_mixed<NT, false>;
         if ((rc = grid_for(k, NT, smem, n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<float2*>(vis_out),
                                  static_cast<float>(sign), status);

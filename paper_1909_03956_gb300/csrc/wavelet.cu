@@ -26,6 +26,7 @@
 //   WT_MIXED  phase in double-float turns (float64-accurate), sin/cos of the
 //             reduced phase in float32 (Taylor series, wt_internal.cuh),
 //             recursion in float32, Kahan-compensated float32 V.
+//   WT_MIXED_FAST  as WT_MIXED with sin/cos from the special-function unit.
 #include "staging.cuh"
 #include "wavelet_bodies.cuh"
 #include "wt_internal.cuh"
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const Rec* __restrict__ rec
     }
 }
 
-template <int NT, int VPT, int SUM, class Rec>
+template <int NT, int VPT, int SUM, class Rec, bool FAST>
 __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ recs, const TreeHeader* __restrict__ hdr,
                                                       const double* __restrict__ uvw, int64_t n_vis,
                                                       float2* __restrict__ vis, float sgn, int rows, int J,
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
         bool good;
         float vr[VPT], vi[VPT];
         if constexpr (SUM == 1) {
-            Eq16F<VPT> b;
+            Eq16F<VPT, FAST> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
 #pragma unroll
             for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
         } else if constexpr (SUM == 0) {
-            Eq17F<NT, VPT> b;
+            Eq17F<NT, VPT, FAST> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
 #pragma unroll
             for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
         } else {
-            Eq17WF<NT, VPT> b;
+            Eq17WF<NT, VPT, FAST> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
@@ -242,8 +243,8 @@ int run_fp64(const WaveletJob& jb, cudaStream_t s)
     return WT_OK;
 }
 
-template <int NT, int VPT>
-int run_mixed(const WaveletJob& jb, cudaStream_t s)
+template <int NT, int VPT, bool FAST>
+int run_mixed_form(const WaveletJob& jb, cudaStream_t s)
 {
     const int rows = stack_rows(jb.which, jb.J);
     const size_t stack = static_cast<size_t>(rows) * VPT * NT * sizeof(float2);
@@ -253,20 +254,26 @@ int run_mixed(const WaveletJob& jb, cudaStream_t s)
     float2* out = static_cast<float2*>(jb.vis);
     const float sg = static_cast<float>(jb.sign);
     if (jb.which == WT_SUM_EQ16) {
-        auto k = k_wavelet_mixed<NT, VPT, 1, RecF>;
+        auto k = k_wavelet_mixed<NT, VPT, 1, RecF, FAST>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else if (jb.which == WT_SUM_EQ17) {
-        auto k = k_wavelet_mixed<NT, VPT, 0, RecF>;
+        auto k = k_wavelet_mixed<NT, VPT, 0, RecF, FAST>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else {
-        auto k = k_wavelet_mixed<NT, VPT, 2, RecWF>;
+        auto k = k_wavelet_mixed<NT, VPT, 2, RecWF, FAST>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(jb.recwf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     }
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
+}
+
+template <int NT, int VPT>
+int run_mixed(const WaveletJob& jb, cudaStream_t s)
+{
+    return (jb.mode == WT_MIXED_FAST) ? run_mixed_form<NT, VPT, true>(jb, s) : run_mixed_form<NT, VPT, false>(jb, s);
 }
 
 }  // namespace

@@ -112,7 +112,7 @@ struct Eq16D {
 };
 
 // ---------------------------------------------------------------- mixed
-template <int NT, int VPT>
+template <int NT, int VPT, bool FAST = false>
 struct Eq17F {
     F2 u[VPT], v[VPT], w[VPT];
     float vr[VPT], vi[VPT], cr[VPT], ci[VPT];   // Kahan sums and compensations
@@ -133,7 +133,7 @@ struct Eq17F {
             for (int k = 0; k < VPT; ++k) {
                 float th, tl, s, c;
                 phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
-                sincos_turns_f32(th, tl, s, c);
+                sincos_mixed<FAST>(th, tl, s, c);
                 const float ei = s;
                 if (root) {
                     kahan_add(vr[k], cr[k], r.g * c);
@@ -194,7 +194,7 @@ struct Eq17F {
     }
 };
 
-template <int VPT>
+template <int VPT, bool FAST = false>
 struct Eq16F {
     F2 u[VPT], v[VPT], w[VPT];
     float vr[VPT], vi[VPT], cr[VPT], ci[VPT];
@@ -206,7 +206,7 @@ struct Eq16F {
         for (int k = 0; k < VPT; ++k) {
             float th, tl, s, c;
             phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
-            sincos_turns_f32(th, tl, s, c);
+            sincos_mixed<FAST>(th, tl, s, c);
             kahan_add(vr[k], cr[k], r.g * c);
             kahan_add(vi[k], ci[k], r.g * s);
         }
@@ -293,7 +293,7 @@ struct Eq17WD {
     }
 };
 
-template <int NT, int VPT>
+template <int NT, int VPT, bool FAST = false>
 struct Eq17WF {
     F2 u[VPT], v[VPT], w[VPT];
     float vr[VPT], vi[VPT], cr[VPT], ci[VPT];   // Kahan sums and compensations
@@ -315,7 +315,7 @@ struct Eq17WF {
             for (int k = 0; k < VPT; ++k) {
                 float th, tl, s, c;
                 phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
-                sincos_turns_f32(th, tl, s, c);
+                sincos_mixed<FAST>(th, tl, s, c);
                 if (root) {
                     kahan_add(vr[k], cr[k], r.g * c);
                     kahan_add(vi[k], ci[k], r.g * s);

@@ -286,7 +286,8 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out, i
         return set_error(WT_ERR_ARG, "%s: bad sum selector", fn);
     if (mode == WT_LEARNED)
         return set_error(WT_ERR_UNSUPPORTED, "%s: the learned response has its own entry point", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST)
+        return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
     const size_t ob = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
     if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
         (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
@@ -301,7 +302,8 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
     if (n_comp < 0 || n_vis < 0) return set_error(WT_ERR_ARG, "%s: negative size", fn);
     if (n_comp > (int64_t(1) << 30)) return set_error(WT_ERR_RANGE, "%s: n_comp too large", fn);
     if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST)
+        return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
     const size_t nb = static_cast<size_t>(n_comp) * 8;
     const size_t ob = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
     int rc;
@@ -318,7 +320,8 @@ int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid, 
 {
     const char* fn = "subtract_model";
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_LEARNED) return set_error(WT_ERR_ARG, "%s: bad mode", fn);
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_LEARNED && mode != WT_MIXED_FAST)
+        return set_error(WT_ERR_ARG, "%s: bad mode", fn);
     const size_t b = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
     int rc;
     if ((rc = check_device_buffer(vis_obs, b, fn, "vis_obs")) || (rc = check_device_buffer(vis_model, b, fn, "vis_model")) ||

@@ -209,6 +209,26 @@ __device__ __forceinline__ void sincos_turns_f64(double t, double& s, double& c)
     s = fma(tk.y, pc, tk.x * sx);
 }
 
+// sin and cos of 2 pi (th + tl) from the special-function unit (the fast
+// mixed form, WT_MIXED_FAST): the angle 2 pi th + 2 pi tl (|.| <= pi + small)
+// goes to the hardware approximations (__sincosf; absolute error about
+// 2^-21.4 on [-pi, pi] per the CUDA documentation), so one term carries at
+// most ~7e-7 of its flux in error instead of ~1e-7; the phase itself stays
+// float64-accurate.
+__device__ __forceinline__ void sincos_turns_sfu(float th, float tl, float& s, float& c)
+{
+    const float twopi = 6.28318530717958648f;
+    const float x = __fmaf_rn(twopi, th, __fmul_rn(twopi, tl));
+    __sincosf(x, &s, &c);
+}
+
+template <bool FAST>
+__device__ __forceinline__ void sincos_mixed(float th, float tl, float& s, float& c)
+{
+    if constexpr (FAST) sincos_turns_sfu(th, tl, s, c);
+    else sincos_turns_f32(th, tl, s, c);
+}
+
 // Kahan-compensated float32 accumulation: sum + comp carries the total.
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
 {

@@ -284,7 +284,7 @@ def test_tree_on_wrong_mode_rejected():
 # ---------------------------------------------------------------- launch shapes
 
 @pytest.mark.parametrize("variant", range(8))
-@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX), (wt.WT_MIXED_FAST, TOLMIX)])
 def test_wavelet_every_launch_shape(variant, mode, tol, monkeypatch):
     # Each (threads per CTA, visibilities per thread) shape the autotuner may
     # pick gives the oracle's answer, on a ragged count of visibilities.
@@ -340,3 +340,32 @@ def test_bounded_wait_times_out_and_reports():
     wt.wt_device_status()                     # cleared
     w = synth.small()
     assert _dft_case(w, w.uvw[:100], wt.WT_FP64) <= TOL64
+
+
+# ---------------------------------------------------------------- fast mixed form
+
+@pytest.mark.parametrize("J", [1, 8, 12, 14])
+def test_wavelet_mixed_fast(J):
+    # sin/cos from the special-function unit: the same 1e-6 bar.
+    w = synth.medium(n_t=6)
+    uvw = w.uvw[::3]
+    for which in (wt.WT_SUM_EQ17, wt.WT_SUM_EQ16, wt.WT_SUM_EQ17_REGROUPED):
+        assert _wavelet_case(w, J, uvw, wt.WT_MIXED_FAST, which=which) <= TOLMIX
+    assert _wavelet_case(w, J, uvw[:500], wt.WT_MIXED_FAST, sign=-1) <= TOLMIX
+
+
+def test_wavelet_mixed_fast_single_component_worst_case():
+    # One component: no averaging over terms, so the per-term error bound
+    # of the fast form is what shows.
+    rng = np.random.default_rng(41)
+    uvw = rng.uniform(-3e4, 3e4, (20000, 3))
+    w = synth.Workload("one", uvw, np.array([0.0123]), np.array([-0.0071]), np.array([1.0]), 14)
+    assert _wavelet_case(w, 14, uvw, wt.WT_MIXED_FAST) <= TOLMIX
+    assert _dft_case(w, uvw, wt.WT_MIXED_FAST) <= TOLMIX
+
+
+def test_dft_mixed_fast():
+    w = synth.medium(n_t=2)
+    assert _dft_case(w, w.uvw[::4], wt.WT_MIXED_FAST) <= TOLMIX
+    s = synth.small()
+    assert _dft_case(s, s.uvw[:333], wt.WT_MIXED_FAST, sign=-1) <= TOLMIX

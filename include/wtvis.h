@@ -165,8 +165,9 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
  *   trees    HOST array [n_ch] of built trees (any mix of J and sizes)
  *   freq_hz  HOST array [n_ch], > 0
  *   uvw_m    device float64 [n_vis][3], metres
- *   vis_out  device [n_ch][n_vis], complex128 (WT_FP64) or complex64 (WT_MIXED)
- *   mode     WT_FP64 or WT_MIXED; sign +1 / -1
+ *   vis_out  device [n_ch][n_vis], complex128 (WT_FP64) or complex64 (WT_MIXED,
+ *            WT_MIXED_FAST)
+ *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST; sign +1 / -1
  * All channels run in one persistent kernel that takes (channel, tile) work
  * items, largest trees first, from a device-side counter. The first call for
  * a given (trees, freq_hz, mode, sign) builds a plan: it reads the trees'
@@ -275,8 +276,8 @@ int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, in
 /* R(B) by the network (exact sum beyond x_max); out: device complex64 [n]. */
 int wt_mlp_eval(wt_mlp m, const double* uvw, int64_t n, int sign, void* out, void* stream);
 /* Learned form of the tree prediction: V = R_J(B) sum_k Phi_k exp(sign i 2 pi
- * B.(c_k - P)) -- the level-J sum (Eq. 16) with each leaf's centre-snapped
- * plane wave replaced by the pixel's full response. The network's level must
+ * B.(c_k - P)) -- the level-J sum (Eq. 16, fast mixed form) with each leaf's
+ * centre-snapped plane wave replaced by the pixel's full response. The network's level must
  * equal the tree's J and the phase centres must match. Output complex64. */
 int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis, void* vis_out, int sign,
                            void* stream);

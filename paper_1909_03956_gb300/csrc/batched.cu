@@ -57,7 +57,7 @@ __device__ __forceinline__ int find_channel(const BatchChan* __restrict__ ch, in
     return a;
 }
 
-template <int NT, int VPT, bool MIXED>
+template <int NT, int VPT, bool MIXED, bool FAST = false>
 __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ chans, int n_ch, int64_t total_items,
                                                 const double* __restrict__ uvw_m, int64_t n_vis, void* vis, double sgn,
                                                 int rows_max, unsigned long long* queue, int* status)
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
         const int64_t n0 = (item - ch.tile_base) * per_tile + threadIdx.x;
         bool good;
         if constexpr (MIXED) {
-            Eq17F<NT, VPT> b;
+            Eq17F<NT, VPT, FAST> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const int64_t n = n0 + static_cast<int64_t>(k) * NT;
@@ -158,11 +158,11 @@ size_t batch_smem(int mode, int shape, int rows_max)
 
 bool batch_fits(int mode, int shape, int rows_max) { return batch_smem(mode, shape, rows_max) <= 220 * 1024; }
 
-template <int NT, int VPT, bool MIXED>
+template <int NT, int VPT, bool MIXED, bool FAST = false>
 int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
                  int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
 {
-    auto k = k_batched<NT, VPT, MIXED>;
+    auto k = k_batched<NT, VPT, MIXED, FAST>;
     int per_sm = 0;
     WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
@@ -174,16 +174,16 @@ int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* 
     return WT_OK;
 }
 
-template <bool MIXED>
+template <bool MIXED, bool FAST = false>
 int set_attr(int shape, size_t smem)
 {
     const void* fn;
     switch (shape) {
-        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, MIXED>); break;
-        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, MIXED>); break;
-        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, MIXED>); break;
-        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, MIXED>); break;
-        default: fn = reinterpret_cast<const void*>(k_batched<32, 1, MIXED>); break;
+        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, MIXED, FAST>); break;
+        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, MIXED, FAST>); break;
+        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, MIXED, FAST>); break;
+        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, MIXED, FAST>); break;
+        default: fn = reinterpret_cast<const void*>(k_batched<32, 1, MIXED, FAST>); break;
     }
     WT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     return WT_OK;
@@ -201,6 +201,15 @@ int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t 
             case 2: return launch_shape<128, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
             case 3: return launch_shape<64, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
             default: return launch_shape<32, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        }
+    }
+    if (mode == WT_MIXED_FAST) {
+        switch (shape) {
+            case 0: return launch_shape<256, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 1: return launch_shape<128, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 2: return launch_shape<128, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 3: return launch_shape<64, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            default: return launch_shape<32, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
         }
     }
     switch (shape) {
@@ -309,8 +318,9 @@ int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cu
     float best_ms = 1e30f;
     for (int sh = 0; sh < kNumBatchShapes; ++sh) {
         if (!batch_fits(p.mode, sh, p.rows_max)) continue;
-        int rc = (p.mode == WT_FP64) ? set_attr<false>(sh, batch_smem(p.mode, sh, p.rows_max))
-                                     : set_attr<true>(sh, batch_smem(p.mode, sh, p.rows_max));
+        const size_t sm = batch_smem(p.mode, sh, p.rows_max);
+        int rc = (p.mode == WT_FP64) ? set_attr<false>(sh, sm)
+                 : (p.mode == WT_MIXED_FAST) ? set_attr<true, true>(sh, sm) : set_attr<true>(sh, sm);
         if (rc) continue;
         if (write_table(p, sample, sh, s)) continue;
         float ms_best_rep = 1e30f;
@@ -407,7 +417,8 @@ int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const
         }
     }
     const size_t smem = batch_smem(mode, p->shape, p->rows_max);
-    int rc = (mode == WT_FP64) ? set_attr<false>(p->shape, smem) : set_attr<true>(p->shape, smem);
+    int rc = (mode == WT_FP64) ? set_attr<false>(p->shape, smem)
+             : (mode == WT_MIXED_FAST) ? set_attr<true, true>(p->shape, smem) : set_attr<true>(p->shape, smem);
     if (rc) return rc;
     if ((rc = write_table(*p, n_vis, p->shape, s))) return rc;
     if (!p->exec || p->g_uvw != uvw_m || p->g_nvis != n_vis || p->g_vis != vis || p->g_shape != p->shape) {
@@ -449,7 +460,8 @@ extern "C" int wt_predict_vis_batched(const wt_tree* trees, const double* freq_h
     if (n_ch < 1 || n_ch > 65536) return set_error(WT_ERR_ARG, "%s: n_ch = %d outside 1..65536", fn, n_ch);
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
     if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST)
+        return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
     int dev = 0;
     WT_CUDA_TRY(cudaGetDevice(&dev));
     for (int c = 0; c < n_ch; ++c) {

@@ -733,7 +733,7 @@ int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis
                                            m->level, t->J);
     if (t->ra0 != m->ra0 || t->dec0 != m->dec0)
         return set_error(WT_ERR_ARG, "%s: tree and network have different phase centres", fn);
-    if ((rc = wt_predict_vis(t, uvw, n_vis, vis_out, WT_MIXED, sign, WT_SUM_EQ16, stream))) return rc;
+    if ((rc = wt_predict_vis(t, uvw, n_vis, vis_out, WT_MIXED_FAST, sign, WT_SUM_EQ16, stream))) return rc;
     if (n_vis == 0) return WT_OK;
     return launch_apply(m, uvw, n_vis, vis_out, sign, true, static_cast<cudaStream_t>(stream));
 }

@@ -16,7 +16,7 @@ wt = pytest.importorskip("paper_1909_03956_gb300")
 pytestmark = pytest.mark.gpu
 
 C_LIGHT = 299792458.0
-TOL = {wt.WT_FP64: 1e-10, wt.WT_MIXED: 1e-6}
+TOL = {wt.WT_FP64: 1e-10, wt.WT_MIXED: 1e-6, wt.WT_MIXED_FAST: 1e-6}
 
 
 def dev(a):
@@ -51,7 +51,7 @@ def _gpu_trees(chans):
     return [wt.wt_build_tree(dev(c["l"]), dev(c["m"]), dev(c["flux"]), synth.RA0, synth.DEC0, c["J"]) for c in chans]
 
 
-@pytest.mark.parametrize("mode", [wt.WT_FP64, wt.WT_MIXED])
+@pytest.mark.parametrize("mode", [wt.WT_FP64, wt.WT_MIXED, wt.WT_MIXED_FAST])
 def test_batched_matches_oracle_per_channel(mode):
     chans = _channels(9)
     uvw_m = _uvw_m(3001)                       # ragged against every tile size

@@ -18,7 +18,7 @@ wt = pytest.importorskip("paper_1909_03956_gb300")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {wt.WT_FP64: 1e-10, wt.WT_MIXED: 1e-6}
+TOL = {wt.WT_FP64: 1e-10, wt.WT_MIXED: 1e-6, wt.WT_MIXED_FAST: 1e-6}
 
 
 def dev(a):
@@ -29,7 +29,7 @@ def _sample(n, k=300):
     return np.unique(np.concatenate([np.arange(0, n, max(1, n // k)), [n - 1]]))
 
 
-@pytest.mark.parametrize("mode", [wt.WT_MIXED, wt.WT_FP64])
+@pytest.mark.parametrize("mode", [wt.WT_MIXED_FAST, wt.WT_MIXED, wt.WT_FP64])
 def test_medium_full_size(mode):
     w = synth.medium(J=12)
     t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
@@ -65,7 +65,7 @@ def test_batched_full_size():
     chans = w.extra["channels"]
     uvw_m = w.extra["uvw_m"]
     trees = [wt.wt_build_tree(dev(c["l"]), dev(c["m"]), dev(c["flux"]), w.ra0, w.dec0, c["J"]) for c in chans]
-    v = wt.wt_predict_vis_batched(trees, [c["freq"] for c in chans], dev(uvw_m), mode=wt.WT_MIXED)
+    v = wt.wt_predict_vis_batched(trees, [c["freq"] for c in chans], dev(uvw_m), mode=wt.WT_MIXED_FAST)
     idx = _sample(uvw_m.shape[0], 40)
     got = v.cpu().numpy()[:, idx]
     for c, ch in enumerate(chans):

@@ -54,6 +54,14 @@
 
 #define ORC_PI 3.14159265358979323846
 
+/* Mutation testing of the pins: a test build may define ORC_PLANT = k > 0
+ * to plant the k-th known mistake (tests/test_oracle_planted.py checks that
+ * a pin catches each one). The normal build plants nothing. */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+#define PLANTED(k) (ORC_PLANT == (k))
+
 /* ========================================================================== */
 /* Eq. 12 -- direct sum over the component list                              */
 /* ========================================================================== */
@@ -62,7 +70,7 @@
 static double n_minus_1(double l, double m)
 {
     double r2 = l * l + m * m;
-    return -r2 / (1.0 + sqrt(1.0 - r2));
+    return (PLANTED(1) ? 1.0 : -1.0) * r2 / (1.0 + sqrt(1.0 - r2));
 }
 
 /* V_n = sum_m C_m exp(sign * i 2 pi [u l_m + v m_m + w (n_m - 1)]), Eq. 12
@@ -75,7 +83,7 @@ int orc_dft(int64_t n_comp, const double* l, const double* m, const double* flux
         const double u = uvw[3 * n], v = uvw[3 * n + 1], w = uvw[3 * n + 2];
         double re = 0.0, im = 0.0;
         for (int64_t c = 0; c < n_comp; ++c) {
-            double t = u * l[c] + v * m[c] + w * n_minus_1(l[c], m[c]);
+            double t = u * l[c] + v * (PLANTED(2) ? l[c] : m[c]) + w * n_minus_1(l[c], m[c]);
             t = t - rint(t);                          /* R3 */
             const double phase = 2.0 * ORC_PI * t;
             re += flux[c] * cos(phase);
@@ -125,7 +133,7 @@ void orc_rotation(double ra0, double dec0, double* R)
 {
     double Ry[9], Rx[9];
     const double ca = cos(ra0), sa = sin(ra0);
-    const double cd = cos(-dec0), sd = sin(-dec0);
+    const double cd = cos(PLANTED(3) ? dec0 : -dec0), sd = sin(PLANTED(3) ? dec0 : -dec0);
     Ry[0] = ca;   Ry[1] = 0.0; Ry[2] = sa;
     Ry[3] = 0.0;  Ry[4] = 1.0; Ry[5] = 0.0;
     Ry[6] = -sa;  Ry[7] = 0.0; Ry[8] = ca;
@@ -185,7 +193,7 @@ int64_t orc_ang2pix_nest(int order, double z, double phi, double* margin)
 {
     const int64_t ns = (int64_t)1 << order;
     const double za = fabs(z);
-    const double t = phi / (0.5 * ORC_PI);          /* in [0, 4) */
+    const double t = phi / ((PLANTED(5) ? 1.0 : 0.5) * ORC_PI);   /* in [0, 4) */
     int64_t face, ix, iy;
     double marg;
     if (za <= 2.0 / 3.0) {
@@ -201,7 +209,7 @@ int64_t orc_ang2pix_nest(int order, double z, double phi, double* margin)
         else if (fp < fm) face = fp;                   /* north row */
         else face = fm + 8;                            /* south row */
         ix = jm & (ns - 1);
-        iy = ns - (jp & (ns - 1)) - 1;
+        iy = ns - (jp & (ns - 1)) - (PLANTED(4) ? 0 : 1);
     } else {
         int64_t q = (int64_t)t;                        /* quarter 0..3 */
         if (q > 3) q = 3;
@@ -253,7 +261,7 @@ void orc_pix2ang_nest(int order, int64_t pix, double* z, double* sin_theta, doub
         shift = 0;
     } else {                                            /* equatorial belt */
         nr = ns;
-        zz = (double)(2 * ns - ring) * 2.0 / (3.0 * (double)ns);
+        zz = (double)(2 * ns - ring) * (PLANTED(10) ? 4.0 : 2.0) / (3.0 * (double)ns);
         st = sqrt((1.0 - zz) * (1.0 + zz));
         shift = (ring - ns) & 1;
     }
@@ -280,7 +288,7 @@ void orc_pixel_dir_uvw(int J, int64_t k, double ra0, double dec0, double* out3)
     out3[0] = su;
     out3[1] = sv;
     /* s_w - 1 without cancellation when s_w > 0 (reading R2's identity) */
-    out3[2] = (sw > 0.0) ? -(su * su + sv * sv) / (1.0 + sw) : sw - 1.0;
+    out3[2] = (sw > 0.0) ? (PLANTED(11) ? 1.0 : -1.0) * (su * su + sv * sv) / (1.0 + sw) : sw - 1.0;
 }
 
 /* Sec. 3.5 cross-reference: image position [l, m] -> SIN projection onto the
@@ -369,9 +377,9 @@ static void image_coefficients(orc_node* nd, int J)
         }
     }
     const double q = sqrt_area_of_level(nd->level) * 0.25;
-    nd->lambda = 0.25 * (((c[0] + c[1]) + c[2]) + c[3]);
+    nd->lambda = (PLANTED(6) ? 0.5 : 0.25) * (((c[0] + c[1]) + c[2]) + c[3]);
     nd->gamma[0] = q * (((c[0] - c[1]) + c[2]) - c[3]);
-    nd->gamma[1] = q * (((c[0] + c[1]) - c[2]) - c[3]);
+    nd->gamma[1] = q * (((c[0] + c[1]) - c[2]) + (PLANTED(7) ? c[3] : -c[3]));
     nd->gamma[2] = q * (((c[0] - c[1]) - c[2]) + c[3]);
 }
 
@@ -419,7 +427,7 @@ orc_tree* orc_tree_build(int64_t n, const double* l, const double* m, const doub
             }
             nd = nd->child[slot];
         }
-        nd->flux += flux[i];
+        nd->flux = (PLANTED(9) ? 0.0 : nd->flux) + flux[i];
     }
     free(kJ);
     /* Breadth-first lists, sorted by key within each level. */
@@ -548,7 +556,7 @@ int orc_tree_vis_eq17(const orc_tree* t, int64_t n_vis, const double* uvw, int s
                 for (int s = 0; s < 4; ++s)
                     c[s] = nd->child[s] ? eta[2 * nd->child[s]->bfs + part] : 0.0;
                 eta[2 * i + part] = 0.25 * (((c[0] + c[1]) + c[2]) + c[3]);
-                sig[6 * i + 0 + part] = q * (((c[0] - c[1]) + c[2]) - c[3]);
+                sig[6 * i + 0 + part] = q * (((c[0] - c[1]) + c[2]) + (PLANTED(12) ? c[3] : -c[3]));
                 sig[6 * i + 2 + part] = q * (((c[0] + c[1]) - c[2]) - c[3]);
                 sig[6 * i + 4 + part] = q * (((c[0] - c[1]) - c[2]) + c[3]);
             }
@@ -559,13 +567,13 @@ int orc_tree_vis_eq17(const orc_tree* t, int64_t n_vis, const double* uvw, int s
         const int64_t n1 = t->per_level[1];
         if (t->J == 1) {
             for (int64_t i = 0; i < n1; ++i) {
-                re += A1 * (t->bfs[i]->lambda * eta[2 * i]);
-                im += A1 * (t->bfs[i]->lambda * eta[2 * i + 1]);
+                re += (PLANTED(8) ? 1.0 : A1) * (t->bfs[i]->lambda * eta[2 * i]);
+                im += (PLANTED(8) ? 1.0 : A1) * (t->bfs[i]->lambda * eta[2 * i + 1]);
             }
         } else {
             for (int64_t i = 0; i < n1; ++i) {
-                re += A1 * (t->bfs[i]->lambda * eta[2 * i]);
-                im += A1 * (t->bfs[i]->lambda * eta[2 * i + 1]);
+                re += (PLANTED(8) ? 1.0 : A1) * (t->bfs[i]->lambda * eta[2 * i]);
+                im += (PLANTED(8) ? 1.0 : A1) * (t->bfs[i]->lambda * eta[2 * i + 1]);
             }
             for (int64_t i = 0; i < leaf0; ++i)
                 for (int mm = 0; mm < 3; ++mm) {

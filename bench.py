@@ -56,11 +56,16 @@ def parse():
     p.add_argument("--J", type=int, default=MEDIUM_J)
     p.add_argument("--form", default="fast", choices=["fast", "mixed"],
                    help="chosen form of the step: WT_MIXED_FAST (default) or WT_MIXED")
+    p.add_argument("--sum", default="regrouped", choices=["regrouped", "explicit"],
+                   help="evaluation order of Eq. 17 in the step: regrouped (V = sum_n w_n eta_n, default) or "
+                        "explicit (eta and the three sigma per node)")
     p.add_argument("--no-extras", action="store_true", help="skip the per-form side measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--forms-once", action="store_true",
                    help="run each predictor once on the medium workload after one warm-up (a bounded "
                         "command for profilers); prints nothing but a short summary")
+    p.add_argument("--only", default="",
+                   help="with --forms-once: comma-separated names of the calls to run (default: all)")
     p.add_argument("--sweep", action="store_true",
                    help="print the run-time scaling study (J and distinct-component sweeps, paper-context "
                         "workload) as one JSON line instead of the benchmark line")
@@ -168,10 +173,11 @@ def native(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     mode = wt.WT_MIXED_FAST if args.form == "fast" else wt.WT_MIXED
+    which = wt.WT_SUM_EQ17_REGROUPED if args.sum == "regrouped" else wt.WT_SUM_EQ17
 
     def step():
         tree = wt.wt_build_tree(l, m, fl, w.ra0, w.dec0, J)
-        wt.wt_predict_vis(tree, uvw, mode=mode, out=model)
+        wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=model)
         wt.subtract_model(obs, model, mode=mode, out=resid)
         return tree
 
@@ -199,7 +205,7 @@ def native(args):
         e0.record(stream)
         tree = wt.wt_build_tree(l, m, fl, w.ra0, w.dec0, J)
         p0.record(stream)
-        wt.wt_predict_vis(tree, uvw, mode=mode, out=model)
+        wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=model)
         p1.record(stream)
         wt.subtract_model(obs, model, mode=mode, out=resid)
         e1.record(stream)
@@ -246,7 +252,7 @@ def native(args):
         duvw.copy_(huvw, non_blocking=True)
         dobs.copy_(hobs, non_blocking=True)
         tree = wt.wt_build_tree(dl, dm, df, w.ra0, w.dec0, J)
-        wt.wt_predict_vis(tree, duvw, mode=mode, out=model)
+        wt.wt_predict_vis(tree, duvw, mode=mode, which=which, out=model)
         wt.subtract_model(dobs, model, mode=mode, out=resid)
         hres.copy_(resid, non_blocking=True)
         e1.record(stream)
@@ -277,8 +283,9 @@ def native(args):
 
     # roofline of the dominant kernel (the mixed Eq. 17 predictor)
     n_leaves, n_nodes = info["n_leaves"], info["n_nodes"]
-    op_leaf = OPS_LEAF_FAST if args.form == "fast" else OPS_LEAF
-    ops = n_vis * (op_leaf * n_leaves + OPS_NODE * (n_nodes - n_leaves))
+    op_leaf, op_node = OPS[(args.form, args.sum)]
+    ops = n_vis * (op_leaf * n_leaves + op_node * (n_nodes - n_leaves))
+    traffic = TRAFFIC_BYTES_MEDIUM_J12.get((args.form, args.sum)) if (J == MEDIUM_J and n_vis == 1008000) else None
     achieved = ops / t_pred / 1e12
     peak = FP32_PEAK_TOPS
     passes = (2 * J + 2 + 7) // 8
@@ -294,8 +301,9 @@ def native(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f32+f64 (double-float phase, f32 SFU sincos, Kahan f32 sum)" if args.form == "fast"
-                  else "f32+f64 (double-float phase, f32 polynomial sincos, Kahan f32 sum)"),
+        "dtype": ("f32+f64 (double-float phase, f32 SFU sincos, Kahan f32 sum, packed f32 pairs)"
+                  if args.form == "fast"
+                  else "f32+f64 (double-float phase, f32 polynomial sincos, Kahan f32 sum, packed f32 pairs)"),
         "data": "synthetic (seeded; medium array stand-in for the paper's simulated VLA data)",
         "config": {
             "workload": w.name,
@@ -304,7 +312,8 @@ def native(args):
             "J": J,
             "n_leaves": n_leaves,
             "n_nodes": n_nodes,
-            "form": "wavelet Eq.17, " + ("WT_MIXED_FAST" if args.form == "fast" else "WT_MIXED"),
+            "form": ("wavelet Eq.17 " + ("regrouped" if args.sum == "regrouped" else "explicit") + ", "
+                     + ("WT_MIXED_FAST" if args.form == "fast" else "WT_MIXED")),
             "step": "wt_build_tree + wt_predict_vis + subtract_model",
             "parallelism": "dp%d (replicated tree, sharded visibilities)" % world,
             "l2": "flushed (512 MB write) before every timed step",
@@ -319,12 +328,14 @@ def native(args):
             "peak": peak,
             "unit": "TOP/s (FP32-pipe ops; an SFU op counts 8, its pipe-time ratio)",
             "frac": achieved / peak,
-            "traffic": (TRAFFIC_BYTES_MEDIUM_J12 if (J == MEDIUM_J and n_vis == 1008000 and args.form == "fast")
-                        else None),
-            "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch "
-                            "(profiles/k_wavelet_mixed_fast_medium_1008000vis_J12.md); output still in L2 at exit",
+            "traffic": traffic,
+            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of this form "
+                             "(profiles/); output still in L2 at exit" if traffic is not None
+                             else "not captured for this form and size"),
             "algorithmic_bytes": 32 * n_vis,
-            "kernel": "k_wavelet_mixed (Eq. 17)",
+            "ops_per_leaf": op_leaf,
+            "ops_per_internal_node": op_node,
+            "kernel": "k_wavelet_mixed (Eq. 17 %s)" % args.sum,
         },
         "e2e": {"value": world * n_vis / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -340,19 +351,36 @@ def native(args):
         dist.destroy_process_group()
 
 
-# FP32 pipe operations of the mixed Eq. 17 form, counted from the method's
-# arithmetic (double-float phase, quadrant-reduced Taylor sin/cos, eta/sigma
-# recursion, compensated sum); instruction overhead (record decode, loads,
-# branches) is not counted.
-OPS_LEAF = 68
-OPS_NODE = 38
-# Fast form: the same phase (33 ops) and angle (3) on the FP32 pipe, sin and
-# cos on the special-function unit (16 lanes per SM against 128 FP32 lanes:
-# each SFU op occupies its pipe for the time of 8 FP32 ops).
-OPS_LEAF_FAST = 36 + 2 * 8
-# DRAM bytes of one k_wavelet_mixed launch (fast form) on the medium workload
-# at J = 12, from ncu (dram__bytes_read.sum 24 263 680 + dram__bytes_write.sum 0).
-TRAFFIC_BYTES_MEDIUM_J12 = 24263680
+# FP32 pipe operations of the mixed Eq. 17 forms, counted from each form's
+# arithmetic; instruction overhead (record decode, loads, stores, branches,
+# register moves) is not counted. A complex add is 2 ops.
+#   phase (every leaf): three double-float products (5 each), two
+#     error-free sums (6 each), reduction by the nearest integer (2), tail
+#     (4): 33.
+#   polynomial sin/cos: quadrant reduction and angle (6), sin and cos
+#     polynomials (5 each), quadrant selection (4): 20.
+#   fast sin/cos: the angle (2) and the SFU argument scaling (1) on the FP32
+#     pipe, sin and cos on the special-function unit (16 lanes per SM against
+#     128 FP32 lanes: each SFU op occupies its pipe for the time of 8 FP32
+#     ops): 3 + 2 x 8.
+#   explicit internal node: butterflies (8), xi (2), three sigma (6),
+#     gamma.sigma (6), Kahan add (8): 30.
+#   regrouped: a leaf adds xi to its parent's sum (2) and w xi to its
+#     parent's plain sum of leaf terms (2); an internal node adds w xi to V
+#     (2, with a Kahan add of 8) and passes xi to its parent's sum (2).
+OPS_LEAF = 33 + 20
+OPS_NODE = 30
+OPS_LEAF_FAST = 33 + 3 + 2 * 8
+OPS_RG_LEAF = 2 + 2
+OPS_RG_NODE = 2 + 8 + 2
+OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE),
+       ("fast", "explicit"): (OPS_LEAF_FAST, OPS_NODE),
+       ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE),
+       ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE)}
+# DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
+# a form whose kernel changed since its capture has no entry.
+TRAFFIC_BYTES_MEDIUM_J12 = {}
 # Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
 HBM_PEAK_GBPS = 6690.1
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
@@ -388,6 +416,8 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
                                    ("wavelet_fp64_eq16", wt.WT_FP64, wt.WT_SUM_EQ16, out64),
                                    ("wavelet_mixed_eq16", wt.WT_MIXED, wt.WT_SUM_EQ16, out32),
                                    ("wavelet_mixed_fast_eq17", wt.WT_MIXED_FAST, wt.WT_SUM_EQ17, out32),
+                                   ("wavelet_mixed_fast_eq17_regrouped", wt.WT_MIXED_FAST, wt.WT_SUM_EQ17_REGROUPED,
+                                    out32),
                                    ("wavelet_mixed_fast_eq16", wt.WT_MIXED_FAST, wt.WT_SUM_EQ16, out32)]:
         t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out), stream, flush)
         r[name + "_vis_per_s"] = n / t
@@ -443,7 +473,8 @@ def batched_measurement(wt, torch, dev, stream, flush):
 
     def per_channel():
         for c in range(len(chans)):
-            wt.wt_predict_vis(trees[c], uvws[c], mode=wt.WT_MIXED_FAST, out=outs[c])
+            wt.wt_predict_vis(trees[c], uvws[c], mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ17_REGROUPED,
+                              out=outs[c])
     per_channel()
     t_p = _time_call(per_channel, stream, flush, reps=3)
     sizes = [t.info() for t in trees]
@@ -456,7 +487,7 @@ def batched_measurement(wt, torch, dev, stream, flush):
             "nodes_range": [min(x["n_nodes"] for x in sizes), max(x["n_nodes"] for x in sizes)],
             "graph_launch_vis_per_s": total_vis / t_b, "per_channel_launches_vis_per_s": total_vis / t_p,
             "graph_launch_ms": t_b * 1e3, "per_channel_ms": t_p * 1e3, "max_rel_err_vs_fp64_oracle": err,
-            "form": "WT_MIXED_FAST Eq. 17"}
+            "form": "WT_MIXED_FAST Eq. 17 regrouped (both legs)"}
 
 
 def mixed_measurement(wt, torch, dev, stream, flush):
@@ -472,24 +503,34 @@ def mixed_measurement(wt, torch, dev, stream, flush):
     tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, w.J)
     info = tree.info()
     out["n_leaves"], out["n_nodes"] = info["n_leaves"], info["n_nodes"]
-    errs_w, errs_d, tw, td = [], [], 0.0, 0.0
+    rg = wt.WT_SUM_EQ17_REGROUPED
+    forms = [("wavelet_mixed", wt.WT_MIXED, wt.WT_SUM_EQ17), ("wavelet_mixed_regrouped", wt.WT_MIXED, rg),
+             ("wavelet_mixed_fast_regrouped", wt.WT_MIXED_FAST, rg)]
+    errs = {n: [] for n, _, _ in forms}
+    tws = {n: 0.0 for n, _, _ in forms}
+    errs_d, td = [], 0.0
     ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J)
     for fr in w.extra["freqs"]:
         uvw_np = w.extra["uvw_m"] * (fr / synth.C_LIGHT)
         uvw = d(uvw_np)
         vw = torch.empty(uvw.shape[0], dtype=torch.complex64, device=dev)
         vd = torch.empty_like(vw)
-        wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=vw)
-        wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd)
-        tw += _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=vw), stream, flush)
-        td += _time_call(lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd), stream, flush, reps=1)
         idx = np.arange(0, uvw_np.shape[0], uvw_np.shape[0] // 400)
-        errs_w.append(float(np.max(np.abs(vw.cpu().numpy()[idx] - ot.vis_eq17(uvw_np[idx]))) / S))
+        ref = ot.vis_eq17(uvw_np[idx])
+        for name, mode, which in forms:
+            wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=vw)
+            tws[name] += _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=vw), stream,
+                                    flush)
+            errs[name].append(float(np.max(np.abs(vw.cpu().numpy()[idx] - ref)) / S))
+        wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd)
+        td += _time_call(lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd), stream, flush, reps=1)
         errs_d.append(float(np.max(np.abs(vd.cpu().numpy()[idx] - O.dft(w.l, w.m, w.flux, uvw_np[idx]))) / S))
     n_tot = 2 * out["n_vis_per_ch"]
     tree.close()
-    out.update({"wavelet_mixed_vis_per_s": n_tot / tw, "wavelet_max_rel_err": max(errs_w),
-                "dft_mixed_vis_per_s": n_tot / td, "dft_mixed_vis_terms_per_s": n_tot * w.n_comp / td,
+    for name, _, _ in forms:
+        out[name + "_vis_per_s"] = n_tot / tws[name]
+        out[name + "_max_rel_err"] = max(errs[name])
+    out.update({"dft_mixed_vis_per_s": n_tot / td, "dft_mixed_vis_terms_per_s": n_tot * w.n_comp / td,
                 "dft_max_rel_err": max(errs_d)})
     return out
 
@@ -694,6 +735,29 @@ def forms_once(args):
             ("dft_mixed", lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=o32)),
             ("dft_fp64_131072", lambda: wt.dft_predict_vis(l, m, f, sub, mode=wt.WT_FP64, out=o64[:131072])),
             ("subtract_c64", lambda: wt.subtract_model(o32, o32, mode=wt.WT_MIXED, out=o32))]
+    # the learned response's tensor-core inference on every visibility
+    mlp = wt.Mlp(w.J, w.ra0, w.dec0, depth=3, x_max=1e30, seed=1)
+    r_out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+    runs.append(("mlp_eval", lambda: mlp.eval(uvw, out=r_out)))
+    # batched: 8 channels of the medium workload's components at 1.0 .. 1.8 GHz
+    freqs = list(np.linspace(1.0e9, 1.8e9, 8))
+    btrees = [wt.wt_build_tree(l, m, f, w.ra0, w.dec0, 10 + (c % 4)) for c in range(8)]
+    uvw_m = d(w.uvw * (synth.C_LIGHT / 1.4e9))
+    b_out = torch.empty((8, w.n_vis), dtype=torch.complex64, device=dev)
+    runs.append(("batched_8ch", lambda: wt.wt_predict_vis_batched(btrees, freqs, uvw_m, mode=wt.WT_MIXED_FAST,
+                                                                   out=b_out)))
+    # the subtraction where HBM sets the time: 64 Mi complex64
+    big_a = torch.zeros(64 * 1024 * 1024, dtype=torch.complex64, device=dev)
+    big_b = torch.zeros_like(big_a)
+    runs.append(("subtract_64Mi", lambda: wt.subtract_model(big_a, big_b, mode=wt.WT_MIXED, out=big_a)))
+    runs.append(("build_tree", lambda: wt.wt_build_tree(l, m, f, w.ra0, w.dec0, w.J).close()))
+    rg = wt.WT_SUM_EQ17_REGROUPED
+    runs.append(("wavelet_mixed_fast_regrouped",
+                 lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED_FAST, which=rg, out=o32)))
+    runs.append(("wavelet_mixed_regrouped", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, which=rg, out=o32)))
+    if args.only:
+        keep = set(args.only.split(","))
+        runs = [(n, fn) for n, fn in runs if n in keep]
     for name, fn in runs:
         fn()
         torch.cuda.synchronize()
@@ -701,6 +765,9 @@ def forms_once(args):
         torch.cuda.synchronize()
     wt.wt_device_status()
     tree.close()
+    for t in btrees:
+        t.close()
+    mlp.close()
     print("forms-once ok: " + ", ".join(n for n, _ in runs), flush=True)
 
 

@@ -3,9 +3,10 @@
 // The best shape (threads per CTA x visibilities per thread) depends on the
 // tree (depth J sets the per-thread stack, node count the work per
 // visibility) and on the form. The first call for a new key times every
-// shape that fits on a sample of the caller's own visibilities (up to
-// 131 072 of them, written into the caller's output buffer, which the real
-// launch then overwrites) and remembers the fastest. Keys are (device, form,
+// shape that fits on a sample of the caller's own visibilities (two waves
+// of the shape's resident CTAs, at least 131 072 and at most all of them,
+// written into the caller's output buffer, which the real launch then
+// overwrites) and remembers the one with the least time per visibility. Keys are (device, form,
 // sum, J, log2 of the node count, log2 of the leaf count).
 //
 // Tuning synchronises the caller's stream once. It is skipped, in favour of
@@ -81,6 +82,26 @@ void append_file(const std::string& key, int v)
 
 }  // namespace
 
+// Visibilities a variant is timed on: two full waves of its resident CTAs
+// (as many as fit an SM by shared memory and threads; registers may admit
+// fewer, which only adds waves), so that small-CTA shapes are measured at
+// the occupancy they reach on a large batch, not on a sample that leaves
+// SMs idle; at least 131072, at most the whole batch. Variants are compared
+// by time per visibility.
+static int64_t sample_size(int v, const WaveletJob& jb)
+{
+    int nt = 0, vpt = 0;
+    wavelet_variant_shape(v, &nt, &vpt);
+    const size_t smem = wavelet_variant_smem(v, jb.mode, jb.which, jb.J) + 1024;   // + per-CTA reserve
+    int64_t per_sm = static_cast<int64_t>((228 * 1024) / smem);
+    if (per_sm > 2048 / nt) per_sm = 2048 / nt;
+    if (per_sm > 32) per_sm = 32;
+    if (per_sm < 1) per_sm = 1;
+    int64_t n = 2 * static_cast<int64_t>(num_sms()) * per_sm * nt * vpt;
+    if (n < 131072) n = 131072;
+    return n < jb.n_vis ? n : jb.n_vis;
+}
+
 int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s)
 {
     const int fallback = default_wavelet_variant(jb.mode, jb.which, jb.J);
@@ -110,7 +131,6 @@ int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s)
         if (it != g_cache.end()) return it->second;
     }
     WaveletJob sample = jb;
-    sample.n_vis = jb.n_vis < 131072 ? jb.n_vis : 131072;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -120,6 +140,7 @@ int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s)
     float best_ms = 1e30f;
     for (int v = 0; v < kNumWaveletVariants; ++v) {
         if (!wavelet_variant_fits(v, jb.mode, jb.which, jb.J)) continue;
+        sample.n_vis = sample_size(v, jb);
         if (launch_wavelet(sample, v, s) != WT_OK) continue;   // warm-up
         cudaEventRecord(e0, s);
         bool ok = launch_wavelet(sample, v, s) == WT_OK;
@@ -130,14 +151,15 @@ int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s)
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        const float per_vis = ms / static_cast<float>(sample.n_vis);
         if (verbose()) {
             int nt = 0, vpt = 0;
             wavelet_variant_shape(v, &nt, &vpt);
             fprintf(stderr, "[wt autotune] %s variant %d (%d threads x %d vis): %.4f ms for %lld vis\n", key.c_str(), v,
                     nt, vpt, ms, static_cast<long long>(sample.n_vis));
         }
-        if (ms < best_ms) {
-            best_ms = ms;
+        if (per_vis < best_ms) {
+            best_ms = per_vis;
             best = v;
         }
     }

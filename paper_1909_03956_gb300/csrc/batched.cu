@@ -3,12 +3,15 @@
 //
 // Work items are (channel, tile of NT * VPT visibilities). Channels are
 // ordered by decreasing tree size (largest work first), items numbered
-// channel-major in that order, and CTAs (one or two per SM, persistent) take
-// the next item from a device-wide atomic counter, so channels of very
+// channel-major in that order, and CTAs (as many per SM as fit, persistent)
+// take the next item from a device-wide atomic counter, so channels of very
 // uneven size keep every SM busy to the end. Items depend on nothing but
 // their own inputs: no CTA ever waits for another. A CTA re-targets its
 // shared-memory record staging only when the channel changes. Baselines are
-// shared in metres and scaled per channel, u_lambda = u_m f_c / c.
+// shared in metres and scaled per channel, u_lambda = u_m f_c / c. The
+// float64 form evaluates Eq. 17 explicitly (Eq17D), the mixed forms in the
+// regrouped order (Eq17WF: one stack pair per level, so small CTAs fit many
+// to an SM).
 //
 // The memset of the counter plus the kernel are captured once into a CUDA
 // graph per plan (tree set, frequencies, form, sign, buffers, launch shape)
@@ -36,7 +39,7 @@ constexpr double kLightSpeed = 299792458.0;   // m/s
 
 struct BatchChan {
     const RecD* recd;
-    const RecF* recf;
+    const RecWF* recwf;
     const TreeHeader* hdr;
     double scale;          // f_c / c: metres -> wavelengths
     int64_t out_offset;    // channel * n_vis
@@ -62,8 +65,8 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
                                                 const double* __restrict__ uvw_m, int64_t n_vis, void* vis, double sgn,
                                                 int rows_max, unsigned long long* queue, int* status)
 {
-    using Rec = typename std::conditional<MIXED, RecF, RecD>::type;
-    constexpr int kChunk = MIXED ? kChunkF : kChunkD;
+    using Rec = typename std::conditional<MIXED, RecWF, RecD>::type;
+    constexpr int kChunk = MIXED ? kChunkW : kChunkD;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
     Stager<Rec> st;
@@ -82,16 +85,17 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
         const BatchChan ch = chans[c];
         if (c != cur) {
             const Rec* recs;
-            if constexpr (MIXED) recs = ch.recf;
+            if constexpr (MIXED) recs = ch.recwf;
             else recs = ch.recd;
             st.retarget(recs, ch.hdr->n_nodes);
             cur = c;
-            maxrow = min(4 * (ch.J > 1 ? ch.J - 1 : 1), rows_max) - 1;
+            if constexpr (MIXED) maxrow = min(ch.J > 3 ? ch.J - 2 : 1, rows_max) - 1;
+            else maxrow = min(4 * (ch.J > 1 ? ch.J - 1 : 1), rows_max) - 1;
         }
         const int64_t n0 = (item - ch.tile_base) * per_tile + threadIdx.x;
         bool good;
         if constexpr (MIXED) {
-            Eq17F<NT, VPT, FAST> b;
+            Eq17WF<NT, VPT, FAST> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const int64_t n = n0 + static_cast<int64_t>(k) * NT;
@@ -100,17 +104,17 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
                 b.u[k] = split_f64(ok ? uvw_m[3 * n] * s : 0.0);
                 b.v[k] = split_f64(ok ? uvw_m[3 * n + 1] * s : 0.0);
                 b.w[k] = split_f64(ok ? uvw_m[3 * n + 2] * s : 0.0);
-                b.vr[k] = 0.f; b.vi[k] = 0.f; b.cr[k] = 0.f; b.ci[k] = 0.f;
             }
-            b.sgn = 1.0f;
+            b.start();
             b.stk = reinterpret_cast<float2*>(stk_base) + threadIdx.x;
+            b.J = ch.J;
             b.maxrow = maxrow;
             good = st.sweep(b);
             float2* out = static_cast<float2*>(vis) + ch.out_offset;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const int64_t n = n0 + static_cast<int64_t>(k) * NT;
-                if (good && n < n_vis) out[n] = make_float2(b.vr[k] - b.cr[k], b.vi[k] - b.ci[k]);
+                if (good && n < n_vis) out[n] = b.result(k);
             }
         } else {
             Eq17D<NT, VPT> b;
@@ -146,17 +150,38 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
 struct Shape {
     int nt, vpt;
 };
-constexpr int kNumBatchShapes = 5;
-const Shape kBatchShapes[kNumBatchShapes] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}, {32, 1}};
+constexpr int kNumBatchShapes = 6;
+const Shape kBatchShapes[kNumBatchShapes] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}, {32, 1}, {32, 2}};
+
+// Stack rows for the deepest tree of a plan: the explicit float64 sum keeps
+// four child slots per level, the regrouped mixed sum one pair per level.
+int batch_rows(int mode, int jmax)
+{
+    if (mode == WT_FP64) return jmax > 1 ? 4 * (jmax - 1) : 4;
+    return jmax > 3 ? jmax - 2 : 1;
+}
 
 size_t batch_smem(int mode, int shape, int rows_max)
 {
     const size_t cplx = mode == WT_FP64 ? sizeof(double2) : sizeof(float2);
-    const size_t stage = mode == WT_FP64 ? stager_bytes<RecD>(kChunkD) : stager_bytes<RecF>(kChunkF);
+    const size_t stage = mode == WT_FP64 ? stager_bytes<RecD>(kChunkD) : stager_bytes<RecWF>(kChunkW);
     return stage + static_cast<size_t>(rows_max) * kBatchShapes[shape].nt * kBatchShapes[shape].vpt * cplx;
 }
 
 bool batch_fits(int mode, int shape, int rows_max) { return batch_smem(mode, shape, rows_max) <= 220 * 1024; }
+
+// Shape used without timing (WT_AUTOTUNE=0, or under stream capture): the
+// first that fits in a measured preference order (the regrouped mixed sum
+// runs best with two visibilities per thread in small CTAs).
+int default_shape(int mode, int rows_max)
+{
+    static const int order_fp64[kNumBatchShapes] = {0, 1, 2, 3, 4, 5};
+    static const int order_mixed[kNumBatchShapes] = {5, 2, 3, 0, 1, 4};
+    const int* order = (mode == WT_FP64) ? order_fp64 : order_mixed;
+    for (int i = 0; i < kNumBatchShapes; ++i)
+        if (batch_fits(mode, order[i], rows_max)) return order[i];
+    return -1;
+}
 
 template <int NT, int VPT, bool MIXED, bool FAST = false>
 int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
@@ -183,7 +208,8 @@ int set_attr(int shape, size_t smem)
         case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, MIXED, FAST>); break;
         case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, MIXED, FAST>); break;
         case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, MIXED, FAST>); break;
-        default: fn = reinterpret_cast<const void*>(k_batched<32, 1, MIXED, FAST>); break;
+        case 4: fn = reinterpret_cast<const void*>(k_batched<32, 1, MIXED, FAST>); break;
+        default: fn = reinterpret_cast<const void*>(k_batched<32, 2, MIXED, FAST>); break;
     }
     WT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     return WT_OK;
@@ -200,7 +226,8 @@ int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t 
             case 1: return launch_shape<128, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
             case 2: return launch_shape<128, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
             case 3: return launch_shape<64, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            default: return launch_shape<32, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 4: return launch_shape<32, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            default: return launch_shape<32, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
         }
     }
     if (mode == WT_MIXED_FAST) {
@@ -209,7 +236,8 @@ int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t 
             case 1: return launch_shape<128, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
             case 2: return launch_shape<128, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
             case 3: return launch_shape<64, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            default: return launch_shape<32, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            case 4: return launch_shape<32, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+            default: return launch_shape<32, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
         }
     }
     switch (shape) {
@@ -217,7 +245,8 @@ int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t 
         case 1: return launch_shape<128, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
         case 2: return launch_shape<128, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
         case 3: return launch_shape<64, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        default: return launch_shape<32, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 4: return launch_shape<32, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        default: return launch_shape<32, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
     }
 }
 
@@ -280,7 +309,7 @@ int write_table(Plan& p, int64_t n_vis, int shape, cudaStream_t s)
         wt_tree t = p.trees[c];
         BatchChan& b = h[i];
         b.recd = t->d.recd;
-        b.recf = t->d.recf;
+        b.recwf = t->d.recwf;
         b.hdr = t->d.hdr;
         b.scale = p.freqs[c] / kLightSpeed;
         b.out_offset = static_cast<int64_t>(c) * n_vis;
@@ -301,12 +330,7 @@ int write_table(Plan& p, int64_t n_vis, int shape, cudaStream_t s)
 
 int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cudaStream_t s)
 {
-    int first = -1;
-    for (int sh = 0; sh < kNumBatchShapes; ++sh)
-        if (batch_fits(p.mode, sh, p.rows_max)) {
-            first = sh;
-            break;
-        }
+    const int first = default_shape(p.mode, p.rows_max);
     if (first < 0) return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis_batched: no launch shape fits J");
     const char* e = getenv("WT_AUTOTUNE");
     if (e && e[0] == '0') return first;
@@ -389,7 +413,7 @@ int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const
             np->nodes[c] = trees[c]->host_hdr->n_nodes;
             if (trees[c]->J > jmax) jmax = trees[c]->J;
         }
-        np->rows_max = jmax > 1 ? 4 * (jmax - 1) : 4;
+        np->rows_max = batch_rows(mode, jmax);
         np->order.resize(n_ch);
         for (int c = 0; c < n_ch; ++c) np->order[c] = c;
         std::stable_sort(np->order.begin(), np->order.end(),
@@ -408,8 +432,8 @@ int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         WT_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
         if (cs != cudaStreamCaptureStatusNone) {
-            for (int sh = 0; sh < kNumBatchShapes && p->shape < 0; ++sh)
-                if (batch_fits(mode, sh, p->rows_max)) p->shape = sh;
+            p->shape = default_shape(mode, p->rows_max);
+            if (p->shape < 0) return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis_batched: no launch shape fits J");
         } else {
             const int best = tune(*p, uvw_m, n_vis, vis, status, s);
             if (best < 0) return best;

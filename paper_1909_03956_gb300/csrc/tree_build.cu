@@ -393,13 +393,21 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
             rd.c = g2;
             rd.d = q;
             rd.e = root;
-            rf.a = static_cast<float>(g0);
-            rf.b = static_cast<float>(g1);
-            rf.c = static_cast<float>(g2);
-            rf.d = static_cast<float>(q);
+            // mixed forms: xi = 4^(J-j) eta, scale factors folded in (RecF)
+            const double sc = ldexp(q, -2 * (J - j - 1));
+            if (single) {
+                rf.a = static_cast<float>(((g0 + g1) + g2) * sc);
+                rf.b = 0.0f;
+                rf.c = 0.0f;
+            } else {
+                rf.a = static_cast<float>(g0 * sc);
+                rf.b = static_cast<float>(g1 * sc);
+                rf.c = static_cast<float>(g2 * sc);
+            }
+            rf.d = 0.0f;
             rf.e = 0.0f;
             rf.f = 0.0f;
-            rf.g = static_cast<float>(root);
+            rf.g = static_cast<float>(ldexp(root, -2 * (J - 1)));
         }
         d.recd[post] = rd;
         d.recf[post] = rf;
@@ -436,7 +444,7 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         wf.d = leaf ? rf.d : 0.f;
         wf.e = leaf ? rf.e : 0.f;
         wf.f = leaf ? rf.f : 0.f;
-        wf.g = static_cast<float>(wgt);
+        wf.g = static_cast<float>(ldexp(wgt, -2 * (J - j)));   // weight of xi = 4^(J-j) eta
         if (!leaf) {
             wd.a = wd.b = wd.c = 0.0;
         }

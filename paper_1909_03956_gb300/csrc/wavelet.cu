@@ -18,7 +18,9 @@
 // Per internal node the kernel forms eta (Eq. 9 form) and the three sigma
 // (Eq. 10 form) explicitly and adds gamma^m sigma^m. A node with a single
 // child needs no butterfly: its sigma^m are +-q eta_c, the sign folded into
-// gamma^m by the build.
+// gamma^m by the build. The mixed forms carry xi = 4^(J-j) eta instead of
+// eta, with the scale factors folded into gamma by the build, and do their
+// float32 arithmetic on packed pairs (wavelet_bodies.cuh).
 //
 // Forms:
 //   WT_FP64   float64 throughout; sin/cos by table-driven reduction
@@ -118,10 +120,11 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
                                                       int* status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int kChunk = (SUM == 2) ? kChunkW : kChunkF;
     Stager<Rec> st;
     const int64_t count = (SUM == 1) ? hdr->n_leaves : hdr->n_nodes;
-    stager_setup(st, smem, recs, count, kChunkF);
-    float2* stk = reinterpret_cast<float2*>(smem + stager_bytes<Rec>(kChunkF)) + threadIdx.x;
+    stager_setup(st, smem, recs, count, kChunk);
+    float2* stk = reinterpret_cast<float2*>(smem + stager_bytes<Rec>(kChunk)) + threadIdx.x;
     const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -152,30 +155,32 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
         } else if constexpr (SUM == 0) {
             Eq17F<NT, VPT, FAST> b;
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
-                b.vr[k] = 0.f; b.vi[k] = 0.f; b.cr[k] = 0.f; b.ci[k] = 0.f;
-            }
-            b.sgn = sgn;
+            for (int k = 0; k < VPT; ++k) { b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k]; }
+            b.start();
             b.stk = stk;
             b.maxrow = rows - 1;
             good = st.sweep(b);
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
+            for (int k = 0; k < VPT; ++k) {
+                const float2 r = b.result(k);
+                vr[k] = r.x;
+                vi[k] = r.y;
+            }
         } else {
             Eq17WF<NT, VPT, FAST> b;
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
-                b.vr[k] = 0.f; b.vi[k] = 0.f; b.cr[k] = 0.f; b.ci[k] = 0.f;
-                b.sr[k] = 0.f; b.si[k] = 0.f; b.xr[k] = 0.f; b.xi[k] = 0.f;
-            }
+            for (int k = 0; k < VPT; ++k) { b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k]; }
+            b.start();
             b.stk = stk;
             b.J = J;
             b.maxrow = rows - 1;
             good = st.sweep(b);
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
+            for (int k = 0; k < VPT; ++k) {
+                const float2 r = b.result(k);
+                vr[k] = r.x;
+                vi[k] = r.y;
+            }
         }
         if (!good) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
@@ -209,19 +214,29 @@ int prepare(K kernel, int nt, size_t smem, int64_t per_tile, int64_t n_vis, dim3
 }
 
 // Shared-memory stack rows a form needs for a tree of depth J.
-int stack_rows(int which, int J)
+int stack_rows(int mode, int which, int J)
 {
     if (which == WT_SUM_EQ16) return 0;
-    if (which == WT_SUM_EQ17_REGROUPED) return J > 3 ? 2 * (J - 2) : 2;
+    if (which == WT_SUM_EQ17_REGROUPED) {
+        if (mode == WT_FP64) return J > 3 ? 2 * (J - 2) : 2;
+        return J > 3 ? J - 2 : 1;
+    }
     return J > 1 ? 4 * (J - 1) : 4;
+}
+
+// Staging bytes of a form (two buffers of records plus the mbarriers).
+size_t stage_bytes(int mode, int which)
+{
+    if (mode == WT_FP64) return stager_bytes<RecD>(kChunkD);
+    return (which == WT_SUM_EQ17_REGROUPED) ? stager_bytes<RecWF>(kChunkW) : stager_bytes<RecF>(kChunkF);
 }
 
 template <int NT, int VPT>
 int run_fp64(const WaveletJob& jb, cudaStream_t s)
 {
-    const int rows = stack_rows(jb.which, jb.J);
+    const int rows = stack_rows(WT_FP64, jb.which, jb.J);
     const size_t stack = static_cast<size_t>(rows) * VPT * NT * sizeof(double2);
-    const size_t smem = static_cast<size_t>(stager_bytes<RecD>(kChunkD)) + stack;
+    const size_t smem = stage_bytes(WT_FP64, jb.which) + stack;
     dim3 grid;
     int rc;
     double2* out = static_cast<double2*>(jb.vis);
@@ -246,9 +261,9 @@ int run_fp64(const WaveletJob& jb, cudaStream_t s)
 template <int NT, int VPT, bool FAST>
 int run_mixed_form(const WaveletJob& jb, cudaStream_t s)
 {
-    const int rows = stack_rows(jb.which, jb.J);
+    const int rows = stack_rows(jb.mode, jb.which, jb.J);
     const size_t stack = static_cast<size_t>(rows) * VPT * NT * sizeof(float2);
-    const size_t smem = static_cast<size_t>(stager_bytes<RecF>(kChunkF)) + stack;
+    const size_t smem = stage_bytes(jb.mode, jb.which) + stack;
     dim3 grid;
     int rc;
     float2* out = static_cast<float2*>(jb.vis);
@@ -295,13 +310,19 @@ int wavelet_variant_shape(int v, int* nt, int* vpt)
 
 // Shared memory a variant needs for a tree of depth J (stack only; the
 // staging buffers add a fixed amount).
+size_t wavelet_variant_smem(int v, int mode, int which, int J)
+{
+    if (v < 0 || v >= kNumWaveletVariants) return 0;
+    const size_t cplx = (mode == WT_FP64) ? sizeof(double2) : sizeof(float2);
+    const size_t stage = stage_bytes(mode, which);
+    const size_t stack = static_cast<size_t>(stack_rows(mode, which, J)) * kVariants[v].nt * kVariants[v].vpt * cplx;
+    return stage + stack;
+}
+
 bool wavelet_variant_fits(int v, int mode, int which, int J)
 {
     if (v < 0 || v >= kNumWaveletVariants) return false;
-    const size_t cplx = (mode == WT_FP64) ? sizeof(double2) : sizeof(float2);
-    const size_t stage = (mode == WT_FP64) ? stager_bytes<RecD>(kChunkD) : stager_bytes<RecF>(kChunkF);
-    const size_t stack = static_cast<size_t>(stack_rows(which, J)) * kVariants[v].nt * kVariants[v].vpt * cplx;
-    return stage + stack <= 220 * 1024;
+    return wavelet_variant_smem(v, mode, which, J) <= 220 * 1024;
 }
 
 int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
@@ -332,12 +353,18 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
     }
 }
 
-// Default when nothing is tuned: the widest variant whose stack fits.
+// Default when nothing is tuned: the first variant that fits in a measured
+// preference order.
 int default_wavelet_variant(int mode, int which, int J)
 {
+    // measured on the medium workload (J = 12): the explicit mixed sum runs
+    // best at 256 x 1 (its stack limits the CTAs per SM), the regrouped one,
+    // whose stack is small, with two visibilities per thread in small CTAs
     static const int order_mixed[kNumWaveletVariants] = {0, 2, 1, 3, 4, 5, 6, 7};
+    static const int order_mixed_rg[kNumWaveletVariants] = {6, 2, 3, 4, 5, 0, 1, 7};
     static const int order_fp64[kNumWaveletVariants] = {1, 0, 2, 3, 4, 5, 6, 7};
-    const int* order = (mode == WT_FP64) ? order_fp64 : order_mixed;
+    const int* order = (mode == WT_FP64) ? order_fp64
+                       : (which == WT_SUM_EQ17_REGROUPED) ? order_mixed_rg : order_mixed;
     for (int i = 0; i < kNumWaveletVariants; ++i)
         if (wavelet_variant_fits(order[i], mode, which, J)) return order[i];
     return kNumWaveletVariants - 1;

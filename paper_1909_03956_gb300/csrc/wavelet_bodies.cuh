@@ -12,6 +12,8 @@ namespace {
 
 constexpr int kChunkD = 256;   // records per staging buffer (48 B each)
 constexpr int kChunkF = 384;   // (32 B each)
+constexpr int kChunkW = 128;   // regrouped float32 form (32 B each): its stack is small, so the
+                               // staging buffers set how many CTAs fit on an SM
 
 __device__ __forceinline__ int clamp_row(uint32_t r, int maxrow) { return min(static_cast<int>(r), maxrow); }
 
@@ -112,15 +114,47 @@ struct Eq16D {
 };
 
 // ---------------------------------------------------------------- mixed
+// Eq. 17 in the mixed forms, on packed float32 pairs. A thread's stack
+// holds xi = 4^(J-j) eta (RecF): a node's xi is the plain sum of its
+// children's, and gamma^m sigma^m = a_m (H_m xi_children) with the scale
+// factors already in a_m. A complex value is one pair; the leaf phases of
+// visibilities 2p and 2p + 1 are formed as one pair (VPT = 1 forms its one
+// phase on scalars). Per visibility a four-child node costs 15 paired
+// operations, Kahan included.
 template <int NT, int VPT, bool FAST = false>
 struct Eq17F {
-    F2 u[VPT], v[VPT], w[VPT];
-    float vr[VPT], vi[VPT], cr[VPT], ci[VPT];   // Kahan sums and compensations
-    float sgn;
+    static constexpr int NP = VPT / 2;                // visibility pairs
+    static constexpr bool ODD = (VPT & 1) != 0;       // a last, unpaired visibility
+    F2 u[VPT], v[VPT], w[VPT];                        // set by the caller, then start()
+    DF2 U[NP > 0 ? NP : 1], V[NP > 0 ? NP : 1], W[NP > 0 ? NP : 1];
+    float2 acc[VPT], comp[VPT];                       // Kahan sum of V and its compensation
     float2* stk;
     int maxrow;
 
     __device__ __forceinline__ float2& slot(int row, int k) { return stk[(row * VPT + k) * NT]; }
+
+    __device__ __forceinline__ void start()
+    {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            U[p] = df2_pack(u[2 * p], u[2 * p + 1]);
+            V[p] = df2_pack(v[2 * p], v[2 * p + 1]);
+            W[p] = df2_pack(w[2 * p], w[2 * p + 1]);
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            acc[k] = make_float2(0.f, 0.f);
+            comp[k] = make_float2(0.f, 0.f);
+        }
+    }
+
+    __device__ __forceinline__ float2 result(int k) const { return sub2(acc[k], comp[k]); }
+
+    __device__ __forceinline__ void emit(int k, bool root, int srow, float g, float2 e)
+    {
+        if (root) kahan_add2(acc[k], comp[k], mul2(bcast2(g), e));
+        else slot(srow, k) = e;
+    }
 
     __device__ void operator()(const RecF& r)
     {
@@ -130,39 +164,35 @@ struct Eq17F {
         if (meta & kRecLeaf) {
             const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
+            for (int p = 0; p < NP; ++p) {
+                float2 th, tl, s, c;
+                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, th, tl);
+                sincos_mixed2<FAST>(th, tl, s, c);
+                emit(2 * p, root, srow, r.g, make_float2(c.x, s.x));
+                emit(2 * p + 1, root, srow, r.g, make_float2(c.y, s.y));
+            }
+            if constexpr (ODD) {
+                constexpr int k = VPT - 1;
                 float th, tl, s, c;
                 phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
                 sincos_mixed<FAST>(th, tl, s, c);
-                const float ei = s;
-                if (root) {
-                    kahan_add(vr[k], cr[k], r.g * c);
-                    kahan_add(vi[k], ci[k], r.g * ei);
-                } else {
-                    slot(srow, k) = make_float2(c, ei);
-                }
+                emit(k, root, srow, r.g, make_float2(c, s));
             }
         } else if (meta & kRecSingle) {
             const int crow = clamp_row(rec_child_row(meta), maxrow);
+            const float2 a = bcast2(r.a), g = bcast2(r.g);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
-                const float2 c = slot(crow, k);
-                const float er = 0.25f * c.x, ei = 0.25f * c.y;
-                const float sr = r.d * c.x, si = r.d * c.y;
-                float xr = fmaf(r.a, sr, fmaf(r.b, sr, r.c * sr));
-                float xi = fmaf(r.a, si, fmaf(r.b, si, r.c * si));
-                if (root) {
-                    xr = fmaf(r.g, er, xr);
-                    xi = fmaf(r.g, ei, xi);
-                } else {
-                    slot(srow, k) = make_float2(er, ei);
-                }
-                kahan_add(vr[k], cr[k], xr);
-                kahan_add(vi[k], ci[k], xi);
+                const float2 xi = slot(crow, k);             // the node's xi is its child's
+                float2 x = mul2(a, xi);
+                if (root) x = fma2(g, xi, x);
+                else slot(srow, k) = xi;
+                kahan_add2(acc[k], comp[k], x);
             }
         } else {
             const int crow = clamp_row(rec_child_row(meta), maxrow - 3);
             const uint32_t mask = rec_mask(meta);
+            const float2 ga = bcast2(r.a), gb = bcast2(r.b), gc = bcast2(r.c), g = bcast2(r.g);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 float2 c0 = make_float2(0.f, 0.f), c1 = c0, c2 = c0, c3 = c0;
@@ -170,25 +200,14 @@ struct Eq17F {
                 if (mask & 2u) c1 = slot(crow + 1, k);
                 if (mask & 4u) c2 = slot(crow + 2, k);
                 if (mask & 8u) c3 = slot(crow + 3, k);
-                const float ar = c0.x + c1.x, ai = c0.y + c1.y;
-                const float br = c0.x - c1.x, bi = c0.y - c1.y;
-                const float cr_ = c2.x + c3.x, ci_ = c2.y + c3.y;
-                const float dr = c2.x - c3.x, di = c2.y - c3.y;
-                const float er = 0.25f * (ar + cr_), ei = 0.25f * (ai + ci_);
-                const float q = r.d;
-                const float s0r = q * (br + dr), s0i = q * (bi + di);
-                const float s1r = q * (ar - cr_), s1i = q * (ai - ci_);
-                const float s2r = q * (br - dr), s2i = q * (bi - di);
-                float xr = fmaf(r.a, s0r, fmaf(r.b, s1r, r.c * s2r));
-                float xi = fmaf(r.a, s0i, fmaf(r.b, s1i, r.c * s2i));
-                if (root) {
-                    xr = fmaf(r.g, er, xr);
-                    xi = fmaf(r.g, ei, xi);
-                } else {
-                    slot(srow, k) = make_float2(er, ei);
-                }
-                kahan_add(vr[k], cr[k], xr);
-                kahan_add(vi[k], ci[k], xi);
+                const float2 a = add2(c0, c1), b = sub2(c0, c1);   // c0 +- c1
+                const float2 c = add2(c2, c3), d = sub2(c2, c3);   // c2 +- c3
+                const float2 xi = add2(a, c);                      // Eq. 9 (times 4^(J-j))
+                // Eq. 10 rows (+ - + -), (+ + - -), (+ - - +), weighted by gamma
+                float2 x = fma2(ga, add2(b, d), fma2(gb, sub2(a, c), mul2(gc, sub2(b, d))));
+                if (root) x = fma2(g, xi, x);
+                else slot(srow, k) = xi;
+                kahan_add2(acc[k], comp[k], x);
             }
         }
     }
@@ -293,73 +312,113 @@ struct Eq17WD {
     }
 };
 
+// Regrouped Eq. 17 in the mixed forms: V = sum_n w_n xi_n over every node,
+// xi = 4^(J-j) eta and w_n scaled to match by the build (RecWF). Per
+// visibility a thread keeps one pair per level: the xi sum of the open
+// level-j node (j = 1 .. J-2) in shared-memory row j - 1; the open
+// level-(J-1) node's xi sum, and the plain float32 sum of its leaves'
+// w xi (at most four terms), live in registers, so a leaf touches neither
+// shared memory nor the compensated sum. An internal node reads its xi, adds
+// w xi (plus, at level J-1, its leaves' sum) to V with compensation and
+// passes xi up (the first child writes its parent's sum, the others add).
+// Packed pairs as in Eq17F.
 template <int NT, int VPT, bool FAST = false>
 struct Eq17WF {
-    F2 u[VPT], v[VPT], w[VPT];
-    float vr[VPT], vi[VPT], cr[VPT], ci[VPT];   // Kahan sums and compensations
-    float sr[VPT], si[VPT], xr[VPT], xi[VPT];
+    static constexpr int NP = VPT / 2;
+    static constexpr bool ODD = (VPT & 1) != 0;
+    F2 u[VPT], v[VPT], w[VPT];                        // set by the caller, then start()
+    DF2 U[NP > 0 ? NP : 1], V[NP > 0 ? NP : 1], W[NP > 0 ? NP : 1];
+    float2 acc[VPT], comp[VPT];                       // Kahan sum of V and its compensation
+    float2 low[VPT];                                  // xi sum of the open level-(J-1) node
+    float2 lowx[VPT];                                 // w xi sum of its leaves
     float2* stk;
     int J;
     int maxrow;
 
     __device__ __forceinline__ float2& slot(int row, int k) { return stk[(row * VPT + k) * NT]; }
 
+    __device__ __forceinline__ void start()
+    {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            U[p] = df2_pack(u[2 * p], u[2 * p + 1]);
+            V[p] = df2_pack(v[2 * p], v[2 * p + 1]);
+            W[p] = df2_pack(w[2 * p], w[2 * p + 1]);
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            acc[k] = make_float2(0.f, 0.f);
+            comp[k] = make_float2(0.f, 0.f);
+            low[k] = make_float2(0.f, 0.f);
+            lowx[k] = make_float2(0.f, 0.f);
+        }
+    }
+
+    __device__ __forceinline__ float2 result(int k) const { return sub2(acc[k], comp[k]); }
+
+    // A leaf's sums start from zero: its parent clears them after reading.
+    __device__ __forceinline__ void leaf_up(int k, float2 xi, float2 wv, bool root)
+    {
+        if (root) {                                   // J = 1: the leaf is a level-1 pixel
+            kahan_add2(acc[k], comp[k], mul2(wv, xi));
+            return;
+        }
+        low[k] = add2(low[k], xi);
+        lowx[k] = fma2(wv, xi, lowx[k]);
+    }
+
     __device__ void operator()(const RecWF& r)
     {
         const uint32_t meta = r.meta;
         const int lev = static_cast<int>(meta & 31u);
         const bool root = meta & kRwRoot, first = meta & kRwFirst;
+        const float2 wv = bcast2(r.g);
         if (meta & kRwLeaf) {
             const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
+            for (int p = 0; p < NP; ++p) {
+                float2 th, tl, s, c;
+                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, th, tl);
+                sincos_mixed2<FAST>(th, tl, s, c);
+                leaf_up(2 * p, make_float2(c.x, s.x), wv, root);
+                leaf_up(2 * p + 1, make_float2(c.y, s.y), wv, root);
+            }
+            if constexpr (ODD) {
+                constexpr int k = VPT - 1;
                 float th, tl, s, c;
                 phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
                 sincos_mixed<FAST>(th, tl, s, c);
-                if (root) {
-                    kahan_add(vr[k], cr[k], r.g * c);
-                    kahan_add(vi[k], ci[k], r.g * s);
-                } else if (first) {
-                    sr[k] = c;
-                    si[k] = s;
-                    xr[k] = r.g * c;
-                    xi[k] = r.g * s;
-                } else {
-                    sr[k] += c;
-                    si[k] += s;
-                    xr[k] = fmaf(r.g, c, xr[k]);
-                    xi[k] = fmaf(r.g, s, xi[k]);
-                }
+                leaf_up(k, make_float2(c, s), wv, root);
             }
             return;
         }
-        const bool in_regs = (lev == J - 1);
-        const int own = clamp_row(static_cast<uint32_t>(2 * (lev - 1)), maxrow - 1);
-        const int par = clamp_row(static_cast<uint32_t>(2 * (lev > 1 ? lev - 2 : 0)), maxrow - 1);
+        const int own = clamp_row(static_cast<uint32_t>(lev - 1), maxrow);
+        const int par = clamp_row(static_cast<uint32_t>(lev > 1 ? lev - 2 : 0), maxrow);
+        float2 xi[VPT];
+        if (lev == J - 1) {
 #pragma unroll
-        for (int k = 0; k < VPT; ++k) {
-            float2 S, X;
-            if (in_regs) {
-                S = make_float2(sr[k], si[k]);
-                X = make_float2(xr[k], xi[k]);
-            } else {
-                S = slot(own, k);
-                X = slot(own + 1, k);
+            for (int k = 0; k < VPT; ++k) {
+                xi[k] = low[k];
+                kahan_add2(acc[k], comp[k], fma2(wv, xi[k], lowx[k]));
+                low[k] = make_float2(0.f, 0.f);
+                lowx[k] = make_float2(0.f, 0.f);
             }
-            const float er = 0.25f * S.x, ei = 0.25f * S.y;
-            kahan_add(vr[k], cr[k], X.x);
-            kahan_add(vi[k], ci[k], X.y);
-            if (root) {
-                kahan_add(vr[k], cr[k], r.g * er);
-                kahan_add(vi[k], ci[k], r.g * ei);
-            } else if (first) {
-                slot(par, k) = make_float2(er, ei);
-                slot(par + 1, k) = make_float2(r.g * er, r.g * ei);
-            } else {
+        } else {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                xi[k] = slot(own, k);
+                kahan_add2(acc[k], comp[k], mul2(wv, xi[k]));
+            }
+        }
+        if (root) return;
+        if (first) {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) slot(par, k) = xi[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
                 float2& ps = slot(par, k);
-                float2& px = slot(par + 1, k);
-                ps = make_float2(ps.x + er, ps.y + ei);
-                px = make_float2(fmaf(r.g, er, px.x), fmaf(r.g, ei, px.y));
+                ps = add2(ps, xi[k]);
             }
         }
     }

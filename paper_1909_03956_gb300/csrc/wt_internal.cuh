@@ -229,6 +229,120 @@ __device__ __forceinline__ void sincos_mixed(float th, float tl, float& s, float
     else sincos_turns_f32(th, tl, s, c);
 }
 
+// ---- packed float32 pairs ---------------------------------------------------
+// The sm_100 family issues two float32 adds, multiplies or FMAs per lane in
+// one instruction (__fadd2_rn, __fmul2_rn, __ffma2_rn), each element rounded
+// as the scalar operation rounds it; the FMA pipe's rate per element is
+// unchanged, the issue slots halve. The mixed predictors are issue-bound, so
+// they pair the real and imaginary parts of a complex value, or the same
+// quantity of two visibilities. A difference is an FMA with -1: the exact
+// difference rounded once, as a subtraction rounds it.
+__device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Two double-floats side by side (element 0 one visibility, element 1
+// another); nhi = -hi, kept so that the rounding error of a product comes
+// out of one FMA without a negation.
+struct DF2 {
+    float2 hi, lo, nhi;
+};
+
+__device__ __forceinline__ DF2 df2_pack(F2 a, F2 b)
+{
+    DF2 r;
+    r.hi = make_float2(a.hi, b.hi);
+    r.lo = make_float2(a.lo, b.lo);
+    r.nhi = make_float2(-a.hi, -b.hi);
+    return r;
+}
+
+// df_product for both elements of x against one double-float y; the same
+// roundings as df_product: p = fl(x.hi y.hi), t = fl(c + e) with e the exact
+// error of p (here as -e = fl(p - x.hi y.hi), exact) and
+// c = fl(x.hi y.lo + fl(x.lo y.hi)).
+__device__ __forceinline__ void df_product2(const DF2& x, F2 y, float2& p, float2& t)
+{
+    const float2 yh = bcast2(y.hi), yl = bcast2(y.lo);
+    p = mul2(x.hi, yh);
+    const float2 ne = fma2(x.nhi, yh, p);
+    const float2 c = fma2(x.hi, yl, mul2(x.lo, yh));
+    t = sub2(c, ne);
+}
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e)
+{
+    s = add2(a, b);
+    const float2 bp = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bp)), sub2(b, bp));
+}
+
+// phase_turns_df for two visibilities at once (identical roundings).
+__device__ __forceinline__ void phase_turns_df2(const DF2& u, const DF2& v, const DF2& w, F2 su, F2 sv, F2 sw1,
+                                                float2& th, float2& tl)
+{
+    float2 p1, t1, p2, t2, p3, t3, s, e1, s2, e2;
+    df_product2(u, su, p1, t1);
+    df_product2(v, sv, p2, t2);
+    df_product2(w, sw1, p3, t3);
+    two_sum2(p1, p2, s, e1);
+    two_sum2(s, p3, s2, e2);
+    th = sub2(s2, make_float2(rintf(s2.x), rintf(s2.y)));
+    tl = add2(add2(add2(t1, t2), add2(t3, e1)), e2);
+}
+
+// sincos_turns_f32 for two phases: the reduction and both polynomials on
+// pairs, the quadrant fix-up per element (identical roundings).
+__device__ __forceinline__ void sincos_turns_f32x2(float2 th, float2 tl, float2& s, float2& c)
+{
+    const float2 t4 = mul2(bcast2(4.0f), th);
+    const float2 q = make_float2(rintf(t4.x), rintf(t4.y));
+    const float2 f = fma2(bcast2(4.0f), tl, sub2(t4, q));
+    const float2 x = mul2(f, bcast2(1.57079637050628662109375f));
+    const float2 x2 = mul2(x, x);
+    float2 ps = fma2(x2, bcast2(2.7557319223985893e-6f), bcast2(-1.9841269841269841e-4f));
+    ps = fma2(x2, ps, bcast2(8.3333333333333333e-3f));
+    ps = fma2(x2, ps, bcast2(-1.6666666666666667e-1f));
+    const float2 sx = fma2(mul2(x, x2), ps, x);
+    float2 pc = fma2(x2, bcast2(-2.7557319223985891e-7f), bcast2(2.4801587301587302e-5f));
+    pc = fma2(x2, pc, bcast2(-1.3888888888888889e-3f));
+    pc = fma2(x2, pc, bcast2(4.1666666666666667e-2f));
+    pc = fma2(x2, pc, bcast2(-0.5f));
+    const float2 cx = fma2(x2, pc, bcast2(1.0f));
+    const int q0 = static_cast<int>(q.x) & 3, q1 = static_cast<int>(q.y) & 3;
+    const float ss0 = (q0 & 1) ? cx.x : sx.x, cc0 = (q0 & 1) ? sx.x : cx.x;
+    const float ss1 = (q1 & 1) ? cx.y : sx.y, cc1 = (q1 & 1) ? sx.y : cx.y;
+    s = make_float2((q0 & 2) ? -ss0 : ss0, (q1 & 2) ? -ss1 : ss1);
+    c = make_float2(((q0 + 1) & 2) ? -cc0 : cc0, ((q1 + 1) & 2) ? -cc1 : cc1);
+}
+
+// sincos_turns_sfu for two phases (the angle on pairs, identical roundings).
+__device__ __forceinline__ void sincos_turns_sfu2(float2 th, float2 tl, float2& s, float2& c)
+{
+    const float2 twopi = bcast2(6.28318530717958648f);
+    const float2 x = fma2(twopi, th, mul2(twopi, tl));
+    __sincosf(x.x, &s.x, &c.x);
+    __sincosf(x.y, &s.y, &c.y);
+}
+
+template <bool FAST>
+__device__ __forceinline__ void sincos_mixed2(float2 th, float2 tl, float2& s, float2& c)
+{
+    if constexpr (FAST) sincos_turns_sfu2(th, tl, s, c);
+    else sincos_turns_f32x2(th, tl, s, c);
+}
+
+// Kahan-compensated sum of pairs (each element as kahan_add).
+__device__ __forceinline__ void kahan_add2(float2& sum, float2& comp, float2 x)
+{
+    const float2 y = sub2(x, comp);
+    const float2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
 // Kahan-compensated float32 accumulation: sum + comp carries the total.
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
 {
@@ -272,10 +386,17 @@ struct RecD {
 };
 static_assert(sizeof(RecD) == 48, "RecD layout");
 
-// float32 record of the mixed form (32 bytes).
+// float32 record of the mixed form (32 bytes). The mixed predictors carry,
+// per node, xi_j = 4^(J-j) eta_j: the plain sum of the children's xi (a
+// leaf's xi is its eta), so the 1/4 of Eq. 9 disappears, and the factors
+// q_j = sqrt(A_j)/4 and 4^-(J-j-1) that turn the children's xi into
+// sigma^m are folded into gamma^m here, in float64, rounded once.
 //   leaf:     (a, b), (c, d), (e, f) = s_u, s_v, s_w - 1 as double-float
 //             pairs; g = Phi
-//   internal: a, b, c = gamma as above; d = q; g = A_1 lambda_1 at level 1
+//   internal: a, b, c = gamma^m q_j 4^-(J-j-1) (m = 0, 1, 2); for a
+//             single-child node a = the sum of the three, each with that
+//             child's Hadamard sign, and b = c = 0; d = 0;
+//             g = A_1 lambda_1 4^-(J-1) at level 1, else 0
 struct RecF {
     uint32_t meta;
     float a, b, c, d, e, f, g;
@@ -303,7 +424,7 @@ struct RecWD {
 static_assert(sizeof(RecWD) == 48, "RecWD layout");
 
 // mixed (32 bytes): (a, b), (c, d), (e, f) = leaf pixel centre as
-// double-float pairs; g = w.
+// double-float pairs; g = w_n 4^-(J-j), the weight of xi = 4^(J-j) eta.
 struct RecWF {
     uint32_t meta;
     float a, b, c, d, e, f, g;
@@ -389,6 +510,7 @@ int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int 
 extern const int kNumWaveletVariants;
 int wavelet_variant_shape(int v, int* nt, int* vpt);
 bool wavelet_variant_fits(int v, int mode, int which, int J);
+size_t wavelet_variant_smem(int v, int mode, int which, int J);
 int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s);
 int default_wavelet_variant(int mode, int which, int J);
 // autotune.cu

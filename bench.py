@@ -380,7 +380,7 @@ OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE),
 # DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
 # a form whose kernel changed since its capture has no entry.
-TRAFFIC_BYTES_MEDIUM_J12 = {}
+TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24260352}
 # Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
 HBM_PEAK_GBPS = 6690.1
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
@@ -666,7 +666,8 @@ def reference(args):
 
 def sweep(args):
     """Run-time scaling as in Sec. 3.6.1: per-visibility time of the Eq. 17
-    predictor (both forms) against J on the medium workload and on a fixed
+    predictor (the bench's fast regrouped form, the explicit mixed form and
+    float64) against J on the medium workload and on a fixed
     set of distinct components, against the number of distinct components at
     fixed J, and the paper-context workload (27 antennas, 1 263 600
     visibilities, J = 20, 15 and 140 distinct components) beside the paper's
@@ -681,17 +682,22 @@ def sweep(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
 
-    def measure(w, J, forms=("mixed", "fp64")):
+    # form name -> (mode, sum): the bench's form, the explicit mixed form, float64
+    kinds = {"fast_regrouped": (wt.WT_MIXED_FAST, wt.WT_SUM_EQ17_REGROUPED), "mixed": (wt.WT_MIXED, wt.WT_SUM_EQ17),
+             "fp64": (wt.WT_FP64, wt.WT_SUM_EQ17)}
+
+    def measure(w, J, forms=("fast_regrouped", "mixed", "fp64")):
         l, m, f, uvw = d(w.l), d(w.m), d(w.flux), d(w.uvw)
         tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, J)
         info = tree.info()
         r = {"J": J, "n_leaves": info["n_leaves"], "n_nodes": info["n_nodes"]}
         for name in forms:
-            mode = wt.WT_MIXED if name == "mixed" else wt.WT_FP64
-            out = torch.empty(w.n_vis, dtype=torch.complex64 if name == "mixed" else torch.complex128, device=dev)
-            wt.wt_predict_vis(tree, uvw, mode=mode, out=out)
-            t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, out=out), stream, flush,
-                           reps=3 if name == "mixed" else 1)
+            mode, which = kinds[name]
+            c64 = mode != wt.WT_FP64
+            out = torch.empty(w.n_vis, dtype=torch.complex64 if c64 else torch.complex128, device=dev)
+            wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out)
+            t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out), stream, flush,
+                           reps=3 if c64 else 1)
             r[name + "_ns_per_vis"] = t / w.n_vis * 1e9
         tree.close()
         return r
@@ -702,7 +708,7 @@ def sweep(args):
     fixed = {}
     for nd in (10, 20, 40, 80, 140):
         w = synth.medium_fixed(nd)
-        fixed[str(nd)] = [measure(w, J, forms=("mixed",)) for J in (12, 15, 20, 25)]
+        fixed[str(nd)] = [measure(w, J, forms=("fast_regrouped", "mixed")) for J in (12, 15, 20, 25)]
     res["fixed_distinct_J_sweep"] = fixed
     res["paper_context"] = []
     for nd, paper_s in ((15, 146.0), (140, 1000.0)):
@@ -710,7 +716,8 @@ def sweep(args):
         r = measure(w, 20)
         r.update({"n_vis": w.n_vis, "n_distinct": nd, "paper_s_per_major_cycle": paper_s,
                   "gpu_fp64_s_per_major_cycle": r["fp64_ns_per_vis"] * w.n_vis / 1e9,
-                  "gpu_mixed_s_per_major_cycle": r["mixed_ns_per_vis"] * w.n_vis / 1e9})
+                  "gpu_mixed_s_per_major_cycle": r["mixed_ns_per_vis"] * w.n_vis / 1e9,
+                  "gpu_fast_regrouped_s_per_major_cycle": r["fast_regrouped_ns_per_vis"] * w.n_vis / 1e9})
         res["paper_context"].append(r)
     print(json.dumps(res), flush=True)
 

@@ -287,6 +287,7 @@ def native(args):
     ops = n_vis * (op_leaf * n_leaves + op_node * (n_nodes - n_leaves))
     traffic = TRAFFIC_BYTES_MEDIUM_J12.get((args.form, args.sum)) if (J == MEDIUM_J and n_vis == 1008000) else None
     achieved = ops / t_pred / 1e12
+    sfu_achieved = n_vis * SFU_OPS_LEAF[args.form] * n_leaves / t_pred / 1e12
     peak = FP32_PEAK_TOPS
     passes = (2 * J + 2 + 7) // 8
     launches = (4 + 3 * passes) + 1 + 1
@@ -326,8 +327,10 @@ def native(args):
             "bound": "alu",
             "achieved": achieved,
             "peak": peak,
-            "unit": "TOP/s (FP32-pipe ops; an SFU op counts 8, its pipe-time ratio)",
+            "unit": "TOP/s (float32 FMA-pipe element ops)",
             "frac": achieved / peak,
+            "sfu": ({"achieved": sfu_achieved, "peak": SFU_PEAK_TOPS, "unit": "TOP/s (sin, cos)",
+                     "frac": sfu_achieved / SFU_PEAK_TOPS} if sfu_achieved else None),
             "traffic": traffic,
             "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of this form "
                              "(profiles/); output still in L2 at exit" if traffic is not None
@@ -351,40 +354,46 @@ def native(args):
         dist.destroy_process_group()
 
 
-# FP32 pipe operations of the mixed Eq. 17 forms, counted from each form's
-# arithmetic; instruction overhead (record decode, loads, stores, branches,
-# register moves) is not counted. A complex add is 2 ops.
-#   phase (every leaf): three double-float products (5 each), two
-#     error-free sums (6 each), reduction by the nearest integer (2), tail
-#     (4): 33.
-#   polynomial sin/cos: quadrant reduction and angle (6), sin and cos
-#     polynomials (5 each), quadrant selection (4): 20.
-#   fast sin/cos: the angle (2) and the SFU argument scaling (1) on the FP32
-#     pipe, sin and cos on the special-function unit (16 lanes per SM against
-#     128 FP32 lanes: each SFU op occupies its pipe for the time of 8 FP32
-#     ops): 3 + 2 x 8.
+# Float32 FMA-pipe operations (adds, multiplies, FMAs; a packed pair counts
+# 2) of the mixed Eq. 17 forms, counted from each form's arithmetic at two
+# visibilities per thread (the bench's launch shape); instruction overhead
+# (record decode, loads, stores, branches, register moves, roundings to
+# integer) is not counted, and the special-function unit's sin and cos are
+# counted separately against that unit's own peak. A complex add is 2 ops.
+#   phase (every leaf): three double-float products (4 each), two
+#     error-free sums (6 each), reduction by the nearest integer (1), tail
+#     (4): 29.
+#   polynomial sin/cos: quadrant reduction and angle (5), sin and cos
+#     polynomials (5 each): 15 (the quadrant selection runs on the ALU).
+#   fast sin/cos: the angle (2) and the SFU argument scaling (1): 3, plus
+#     sin and cos on the special-function unit (2 SFU ops).
 #   explicit internal node: butterflies (8), xi (2), three sigma (6),
 #     gamma.sigma (6), Kahan add (8): 30.
 #   regrouped: a leaf adds xi to its parent's sum (2) and w xi to its
 #     parent's plain sum of leaf terms (2); an internal node adds w xi to V
 #     (2, with a Kahan add of 8) and passes xi to its parent's sum (2).
-OPS_LEAF = 33 + 20
+OPS_PHASE = 12 + 12 + 1 + 4
+OPS_LEAF = OPS_PHASE + 15
 OPS_NODE = 30
-OPS_LEAF_FAST = 33 + 3 + 2 * 8
+OPS_LEAF_FAST = OPS_PHASE + 3
 OPS_RG_LEAF = 2 + 2
 OPS_RG_NODE = 2 + 8 + 2
 OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE),
        ("fast", "explicit"): (OPS_LEAF_FAST, OPS_NODE),
        ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE),
        ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE)}
+SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
 # a form whose kernel changed since its capture has no entry.
 TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24260352}
 # Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
 HBM_PEAK_GBPS = 6690.1
-# 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock.
+# 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock
+# (a packed pair instruction does two per lane in two clocks: the same rate).
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# 152 SMs x 16 special-function lanes x 2.07 GHz.
+SFU_PEAK_TOPS = 152 * 16 * 2.07e9 / 1e12
 
 
 def _time_call(fn, stream, flush, reps=3):

@@ -3,10 +3,12 @@
 // The best shape (threads per CTA x visibilities per thread) depends on the
 // tree (depth J sets the per-thread stack, node count the work per
 // visibility) and on the form. The first call for a new key times every
-// shape that fits on a sample of the caller's own visibilities (two waves
-// of the shape's resident CTAs, at least 131 072 and at most all of them,
+// shape that fits on one sample of the caller's own visibilities (float64
+// forms: two waves of the resident CTAs of the shape that holds the most,
+// at least 131 072; mixed forms: up to 2 Mi; never more than the batch;
 // written into the caller's output buffer, which the real launch then
-// overwrites) and remembers the one with the least time per visibility. Keys are (device, form,
+// overwrites), a warm-up and the best of two timed launches each, and
+// remembers the fastest. Keys are (device, form,
 // sum, J, log2 of the node count, log2 of the leaf count).
 //
 // Tuning synchronises the caller's stream once. It is skipped, in favour of
@@ -82,12 +84,11 @@ void append_file(const std::string& key, int v)
 
 }  // namespace
 
-// Visibilities a variant is timed on: two full waves of its resident CTAs
-// (as many as fit an SM by shared memory and threads; registers may admit
-// fewer, which only adds waves), so that small-CTA shapes are measured at
-// the occupancy they reach on a large batch, not on a sample that leaves
-// SMs idle; at least 131072, at most the whole batch. Variants are compared
-// by time per visibility.
+// Two full waves of a variant's resident CTAs (as many as fit an SM by
+// shared memory and threads; registers may admit fewer, which only adds
+// waves), so that small-CTA shapes are measured at the occupancy they reach
+// on a large batch, not on a sample that leaves SMs idle; at least 131072,
+// at most the whole batch.
 static int64_t sample_size(int v, const WaveletJob& jb)
 {
     int nt = 0, vpt = 0;
@@ -138,19 +139,41 @@ int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s)
     }
     int best = fallback;
     float best_ms = 1e30f;
+    // one sample for every shape: the largest two-wave size among them, so
+    // that all are timed on the same visibilities with the GPU full
+    int64_t common = 0;
+    for (int v = 0; v < kNumWaveletVariants; ++v)
+        if (wavelet_variant_fits(v, jb.mode, jb.which, jb.J)) {
+            const int64_t n = sample_size(v, jb);
+            if (n > common) common = n;
+        }
+    // the mixed forms are fast enough to time on up to 2 Mi visibilities:
+    // with a persistent grid the shapes' tails differ with the batch size,
+    // so the closer the sample is to the real batch, the better the choice
+    if (jb.mode != WT_FP64) {
+        const int64_t cap = int64_t(1) << 21;
+        common = jb.n_vis < cap ? jb.n_vis : (common > cap ? common : cap);
+    }
+    sample.n_vis = common;
     for (int v = 0; v < kNumWaveletVariants; ++v) {
         if (!wavelet_variant_fits(v, jb.mode, jb.which, jb.J)) continue;
-        sample.n_vis = sample_size(v, jb);
         if (launch_wavelet(sample, v, s) != WT_OK) continue;   // warm-up
-        cudaEventRecord(e0, s);
-        bool ok = launch_wavelet(sample, v, s) == WT_OK;
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess || !ok) {
-            cudaGetLastError();
-            continue;
+        float ms = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = launch_wavelet(sample, v, s) == WT_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || !ok) {
+                cudaGetLastError();
+                ok = false;
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t < ms) ms = t;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if (!ok) continue;
         const float per_vis = ms / static_cast<float>(sample.n_vis);
         if (verbose()) {
             int nt = 0, vpt = 0;

@@ -106,10 +106,10 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
                 b.w[k] = split_f64(ok ? uvw_m[3 * n + 2] * s : 0.0);
             }
             b.start();
-            b.stk = reinterpret_cast<float2*>(stk_base) + threadIdx.x;
+            b.stk = reinterpret_cast<float2*>(stk_base) + threadIdx.x * VPT;   // [row][thread][vis] layout
             b.J = ch.J;
             b.maxrow = maxrow;
-            good = st.sweep(b);
+            good = st.sweep_steps(b);
             float2* out = static_cast<float2*>(vis) + ch.out_offset;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -172,11 +172,11 @@ bool batch_fits(int mode, int shape, int rows_max) { return batch_smem(mode, sha
 
 // Shape used without timing (WT_AUTOTUNE=0, or under stream capture): the
 // first that fits in a measured preference order (the regrouped mixed sum
-// runs best with two visibilities per thread in small CTAs).
+// runs best with two visibilities per thread).
 int default_shape(int mode, int rows_max)
 {
     static const int order_fp64[kNumBatchShapes] = {0, 1, 2, 3, 4, 5};
-    static const int order_mixed[kNumBatchShapes] = {5, 2, 3, 0, 1, 4};
+    static const int order_mixed[kNumBatchShapes] = {2, 3, 5, 0, 1, 4};
     const int* order = (mode == WT_FP64) ? order_fp64 : order_mixed;
     for (int i = 0; i < kNumBatchShapes; ++i)
         if (batch_fits(mode, order[i], rows_max)) return order[i];
@@ -334,7 +334,10 @@ int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cu
     if (first < 0) return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis_batched: no launch shape fits J");
     const char* e = getenv("WT_AUTOTUNE");
     if (e && e[0] == '0') return first;
-    const int64_t sample = n_vis < 16384 ? n_vis : 16384;
+    // per channel: the mixed forms are timed on up to 131 072 visibilities
+    // (with 64 channels, several waves of every shape), float64 on 16 384
+    const int64_t cap = (p.mode == WT_FP64) ? 16384 : 131072;
+    const int64_t sample = n_vis < cap ? n_vis : cap;
     cudaEvent_t e0, e1;
     WT_CUDA_TRY(cudaEventCreate(&e0));
     WT_CUDA_TRY(cudaEventCreate(&e1));

@@ -414,6 +414,7 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         // regrouped Eq. 17: the node's weight from its parent's gammas
         double wgt;
         bool first = true;
+        bool next_sibling_leaf = false;
         if (j == 1) {
             wgt = A1 * d.lambda[n];
         } else {
@@ -425,9 +426,12 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
             wgt = quarter_sqrt_area(j - 1) * ((h0 * g0 + h1 * g1) + h2 * g2);
             const uint32_t pmask = d.mask[P];
             first = slot == static_cast<uint32_t>(__ffs(pmask) - 1);
+            // a leaf's next record in post-order is its next sibling, if any
+            next_sibling_leaf = leaf && ((pmask >> (slot + 1u)) != 0u);
         }
         const uint32_t wmeta = static_cast<uint32_t>(j) | (leaf ? kRwLeaf : 0u) | (j == 1 ? kRwRoot : 0u) |
-                               (first ? kRwFirst : 0u);
+                               (first ? kRwFirst : 0u) | (next_sibling_leaf ? kRwNextLeaf : 0u) |
+                               ((!leaf && j == J - 1) ? kRwLowSum : 0u);
         RecWD wd;
         RecWF wf;
         wd.meta = wmeta;
@@ -438,8 +442,9 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         wd.d = wgt;
         wd.e = 0.0;
         wf.meta = wmeta;
-        wf.a = leaf ? rf.a : 0.f;
-        wf.b = leaf ? rf.b : 0.f;
+        // internal nodes: stack rows of the node's own xi sum and its parent's
+        wf.a = leaf ? rf.a : __uint_as_float(static_cast<uint32_t>(j - 1));
+        wf.b = leaf ? rf.b : __uint_as_float(static_cast<uint32_t>(j > 1 ? j - 2 : 0));
         wf.c = leaf ? rf.c : 0.f;
         wf.d = leaf ? rf.d : 0.f;
         wf.e = leaf ? rf.e : 0.f;

@@ -171,10 +171,10 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
 #pragma unroll
             for (int k = 0; k < VPT; ++k) { b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k]; }
             b.start();
-            b.stk = stk;
+            b.stk = stk - threadIdx.x + threadIdx.x * VPT;   // [row][thread][vis] layout
             b.J = J;
             b.maxrow = rows - 1;
-            good = st.sweep(b);
+            good = st.sweep_steps(b);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const float2 r = b.result(k);
@@ -298,7 +298,7 @@ int run_mixed(const WaveletJob& jb, cudaStream_t s)
 // stack_fits() when no tuning is available.
 const int kNumWaveletVariants = 8;
 static const Variant kVariants[kNumWaveletVariants] = {{256, 1}, {128, 1}, {128, 2}, {64, 2},
-                                                       {64, 4},  {32, 4},  {32, 2},  {32, 1}};
+                                                       {64, 4},  {32, 4},  {32, 2},  {256, 2}};
 
 int wavelet_variant_shape(int v, int* nt, int* vpt)
 {
@@ -338,7 +338,7 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
             case 4: return run_fp64<64, 4>(jb, s);
             case 5: return run_fp64<32, 4>(jb, s);
             case 6: return run_fp64<32, 2>(jb, s);
-            default: return run_fp64<32, 1>(jb, s);
+            default: return run_fp64<256, 2>(jb, s);
         }
     }
     switch (v) {
@@ -349,7 +349,7 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
         case 4: return run_mixed<64, 4>(jb, s);
         case 5: return run_mixed<32, 4>(jb, s);
         case 6: return run_mixed<32, 2>(jb, s);
-        default: return run_mixed<32, 1>(jb, s);
+        default: return run_mixed<256, 2>(jb, s);
     }
 }
 
@@ -359,9 +359,9 @@ int default_wavelet_variant(int mode, int which, int J)
 {
     // measured on the medium workload (J = 12): the explicit mixed sum runs
     // best at 256 x 1 (its stack limits the CTAs per SM), the regrouped one,
-    // whose stack is small, with two visibilities per thread in small CTAs
+    // whose stack is small, with two visibilities per thread
     static const int order_mixed[kNumWaveletVariants] = {0, 2, 1, 3, 4, 5, 6, 7};
-    static const int order_mixed_rg[kNumWaveletVariants] = {6, 2, 3, 4, 5, 0, 1, 7};
+    static const int order_mixed_rg[kNumWaveletVariants] = {2, 7, 4, 6, 3, 5, 0, 1};
     static const int order_fp64[kNumWaveletVariants] = {1, 0, 2, 3, 4, 5, 6, 7};
     const int* order = (mode == WT_FP64) ? order_fp64
                        : (which == WT_SUM_EQ17_REGROUPED) ? order_mixed_rg : order_mixed;

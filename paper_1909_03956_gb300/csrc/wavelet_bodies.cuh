@@ -165,11 +165,11 @@ struct Eq17F {
             const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                float2 th, tl, s, c;
-                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, th, tl);
-                sincos_mixed2<FAST>(th, tl, s, c);
-                emit(2 * p, root, srow, r.g, make_float2(c.x, s.x));
-                emit(2 * p + 1, root, srow, r.g, make_float2(c.y, s.y));
+                float2 h, tl, e0, e1;
+                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
+                sincos_mixed2<FAST>(h, tl, e0, e1);
+                emit(2 * p, root, srow, r.g, e0);
+                emit(2 * p + 1, root, srow, r.g, e1);
             }
             if constexpr (ODD) {
                 constexpr int k = VPT - 1;
@@ -315,7 +315,9 @@ struct Eq17WD {
 // Regrouped Eq. 17 in the mixed forms: V = sum_n w_n xi_n over every node,
 // xi = 4^(J-j) eta and w_n scaled to match by the build (RecWF). Per
 // visibility a thread keeps one pair per level: the xi sum of the open
-// level-j node (j = 1 .. J-2) in shared-memory row j - 1; the open
+// level-j node (j = 1 .. J-2) in shared-memory row j - 1 (layout
+// [row][thread][vis]: a thread's visibilities side by side, one 16-byte
+// access per row at two visibilities per thread); the open
 // level-(J-1) node's xi sum, and the plain float32 sum of its leaves'
 // w xi (at most four terms), live in registers, so a leaf touches neither
 // shared memory nor the compensated sum. An internal node reads its xi, adds
@@ -331,11 +333,40 @@ struct Eq17WF {
     float2 acc[VPT], comp[VPT];                       // Kahan sum of V and its compensation
     float2 low[VPT];                                  // xi sum of the open level-(J-1) node
     float2 lowx[VPT];                                 // w xi sum of its leaves
-    float2* stk;
+    float2* stk;                                      // shared stack + threadIdx.x * VPT
     int J;
     int maxrow;
 
-    __device__ __forceinline__ float2& slot(int row, int k) { return stk[(row * VPT + k) * NT]; }
+    __device__ __forceinline__ float2* row_ptr(int row) { return stk + row * (NT * VPT); }
+
+    __device__ __forceinline__ void load_row(int row, float2 (&x)[VPT])
+    {
+        const float2* p = row_ptr(row);
+        if constexpr (VPT % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < VPT; k += 2) {
+                const float4 q = *reinterpret_cast<const float4*>(p + k);
+                x[k] = make_float2(q.x, q.y);
+                x[k + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) x[k] = p[k];
+        }
+    }
+
+    __device__ __forceinline__ void store_row(int row, const float2 (&x)[VPT])
+    {
+        float2* p = row_ptr(row);
+        if constexpr (VPT % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < VPT; k += 2)
+                *reinterpret_cast<float4*>(p + k) = make_float4(x[k].x, x[k].y, x[k + 1].x, x[k + 1].y);
+        } else {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) p[k] = x[k];
+        }
+    }
 
     __device__ __forceinline__ void start()
     {
@@ -367,21 +398,69 @@ struct Eq17WF {
         lowx[k] = fma2(wv, xi, lowx[k]);
     }
 
+    // Two sibling leaves together: four independent phase chains per thread
+    // (two visibilities x two leaves), one dispatch.
+    __device__ __forceinline__ void leaf_pair(const RecWF& a, const RecWF& b)
+    {
+        const F2 su0{a.a, a.b}, sv0{a.c, a.d}, sw0{a.e, a.f};
+        const F2 su1{b.a, b.b}, sv1{b.c, b.d}, sw1{b.e, b.f};
+        const float2 w0 = bcast2(a.g), w1 = bcast2(b.g);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float2 h0, tl0, h1, tl1, e00, e01, e10, e11;
+            phase_turns_df2(U[p], V[p], W[p], su0, sv0, sw0, h0, tl0);
+            phase_turns_df2(U[p], V[p], W[p], su1, sv1, sw1, h1, tl1);
+            sincos_mixed2<FAST>(h0, tl0, e00, e01);
+            sincos_mixed2<FAST>(h1, tl1, e10, e11);
+            low[2 * p] = add2(low[2 * p], add2(e00, e10));
+            low[2 * p + 1] = add2(low[2 * p + 1], add2(e01, e11));
+            lowx[2 * p] = fma2(w1, e10, fma2(w0, e00, lowx[2 * p]));
+            lowx[2 * p + 1] = fma2(w1, e11, fma2(w0, e01, lowx[2 * p + 1]));
+        }
+        if constexpr (ODD) {
+            constexpr int k = VPT - 1;
+            float th0, tl0, s0, c0, th1, tl1, s1, c1;
+            phase_turns_df(u[k], v[k], w[k], su0, sv0, sw0, th0, tl0);
+            phase_turns_df(u[k], v[k], w[k], su1, sv1, sw1, th1, tl1);
+            sincos_mixed<FAST>(th0, tl0, s0, c0);
+            sincos_mixed<FAST>(th1, tl1, s1, c1);
+            const float2 e0 = make_float2(c0, s0), e1 = make_float2(c1, s1);
+            low[k] = add2(low[k], add2(e0, e1));
+            lowx[k] = fma2(w1, e1, fma2(w0, e0, lowx[k]));
+        }
+    }
+
+    // One step of the record sweep: a leaf whose next record is its sibling
+    // leaf takes both (when both are in this chunk), anything else one.
+    // Pairs only in the fast form: the polynomial form's four chains need
+    // more registers than the pairing saves (measured 2 % slower).
+    __device__ __forceinline__ int step(const RecWF* cb, int r, int n)
+    {
+        const RecWF& a = cb[r];
+        if constexpr (FAST) {
+            if ((a.meta & kRwNextLeaf) && r + 1 < n) {
+                leaf_pair(a, cb[r + 1]);
+                return 2;
+            }
+        }
+        (*this)(a);
+        return 1;
+    }
+
     __device__ void operator()(const RecWF& r)
     {
         const uint32_t meta = r.meta;
-        const int lev = static_cast<int>(meta & 31u);
         const bool root = meta & kRwRoot, first = meta & kRwFirst;
         const float2 wv = bcast2(r.g);
         if (meta & kRwLeaf) {
             const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                float2 th, tl, s, c;
-                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, th, tl);
-                sincos_mixed2<FAST>(th, tl, s, c);
-                leaf_up(2 * p, make_float2(c.x, s.x), wv, root);
-                leaf_up(2 * p + 1, make_float2(c.y, s.y), wv, root);
+                float2 h, tl, e0, e1;
+                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
+                sincos_mixed2<FAST>(h, tl, e0, e1);
+                leaf_up(2 * p, e0, wv, root);
+                leaf_up(2 * p + 1, e1, wv, root);
             }
             if constexpr (ODD) {
                 constexpr int k = VPT - 1;
@@ -392,10 +471,12 @@ struct Eq17WF {
             }
             return;
         }
-        const int own = clamp_row(static_cast<uint32_t>(lev - 1), maxrow);
-        const int par = clamp_row(static_cast<uint32_t>(lev > 1 ? lev - 2 : 0), maxrow);
+        // rows pre-decoded by the build (own: lev - 1, parent's: lev - 2),
+        // clamped to the stack
+        const int own = clamp_row(__float_as_uint(r.a), maxrow);
+        const int par = clamp_row(__float_as_uint(r.b), maxrow);
         float2 xi[VPT];
-        if (lev == J - 1) {
+        if (meta & kRwLowSum) {                        // level J - 1: its sums are in registers
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 xi[k] = low[k];
@@ -404,22 +485,19 @@ struct Eq17WF {
                 lowx[k] = make_float2(0.f, 0.f);
             }
         } else {
+            load_row(own, xi);
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                xi[k] = slot(own, k);
-                kahan_add2(acc[k], comp[k], mul2(wv, xi[k]));
-            }
+            for (int k = 0; k < VPT; ++k) kahan_add2(acc[k], comp[k], mul2(wv, xi[k]));
         }
         if (root) return;
         if (first) {
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) slot(par, k) = xi[k];
+            store_row(par, xi);
         } else {
+            float2 ps[VPT];
+            load_row(par, ps);
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                float2& ps = slot(par, k);
-                ps = add2(ps, xi[k]);
-            }
+            for (int k = 0; k < VPT; ++k) ps[k] = add2(ps[k], xi[k]);
+            store_row(par, ps);
         }
     }
 };

@@ -259,17 +259,18 @@ __device__ __forceinline__ DF2 df2_pack(F2 a, F2 b)
     return r;
 }
 
-// df_product for both elements of x against one double-float y; the same
-// roundings as df_product: p = fl(x.hi y.hi), t = fl(c + e) with e the exact
-// error of p (here as -e = fl(p - x.hi y.hi), exact) and
-// c = fl(x.hi y.lo + fl(x.lo y.hi)).
-__device__ __forceinline__ void df_product2(const DF2& x, F2 y, float2& p, float2& t)
+// Product of two double-floats for both elements of x against one
+// double-float y, returned with its head negated: q = -fl(x.hi y.hi)
+// (exact negation, from x.nhi), e = x.hi y.hi + q exactly (the rounding
+// error of the head, one FMA), t = fl(x.hi y.lo + fl(x.lo y.hi + e)) (the
+// tail; x.lo y.lo, below 2^-48 of the product, dropped). x y = t - q up to
+// the tail's roundings, of the size of ulp(t).
+__device__ __forceinline__ void df_product2n(const DF2& x, F2 y, float2& q, float2& t)
 {
-    const float2 yh = bcast2(y.hi), yl = bcast2(y.lo);
-    p = mul2(x.hi, yh);
-    const float2 ne = fma2(x.nhi, yh, p);
-    const float2 c = fma2(x.hi, yl, mul2(x.lo, yh));
-    t = sub2(c, ne);
+    const float2 yh = bcast2(y.hi);
+    q = mul2(x.nhi, yh);
+    const float2 e = fma2(x.hi, yh, q);
+    t = fma2(x.hi, bcast2(y.lo), fma2(x.lo, yh, e));
 }
 
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e)
@@ -279,25 +280,33 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& 
     e = add2(sub2(a, sub2(s, bp)), sub2(b, bp));
 }
 
-// phase_turns_df for two visibilities at once (identical roundings).
+// Phase in turns of B.(s - P) for two visibilities at once (u, v, w of
+// visibility 0 in element 0, of visibility 1 in element 1), float64-
+// accurate as phase_turns_df: the three negated heads are added with
+// error-free sums and reduced by their nearest integer (exact), the
+// rounding errors join the tail. Returns h = (sum of negated heads) -
+// nearest integer, so that the phase is tl - h modulo 1, |h| <= 1/2.
 __device__ __forceinline__ void phase_turns_df2(const DF2& u, const DF2& v, const DF2& w, F2 su, F2 sv, F2 sw1,
-                                                float2& th, float2& tl)
+                                                float2& h, float2& tl)
 {
-    float2 p1, t1, p2, t2, p3, t3, s, e1, s2, e2;
-    df_product2(u, su, p1, t1);
-    df_product2(v, sv, p2, t2);
-    df_product2(w, sw1, p3, t3);
-    two_sum2(p1, p2, s, e1);
-    two_sum2(s, p3, s2, e2);
-    th = sub2(s2, make_float2(rintf(s2.x), rintf(s2.y)));
-    tl = add2(add2(add2(t1, t2), add2(t3, e1)), e2);
+    float2 q1, t1, q2, t2, q3, t3, a, ea, b, eb;
+    df_product2n(u, su, q1, t1);
+    df_product2n(v, sv, q2, t2);
+    df_product2n(w, sw1, q3, t3);
+    two_sum2(q1, q2, a, ea);
+    two_sum2(a, q3, b, eb);
+    h = sub2(b, make_float2(rintf(b.x), rintf(b.y)));
+    tl = sub2(add2(add2(t1, t2), sub2(t3, ea)), eb);
 }
 
-// sincos_turns_f32 for two phases: the reduction and both polynomials on
-// pairs, the quadrant fix-up per element (identical roundings).
-__device__ __forceinline__ void sincos_turns_f32x2(float2 th, float2 tl, float2& s, float2& c)
+// sincos_turns_f32 of the phase tl - h (turns) of two visibilities, each
+// result written as the pair (cos, sin) of its own visibility: e0 for
+// element 0, e1 for element 1. Quadrant reduction and both polynomials on
+// pairs (the same steps and roundings as sincos_turns_f32 on th = -h), the
+// quadrant fix-up per element.
+__device__ __forceinline__ void sincos_turns_f32x2(float2 h, float2 tl, float2& e0, float2& e1)
 {
-    const float2 t4 = mul2(bcast2(4.0f), th);
+    const float2 t4 = mul2(bcast2(-4.0f), h);                      // 4 th, exact
     const float2 q = make_float2(rintf(t4.x), rintf(t4.y));
     const float2 f = fma2(bcast2(4.0f), tl, sub2(t4, q));
     const float2 x = mul2(f, bcast2(1.57079637050628662109375f));
@@ -314,24 +323,25 @@ __device__ __forceinline__ void sincos_turns_f32x2(float2 th, float2 tl, float2&
     const int q0 = static_cast<int>(q.x) & 3, q1 = static_cast<int>(q.y) & 3;
     const float ss0 = (q0 & 1) ? cx.x : sx.x, cc0 = (q0 & 1) ? sx.x : cx.x;
     const float ss1 = (q1 & 1) ? cx.y : sx.y, cc1 = (q1 & 1) ? sx.y : cx.y;
-    s = make_float2((q0 & 2) ? -ss0 : ss0, (q1 & 2) ? -ss1 : ss1);
-    c = make_float2(((q0 + 1) & 2) ? -cc0 : cc0, ((q1 + 1) & 2) ? -cc1 : cc1);
+    e0 = make_float2(((q0 + 1) & 2) ? -cc0 : cc0, (q0 & 2) ? -ss0 : ss0);
+    e1 = make_float2(((q1 + 1) & 2) ? -cc1 : cc1, (q1 & 2) ? -ss1 : ss1);
 }
 
-// sincos_turns_sfu for two phases (the angle on pairs, identical roundings).
-__device__ __forceinline__ void sincos_turns_sfu2(float2 th, float2 tl, float2& s, float2& c)
+// sincos_turns_sfu of the phase tl - h of two visibilities (the angle on
+// pairs, the same roundings as 2 pi th + 2 pi tl), each result written as
+// its visibility's (cos, sin) pair.
+__device__ __forceinline__ void sincos_turns_sfu2(float2 h, float2 tl, float2& e0, float2& e1)
 {
-    const float2 twopi = bcast2(6.28318530717958648f);
-    const float2 x = fma2(twopi, th, mul2(twopi, tl));
-    __sincosf(x.x, &s.x, &c.x);
-    __sincosf(x.y, &s.y, &c.y);
+    const float2 x = fma2(bcast2(-6.28318530717958648f), h, mul2(bcast2(6.28318530717958648f), tl));
+    __sincosf(x.x, &e0.y, &e0.x);
+    __sincosf(x.y, &e1.y, &e1.x);
 }
 
 template <bool FAST>
-__device__ __forceinline__ void sincos_mixed2(float2 th, float2 tl, float2& s, float2& c)
+__device__ __forceinline__ void sincos_mixed2(float2 h, float2 tl, float2& e0, float2& e1)
 {
-    if constexpr (FAST) sincos_turns_sfu2(th, tl, s, c);
-    else sincos_turns_f32x2(th, tl, s, c);
+    if constexpr (FAST) sincos_turns_sfu2(h, tl, e0, e1);
+    else sincos_turns_f32x2(h, tl, e0, e1);
 }
 
 // Kahan-compensated sum of pairs (each element as kahan_add).
@@ -410,10 +420,14 @@ static_assert(sizeof(RecF) == 32, "RecF layout");
 // V = sum_n w_n eta_n, the same sum as Eq. 17 with each node's
 // sum_m gamma^m sigma^m distributed over its children
 // (gamma^T (H eta) = (H^T gamma)^T eta). meta bits: 0-4 level, 5 leaf,
-// 6 level 1, 7 first child of its parent (in post-order).
+// 6 level 1, 7 first child of its parent (in post-order), 8 a leaf whose
+// next record is a leaf of the same parent (its next sibling), 9 a node at
+// level J - 1 (its children are leaves).
 constexpr uint32_t kRwLeaf = 1u << 5;
 constexpr uint32_t kRwRoot = 1u << 6;
 constexpr uint32_t kRwFirst = 1u << 7;
+constexpr uint32_t kRwNextLeaf = 1u << 8;
+constexpr uint32_t kRwLowSum = 1u << 9;
 
 // float64 (48 bytes): a, b, c = leaf pixel centre (s_u, s_v, s_w - 1); d = w.
 struct RecWD {
@@ -423,8 +437,10 @@ struct RecWD {
 };
 static_assert(sizeof(RecWD) == 48, "RecWD layout");
 
-// mixed (32 bytes): (a, b), (c, d), (e, f) = leaf pixel centre as
-// double-float pairs; g = w_n 4^-(J-j), the weight of xi = 4^(J-j) eta.
+// mixed (32 bytes): leaf: (a, b), (c, d), (e, f) = pixel centre as
+// double-float pairs; internal node: a, b = the stack rows of its own and
+// its parent's xi sums (j - 1 and j - 2, 0 at level 1) as unsigned integers
+// in the float fields; g = w_n 4^-(J-j), the weight of xi = 4^(J-j) eta.
 struct RecWF {
     uint32_t meta;
     float a, b, c, d, e, f, g;

@@ -283,8 +283,9 @@ def native(args):
 
     # roofline of the dominant kernel (the mixed Eq. 17 predictor)
     n_leaves, n_nodes = info["n_leaves"], info["n_nodes"]
-    op_leaf, op_node = OPS[(args.form, args.sum)]
-    ops = n_vis * (op_leaf * n_leaves + op_node * (n_nodes - n_leaves))
+    op_leaf, op_node, op_low = OPS[(args.form, args.sum)]
+    n_low = int(info["per_level"][J - 2]) if J >= 3 else 0     # internal nodes at level J - 1
+    ops = n_vis * (op_leaf * n_leaves + op_node * (n_nodes - n_leaves - n_low) + op_low * n_low)
     traffic = TRAFFIC_BYTES_MEDIUM_J12.get((args.form, args.sum)) if (J == MEDIUM_J and n_vis == 1008000) else None
     achieved = ops / t_pred / 1e12
     sfu_achieved = n_vis * SFU_OPS_LEAF[args.form] * n_leaves / t_pred / 1e12
@@ -338,6 +339,8 @@ def native(args):
             "algorithmic_bytes": 32 * n_vis,
             "ops_per_leaf": op_leaf,
             "ops_per_internal_node": op_node,
+            "ops_per_level_J_minus_1_node": op_low,
+            "level_J_minus_1_nodes": n_low,
             "kernel": "k_wavelet_mixed (Eq. 17 %s)" % args.sum,
         },
         "e2e": {"value": world * n_vis / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -370,18 +373,23 @@ def native(args):
 #   explicit internal node: butterflies (8), xi (2), three sigma (6),
 #     gamma.sigma (6), Kahan add (8): 30.
 #   regrouped: a leaf adds xi to its parent's sum (2) and w xi to its
-#     parent's plain sum of leaf terms (2); an internal node adds w xi to V
-#     (2, with a Kahan add of 8) and passes xi to its parent's sum (2).
+#     parent's plain sum of leaf terms (2); a node at level J - 1 adds w xi
+#     to its leaves' sum (2) and that to its parent's plain sum (2); any
+#     other internal node adds w xi (plus, at level J - 2, its children's
+#     sum) to V (2, with a Kahan add of 8); every internal node passes xi to
+#     its parent's sum (2).
 OPS_PHASE = 12 + 12 + 1 + 4
 OPS_LEAF = OPS_PHASE + 15
 OPS_NODE = 30
 OPS_LEAF_FAST = OPS_PHASE + 3
 OPS_RG_LEAF = 2 + 2
 OPS_RG_NODE = 2 + 8 + 2
-OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE),
-       ("fast", "explicit"): (OPS_LEAF_FAST, OPS_NODE),
-       ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE),
-       ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE)}
+OPS_RG_LOW = 2 + 2 + 2
+# (form, sum) -> (per leaf, per internal node, per internal node at level J - 1)
+OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE, OPS_NODE),
+       ("fast", "explicit"): (OPS_LEAF_FAST, OPS_NODE, OPS_NODE),
+       ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW),
+       ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW)}
 SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
             else recs = ch.recd;
             st.retarget(recs, ch.hdr->n_nodes);
             cur = c;
-            if constexpr (MIXED) maxrow = min(ch.J > 3 ? ch.J - 2 : 1, rows_max) - 1;
+            if constexpr (MIXED) maxrow = min(ch.J > 4 ? ch.J - 3 : 1, rows_max) - 1;
             else maxrow = min(4 * (ch.J > 1 ? ch.J - 1 : 1), rows_max) - 1;
         }
         const int64_t n0 = (item - ch.tile_base) * per_tile + threadIdx.x;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
             b.stk = reinterpret_cast<float2*>(stk_base) + threadIdx.x * VPT;   // [row][thread][vis] layout
             b.J = ch.J;
             b.maxrow = maxrow;
-            good = st.sweep_steps(b);
+            good = st.sweep_at(b);
             float2* out = static_cast<float2*>(vis) + ch.out_offset;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -154,11 +154,12 @@ constexpr int kNumBatchShapes = 6;
 const Shape kBatchShapes[kNumBatchShapes] = {{256, 1}, {128, 1}, {128, 2}, {64, 2}, {32, 1}, {32, 2}};
 
 // Stack rows for the deepest tree of a plan: the explicit float64 sum keeps
-// four child slots per level, the regrouped mixed sum one pair per level.
+// four child slots per level, the regrouped mixed sum one pair per level
+// above J - 2.
 int batch_rows(int mode, int jmax)
 {
     if (mode == WT_FP64) return jmax > 1 ? 4 * (jmax - 1) : 4;
-    return jmax > 3 ? jmax - 2 : 1;
+    return jmax > 4 ? jmax - 3 : 1;
 }
 
 size_t batch_smem(int mode, int shape, int rows_max)

@@ -91,12 +91,11 @@ struct Stager {
         return true;
     }
 
-    // As sweep, but the body takes the chunk, the position and the chunk's
-    // record count (body.step(chunk, r, n)) and returns how many records it
-    // consumed (at least one, never past n): a body may handle a run of
-    // records together.
+    // As sweep, but the body sees the chunk, the position and the chunk's
+    // record count (body.at(chunk, r, n)), so that it may handle a record
+    // together with its neighbour.
     template <class Body>
-    __device__ bool sweep_steps(Body& body)
+    __device__ bool sweep_at(Body& body)
     {
         const int64_t nc = nchunks();
         if (nc == 0) return true;
@@ -117,7 +116,7 @@ struct Stager {
             const int n = static_cast<int>((count - first < chunk) ? (count - first) : chunk);
             const Rec* cb = buf + static_cast<int64_t>(b) * chunk;
 #pragma unroll 4
-            for (int r = 0; r < n;) r += body.step(cb, r, n);
+            for (int r = 0; r < n; ++r) body.at(cb, r, n);
             if (!resident) {
                 __syncthreads();
                 if (threadIdx.x == 0 && c + 2 < nc) issue(c + 2, b);

@@ -414,7 +414,7 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         // regrouped Eq. 17: the node's weight from its parent's gammas
         double wgt;
         bool first = true;
-        bool next_sibling_leaf = false;
+        bool pair_first = false, pair_second = false;
         if (j == 1) {
             wgt = A1 * d.lambda[n];
         } else {
@@ -426,12 +426,24 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
             wgt = quarter_sqrt_area(j - 1) * ((h0 * g0 + h1 * g1) + h2 * g2);
             const uint32_t pmask = d.mask[P];
             first = slot == static_cast<uint32_t>(__ffs(pmask) - 1);
-            // a leaf's next record in post-order is its next sibling, if any
-            next_sibling_leaf = leaf && ((pmask >> (slot + 1u)) != 0u);
+            if (leaf) {
+                // sibling leaves are consecutive in post-order: this run
+                // spans [post - sib_before, ... + nsib - 1]; pair it greedily
+                // from the start of its part in this staging chunk
+                const uint32_t sib_before = __popc(pmask & ((1u << slot) - 1u));
+                const int64_t run_lo = post - sib_before;
+                const int64_t run_hi = run_lo + __popc(pmask) - 1;
+                const int64_t chunk_lo = post - post % kRecChunkW;
+                const int64_t seg_lo = run_lo > chunk_lo ? run_lo : chunk_lo;
+                const int64_t k = post - seg_lo;
+                pair_second = (k & 1) != 0;
+                pair_first = (k & 1) == 0 && post + 1 <= run_hi && (post + 1) % kRecChunkW != 0;
+            }
         }
         const uint32_t wmeta = static_cast<uint32_t>(j) | (leaf ? kRwLeaf : 0u) | (j == 1 ? kRwRoot : 0u) |
-                               (first ? kRwFirst : 0u) | (next_sibling_leaf ? kRwNextLeaf : 0u) |
-                               ((!leaf && j == J - 1) ? kRwLowSum : 0u);
+                               (first ? kRwFirst : 0u) | (pair_first ? kRwPairFirst : 0u) |
+                               (pair_second ? kRwPairSecond : 0u) | ((!leaf && j == J - 1) ? kRwLowSum : 0u) |
+                               ((!leaf && j == J - 2) ? kRwMidSum : 0u);
         RecWD wd;
         RecWF wf;
         wd.meta = wmeta;

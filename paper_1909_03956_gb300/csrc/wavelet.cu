@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
             b.stk = stk - threadIdx.x + threadIdx.x * VPT;   // [row][thread][vis] layout
             b.J = J;
             b.maxrow = rows - 1;
-            good = st.sweep_steps(b);
+            good = st.sweep_at(b);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const float2 r = b.result(k);
@@ -219,7 +219,7 @@ int stack_rows(int mode, int which, int J)
     if (which == WT_SUM_EQ16) return 0;
     if (which == WT_SUM_EQ17_REGROUPED) {
         if (mode == WT_FP64) return J > 3 ? 2 * (J - 2) : 2;
-        return J > 3 ? J - 2 : 1;
+        return J > 4 ? J - 3 : 1;
     }
     return J > 1 ? 4 * (J - 1) : 4;
 }

@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kChunkD = 256;   // records per staging buffer (48 B each)
 constexpr int kChunkF = 384;   // (32 B each)
-constexpr int kChunkW = 128;   // regrouped float32 form (32 B each): its stack is small, so the
+constexpr int kChunkW = kRecChunkW;   // regrouped float32 form (32 B each): its stack is small, so the
                                // staging buffers set how many CTAs fit on an SM
 
 __device__ __forceinline__ int clamp_row(uint32_t r, int maxrow) { return min(static_cast<int>(r), maxrow); }
@@ -315,14 +315,15 @@ struct Eq17WD {
 // Regrouped Eq. 17 in the mixed forms: V = sum_n w_n xi_n over every node,
 // xi = 4^(J-j) eta and w_n scaled to match by the build (RecWF). Per
 // visibility a thread keeps one pair per level: the xi sum of the open
-// level-j node (j = 1 .. J-2) in shared-memory row j - 1 (layout
+// level-j node (j = 1 .. J-3) in shared-memory row j - 1 (layout
 // [row][thread][vis]: a thread's visibilities side by side, one 16-byte
-// access per row at two visibilities per thread); the open
-// level-(J-1) node's xi sum, and the plain float32 sum of its leaves'
-// w xi (at most four terms), live in registers, so a leaf touches neither
-// shared memory nor the compensated sum. An internal node reads its xi, adds
-// w xi (plus, at level J-1, its leaves' sum) to V with compensation and
-// passes xi up (the first child writes its parent's sum, the others add).
+// access per row at two visibilities per thread); those of the open
+// level-(J-1) and level-(J-2) nodes live in registers, with the plain
+// float32 sums of their children's terms (w xi, at most four each), so
+// leaves and level-(J-1) nodes touch neither shared memory nor the
+// compensated sum. Any other internal node reads its xi, adds w xi (plus,
+// at level J-2, its children's terms) to V with compensation and passes xi
+// up (the first child writes its parent's sum, the others add).
 // Packed pairs as in Eq17F.
 template <int NT, int VPT, bool FAST = false>
 struct Eq17WF {
@@ -333,6 +334,9 @@ struct Eq17WF {
     float2 acc[VPT], comp[VPT];                       // Kahan sum of V and its compensation
     float2 low[VPT];                                  // xi sum of the open level-(J-1) node
     float2 lowx[VPT];                                 // w xi sum of its leaves
+    float2 mid[VPT];                                  // xi sum of the open level-(J-2) node
+    float2 midx[VPT];                                 // plain sum of the terms of its children
+                                                      // (at most 4)
     float2* stk;                                      // shared stack + threadIdx.x * VPT
     int J;
     int maxrow;
@@ -382,6 +386,8 @@ struct Eq17WF {
             comp[k] = make_float2(0.f, 0.f);
             low[k] = make_float2(0.f, 0.f);
             lowx[k] = make_float2(0.f, 0.f);
+            mid[k] = make_float2(0.f, 0.f);
+            midx[k] = make_float2(0.f, 0.f);
         }
     }
 
@@ -432,19 +438,22 @@ struct Eq17WF {
 
     // One step of the record sweep: a leaf whose next record is its sibling
     // leaf takes both (when both are in this chunk), anything else one.
-    // Pairs only in the fast form: the polynomial form's four chains need
-    // more registers than the pairing saves (measured 2 % slower).
-    __device__ __forceinline__ int step(const RecWF* cb, int r, int n)
+    // One record of the sweep. In the fast form a leaf marked as the first of
+    // a pair takes its next record (its sibling leaf, in the same chunk by
+    // construction) with it, and the second is skipped. The polynomial form
+    // takes every record alone: its four chains need more registers than the
+    // pairing saves (measured 2 % slower).
+    __device__ __forceinline__ void at(const RecWF* cb, int r, int n)
     {
         const RecWF& a = cb[r];
         if constexpr (FAST) {
-            if ((a.meta & kRwNextLeaf) && r + 1 < n) {
-                leaf_pair(a, cb[r + 1]);
-                return 2;
+            if (a.meta & kRwPairSecond) return;
+            if (a.meta & kRwPairFirst) {
+                leaf_pair(a, cb[r + 1 < n ? r + 1 : r]);
+                return;
             }
         }
         (*this)(a);
-        return 1;
     }
 
     __device__ void operator()(const RecWF& r)
@@ -476,13 +485,29 @@ struct Eq17WF {
         const int own = clamp_row(__float_as_uint(r.a), maxrow);
         const int par = clamp_row(__float_as_uint(r.b), maxrow);
         float2 xi[VPT];
-        if (meta & kRwLowSum) {                        // level J - 1: its sums are in registers
+        if (meta & kRwLowSum) {                        // level J - 1: registers only
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 xi[k] = low[k];
-                kahan_add2(acc[k], comp[k], fma2(wv, xi[k], lowx[k]));
+                const float2 x = fma2(wv, xi[k], lowx[k]);
                 low[k] = make_float2(0.f, 0.f);
                 lowx[k] = make_float2(0.f, 0.f);
+                if (root) {
+                    kahan_add2(acc[k], comp[k], x);
+                } else {                               // the parent (level J - 2) takes both
+                    midx[k] = add2(midx[k], x);
+                    mid[k] = add2(mid[k], xi[k]);
+                }
+            }
+            return;
+        }
+        if (meta & kRwMidSum) {                        // level J - 2: xi and its children's terms in registers
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                xi[k] = mid[k];
+                kahan_add2(acc[k], comp[k], fma2(wv, xi[k], midx[k]));
+                mid[k] = make_float2(0.f, 0.f);
+                midx[k] = make_float2(0.f, 0.f);
             }
         } else {
             load_row(own, xi);

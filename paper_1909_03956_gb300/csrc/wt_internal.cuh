@@ -420,14 +420,19 @@ static_assert(sizeof(RecF) == 32, "RecF layout");
 // V = sum_n w_n eta_n, the same sum as Eq. 17 with each node's
 // sum_m gamma^m sigma^m distributed over its children
 // (gamma^T (H eta) = (H^T gamma)^T eta). meta bits: 0-4 level, 5 leaf,
-// 6 level 1, 7 first child of its parent (in post-order), 8 a leaf whose
-// next record is a leaf of the same parent (its next sibling), 9 a node at
-// level J - 1 (its children are leaves).
+// 6 level 1, 7 first child of its parent (in post-order), 8 a leaf that
+// takes its next record (its next sibling leaf) as a pair, 9 that second
+// leaf of a pair, 10 a node at level J - 1 (its children are leaves),
+// 11 a node at level J - 2. Pairs are formed greedily along each run of
+// sibling leaves, never across a staging chunk of kRecChunkW records.
 constexpr uint32_t kRwLeaf = 1u << 5;
 constexpr uint32_t kRwRoot = 1u << 6;
 constexpr uint32_t kRwFirst = 1u << 7;
-constexpr uint32_t kRwNextLeaf = 1u << 8;
-constexpr uint32_t kRwLowSum = 1u << 9;
+constexpr uint32_t kRwPairFirst = 1u << 8;
+constexpr uint32_t kRwPairSecond = 1u << 9;
+constexpr uint32_t kRwLowSum = 1u << 10;
+constexpr uint32_t kRwMidSum = 1u << 11;
+constexpr int kRecChunkW = 128;   // records per staging buffer of the regrouped float32 form
 
 // float64 (48 bytes): a, b, c = leaf pixel centre (s_u, s_v, s_w - 1); d = w.
 struct RecWD {

@@ -47,6 +47,18 @@ constexpr int kNumParams = kH * 3 + kH + kH * kH + kH + 2 * kH + 2;   // 4546
 constexpr int oW1 = 0, ob1 = oW1 + kH * 3, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH, ob3 = oW3 + 2 * kH;
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+
+// SiLU for inference: z sigma(z) = z/2 (1 + tanh(z/2)) with the hardware
+// tanh (PTX tanh.approx.f32, one special-function op; its absolute error of
+// about 2^-11 is below the bfloat16 rounding the hidden units get anyway).
+// Training keeps silu_f, so that its gradients match the oracle's.
+__device__ __forceinline__ float silu_fast(float z)
+{
+    const float hz = 0.5f * z;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(hz));
+    return fmaf(hz, t, hz);
+}
 __device__ __forceinline__ float dsilu_f(float z)
 {
     const float s = 1.0f / (1.0f + __expf(-z));
@@ -192,8 +204,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const dou
             for (int e = 0; e < 4; ++e) {
                 const int col = 16 * kt + 2 * tq + (e & 1) + 8 * (e >> 1);
                 const float w0 = sW1[3 * col], w1 = sW1[3 * col + 1], w2 = sW1[3 * col + 2], b = sb1[col];
-                h0[e] = silu_f(fmaf(w2, x0[2], fmaf(w1, x0[1], fmaf(w0, x0[0], b))));
-                h1[e] = silu_f(fmaf(w2, x1[2], fmaf(w1, x1[1], fmaf(w0, x1[0], b))));
+                h0[e] = silu_fast(fmaf(w2, x0[2], fmaf(w1, x0[1], fmaf(w0, x0[0], b))));
+                h1[e] = silu_fast(fmaf(w2, x1[2], fmaf(w1, x1[1], fmaf(w0, x1[0], b))));
             }
             a[kt][0] = pack_bf16x2(h0[0], h0[1]);
             a[kt][1] = pack_bf16x2(h1[0], h1[1]);
@@ -210,7 +222,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const dou
             for (int kt = 0; kt < 4; ++kt) mma_bf16_16816(acc, a[kt], bfr[kt][nt]);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const float hr0 = silu_f(acc[j]), hr1 = silu_f(acc[2 + j]);
+                const float hr0 = silu_fast(acc[j]), hr1 = silu_fast(acc[2 + j]);
                 y00 = fmaf(sW3[col + j], hr0, y00);
                 y01 = fmaf(sW3[kH + col + j], hr0, y01);
                 y10 = fmaf(sW3[col + j], hr1, y10);

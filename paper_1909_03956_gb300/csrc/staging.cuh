@@ -115,6 +115,9 @@ struct Stager {
             const int64_t first = c * chunk;
             const int n = static_cast<int>((count - first < chunk) ? (count - first) : chunk);
             const Rec* cb = buf + static_cast<int64_t>(b) * chunk;
+            // four records per trip (measured against two: 2 % faster on the
+            // blob workloads, 4-6 % slower on deep trees of isolated
+            // components, whose records are mostly internal nodes)
 #pragma unroll 4
             for (int r = 0; r < n; ++r) body.at(cb, r, n);
             if (!resident) {

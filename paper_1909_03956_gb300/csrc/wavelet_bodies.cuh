@@ -447,21 +447,63 @@ struct Eq17WF {
     {
         const RecWF& a = cb[r];
         if constexpr (FAST) {
-            if (a.meta & kRwPairSecond) return;
-            if (a.meta & kRwPairFirst) {
-                leaf_pair(a, cb[r + 1 < n ? r + 1 : r]);
+            if (a.meta & (kRwPairFirst | kRwPairSecond)) {
+                if (a.meta & kRwPairFirst) leaf_pair(a, cb[r + 1 < n ? r + 1 : r]);
                 return;
             }
         }
         (*this)(a);
     }
 
+    // Parent's xi sum: the first child writes it, the others add (a select,
+    // not a branch: internal nodes are most records of deep, sparse trees).
+    __device__ __forceinline__ void pass_up(int par, bool first, const float2 (&xi)[VPT])
+    {
+        float2 ps[VPT];
+        load_row(par, ps);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) ps[k] = first ? xi[k] : add2(ps[k], xi[k]);
+        store_row(par, ps);
+    }
+
+    // Nodes at levels J - 1 and J - 2, whose sums are in registers.
+    __device__ __forceinline__ void low_levels(const RecWF& r, uint32_t meta)
+    {
+        const bool root = meta & kRwRoot, first = meta & kRwFirst;
+        const float2 wv = bcast2(r.g);
+        float2 xi[VPT];
+        if (meta & kRwLowSum) {                        // level J - 1: registers only
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                xi[k] = low[k];
+                const float2 x = fma2(wv, xi[k], lowx[k]);
+                low[k] = make_float2(0.f, 0.f);
+                lowx[k] = make_float2(0.f, 0.f);
+                if (root) {
+                    kahan_add2(acc[k], comp[k], x);
+                } else {                               // the parent (level J - 2) takes both
+                    midx[k] = add2(midx[k], x);
+                    mid[k] = add2(mid[k], xi[k]);
+                }
+            }
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {                // level J - 2
+            xi[k] = mid[k];
+            kahan_add2(acc[k], comp[k], fma2(wv, xi[k], midx[k]));
+            mid[k] = make_float2(0.f, 0.f);
+            midx[k] = make_float2(0.f, 0.f);
+        }
+        if (!root) pass_up(clamp_row(__float_as_uint(r.b), maxrow), first, xi);
+    }
+
     __device__ void operator()(const RecWF& r)
     {
         const uint32_t meta = r.meta;
-        const bool root = meta & kRwRoot, first = meta & kRwFirst;
         const float2 wv = bcast2(r.g);
         if (meta & kRwLeaf) {
+            const bool root = meta & kRwRoot;
             const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
@@ -480,50 +522,21 @@ struct Eq17WF {
             }
             return;
         }
-        // rows pre-decoded by the build (own: lev - 1, parent's: lev - 2),
-        // clamped to the stack
+        if (meta & (kRwLowSum | kRwMidSum)) {
+            low_levels(r, meta);
+            return;
+        }
+        // any other internal node (level <= J - 3): rows pre-decoded by the
+        // build (own: lev - 1, parent's: lev - 2), clamped to the stack. A
+        // level-1 node (a root, always a first child) writes its xi back into
+        // its own row 0, which the next level-1 node's first child overwrites.
         const int own = clamp_row(__float_as_uint(r.a), maxrow);
         const int par = clamp_row(__float_as_uint(r.b), maxrow);
         float2 xi[VPT];
-        if (meta & kRwLowSum) {                        // level J - 1: registers only
+        load_row(own, xi);
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                xi[k] = low[k];
-                const float2 x = fma2(wv, xi[k], lowx[k]);
-                low[k] = make_float2(0.f, 0.f);
-                lowx[k] = make_float2(0.f, 0.f);
-                if (root) {
-                    kahan_add2(acc[k], comp[k], x);
-                } else {                               // the parent (level J - 2) takes both
-                    midx[k] = add2(midx[k], x);
-                    mid[k] = add2(mid[k], xi[k]);
-                }
-            }
-            return;
-        }
-        if (meta & kRwMidSum) {                        // level J - 2: xi and its children's terms in registers
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-                xi[k] = mid[k];
-                kahan_add2(acc[k], comp[k], fma2(wv, xi[k], midx[k]));
-                mid[k] = make_float2(0.f, 0.f);
-                midx[k] = make_float2(0.f, 0.f);
-            }
-        } else {
-            load_row(own, xi);
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) kahan_add2(acc[k], comp[k], mul2(wv, xi[k]));
-        }
-        if (root) return;
-        if (first) {
-            store_row(par, xi);
-        } else {
-            float2 ps[VPT];
-            load_row(par, ps);
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) ps[k] = add2(ps[k], xi[k]);
-            store_row(par, ps);
-        }
+        for (int k = 0; k < VPT; ++k) kahan_add2(acc[k], comp[k], mul2(wv, xi[k]));
+        pass_up(par, (meta & kRwFirst) != 0, xi);
     }
 };
 

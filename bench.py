@@ -394,7 +394,7 @@ SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
 # a form whose kernel changed since its capture has no entry.
-TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24281344}
+TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24282880}
 # Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
 HBM_PEAK_GBPS = 6690.1
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock

@@ -395,8 +395,23 @@ SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
 # a form whose kernel changed since its capture has no entry.
 TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24282880}
+# Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
+# element ops per (visibility, component): phase 29, angle and SFU scaling 3
+# (fast) or polynomial sin/cos 15, the flux times (cos, sin) 2, half a Kahan
+# add of a pair of terms 4. float64 (k_dft_fp64), FP64-pipe instructions per
+# term: phase 3, table reduction and polynomials 14, rotation by the table
+# entry 2 (+2 multiplies), multiply-add into V 2 -> 21 (roundings to integer
+# and the table load not counted).
+OPS_DFT_FAST = OPS_PHASE + 3 + 2 + 4
+OPS_DFT = OPS_PHASE + 15 + 2 + 4
+OPS_DFT_FP64 = 21
+# 152 SMs x 1.89 FP64 instructions per clock per SM (a probe of independent
+# DFMA chains on this pool: 1.19 TFLOP/s) x 2.07 GHz.
+FP64_PEAK_INST_PER_S = 152 * 1.89 * 2.07e9
 # Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
 HBM_PEAK_GBPS = 6690.1
+# Measured cuBLAS bf16 GEMM throughput (MEASURED_PEAKS.json, bf16_tflops, burst).
+BF16_PEAK_TFLOPS = 1861.7
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock
 # (a packed pair instruction does two per lane in two clocks: the same rate).
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
@@ -456,7 +471,26 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
     r["subtract_c64_64Mi_GBps"] = 24 * big / t / 1e9
     r["subtract_c64_64Mi_frac_of_hbm"] = 24 * big / t / 1e9 / HBM_PEAK_GBPS
     del a, b
-    return {"forms": r}
+    # the learned response's inference alone, one sample per visibility
+    mlp = wt.Mlp(w.J, w.ra0, w.dec0, depth=3, x_max=1e30, seed=1)
+    t_mlp = _time_call(lambda: mlp.eval(uvw, out=out32), stream, flush)
+    mlp.close()
+    r["mlp_eval_samples_per_s"] = n / t_mlp
+    # rooflines of the side kernels, from the op counts per unit (see the
+    # constants) and the times above
+    nc = w.n_comp
+    roof = {
+        "dft_mixed_fast": {"bound": "alu", "frac": r["dft_mixed_fast_vis_per_s"] * nc * OPS_DFT_FAST / 1e12
+                           / FP32_PEAK_TOPS, "ops_per_term": OPS_DFT_FAST},
+        "dft_mixed": {"bound": "alu", "frac": r["dft_mixed_vis_per_s"] * nc * OPS_DFT / 1e12 / FP32_PEAK_TOPS,
+                      "ops_per_term": OPS_DFT},
+        "dft_fp64": {"bound": "fp64", "frac": r["dft_fp64_vis_per_s"] * nc * OPS_DFT_FP64 / FP64_PEAK_INST_PER_S,
+                     "ops_per_term": OPS_DFT_FP64},
+        "subtract_c64_64Mi": {"bound": "hbm", "frac": r["subtract_c64_64Mi_frac_of_hbm"]},
+        "mlp_eval": {"bound": "tensor", "achieved_tflops": n * 8832 / t_mlp / 1e12,
+                     "frac": n * 8832 / t_mlp / 1e12 / BF16_PEAK_TFLOPS},
+    }
+    return {"forms": r, "side_rooflines": roof}
 
 
 def batched_measurement(wt, torch, dev, stream, flush):

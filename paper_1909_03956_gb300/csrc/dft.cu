@@ -5,8 +5,9 @@
 // A prologue kernel packs each component once into a 32-byte record in a
 // scratch buffer: (l, m, n - 1, C) in float64 for WT_FP64, or double-float
 // halves of l, m, n - 1 plus C in float32 for WT_MIXED. The main kernel gives
-// each thread one visibility and streams the records through shared memory
-// (bulk copies, double-buffered, broadcast reads), like the wavelet kernels.
+// each thread one visibility (float64) or two (mixed, on packed float32
+// pairs) and streams the records through shared memory (bulk copies,
+// double-buffered, broadcast reads), like the wavelet kernels.
 #include "staging.cuh"
 #include "wt_internal.cuh"
 
@@ -57,18 +58,42 @@ struct BodyD {
     }
 };
 
+// Mixed forms on packed float32 pairs: a thread owns two visibilities
+// (n and n + NT of its tile), and components are taken two at a time. The
+// phases of the two visibilities against one component form one pair of
+// double-floats; each visibility's (cos, sin) comes out as its own pair; the
+// two components' terms of a visibility are added plainly, then into its
+// Kahan sum (one rounding more per two terms than one at a time).
 template <bool FAST>
-struct BodyF {
-    F2 u, v, w;
-    float sgn, vr, vi, cr, ci;
-    __device__ void operator()(const CompF& c)
+struct BodyF2 {
+    DF2 U, V, W;
+    float2 acc[2], comp[2];
+
+    __device__ __forceinline__ void terms(const CompF& c, float2& e0, float2& e1) const
     {
-        float th, tl;
-        phase_turns_df(u, v, w, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, th, tl);
-        float s, co;
-        sincos_mixed<FAST>(th, tl, s, co);
-        kahan_add(vr, cr, c.flux * co);
-        kahan_add(vi, ci, c.flux * s);
+        float2 h, tl;
+        phase_turns_df2(U, V, W, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, h, tl);
+        sincos_mixed2<FAST>(h, tl, e0, e1);
+    }
+
+    __device__ __forceinline__ void at(const CompF* cb, int r, int n)
+    {
+        if (r & 1) return;                         // taken with its even neighbour
+        const CompF& a = cb[r];
+        float2 a0, a1;
+        terms(a, a0, a1);
+        const float2 fa = bcast2(a.flux);
+        float2 x0 = mul2(fa, a0), x1 = mul2(fa, a1);
+        if (r + 1 < n) {                           // chunks hold an even count: only a list's last
+            const CompF& b = cb[r + 1];            // component can be alone
+            float2 b0, b1;
+            terms(b, b0, b1);
+            const float2 fb = bcast2(b.flux);
+            x0 = fma2(fb, b0, x0);
+            x1 = fma2(fb, b1, x1);
+        }
+        kahan_add2(acc[0], comp[0], x0);
+        kahan_add2(acc[1], comp[1], x1);
     }
 };
 
@@ -103,29 +128,33 @@ __global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comp
     extern __shared__ __align__(16) unsigned char smem[];
     Stager<CompF> st;
     stager_setup(st, smem, comps, n_comp, kChunk);
-    const int64_t ntiles = (n_vis + NT - 1) / NT;
+    const int64_t ntiles = (n_vis + 2 * NT - 1) / (2 * NT);
+    const double sg = static_cast<double>(sgn);       // sign folded into the baseline (exact)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t n = tile * NT + threadIdx.x;
-        const bool valid = n < n_vis;
-        const double sg = static_cast<double>(sgn);   // sign folded into the baseline (exact)
-        BodyF<FAST> b{split_f64(valid ? sg * uvw[3 * n] : 0.0), split_f64(valid ? sg * uvw[3 * n + 1] : 0.0),
-                split_f64(valid ? sg * uvw[3 * n + 2] : 0.0), sgn, 0.f, 0.f, 0.f, 0.f};
-        if (!st.sweep(b)) {
+        const int64_t n0 = tile * 2 * NT + threadIdx.x, n1 = n0 + NT;
+        const bool ok0 = n0 < n_vis, ok1 = n1 < n_vis;
+        BodyF2<FAST> b;
+        b.U = df2_pack(split_f64(ok0 ? sg * uvw[3 * n0] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1] : 0.0));
+        b.V = df2_pack(split_f64(ok0 ? sg * uvw[3 * n0 + 1] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1 + 1] : 0.0));
+        b.W = df2_pack(split_f64(ok0 ? sg * uvw[3 * n0 + 2] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1 + 2] : 0.0));
+        b.acc[0] = b.acc[1] = b.comp[0] = b.comp[1] = make_float2(0.f, 0.f);
+        if (!st.sweep_at(b)) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
             return;
         }
-        if (valid) vis[n] = make_float2(b.vr - b.cr, b.vi - b.ci);
+        if (ok0) vis[n0] = sub2(b.acc[0], b.comp[0]);
+        if (ok1) vis[n1] = sub2(b.acc[1], b.comp[1]);
     }
 }
 
 template <class K>
-int grid_for(K kernel, int nt, size_t smem, int64_t n_vis, dim3& grid)
+int grid_for(K kernel, int threads, int nt, size_t smem, int64_t n_vis, dim3& grid)
 {
     WT_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
-    WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem));
+    WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "dft kernel does not fit on an SM");
-    const int64_t ntiles = (n_vis + nt - 1) / nt;
+    const int64_t ntiles = (n_vis + nt - 1) / nt;   // nt = visibilities per CTA tile
     int64_t g = static_cast<int64_t>(num_sms()) * per_sm;
     grid = dim3(static_cast<unsigned>(g < ntiles ? g : ntiles));
     return WT_OK;
@@ -144,7 +173,7 @@ int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, in
         constexpr int NT = 128;
         const size_t smem = static_cast<size_t>(stager_bytes<CompD>(kChunk));
         auto k = k_dft_fp64<NT>;
-        int rc = grid_for(k, NT, smem, n_vis, grid);
+        int rc = grid_for(k, NT, NT, smem, n_vis, grid);
         if (rc) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(scratch), n_comp, uvw, n_vis, static_cast<double2*>(vis),
                                  static_cast<double>(sign), status);
@@ -152,7 +181,7 @@ int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, in
         constexpr int NT = 256;
         const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
         auto k = (mode == WT_MIXED_FAST) ? k_dft_mixed<NT, true> : k_dft_mixed<NT, false>;
-        int rc = grid_for(k, NT, smem, n_vis, grid);
+        int rc = grid_for(k, NT, 2 * NT, smem, n_vis, grid);   // two visibilities per thread
         if (rc) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(scratch), n_comp, uvw, n_vis, static_cast<float2*>(vis),
                                  static_cast<float>(sign), status);
@@ -302,14 +331,14 @@ extern "C" int dft_predict_vis_noalloc(const double* l, const double* m, const d
         constexpr int NT = 128;
         const size_t smem = static_cast<size_t>(stager_bytes<CompD>(kChunk));
         auto k = k_dft_fp64<NT>;
-        if ((rc = grid_for(k, NT, smem, n_vis, grid))) return rc;
+        if ((rc = grid_for(k, NT, NT, smem, n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(records), n_comp, uvw, n_vis, static_cast<double2*>(vis_out),
                                  static_cast<double>(sign), status);
     } else {
         constexpr int NT = 256;
         const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
         auto k = k_dft_mixed<NT, false>;
-        if ((rc = grid_for(k, NT, smem, n_vis, grid))) return rc;
+        if ((rc = grid_for(k, NT, 2 * NT, smem, n_vis, grid))) return rc;   // two visibilities per thread
         k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<float2*>(vis_out),
                                  static_cast<float>(sign), status);
     }

@@ -532,12 +532,21 @@ def batched_measurement(wt, torch, dev, stream, flush):
     for t in trees:
         t.close()
     total_vis = n * len(chans)
+    # FMA-pipe element ops of the graph launch, per channel's tree (fast regrouped counts)
+    op_leaf, op_node, op_low = OPS[("fast", "regrouped")]
+    ops = 0
+    for x in sizes:
+        low = int(x["per_level"][x["J"] - 2]) if x["J"] >= 3 else 0
+        ops += n * (op_leaf * x["n_leaves"] + op_node * (x["n_nodes"] - x["n_leaves"] - low) + op_low * low)
     return {"workload": w.name, "n_ch": len(chans), "n_vis_per_ch": n,
             "n_comp_range": [min(len(c["l"]) for c in chans), max(len(c["l"]) for c in chans)],
             "J_range": [min(c["J"] for c in chans), max(c["J"] for c in chans)],
             "nodes_range": [min(x["n_nodes"] for x in sizes), max(x["n_nodes"] for x in sizes)],
             "graph_launch_vis_per_s": total_vis / t_b, "per_channel_launches_vis_per_s": total_vis / t_p,
             "graph_launch_ms": t_b * 1e3, "per_channel_ms": t_p * 1e3, "max_rel_err_vs_fp64_oracle": err,
+            "graph_launch_roofline": {"bound": "alu", "achieved": ops / t_b / 1e12, "peak": FP32_PEAK_TOPS,
+                                      "unit": "TOP/s (float32 FMA-pipe element ops)",
+                                      "frac": ops / t_b / 1e12 / FP32_PEAK_TOPS},
             "form": "WT_MIXED_FAST Eq. 17 regrouped (both legs)"}
 
 

@@ -2,7 +2,8 @@
 times (autotuned shapes, the same entry points), on strided samples of the
 outputs that the oracle computes one by one.
 
-Workloads: medium (1 008 000 visibilities, 5 000 components, J = 12);
+Workloads: medium (1 008 000 visibilities, 5 000 components, J = 12, and
+J = 8, 14); isolated components (140, J = 20 and 25);
 mixed (2 032 000 visibilities at 1.3 GHz, 20 000 components, J = 12);
 learned-response array (15 993 600 visibilities, 50 000 components, J = 12);
 batched (64 channels x 2 032 000 visibilities, uneven trees).
@@ -29,14 +30,39 @@ def _sample(n, k=300):
     return np.unique(np.concatenate([np.arange(0, n, max(1, n // k)), [n - 1]]))
 
 
+@pytest.mark.parametrize("which", [wt.WT_SUM_EQ17_REGROUPED, wt.WT_SUM_EQ17])
 @pytest.mark.parametrize("mode", [wt.WT_MIXED_FAST, wt.WT_MIXED, wt.WT_FP64])
-def test_medium_full_size(mode):
+def test_medium_full_size(mode, which):
+    # the bench's step uses the regrouped sum in the fast form, autotuned shape
     w = synth.medium(J=12)
     t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
-    v = wt.wt_predict_vis(t, dev(w.uvw), mode=mode).cpu().numpy()
+    v = wt.wt_predict_vis(t, dev(w.uvw), mode=mode, which=which).cpu().numpy()
     idx = _sample(w.n_vis)
     ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(w.uvw[idx])
     assert np.max(np.abs(v[idx] - ref)) / np.abs(w.flux).sum() <= TOL[mode]
+
+
+@pytest.mark.parametrize("J", [8, 14])
+def test_medium_full_size_regrouped_fast_other_depths(J):
+    # the ends of the bench's J sweep, in the bench's form
+    w = synth.medium(J=J)
+    t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
+    v = wt.wt_predict_vis(t, dev(w.uvw), mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ17_REGROUPED).cpu().numpy()
+    idx = _sample(w.n_vis, 150)
+    ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(w.uvw[idx])
+    assert np.max(np.abs(v[idx] - ref)) / np.abs(w.flux).sum() <= 1e-6
+
+
+@pytest.mark.parametrize("J", [20, 25])
+def test_isolated_components_deep_tree_regrouped_fast(J):
+    # deep, sparse trees (every component alone in its pixel: chains of
+    # single-child nodes), the paper's wide-field regime
+    w = synth.medium_fixed(140, J=J)
+    t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
+    v = wt.wt_predict_vis(t, dev(w.uvw), mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ17_REGROUPED).cpu().numpy()
+    idx = _sample(w.n_vis, 150)
+    ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(w.uvw[idx])
+    assert np.max(np.abs(v[idx] - ref)) / np.abs(w.flux).sum() <= 1e-6
 
 
 def test_mixed_config_full_size_wavelet_and_direct():
@@ -44,17 +70,22 @@ def test_mixed_config_full_size_wavelet_and_direct():
     uvw = w.uvw
     t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
     vw = wt.wt_predict_vis(t, dev(uvw), mode=wt.WT_MIXED).cpu().numpy()
+    vr = wt.wt_predict_vis(t, dev(uvw), mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ17_REGROUPED).cpu().numpy()
     vd = wt.dft_predict_vis(dev(w.l), dev(w.m), dev(w.flux), dev(uvw), mode=wt.WT_MIXED).cpu().numpy()
     idx = _sample(w.n_vis, 200)
     S = np.abs(w.flux).sum()
-    assert np.max(np.abs(vw[idx] - O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(uvw[idx]))) / S <= 1e-6
+    ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(uvw[idx])
+    assert np.max(np.abs(vw[idx] - ref)) / S <= 1e-6
+    assert np.max(np.abs(vr[idx] - ref)) / S <= 1e-6
     assert np.max(np.abs(vd[idx] - O.dft(w.l, w.m, w.flux, uvw[idx]))) / S <= 1e-6
 
 
-def test_learned_array_full_size_mixed():
+@pytest.mark.parametrize("mode,which", [(wt.WT_MIXED, wt.WT_SUM_EQ17),
+                                        (wt.WT_MIXED_FAST, wt.WT_SUM_EQ17_REGROUPED)])
+def test_learned_array_full_size_mixed(mode, which):
     w = synth.learned()
     t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
-    v = wt.wt_predict_vis(t, dev(w.uvw), mode=wt.WT_MIXED).cpu().numpy()
+    v = wt.wt_predict_vis(t, dev(w.uvw), mode=mode, which=which).cpu().numpy()
     idx = _sample(w.n_vis, 200)
     ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(w.uvw[idx])
     assert np.max(np.abs(v[idx] - ref)) / np.abs(w.flux).sum() <= 1e-6

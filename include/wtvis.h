@@ -234,6 +234,69 @@ int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid,
                    int64_t n_vis, int mode, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The imaging half of the major cycle (Sec. 2.2: Hogbom clean, Eqs. 4-6, and
+ * the Cotton-Schwab steps after Eq. 6). Conventions: an n x n float32 image,
+ * n even, pixel size dl radians, pixel (ix, iy) at l = (ix - n/2) dl,
+ * m = (iy - n/2) dl, stored row-major [iy][ix]; visibilities complex64 with
+ * uvw in wavelengths (device float64 [n_vis][3]). Gridding is nearest-cell
+ * (cell size 1/(n dl)) with unit weights, each visibility with its Hermitian
+ * conjugate at -B; a visibility whose cell falls outside the grid is left
+ * out; w is not used in imaging (the 2-D transform of Eq. 2). The 2-D FFT is
+ * cuFFT's, loaded at the first call (WT_ERR_UNSUPPORTED if libcufft.so.12
+ * cannot be loaded).
+ * ------------------------------------------------------------------------- */
+
+/* wt_dirty_image -- major-cycle step 3: grid and transform to the dirty image
+ *   I(l, m) = (1/W) Re sum_cells G(u, v) exp(-i 2 pi (ul + vm)),
+ * W = the number of gridded entries, so a unit point source at the phase
+ * centre images to 1. vis = NULL gives the dirty beam (the image of unit
+ * visibilities, 1 at pixel (n/2, n/2)).
+ *   vis    device complex64 [n_vis], or NULL
+ *   image  device float32 [n][n], written
+ * Allocates an n x n complex64 scratch grid on `stream` and releases it. */
+int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis, int n, double dl, float* image,
+                   void* stream);
+
+/* wt_hogbom -- Eqs. 4-5: Hogbom clean of `image` in place. Each iteration
+ * takes the pixel with the largest value C (ties: the first in row-major
+ * order), records the component g C there, and subtracts g C times the beam
+ * centred on it wherever the shifted beam overlaps the image (float32,
+ * fl(I - fl(f B))). Stops after max_iter components or when the largest
+ * value falls below `threshold`.
+ *   image      device float32 [n][n], cleaned in place (the residual)
+ *   psf        device float32 [n][n], the beam with its centre at (n/2, n/2)
+ *   comp_pix   device int32 [max_iter]: row-major pixel index iy n + ix
+ *   comp_flux  device float32 [max_iter]: g C of each component
+ *   n_comp     device int32: the number of components recorded
+ * gain in (0, 1]. One kernel launch per iteration; asynchronous. */
+int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold, int max_iter, int* comp_pix,
+              float* comp_flux, int* n_comp, void* stream);
+
+/* wt_clean -- Cotton-Schwab major cycles (Sec. 2.2) around the paper's
+ * prediction: the dirty beam once; then per major cycle the dirty image of
+ * the residual visibilities, up to minor_iter Hogbom iterations, model
+ * visibilities from every component found so far (predictor
+ * WT_PREDICT_TREE: wt_build_tree at level J and the regrouped Eq. 17;
+ * WT_PREDICT_DIRECT: the direct sum, Eq. 12), and V_resid = V - V_M. Ends
+ * after n_major cycles or a cycle that finds no component, and leaves the
+ * dirty image of the final residual visibilities in image_resid.
+ *   vis_obs     device complex64 [n_vis]
+ *   mode        WT_MIXED or WT_MIXED_FAST (the prediction's form)
+ *   comp_pix, comp_flux  device [minor_iter * n_major], as wt_hogbom,
+ *               every cycle's components in order
+ *   n_comp      HOST int32: the number of components found
+ *   vis_resid   device complex64 [n_vis], written
+ *   image_resid device float32 [n][n], written
+ * Components sit at pixel centres (l, m) of the image. Synchronises the
+ * stream once per major cycle (to read the component count); allocates its
+ * scratch on `stream` and releases it. */
+#define WT_PREDICT_TREE 0
+#define WT_PREDICT_DIRECT 1
+int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, int n, double dl, double ra0, double dec0,
+             int J, int predictor, int mode, float gain, float threshold, int minor_iter, int n_major,
+             int* comp_pix, float* comp_flux, int* n_comp, void* vis_resid, float* image_resid, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Learned response (an addition to the paper's method).
  *
  * For level j, R_j(B) = 4^-D sum_i exp(i 2 pi B.(s_i - c_j)) over the 4^D

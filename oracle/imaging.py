@@ -42,11 +42,11 @@ def grid_nn(uvw, vis, n, dl):
     gridded entries W."""
     uvw = np.asarray(uvw, dtype=np.float64)
     vis = np.asarray(vis, dtype=np.complex128)
-    du = 1.0 / (n * dl)
+    inv_du = n * dl                                   # 1 / du
     G = np.zeros((n, n), dtype=np.complex128)
     W = 0
     for (u, v, _), V in zip(uvw, vis):
-        ru, rv = np.rint(u / du), np.rint(v / du)
+        ru, rv = np.rint(u * inv_du), np.rint(v * inv_du)
         if not (-n // 2 < ru < n // 2 and -n // 2 < rv < n // 2):
             continue
         iu, iv = int(ru) + n // 2, int(rv) + n // 2
@@ -126,20 +126,21 @@ def major_cycles(uvw, vis_obs, n, dl, gain, minor_iter, threshold, n_major, pred
     """Cotton-Schwab major cycles (the steps after Eq. 6) with the model
     visibilities from ``predict(l, m, flux, uvw)`` (Eq. 12 or Eq. 17):
     dirty image of the residuals, Hogbom minor cycles, prediction from every
-    component found so far, subtraction. Returns the component lists
-    (pixels, fluxes), the residual visibilities and the last residual
-    image."""
+    component found so far, subtraction; ends after n_major cycles or a
+    cycle without components. Returns the component lists (pixels, fluxes),
+    the residual visibilities and the dirty image of the final residual
+    visibilities."""
     psf = dirty_beam(uvw, n, dl)
     resid = np.asarray(vis_obs, dtype=np.complex128).copy()
     pix_all, flux_all = [], []
-    img = None
     for _ in range(n_major):
         dirty = dirty_image(uvw, resid, n, dl)
-        img, pix, flux = hogbom(dirty, psf, gain, minor_iter, threshold)
+        _, pix, flux = hogbom(dirty, psf, gain, minor_iter, threshold)
         if len(pix) == 0:
             break
         pix_all.extend(pix.tolist())
         flux_all.extend(flux.tolist())
         l, m = pixel_lm(pix_all, n, dl)
         resid = np.asarray(vis_obs) - predict(l, m, np.asarray(flux_all, dtype=np.float64), uvw)
+    img = dirty_image(uvw, resid, n, dl)
     return np.array(pix_all, dtype=np.int64), np.array(flux_all, dtype=np.float32), resid, img

@@ -17,6 +17,9 @@ Entry points (see include/wtvis.h for the contract of each):
     subtract_model    V_resid = V - V_M (Sec. 2.2)
     wt_recommended_J  Table 1 rule (Sec. 3.3)
     wt_device_status  read and clear the device-side status word
+    wt_dirty_image    gridding and FFT to the dirty image or beam (Sec. 2.2)
+    wt_hogbom         Hogbom clean (Eqs. 4-5)
+    wt_clean          Cotton-Schwab major cycles around the prediction
 """
 from __future__ import annotations
 
@@ -29,6 +32,7 @@ WT_OK, WT_ERR_ARG, WT_ERR_RANGE, WT_ERR_CUDA, WT_ERR_NOMEM, WT_ERR_TIMEOUT, WT_E
     0, -1, -2, -3, -4, -5, -6, -7
 WT_FP64, WT_MIXED, WT_LEARNED, WT_MIXED_FAST = 0, 1, 2, 3
 WT_SUM_EQ17, WT_SUM_EQ16, WT_SUM_EQ17_REGROUPED = 0, 1, 2
+WT_PREDICT_TREE, WT_PREDICT_DIRECT = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwtvis.so")
@@ -40,7 +44,7 @@ EXPORTS = [
     "dft_predict_vis_noalloc", "wt_predict_vis_batched",
     "wt_mlp_create", "wt_mlp_free", "wt_mlp_get_params", "wt_mlp_set_params", "wt_response_exact",
     "wt_mlp_loss_grad", "wt_mlp_train", "wt_mlp_eval", "wt_predict_vis_learned",
-    "wt_selftest_bounded_wait",
+    "wt_selftest_bounded_wait", "wt_dirty_image", "wt_hogbom", "wt_clean",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -98,6 +102,10 @@ def _declare(L):
     L.wt_device_status.argtypes = [vp]
     L.wt_selftest_bounded_wait.argtypes = [C.c_uint32, vp]
     L.wt_last_error.restype = C.c_char_p
+    L.wt_dirty_image.argtypes = [vp, vp, i64, C.c_int, d, vp, vp]
+    L.wt_hogbom.argtypes = [vp, vp, C.c_int, f, f, C.c_int, vp, vp, vp, vp]
+    L.wt_clean.argtypes = [vp, vp, i64, C.c_int, d, d, d, C.c_int, C.c_int, C.c_int, f, f, C.c_int, C.c_int,
+                           vp, vp, C.POINTER(C.c_int), vp, vp, vp]
 
 
 def _check(rc):
@@ -342,3 +350,51 @@ def wt_selftest_bounded_wait(spin_limit=1000, stream=None):
 
 def wt_last_error():
     return load().wt_last_error().decode()
+
+
+# ---------------------------------------------------------------- imaging
+
+def wt_dirty_image(uvw, vis, n, dl, out=None, stream=None):
+    """Dirty image (float32 [n][n]) of complex64 visibilities, or the dirty
+    beam when vis is None (Sec. 2.2, major-cycle step 3)."""
+    import torch
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float32, device=uvw.device)
+    v = _dev(vis, torch.complex64) if vis is not None else C.c_void_p(0)
+    _check(load().wt_dirty_image(_dev(uvw, torch.float64), v, uvw.shape[0], int(n), float(dl),
+                                 _dev(out, torch.float32), _stream(stream)))
+    return out
+
+
+def wt_hogbom(image, psf, gain, max_iter, threshold=0.0, stream=None):
+    """Hogbom clean of `image` (float32 [n][n], cleaned in place) with the
+    beam `psf`; returns (pixels int32, fluxes float32) of the components."""
+    import torch
+    n = image.shape[0]
+    pix = torch.empty(max(max_iter, 1), dtype=torch.int32, device=image.device)
+    flux = torch.empty(max(max_iter, 1), dtype=torch.float32, device=image.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=image.device)
+    _check(load().wt_hogbom(_dev(image, torch.float32), _dev(psf, torch.float32), int(n), float(gain), float(threshold),
+                            int(max_iter), _dev(pix, torch.int32), _dev(flux, torch.float32), _dev(cnt, torch.int32),
+                            _stream(stream)))
+    k = int(cnt.item())
+    return pix[:k], flux[:k]
+
+
+def wt_clean(uvw, vis_obs, n, dl, ra0, dec0, J, predictor=WT_PREDICT_TREE, mode=WT_MIXED_FAST, gain=0.1,
+             threshold=0.0, minor_iter=100, n_major=3, stream=None):
+    """Cotton-Schwab major cycles with the tree (or direct-sum) prediction;
+    returns (pixels, fluxes, residual visibilities, residual image)."""
+    import torch
+    n_vis = uvw.shape[0]
+    cap = max(minor_iter * n_major, 1)
+    pix = torch.empty(cap, dtype=torch.int32, device=uvw.device)
+    flux = torch.empty(cap, dtype=torch.float32, device=uvw.device)
+    resid = torch.empty(n_vis, dtype=torch.complex64, device=uvw.device)
+    img = torch.empty((n, n), dtype=torch.float32, device=uvw.device)
+    cnt = C.c_int(0)
+    _check(load().wt_clean(_dev(uvw, torch.float64), _dev(vis_obs, torch.complex64), n_vis, int(n), float(dl),
+                           float(ra0), float(dec0), int(J), int(predictor), int(mode), float(gain), float(threshold),
+                           int(minor_iter), int(n_major), _dev(pix, torch.int32), _dev(flux, torch.float32),
+                           C.byref(cnt), _dev(resid, torch.complex64), _dev(img, torch.float32), _stream(stream)))
+    return pix[:cnt.value], flux[:cnt.value], resid, img

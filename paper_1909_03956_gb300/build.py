@@ -71,7 +71,7 @@ def build(force=False, verbose=False, ptxas_info=False):
                 sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -271,6 +271,7 @@ def native(args):
         extras = side_measurements(wt, torch, w, l, m, fl, uvw, tree_keep, stream, flush, S)
     tree_keep.close()
     if rank == 0 and not args.no_extras:
+        extras["major_cycle"] = major_cycle_measurement(wt, torch, dev, stream, flush)
         extras["batched"] = batched_measurement(wt, torch, dev, stream, flush)
         extras["mixed_config"] = mixed_measurement(wt, torch, dev, stream, flush)
         extras["learned"] = learned_measurement(wt, torch, dev, stream, flush)
@@ -550,6 +551,59 @@ def batched_measurement(wt, torch, dev, stream, flush):
             "form": "WT_MIXED_FAST Eq. 17 regrouped (both legs)"}
 
 
+def major_cycle_measurement(wt, torch, dev, stream, flush, n=2048, minor_iter=1000, n_major=3, gain=0.1):
+    """The major cycle closed on the GPU (Sec. 2.2): the medium array's
+    visibilities of the medium sky (5 000 components in 20 blobs), imaged on
+    an n x n grid with pixels of 0.45 / max |u| (every baseline inside the
+    grid), n_major Cotton-Schwab cycles of minor_iter Hogbom iterations with
+    the tree prediction (regrouped Eq. 17, fast form, J from the Table 1
+    rule for the pixel size). Timed: the whole clean, and its parts alone
+    (dirty image, minor cycle, tree build + prediction + subtraction)."""
+    w = synth.medium()
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    uvw = d(w.uvw)
+    dl = 0.45 / float(np.max(np.abs(w.uvw[:, :2])))
+    J = wt.wt_recommended_J(dl)
+    obs = wt.dft_predict_vis(d(w.l), d(w.m), d(w.flux), uvw, mode=wt.WT_MIXED)
+    torch.cuda.synchronize()
+    wt.wt_clean(uvw, obs, n, dl, w.ra0, w.dec0, J, mode=wt.WT_MIXED_FAST, gain=gain, minor_iter=minor_iter,
+                n_major=n_major)                                    # warm-up: FFT plan, shapes tuned per tree size
+    res = {}
+    t_clean = _time_call(lambda: res.update(out=wt.wt_clean(uvw, obs, n, dl, w.ra0, w.dec0, J, mode=wt.WT_MIXED_FAST,
+                                                            gain=gain, minor_iter=minor_iter, n_major=n_major)),
+                         stream, flush, reps=1)
+    pix, flux, resid, img = res["out"]
+    # the parts alone
+    beam = wt.wt_dirty_image(uvw, None, n, dl)
+    dirty = torch.empty((n, n), dtype=torch.float32, device=dev)
+    t_dirty = _time_call(lambda: wt.wt_dirty_image(uvw, obs, n, dl, out=dirty), stream, flush)
+    work = dirty.clone()
+    t_minor = _time_call(lambda: (work.copy_(dirty), wt.wt_hogbom(work, beam, gain, minor_iter)), stream, flush,
+                         reps=1)
+    l = d((pix.cpu().numpy() % n - n // 2) * dl)
+    m = d((pix.cpu().numpy() // n - n // 2) * dl)
+    f = flux.double()
+    model = torch.empty_like(obs)
+
+    def predict():
+        t = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, J)
+        wt.wt_predict_vis(t, uvw, mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ17_REGROUPED, out=model)
+        wt.subtract_model(obs, model, mode=wt.WT_MIXED_FAST, out=model)
+        t.close()
+    t_pred = _time_call(predict, stream, flush)
+    rms0 = float(torch.sqrt(torch.mean(torch.abs(obs) ** 2)))
+    rms1 = float(torch.sqrt(torch.mean(torch.abs(resid) ** 2)))
+    nn = n * n
+    return {"workload": "medium_64ant_1008000vis_5000comp", "image": [n, n], "pixel_rad": dl, "J": J,
+            "gain": gain, "minor_iter": minor_iter, "n_major": n_major, "components": int(pix.numel()),
+            "clean_ms": t_clean * 1e3, "dirty_image_ms": t_dirty * 1e3, "minor_cycle_ms": t_minor * 1e3,
+            "minor_iteration_us": t_minor / minor_iter * 1e6,
+            # per Hogbom iteration the kernel reads and writes the image and reads the beam: 12 B per pixel
+            "minor_iteration_GBps": 12 * nn / (t_minor / minor_iter) / 1e9,
+            "predict_subtract_ms": t_pred * 1e3, "residual_rms_over_data_rms": rms1 / rms0,
+            "total_component_flux": float(flux.sum()), "true_flux": float(np.sum(w.flux))}
+
+
 def mixed_measurement(wt, torch, dev, stream, flush):
     """Config X: 128 antennas, 2 032 000 visibilities per channel at 1.3 and
     1.5 GHz, 20 000 clustered components, J = 12; the mixed form against the
@@ -818,6 +872,16 @@ def forms_once(args):
     big_b = torch.zeros_like(big_a)
     runs.append(("subtract_64Mi", lambda: wt.subtract_model(big_a, big_b, mode=wt.WT_MIXED, out=big_a)))
     runs.append(("build_tree", lambda: wt.wt_build_tree(l, m, f, w.ra0, w.dec0, w.J).close()))
+    # the major cycle's imaging at 2048 x 2048 (the bench's major-cycle workload)
+    n_img = 2048
+    dl_img = 0.45 / float(np.max(np.abs(w.uvw[:, :2])))
+    img_obs = torch.zeros(w.n_vis, dtype=torch.complex64, device=dev)
+    img_out = torch.empty((n_img, n_img), dtype=torch.float32, device=dev)
+    img_beam = torch.empty((n_img, n_img), dtype=torch.float32, device=dev)
+    runs.append(("dirty_image_2048", lambda: wt.wt_dirty_image(uvw, img_obs, n_img, dl_img, out=img_out)))
+    runs.append(("hogbom_2048_x20", lambda: (wt.wt_dirty_image(uvw, None, n_img, dl_img, out=img_beam),
+                                             img_out.copy_(img_beam),
+                                             wt.wt_hogbom(img_out, img_beam, 0.1, 20))))
     rg = wt.WT_SUM_EQ17_REGROUPED
     runs.append(("wavelet_mixed_fast_regrouped",
                  lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED_FAST, which=rg, out=o32)))

@@ -146,12 +146,12 @@ __global__ void k_image_from_fft(const float2* __restrict__ f, int n, const unsi
 {
     const unsigned long long W = *count;
     const float inv = W ? static_cast<float>(1.0 / static_cast<double>(W)) : 0.0f;
-    const int64_t nn = static_cast<int64_t>(n) * n;
-    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < nn;
-         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int iy = static_cast<int>(q / n), ix = static_cast<int>(q % n);
-        const float sg = ((ix + iy) & 1) ? -1.0f : 1.0f;
-        image[q] = sg * f[q].x * inv;
+    for (int iy = blockIdx.x; iy < n; iy += gridDim.x) {            // a row per CTA step, no division
+        const int64_t row = static_cast<int64_t>(iy) * n;
+        for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+            const float sg = ((ix + iy) & 1) ? -1.0f : 1.0f;
+            image[row + ix] = sg * f[row + ix].x * inv;
+        }
     }
 }
 
@@ -183,23 +183,53 @@ __global__ void __launch_bounds__(kImgThreads) k_hogbom_step(float* __restrict__
     const int p = st->pend_pix;
     const float f = st->pend_flux;
     const int py = p >= 0 ? p / n : 0, px = p >= 0 ? p % n : 0, c = n / 2;
-    const int64_t nn = static_cast<int64_t>(n) * n;
-    unsigned long long key = 0;
-    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < nn;
-         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        float v = img[q];
-        if (p >= 0) {
-            const int qy = static_cast<int>(q / n), qx = static_cast<int>(q % n);
-            const int by = qy - py + c, bx = qx - px + c;   // beam pixel under image pixel q
-            if (by >= 0 && by < n && bx >= 0 && bx < n) {
-                v = __fsub_rn(v, __fmul_rn(f, psf[static_cast<int64_t>(by) * n + bx]));
-                img[q] = v;
+    // this thread's largest value and its pixel: pixels are visited in
+    // increasing order, so a strict comparison keeps the first of equals
+    float bv = -INFINITY;
+    unsigned int bq = 0xffffffffu;
+    const bool vec4 = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+    for (int qy = blockIdx.x; qy < n; qy += gridDim.x) {            // a row per CTA step, no division
+        const int by = qy - py + c;                                 // beam row under image row qy
+        const bool row_hit = p >= 0 && by >= 0 && by < n;
+        float* irow = img + static_cast<int64_t>(qy) * n;
+        const float* brow = psf + static_cast<int64_t>(row_hit ? by : 0) * n;
+        const unsigned int q0 = static_cast<unsigned int>(qy) * static_cast<unsigned int>(n);
+        if (vec4) {                                                 // four pixels per step, 16-byte image accesses
+            for (int qx = 4 * threadIdx.x; qx < n; qx += 4 * blockDim.x) {
+                float4 v4 = *reinterpret_cast<const float4*>(irow + qx);
+                float v[4] = {v4.x, v4.y, v4.z, v4.w};
+                if (row_hit) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int bx = qx + j - px + c;             // beam column under qx + j
+                        if (bx >= 0 && bx < n) v[j] = __fsub_rn(v[j], __fmul_rn(f, brow[bx]));
+                    }
+                    *reinterpret_cast<float4*>(irow + qx) = make_float4(v[0], v[1], v[2], v[3]);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (v[j] > bv) {
+                        bv = v[j];
+                        bq = q0 + static_cast<unsigned int>(qx + j);
+                    }
+            }
+        } else {
+            for (int qx = threadIdx.x; qx < n; qx += blockDim.x) {
+                float v = irow[qx];
+                const int bx = qx - px + c;
+                if (row_hit && bx >= 0 && bx < n) {
+                    v = __fsub_rn(v, __fmul_rn(f, brow[bx]));
+                    irow[qx] = v;
+                }
+                if (v > bv) {
+                    bv = v;
+                    bq = q0 + static_cast<unsigned int>(qx);
+                }
             }
         }
-        const unsigned long long k =
-            (static_cast<unsigned long long>(ordered(v)) << 32) | (0xffffffffu - static_cast<unsigned int>(q));
-        if (k > key) key = k;
     }
+    unsigned long long key =
+        bq == 0xffffffffu ? 0ull : (static_cast<unsigned long long>(ordered(bv)) << 32) | (0xffffffffu - bq);
     __threadfence();   // this thread's image updates before the CTA's count below
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -266,12 +296,11 @@ __global__ void k_components_lm(const int* __restrict__ pix, const float* __rest
     f[i] = static_cast<double>(flux[i]);
 }
 
-int blocks_for(int64_t work)
+// CTAs for the row loops: one row per CTA step, at most 8 CTAs per SM.
+int rows_blocks(int n)
 {
-    int64_t b = (work + kImgThreads - 1) / kImgThreads;
-    const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
-    if (b > cap) b = cap;
-    return static_cast<int>(b < 1 ? 1 : b);
+    const int cap = num_sms() * 8;
+    return n < cap ? n : cap;
 }
 
 }  // namespace
@@ -292,7 +321,7 @@ int dirty_image(const double* uvw, const float2* vis, int64_t n_vis, int n, doub
     }
     int rc = fft2_forward(grid, n, s);
     if (rc) return rc;
-    k_image_from_fft<<<blocks_for(nn), kImgThreads, 0, s>>>(grid, n, count, image);
+    k_image_from_fft<<<rows_blocks(n), kImgThreads, 0, s>>>(grid, n, count, image);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
@@ -304,8 +333,7 @@ int hogbom(float* image, const float* psf, int n, float gain, float threshold, i
            float* comp_flux, int* n_comp, void* state, cudaStream_t s)
 {
     k_hogbom_reset<<<1, 1, 0, s>>>(static_cast<HogbomState*>(state), n_comp);
-    const int64_t nn = static_cast<int64_t>(n) * n;
-    const int blocks = blocks_for(nn);
+    const int blocks = rows_blocks(n);
     // max_iter + 1 launches: the last subtracts the last component and stops
     for (int it = 0; it <= max_iter; ++it) {
         k_hogbom_step<<<blocks, kImgThreads, 0, s>>>(image, psf, n, gain, threshold, max_iter,

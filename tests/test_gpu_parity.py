@@ -65,7 +65,7 @@ def compare_trees(w, J):
 
 # ---------------------------------------------------------------- tree build
 
-@pytest.mark.parametrize("J", [1, 2, 5, 8, 12, 16, 20, 25])
+@pytest.mark.parametrize("J", [1, 2, 5, 8, 12, 16, 20, 25, 30])
 def test_tree_bit_exact_small(J):
     compare_trees(synth.small(), J)
 
@@ -313,6 +313,17 @@ def test_wavelet_regrouped_medium_and_sign(J, mode, tol):
     w = synth.medium(n_t=6)
     assert _wavelet_case(w, J, w.uvw[::3], mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
     assert _wavelet_case(w, J, w.uvw[:999], mode, which=wt.WT_SUM_EQ17_REGROUPED, sign=-1) <= tol
+
+
+@pytest.mark.parametrize("mode,which,tol", [(wt.WT_FP64, wt.WT_SUM_EQ17, TOL64),
+                                           (wt.WT_FP64, wt.WT_SUM_EQ17_REGROUPED, TOL64),
+                                           (wt.WT_MIXED, wt.WT_SUM_EQ17, TOLMIX),
+                                           (wt.WT_MIXED_FAST, wt.WT_SUM_EQ17_REGROUPED, TOLMIX)])
+def test_wavelet_deepest_tree_J30(mode, which, tol):
+    # the largest J the int64 keys hold: level-29 HEALPix pixels (Nside 2^29),
+    # 29 stack levels, every form's launch shapes at their shared-memory limit
+    w = synth.medium_fixed(20, n_t=2)
+    assert _wavelet_case(w, 30, w.uvw[::5], mode, which=which) <= tol
 
 
 def test_wavelet_regrouped_deep_and_mixed_sign():

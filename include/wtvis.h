@@ -152,6 +152,11 @@ void wt_free_tree(wt_tree t);
  *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST (WT_LEARNED: see
  *            wt_predict_vis_learned)
  *   which    wt_sum
+ * Batches of 2^19 visibilities or more run as two concurrent launches over
+ * the two halves, the second on a library-owned side stream (one per device
+ * and caller's stream, kept for the process) forked from `stream` and joined
+ * back to it by events: work enqueued on `stream` after the call sees every
+ * output.
  * ------------------------------------------------------------------------- */
 int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
                    int mode, int sign, int which, void* stream);

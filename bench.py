@@ -352,8 +352,9 @@ def native(args):
             "sfu": ({"achieved": sfu_achieved, "peak": SFU_PEAK_TOPS, "unit": "TOP/s (sin, cos)",
                      "frac": sfu_achieved / SFU_PEAK_TOPS} if sfu_achieved else None),
             "traffic": traffic,
-            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of this form "
-                             "(profiles/); output still in L2 at exit" if traffic is not None
+            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full-size call of this form "
+                             "(its two half launches summed; profiles/); output still in L2 at exit"
+                             if traffic is not None
                              else "not captured for this form and size"),
             "algorithmic_bytes": 32 * n_vis,
             "ops_per_leaf": op_leaf,
@@ -414,10 +415,11 @@ OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE, OPS_NODE),
        ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW),
        ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW)}
 SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
-# DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
-# a form whose kernel changed since its capture has no entry.
-TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24282880}
+# DRAM bytes of one wt_predict_vis call on the medium workload at J = 12
+# (k_wavelet_mixed, two launches over the halves of the batch, summed), from
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum); a form
+# whose kernel changed since its capture has no entry.
+TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24375040}
 # Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
 # element ops per (visibility, component): phase 29, angle and SFU scaling 3
 # (fast) or polynomial sin/cos 15, the flux times (cos, sin) 2, half a Kahan

@@ -43,9 +43,6 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 MEDIUM_J = 12
-# wt_predict_vis predicts batches of this many visibilities or more as two
-# concurrent halves (the library's split size)
-SPLIT_MIN_VIS = 1 << 19
 METRIC = "model visibilities/s"
 UNIT = "vis/s"
 
@@ -308,9 +305,7 @@ def native(args):
     sfu_achieved = n_vis * SFU_OPS_LEAF[args.form] * n_leaves / t_pred / 1e12
     peak = FP32_PEAK_TOPS
     passes = (2 * J + 2 + 7) // 8
-    # tree build, the predictor (two concurrent halves from SPLIT_MIN_VIS
-    # visibilities on), the subtraction
-    launches = (4 + 3 * passes) + (2 if n_vis >= SPLIT_MIN_VIS else 1) + 1
+    launches = (4 + 3 * passes) + 1 + 1   # tree build, predictor, subtraction
     line = {
         "metric": METRIC,
         "value": world * n_vis / t_step,
@@ -352,18 +347,15 @@ def native(args):
             "sfu": ({"achieved": sfu_achieved, "peak": SFU_PEAK_TOPS, "unit": "TOP/s (sin, cos)",
                      "frac": sfu_achieved / SFU_PEAK_TOPS} if sfu_achieved else None),
             "traffic": traffic,
-            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full-size call of this form "
-                             "(its two half launches summed; profiles/); output still in L2 at exit"
-                             if traffic is not None
+            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of this form "
+                             "(profiles/); output still in L2 at exit" if traffic is not None
                              else "not captured for this form and size"),
             "algorithmic_bytes": 32 * n_vis,
             "ops_per_leaf": op_leaf,
             "ops_per_internal_node": op_node,
             "ops_per_level_J_minus_1_node": op_low,
             "level_J_minus_1_nodes": n_low,
-            "kernel": ("k_wavelet_mixed (Eq. 17 %s)" % args.sum
-                       + (", two concurrent launches over the halves of the batch; achieved over the call's "
-                          "span" if n_vis >= SPLIT_MIN_VIS else "")),
+            "kernel": "k_wavelet_mixed (Eq. 17 %s), one CTA per tile of visibilities" % args.sum,
         },
         "e2e": {"value": world * n_vis / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
@@ -415,11 +407,10 @@ OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE, OPS_NODE),
        ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW),
        ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW)}
 SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
-# DRAM bytes of one wt_predict_vis call on the medium workload at J = 12
-# (k_wavelet_mixed, two launches over the halves of the batch, summed), from
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum); a form
-# whose kernel changed since its capture has no entry.
-TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24375040}
+# DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
+# a form whose kernel or launch shape changed since its capture has no entry.
+TRAFFIC_BYTES_MEDIUM_J12 = {}
 # Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
 # element ops per (visibility, component): phase 29, angle and SFU scaling 3
 # (fast) or polynomial sin/cos 15, the flux times (cos, sin) 2, half a Kahan

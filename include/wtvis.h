@@ -152,11 +152,6 @@ void wt_free_tree(wt_tree t);
  *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST (WT_LEARNED: see
  *            wt_predict_vis_learned)
  *   which    wt_sum
- * Batches of 2^19 visibilities or more run as two concurrent launches over
- * the two halves, the second on a library-owned side stream (one per device
- * and caller's stream, kept for the process) forked from `stream` and joined
- * back to it by events: work enqueued on `stream` after the call sees every
- * output.
  * ------------------------------------------------------------------------- */
 int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
                    int mode, int sign, int which, void* stream);
@@ -273,7 +268,13 @@ int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis, int n, dou
  *   comp_pix   device int32 [max_iter]: row-major pixel index iy n + ix
  *   comp_flux  device float32 [max_iter]: g C of each component
  *   n_comp     device int32: the number of components recorded
- * gain in (0, 1]. One kernel launch per iteration; asynchronous. */
+ * gain in (0, 1]. Asynchronous. When the image's rows fit in shared memory
+ * across the GPU's CTAs (n up to about 2700 on 152 SMs) the whole clean is
+ * one cooperative launch whose CTAs meet at a grid barrier per iteration
+ * (bounded waits: WT_ERR_TIMEOUT in the device status word if one runs out,
+ * the image and the components then undefined); otherwise one launch per
+ * iteration. WT_HOGBOM=launches in the environment forces the latter. The
+ * two give identical results. */
 int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold, int max_iter, int* comp_pix,
               float* comp_flux, int* n_comp, void* stream);
 
@@ -370,6 +371,14 @@ int wt_device_status(void* stream);
  * bounded wait of the library takes when a copy does not arrive. The kernel
  * returns normally; read the outcome with wt_device_status(). */
 int wt_selftest_bounded_wait(uint32_t spin_limit, void* stream);
+
+/* Failure-detection self-test of the grid barrier of the persistent Hogbom
+ * clean (wt_hogbom): a two-CTA cooperative launch meets at a barrier that
+ * never opens (its arrival count starts past the grid size); each CTA gives
+ * up after spin_limit (1..65536) polls and WT_ERR_TIMEOUT is recorded in the
+ * device status word. The kernel returns normally; read the outcome with
+ * wt_device_status(). WT_ERR_UNSUPPORTED without cooperative launches. */
+int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream);
 
 /* Text of the calling thread's last error (never NULL). */
 const char* wt_last_error(void);

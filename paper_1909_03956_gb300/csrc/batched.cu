@@ -75,11 +75,16 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
     int cur = -1;
     int maxrow = 0;
     constexpr int64_t per_tile = static_cast<int64_t>(NT) * VPT;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = static_cast<long long>(atomicAdd(queue, 1ull));
-        __syncthreads();
-        const int64_t item = s_item;
-        __syncthreads();
+    for (int64_t step = 0;; ++step) {
+        int64_t item;
+        if (queue) {   // a persistent CTA takes the next item from the queue
+            if (threadIdx.x == 0) s_item = static_cast<long long>(atomicAdd(queue, 1ull));
+            __syncthreads();
+            item = s_item;
+            __syncthreads();
+        } else {       // one CTA per item
+            item = step == 0 ? static_cast<int64_t>(blockIdx.x) : total_items;
+        }
         if (item >= total_items) break;
         const int c = find_channel(chans, n_ch, item);
         const BatchChan ch = chans[c];
@@ -192,10 +197,14 @@ int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* 
     int per_sm = 0;
     WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
-    int64_t grid = static_cast<int64_t>(num_sms()) * per_sm;
-    if (grid > total) grid = total > 0 ? total : 1;
+    // One CTA per item: the hardware balances the SMs as CTAs finish, as for
+    // the single-channel predictor. The queue serves batches of more items
+    // than a grid holds.
+    const bool per_item = total <= 0x7fffffff;
+    int64_t grid = per_item ? total : static_cast<int64_t>(num_sms()) * per_sm;
+    if (grid < 1) grid = 1;
     k<<<static_cast<unsigned>(grid), NT, smem, s>>>(chans, n_ch, total, uvw_m, n_vis, vis, static_cast<double>(sign),
-                                                    rows_max, queue, status);
+                                                    rows_max, per_item ? nullptr : queue, status);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }

@@ -154,9 +154,10 @@ int grid_for(K kernel, int threads, int nt, size_t smem, int64_t n_vis, dim3& gr
     int per_sm = 0;
     WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "dft kernel does not fit on an SM");
-    const int64_t ntiles = (n_vis + nt - 1) / nt;   // nt = visibilities per CTA tile
-    int64_t g = static_cast<int64_t>(num_sms()) * per_sm;
-    grid = dim3(static_cast<unsigned>(g < ntiles ? g : ntiles));
+    // one CTA per tile (nt visibilities), so that the hardware balances the
+    // SMs as CTAs finish; the kernels stride only if the grid is capped
+    const int64_t ntiles = (n_vis + nt - 1) / nt;
+    grid = dim3(static_cast<unsigned>(ntiles < 0x7fffffff ? ntiles : 0x7fffffff));
     return WT_OK;
 }
 

@@ -22,18 +22,29 @@
 // largest value; ties to the first pixel in row-major order), subtracts
 // g C times the beam centred there wherever it overlaps the image, and
 // stops after max_iter components or when the maximum falls below the
-// threshold. One launch per iteration does it all: every CTA first
-// subtracts the previous iteration's component over its pixels, then finds
-// its largest updated value; a 64-bit atomicMax picks the winner and the
-// last CTA to finish (an atomic counter, no waiting) records the component
-// for the next launch. The arithmetic is float32 without contraction:
-// fl(g C) and fl(I - fl(f B)).
+// threshold. The arithmetic is float32 without contraction: fl(g C) and
+// fl(I - fl(f B)). Two schedules, identical results:
+//   persistent  the whole minor cycle in one cooperative launch: each CTA
+//               keeps its rows of the image in shared memory for every
+//               iteration, subtracts the pending component there (the beam
+//               is read from global memory and stays in L2), and meets the
+//               other CTAs once per iteration at a grid barrier, after
+//               which every CTA reduces the partial maxima itself;
+//   per launch  one launch per iteration when the rows do not fit in shared
+//               memory: every CTA subtracts the previous component over its
+//               pixels and finds its largest updated value; a 64-bit
+//               atomicMax picks the winner and the last CTA to finish (an
+//               atomic counter, no waiting) records the component for the
+//               next launch.
 #include <dlfcn.h>
 #include <math.h>
 #include <stdint.h>
+#include <stddef.h>
+#include <string.h>
 
 #include <cufft.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -283,6 +294,239 @@ __global__ void k_hogbom_reset(HogbomState* st, int* n_comp)
     *n_comp = 0;
 }
 
+// ---------------------------------------------------------------- persistent Hogbom
+constexpr int kHogThreads = 512;
+constexpr int kMaxHogCtas = 1024;
+constexpr int kRowsAhead = 4;   // rows whose beam values a thread loads before using them
+// Polls of the grid barrier before a CTA gives up: each poll is an L2 load
+// and a 40 ns sleep, so the limit is of the order of a second (a healthy
+// barrier completes within microseconds).
+constexpr uint32_t kGridSpinLimit = 1u << 20;
+
+struct HogSync {
+    unsigned int count;                          // CTAs arrived at the open barrier
+    unsigned int gen;                            // barriers completed
+    int abort;                                   // 1 once a CTA gave up waiting
+    int pad;
+    unsigned long long part[2][kMaxHogCtas];     // per-CTA maxima, by iteration parity
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ float unordered(unsigned int o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);   // inverse of ordered()
+}
+
+// Barrier over the CTAs of a cooperative launch (all resident). The last
+// CTA to arrive resets the count and advances the generation with a release
+// store; the others poll it with acquire loads. False when this CTA gave up
+// (WT_ERR_TIMEOUT recorded) or another CTA had.
+__device__ bool grid_barrier(HogSync* sy, unsigned int& gen, int* status, uint32_t limit = kGridSpinLimit)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const unsigned int g = gen;
+        __threadfence();   // this CTA's writes before its arrival
+        if (atomicAdd(&sy->count, 1u) == gridDim.x - 1) {
+            sy->count = 0;   // every CTA has arrived: none touches the count until the generation moves
+            st_release_u32(&sy->gen, g + 1);
+        } else {
+            uint32_t polls = 0;
+            while (ld_acquire_u32(&sy->gen) == g) {
+                if (*reinterpret_cast<volatile int*>(&sy->abort) || ++polls > limit) {
+                    good = 0;
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        if (!good) {
+            atomicExch(&sy->abort, 1);
+            record_status(status, WT_ERR_TIMEOUT);
+        }
+        gen = g + 1;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// A barrier that never opens: the arrival count starts past the grid size.
+__global__ void k_selftest_grid_barrier(HogSync* sy, uint32_t limit, int* status)
+{
+    unsigned int gen = 0;
+    grid_barrier(sy, gen, status, limit);
+}
+
+// CTA b owns image rows b, b + G, b + 2G, ... (G = gridDim.x <= n), held in
+// shared memory as local rows 0, 1, 2, ... for the whole clean. V4: n is a
+// multiple of 4 and the image 16-byte aligned (four pixels per thread step).
+template <bool V4>
+__global__ void __launch_bounds__(kHogThreads) k_hogbom_persistent(float* __restrict__ img,
+                                                                  const float* __restrict__ psf, int n, float gain,
+                                                                  float threshold, int max_iter,
+                                                                  HogSync* __restrict__ sy, int* __restrict__ comp_pix,
+                                                                  float* __restrict__ comp_flux,
+                                                                  int* __restrict__ n_comp, int* status)
+{
+    extern __shared__ __align__(16) float rows[];
+    __shared__ unsigned long long wbest[kHogThreads / 32];
+    __shared__ unsigned long long gbest;
+    const int G = gridDim.x, b = blockIdx.x, c = n / 2;
+    const int nloc = (n - 1 - b) / G + 1;
+    constexpr int kStep = V4 ? 4 : 1;
+    for (int r = 0; r < nloc; ++r) {
+        const float* src = img + static_cast<int64_t>(b + r * G) * n;
+        float* dst = rows + static_cast<int64_t>(r) * n;
+        if constexpr (V4) {
+            for (int x = 4 * threadIdx.x; x < n; x += 4 * kHogThreads)
+                *reinterpret_cast<float4*>(dst + x) = __ldcg(reinterpret_cast<const float4*>(src + x));
+        } else {
+            for (int x = threadIdx.x; x < n; x += kHogThreads) dst[x] = __ldcg(src + x);
+        }
+    }
+    __syncthreads();
+    unsigned int gen = 0;
+    int pend = -1, it = 0;
+    float pf = 0.0f;
+    for (;;) {
+        const int py = pend >= 0 ? pend / n : 0, px = pend >= 0 ? pend % n : 0;
+        // this thread's largest value and its pixel (ties: the lower pixel)
+        float bv = -INFINITY;
+        unsigned int bq = 0xffffffffu;
+        for (int qx = kStep * threadIdx.x; qx < n; qx += kStep * kHogThreads) {
+            for (int r0 = 0; r0 < nloc; r0 += kRowsAhead) {
+                // the beam values of kRowsAhead rows first: their loads overlap
+                float bm[kRowsAhead][kStep];
+                bool in[kRowsAhead][kStep];
+#pragma unroll
+                for (int i = 0; i < kRowsAhead; ++i) {
+                    const int by = b + (r0 + i) * G - py + c;   // beam row under image row b + (r0 + i) G
+                    const bool hit = pend >= 0 && r0 + i < nloc && by >= 0 && by < n;
+                    const float* brow = psf + static_cast<int64_t>(hit ? by : 0) * n;
+#pragma unroll
+                    for (int j = 0; j < kStep; ++j) {
+                        const int bx = qx + j - px + c;         // beam column under qx + j
+                        in[i][j] = hit && bx >= 0 && bx < n;
+                        bm[i][j] = in[i][j] ? __ldg(brow + bx) : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kRowsAhead; ++i) {
+                    const int r = r0 + i;
+                    if (r >= nloc) break;
+                    float* row = rows + static_cast<int64_t>(r) * n;
+                    float v[kStep];
+                    if constexpr (V4) {
+                        const float4 v4 = *reinterpret_cast<const float4*>(row + qx);
+                        v[0] = v4.x; v[1] = v4.y; v[2] = v4.z; v[3] = v4.w;
+                    } else {
+                        v[0] = row[qx];
+                    }
+                    bool any = false;
+#pragma unroll
+                    for (int j = 0; j < kStep; ++j)
+                        if (in[i][j]) {
+                            v[j] = __fsub_rn(v[j], __fmul_rn(pf, bm[i][j]));
+                            any = true;
+                        }
+                    if (any) {
+                        if constexpr (V4) {
+                            *reinterpret_cast<float4*>(row + qx) = make_float4(v[0], v[1], v[2], v[3]);
+                        } else {
+                            row[qx] = v[0];
+                        }
+                    }
+                    const unsigned int q0 = static_cast<unsigned int>(b + r * G) * static_cast<unsigned int>(n);
+#pragma unroll
+                    for (int j = 0; j < kStep; ++j) {
+                        const unsigned int q = q0 + static_cast<unsigned int>(qx + j);
+                        if (v[j] > bv || (v[j] == bv && q < bq)) {
+                            bv = v[j];
+                            bq = q;
+                        }
+                    }
+                }
+            }
+        }
+        unsigned long long key =
+            bq == 0xffffffffu ? 0ull : (static_cast<unsigned long long>(ordered(bv)) << 32) | (0xffffffffu - bq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            if (other > key) key = other;
+        }
+        if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = key;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = wbest[0];
+            for (int w = 1; w < kHogThreads / 32; ++w)
+                if (wbest[w] > m) m = wbest[w];
+            __stcg(&sy->part[it & 1][b], m);
+        }
+        if (!grid_barrier(sy, gen, status)) return;
+        // every CTA reduces the G partial maxima (one load per thread, all in
+        // flight at once): all CTAs take the same decision
+        {
+            unsigned long long m = 0;
+            for (int i = threadIdx.x; i < G; i += kHogThreads) {
+                const unsigned long long o = __ldcg(&sy->part[it & 1][i]);
+                if (o > m) m = o;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+                if (other > m) m = other;
+            }
+            if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long g = wbest[0];
+                for (int w = 1; w < kHogThreads / 32; ++w)
+                    if (wbest[w] > g) g = wbest[w];
+                gbest = g;
+            }
+        }
+        __syncthreads();
+        const unsigned long long k = gbest;
+        const float peak = unordered(static_cast<unsigned int>(k >> 32));
+        if (it >= max_iter || !(peak >= threshold)) break;
+        pend = static_cast<int>(0xffffffffu - static_cast<unsigned int>(k & 0xffffffffu));
+        pf = __fmul_rn(gain, peak);
+        if (b == 0 && threadIdx.x == 0) {
+            comp_pix[it] = pend;
+            comp_flux[it] = pf;
+        }
+        ++it;
+        // the next iteration writes the other parity of `part`: a CTA still
+        // reading this one is not overtaken before the next barrier
+    }
+    for (int r = 0; r < nloc; ++r) {
+        float* dst = img + static_cast<int64_t>(b + r * G) * n;
+        const float* src = rows + static_cast<int64_t>(r) * n;
+        if constexpr (V4) {
+            for (int x = 4 * threadIdx.x; x < n; x += 4 * kHogThreads)
+                *reinterpret_cast<float4*>(dst + x) = *reinterpret_cast<const float4*>(src + x);
+        } else {
+            for (int x = threadIdx.x; x < n; x += kHogThreads) dst[x] = src[x];
+        }
+    }
+    if (b == 0 && threadIdx.x == 0) *n_comp = it;
+}
+
 // ---------------------------------------------------------------- components
 // (l, m, flux) in float64 of recorded components [from, to).
 __global__ void k_components_lm(const int* __restrict__ pix, const float* __restrict__ flux, int from, int to, int n,
@@ -329,9 +573,76 @@ int dirty_image(const double* uvw, const float2* vis, int64_t n_vis, int n, doub
 // Hogbom clean of `image` in place; components appended to comp_pix /
 // comp_flux (device, capacity max_iter), their count in *n_comp (device).
 // `state` is a device HogbomState, reset here.
+namespace {
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// CTAs and shared-memory bytes of a persistent clean of an n x n image, or 0
+// CTAs when the schedule does not apply (rows too large for shared memory,
+// no cooperative launch, or WT_HOGBOM=launches in the environment).
+template <bool V4>
+int persistent_grid(int n, size_t* smem)
+{
+    const char* e = getenv("WT_HOGBOM");
+    if (e && strcmp(e, "launches") == 0) return 0;
+    int dev = 0, coop = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int sms = num_sms();
+    for (int per_sm = 2; per_sm >= 1; --per_sm) {
+        const int G = std::min(std::min(n, per_sm * sms), kMaxHogCtas);
+        const size_t bytes = static_cast<size_t>((n + G - 1) / G) * n * sizeof(float);
+        if (bytes > static_cast<size_t>(optin) - 1024) continue;
+        if (cudaFuncSetAttribute(k_hogbom_persistent<V4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(bytes)) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hogbom_persistent<V4>, kHogThreads, bytes) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (static_cast<int64_t>(occ) * sms >= G) {
+            *smem = bytes;
+            return G;
+        }
+    }
+    return 0;
+}
+
+template <bool V4>
+int launch_persistent(int G, size_t smem, float* image, const float* psf, int n, float gain, float threshold,
+                      int max_iter, HogSync* sy, int* comp_pix, float* comp_flux, int* n_comp, cudaStream_t s)
+{
+    int* status = device_status_word();
+    if (!status) return set_error(WT_ERR_CUDA, "wt_hogbom: no device status word");
+    WT_CUDA_TRY(cudaMemsetAsync(sy, 0, offsetof(HogSync, part), s));
+    void* args[] = {&image, &psf, &n, &gain, &threshold, &max_iter, &sy, &comp_pix, &comp_flux, &n_comp, &status};
+    WT_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_hogbom_persistent<V4>), dim3(G),
+                                            dim3(kHogThreads), args, smem, s));
+    return WT_OK;
+}
+
+}  // namespace
+
 int hogbom(float* image, const float* psf, int n, float gain, float threshold, int max_iter, int* comp_pix,
            float* comp_flux, int* n_comp, void* state, cudaStream_t s)
 {
+    HogSync* sy = reinterpret_cast<HogSync*>(static_cast<char*>(state) + round256(sizeof(HogbomState)));
+    const bool v4 = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(image) & 15) == 0;
+    size_t smem = 0;
+    const int G = v4 ? persistent_grid<true>(n, &smem) : persistent_grid<false>(n, &smem);
+    if (G > 0)
+        return v4 ? launch_persistent<true>(G, smem, image, psf, n, gain, threshold, max_iter, sy, comp_pix,
+                                            comp_flux, n_comp, s)
+                  : launch_persistent<false>(G, smem, image, psf, n, gain, threshold, max_iter, sy, comp_pix,
+                                             comp_flux, n_comp, s);
     k_hogbom_reset<<<1, 1, 0, s>>>(static_cast<HogbomState*>(state), n_comp);
     const int blocks = rows_blocks(n);
     // max_iter + 1 launches: the last subtracts the last component and stops
@@ -343,7 +654,7 @@ int hogbom(float* image, const float* psf, int n, float gain, float threshold, i
     return WT_OK;
 }
 
-size_t hogbom_state_bytes() { return sizeof(HogbomState); }
+size_t hogbom_state_bytes() { return round256(sizeof(HogbomState)) + sizeof(HogSync); }
 
 int components_lm(const int* pix, const float* flux, int from, int to, int n, double dl, double* l, double* m,
                   double* f, cudaStream_t s)
@@ -400,6 +711,34 @@ extern "C" int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis,
     if (rc) return rc;
     if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync");
     return WT_OK;
+}
+
+extern "C" int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream)
+{
+    using namespace wt;
+    const char* fn = "wt_selftest_grid_barrier";
+    if (spin_limit < 1 || spin_limit > 65536) return set_error(WT_ERR_ARG, "%s: spin_limit must be in 1..65536", fn);
+    int dev = 0, coop = 0;
+    WT_CUDA_TRY(cudaGetDevice(&dev));
+    WT_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return set_error(WT_ERR_UNSUPPORTED, "%s: no cooperative launch on this device", fn);
+    int* status = device_status_word();
+    if (!status) return set_error(WT_ERR_CUDA, "%s: no device status word", fn);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HogSync* sy = nullptr;
+    WT_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sy), sizeof(HogSync), s));
+    int rc = WT_OK;
+    cudaError_t e = cudaMemsetAsync(sy, 0, offsetof(HogSync, part), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sy->count, 0x02, sizeof(unsigned int), s);   // 0x02020202 arrivals
+    if (e == cudaSuccess) {
+        void* args[] = {&sy, &spin_limit, &status};
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_selftest_grid_barrier), dim3(2), dim3(32),
+                                        args, 0, s);
+    }
+    if (e != cudaSuccess) rc = cuda_error(e, fn);
+    const cudaError_t ef = cudaFreeAsync(sy, s);
+    if (!rc && ef != cudaSuccess) rc = cuda_error(ef, "cudaFreeAsync");
+    return rc;
 }
 
 extern "C" int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold, int max_iter,

@@ -53,8 +53,25 @@ def test_dirty_image_edge_cases():
     assert not img.any()
 
 
-@pytest.mark.parametrize("n,iters,gain,thr", [(64, 300, 0.1, 0.0), (128, 500, 0.2, 0.05), (64, 50, 1.0, 0.3)])
-def test_hogbom_bit_exact_against_the_float32_oracle(n, iters, gain, thr):
+SCHEDULES = ["persistent", "launches"]
+
+
+@pytest.fixture(params=SCHEDULES)
+def schedule(request, monkeypatch):
+    # the whole clean in one cooperative launch (the default where the rows
+    # fit in shared memory) or one launch per iteration
+    if request.param == "launches":
+        monkeypatch.setenv("WT_HOGBOM", "launches")
+    else:
+        monkeypatch.delenv("WT_HOGBOM", raising=False)
+    return request.param
+
+
+@pytest.mark.parametrize("n,iters,gain,thr", [(64, 300, 0.1, 0.0), (128, 500, 0.2, 0.05), (64, 50, 1.0, 0.3),
+                                              (66, 120, 0.3, 0.0), (1024, 40, 0.1, 0.0)])
+def test_hogbom_bit_exact_against_the_float32_oracle(n, iters, gain, thr, schedule):
+    # n = 66 takes the one-pixel-per-step path (n not a multiple of 4); at
+    # n = 1024 every CTA holds several rows
     uvw, dl = _array(n)
     rng = np.random.default_rng(7)
     k = 6
@@ -72,7 +89,7 @@ def test_hogbom_bit_exact_against_the_float32_oracle(n, iters, gain, thr):
     assert np.array_equal(img.cpu().numpy(), res_o)
 
 
-def test_hogbom_maximum_value_rule_and_zero_iterations():
+def test_hogbom_maximum_value_rule_and_zero_iterations(schedule):
     n = 16
     psf = np.zeros((n, n), np.float32)
     psf[n // 2, n // 2] = 1.0
@@ -97,7 +114,7 @@ def _two_sources(n):
 
 
 @pytest.mark.parametrize("predictor", [wt.WT_PREDICT_DIRECT, wt.WT_PREDICT_TREE])
-def test_clean_recovers_point_sources(predictor):
+def test_clean_recovers_point_sources(predictor, schedule):
     n = 64
     uvw, dl, src, l, m, f = _two_sources(n)
     obs = O.dft(l, m, f, uvw).astype(np.complex64)
@@ -138,3 +155,22 @@ def test_clean_matches_the_oracle_cycle_by_cycle_with_the_direct_sum():
     assert np.array_equal(pix.cpu().numpy(), pix_o.astype(np.int32))
     assert np.allclose(flux.cpu().numpy(), flux_o, rtol=1e-4)
     assert np.max(np.abs(resid.cpu().numpy() - resid_o)) <= 1e-4 * np.max(np.abs(obs))
+
+
+def test_hogbom_grid_barrier_times_out_and_reports():
+    # the persistent clean's grid barrier, made never to open, gives up after
+    # its poll limit and reports WT_ERR_TIMEOUT; the context stays usable
+    wt.wt_device_status()
+    wt.wt_selftest_grid_barrier(500)
+    with pytest.raises(wt.WtError) as e:
+        wt.wt_device_status()
+    assert e.value.status == wt.WT_ERR_TIMEOUT
+    wt.wt_device_status()
+    n = 16
+    psf = np.zeros((n, n), np.float32)
+    psf[n // 2, n // 2] = 1.0
+    img = np.zeros((n, n), np.float32)
+    img[5, 7] = 2.0
+    pix, flux = wt.wt_hogbom(dev(img), dev(psf), 0.5, 3)
+    assert pix.cpu().tolist() == [5 * n + 7] * 3
+    assert flux.cpu().tolist() == [1.0, 0.5, 0.25]

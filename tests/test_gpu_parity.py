@@ -338,17 +338,16 @@ def test_wavelet_regrouped_deep_and_mixed_sign():
     assert _wavelet_case(w2, 11, s.uvw[::5], wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED) <= TOL64
 
 
-# ---------------------------------------------------------------- two concurrent halves
+# ---------------------------------------------------------------- one launch against pieces
 
 @pytest.mark.parametrize("n_extra", [0, 777])
 @pytest.mark.parametrize("mode", [wt.WT_MIXED_FAST, wt.WT_FP64])
-def test_wavelet_two_halves_equal_single_launches(mode, n_extra, monkeypatch):
-    # From 2^19 visibilities on, wt_predict_vis runs two halves at once, the
-    # second on a side stream forked from and joined back to the caller's.
-    # With the launch shape pinned every output equals that of single
-    # launches over pieces below the split size, bit for bit (each
-    # visibility's arithmetic is its own), the cut included; a consumer on
-    # the caller's stream sees the whole result without a synchronisation.
+def test_wavelet_one_launch_equals_pieces(mode, n_extra, monkeypatch):
+    # With the launch shape pinned, predicting a batch of several waves of
+    # CTAs in one call gives, bit for bit, what calls over pieces of it give
+    # (each visibility's arithmetic is its own, wherever its tile runs); a
+    # consumer on the caller's stream sees the whole result without a
+    # synchronisation; the visibilities at the cut match the oracle.
     monkeypatch.setenv("WT_WAVELET_VARIANT", "2")
     w = synth.medium(J=10)
     n = (1 << 19) + n_extra
@@ -359,15 +358,14 @@ def test_wavelet_two_halves_equal_single_launches(mode, n_extra, monkeypatch):
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         v = wt.wt_predict_vis(t, uvw, mode=mode, which=which)
-        seen = v.clone()                       # ordered after both halves by the join
+        seen = v.clone()
     torch.cuda.synchronize()
     q = 1 << 18
     parts = [wt.wt_predict_vis(t, uvw[a:b], mode=mode, which=which) for a, b in ((0, q), (q, n))]
     whole = torch.cat(parts).cpu().numpy()
     assert np.array_equal(v.cpu().numpy(), whole)
     assert np.array_equal(seen.cpu().numpy(), whole)
-    cut = ((n // 2 + 255) // 256) * 256
-    idx = np.array([0, cut - 2, cut - 1, cut, cut + 1, n - 1])
+    idx = np.array([0, q - 2, q - 1, q, q + 1, n - 1])
     ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, 10).vis_eq17(w.uvw[idx])
     assert np.max(np.abs(whole[idx] - ref)) / peak(w.flux) <= (TOL64 if mode == wt.WT_FP64 else TOLMIX)
 

@@ -410,7 +410,7 @@ SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # DRAM bytes of one k_wavelet_mixed launch on the medium workload at J = 12,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
 # a form whose kernel or launch shape changed since its capture has no entry.
-TRAFFIC_BYTES_MEDIUM_J12 = {}
+TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24283136}
 # Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
 # element ops per (visibility, component): phase 29, angle and SFU scaling 3
 # (fast) or polynomial sin/cos 15, the flux times (cos, sin) 2, half a Kahan

@@ -27,9 +27,9 @@
 //   persistent  the whole minor cycle in one cooperative launch: each CTA
 //               keeps its rows of the image in shared memory for every
 //               iteration, subtracts the pending component there (the beam
-//               is read from global memory and stays in L2), and meets the
-//               other CTAs once per iteration at a grid barrier, after
-//               which every CTA reduces the partial maxima itself;
+//               is read from global memory and stays in L2), and joins a
+//               grid-wide maximum of the CTAs' (value, pixel) keys once per
+//               iteration, which also serves as the iteration's barrier;
 //   per launch  one launch per iteration when the rows do not fit in shared
 //               memory: every CTA subtracts the previous component over its
 //               pixels and finds its largest updated value; a 64-bit
@@ -296,31 +296,39 @@ __global__ void k_hogbom_reset(HogbomState* st, int* n_comp)
 
 // ---------------------------------------------------------------- persistent Hogbom
 constexpr int kHogThreads = 512;
-constexpr int kMaxHogCtas = 1024;
+constexpr int kMaxHogCtas = 1024;   // grid cap of the persistent clean
 constexpr int kRowsAhead = 4;   // rows whose beam values a thread loads before using them
 // Polls of the grid barrier before a CTA gives up: each poll is an L2 load
 // and a 40 ns sleep, so the limit is of the order of a second (a healthy
 // barrier completes within microseconds).
 constexpr uint32_t kGridSpinLimit = 1u << 20;
 
+// Grid-wide maximum of one 64-bit key per CTA, once per iteration, in three
+// rotating slots: iteration i uses slot i % 3.
 struct HogSync {
-    unsigned int count;                          // CTAs arrived at the open barrier
-    unsigned int gen;                            // barriers completed
-    int abort;                                   // 1 once a CTA gave up waiting
-    int pad;
-    unsigned long long part[2][kMaxHogCtas];     // per-CTA maxima, by iteration parity
+    unsigned int count[3];        // CTAs arrived
+    int abort;                    // 1 once a CTA gave up waiting
+    unsigned long long key[3];    // running maximum of the arrived CTAs' keys
+    unsigned long long result[3]; // the maximum, published by the last CTA to arrive (0: not yet)
 };
 
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v)
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ float unordered(unsigned int o)
@@ -328,47 +336,52 @@ __device__ __forceinline__ float unordered(unsigned int o)
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);   // inverse of ordered()
 }
 
-// Barrier over the CTAs of a cooperative launch (all resident). The last
-// CTA to arrive resets the count and advances the generation with a release
-// store; the others poll it with acquire loads. False when this CTA gave up
-// (WT_ERR_TIMEOUT recorded) or another CTA had.
-__device__ bool grid_barrier(HogSync* sy, unsigned int& gen, int* status, uint32_t limit = kGridSpinLimit)
+// Called by one thread of every CTA of a cooperative launch (all resident)
+// with the CTA's key (nonzero); returns the grid's maximum in *out, or false
+// when this CTA gave up waiting (WT_ERR_TIMEOUT recorded) or another CTA had.
+// Each CTA folds its key into the slot's maximum and then counts itself in;
+// the last to arrive reads the maximum and publishes it with a release
+// store; the others poll for it with acquire loads, at most `limit` times.
+// CTA 0 clears the slot of the previous iteration once this one's result is
+// out: every CTA has read that slot's result before arriving here, and no
+// CTA uses it again before CTA 0 arrives at the next iteration.
+__device__ bool grid_max(HogSync* sy, int it, unsigned long long key, unsigned long long* out,
+                         uint32_t limit = kGridSpinLimit)
 {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int good = 1;
-        const unsigned int g = gen;
-        __threadfence();   // this CTA's writes before its arrival
-        if (atomicAdd(&sy->count, 1u) == gridDim.x - 1) {
-            sy->count = 0;   // every CTA has arrived: none touches the count until the generation moves
-            st_release_u32(&sy->gen, g + 1);
-        } else {
-            uint32_t polls = 0;
-            while (ld_acquire_u32(&sy->gen) == g) {
-                if (*reinterpret_cast<volatile int*>(&sy->abort) || ++polls > limit) {
-                    good = 0;
-                    break;
-                }
-                __nanosleep(40);
+    const int slot = it % 3;
+    atomicMax(&sy->key[slot], key);
+    unsigned long long r = 0;
+    // release: the key, and this CTA's clearing of a slot, before its
+    // arrival; acquire: for the last to arrive, every other CTA's key
+    if (atom_add_acq_rel(&sy->count[slot], 1u) == gridDim.x - 1) {
+        r = atomicAdd(&sy->key[slot], 0ull);   // every key is in
+        st_release_u64(&sy->result[slot], r);
+    } else {
+        uint32_t polls = 0;
+        while ((r = ld_acquire_u64(&sy->result[slot])) == 0) {
+            if (*reinterpret_cast<volatile int*>(&sy->abort) || ++polls > limit) {
+                atomicExch(&sy->abort, 1);
+                return false;
             }
+            __nanosleep(40);
         }
-        if (!good) {
-            atomicExch(&sy->abort, 1);
-            record_status(status, WT_ERR_TIMEOUT);
-        }
-        gen = g + 1;
-        ok = good;
     }
-    __syncthreads();
-    return ok != 0;
+    if (blockIdx.x == 0) {
+        const int prev = (it + 2) % 3;
+        sy->count[prev] = 0;
+        sy->key[prev] = 0;
+        sy->result[prev] = 0;
+    }
+    *out = r;
+    return true;
 }
 
-// A barrier that never opens: the arrival count starts past the grid size.
+// A grid maximum that never completes: the arrival count starts past the
+// grid size.
 __global__ void k_selftest_grid_barrier(HogSync* sy, uint32_t limit, int* status)
 {
-    unsigned int gen = 0;
-    grid_barrier(sy, gen, status, limit);
+    unsigned long long r;
+    if (threadIdx.x == 0 && !grid_max(sy, 0, 1ull, &r, limit)) record_status(status, WT_ERR_TIMEOUT);
 }
 
 // CTA b owns image rows b, b + G, b + 2G, ... (G = gridDim.x <= n), held in
@@ -399,7 +412,6 @@ __global__ void __launch_bounds__(kHogThreads) k_hogbom_persistent(float* __rest
         }
     }
     __syncthreads();
-    unsigned int gen = 0;
     int pend = -1, it = 0;
     float pf = 0.0f;
     for (;;) {
@@ -475,32 +487,15 @@ __global__ void __launch_bounds__(kHogThreads) k_hogbom_persistent(float* __rest
             unsigned long long m = wbest[0];
             for (int w = 1; w < kHogThreads / 32; ++w)
                 if (wbest[w] > m) m = wbest[w];
-            __stcg(&sy->part[it & 1][b], m);
-        }
-        if (!grid_barrier(sy, gen, status)) return;
-        // every CTA reduces the G partial maxima (one load per thread, all in
-        // flight at once): all CTAs take the same decision
-        {
-            unsigned long long m = 0;
-            for (int i = threadIdx.x; i < G; i += kHogThreads) {
-                const unsigned long long o = __ldcg(&sy->part[it & 1][i]);
-                if (o > m) m = o;
+            unsigned long long g = 0;
+            if (!grid_max(sy, it, m, &g)) {
+                record_status(status, WT_ERR_TIMEOUT);
+                g = 0;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
-                if (other > m) m = other;
-            }
-            if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = m;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned long long g = wbest[0];
-                for (int w = 1; w < kHogThreads / 32; ++w)
-                    if (wbest[w] > g) g = wbest[w];
-                gbest = g;
-            }
+            gbest = g;
         }
         __syncthreads();
+        if (gbest == 0) return;   // gave up waiting: every CTA leaves
         const unsigned long long k = gbest;
         const float peak = unordered(static_cast<unsigned int>(k >> 32));
         if (it >= max_iter || !(peak >= threshold)) break;
@@ -511,8 +506,6 @@ __global__ void __launch_bounds__(kHogThreads) k_hogbom_persistent(float* __rest
             comp_flux[it] = pf;
         }
         ++it;
-        // the next iteration writes the other parity of `part`: a CTA still
-        // reading this one is not overtaken before the next barrier
     }
     for (int r = 0; r < nloc; ++r) {
         float* dst = img + static_cast<int64_t>(b + r * G) * n;
@@ -622,7 +615,7 @@ int launch_persistent(int G, size_t smem, float* image, const float* psf, int n,
 {
     int* status = device_status_word();
     if (!status) return set_error(WT_ERR_CUDA, "wt_hogbom: no device status word");
-    WT_CUDA_TRY(cudaMemsetAsync(sy, 0, offsetof(HogSync, part), s));
+    WT_CUDA_TRY(cudaMemsetAsync(sy, 0, sizeof(HogSync), s));
     void* args[] = {&image, &psf, &n, &gain, &threshold, &max_iter, &sy, &comp_pix, &comp_flux, &n_comp, &status};
     WT_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_hogbom_persistent<V4>), dim3(G),
                                             dim3(kHogThreads), args, smem, s));
@@ -728,8 +721,8 @@ extern "C" int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream)
     HogSync* sy = nullptr;
     WT_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&sy), sizeof(HogSync), s));
     int rc = WT_OK;
-    cudaError_t e = cudaMemsetAsync(sy, 0, offsetof(HogSync, part), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&sy->count, 0x02, sizeof(unsigned int), s);   // 0x02020202 arrivals
+    cudaError_t e = cudaMemsetAsync(sy, 0, sizeof(HogSync), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sy->count[0], 0x02, sizeof(unsigned int), s);   // 0x02020202 arrivals
     if (e == cudaSuccess) {
         void* args[] = {&sy, &spin_limit, &status};
         e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_selftest_grid_barrier), dim3(2), dim3(32),

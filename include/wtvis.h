@@ -111,6 +111,33 @@ typedef enum {
 int wt_build_tree(const double* l, const double* m, const double* flux, int64_t n_comp,
                   double ra0, double dec0, int J, wt_tree* out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * wt_xref_table -- Sec. 3.5: the cross-reference table built before
+ * cleaning, which maps every pixel of the dirty image to its pixel k_J on
+ * the sphere at level J. Pixel (ix, iy) of an n x n image of pixel size dl
+ * sits at l = (ix - n/2) dl, m = (iy - n/2) dl (the imaging convention
+ * below) and is mapped exactly as wt_build_tree maps a component there.
+ *   table   device int64 [n][n] (row-major, iy n + ix), written; -1 where
+ *           l^2 + m^2 >= 1
+ *   n       1..16384; dl > 0 radians; J 1..30
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int wt_xref_table(int n, double dl, double ra0, double dec0, int J, int64_t* table, void* stream);
+
+/* wt_build_tree_xref -- Sec. 3.5: the tree of components found at image
+ * pixels (the clean components of a minor cycle): component i at pixel
+ * pix[i] (row-major iy n + ix) with flux[i], its k_J read from a table made
+ * by wt_xref_table with the same n, dl, ra0, dec0 and J (the table carries
+ * none of them: the caller keeps them consistent). Everything after the
+ * mapping is wt_build_tree's, so the tree equals wt_build_tree of the pixel
+ * centres' (l, m) bit for bit.
+ *   table  device int64 [n][n]; pix device int32 [n_comp];
+ *   flux   device float64 [n_comp]
+ * A pixel index outside 0..n*n-1 or a pixel outside the unit disc, or a
+ * non-finite flux, records WT_ERR_RANGE in the device status word. */
+int wt_build_tree_xref(const int64_t* table, int n, const int32_t* pix, const double* flux, int64_t n_comp,
+                       double ra0, double dec0, int J, wt_tree* out, void* stream);
+
 /* Sizes of a built tree (host outputs; any may be NULL). Waits for the
  * build's stream. nodes_per_level has J entries, level 1 first. */
 int wt_tree_info(wt_tree t, int* J, int64_t* n_leaves, int64_t* n_nodes, int64_t* nodes_per_level);
@@ -282,7 +309,9 @@ int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold
  * prediction: the dirty beam once; then per major cycle the dirty image of
  * the residual visibilities, up to minor_iter Hogbom iterations, model
  * visibilities from every component found so far (predictor
- * WT_PREDICT_TREE: wt_build_tree at level J and the regrouped Eq. 17;
+ * WT_PREDICT_TREE: the tree at level J, its components mapped through the
+ * cross-reference table of the image pixels built once per call
+ * (wt_xref_table, wt_build_tree_xref), and the regrouped Eq. 17;
  * WT_PREDICT_DIRECT: the direct sum, Eq. 12), and V_resid = V - V_M. Ends
  * after n_major cycles or a cycle that finds no component, and leaves the
  * dirty image of the final residual visibilities in image_resid.

@@ -169,6 +169,24 @@ def map_components(l, m, ra0, dec0, J):
     return k, mg
 
 
+def xref_table(n, dl, ra0, dec0, J):
+    """Sec. 3.5: the cross-reference table built before cleaning, image pixel
+    -> level-J sphere pixel. Pixel (ix, iy) of an n x n image sits at
+    l = (ix - n/2) dl, m = (iy - n/2) dl (the imaging geometry); the table is
+    indexed [iy][ix], -1 where l^2 + m^2 >= 1. Returns the table and each
+    pixel's margin to the nearest sphere-pixel edge (inf outside the disc)."""
+    ax = (np.arange(n) - n // 2).astype(np.float64) * dl
+    m, l = np.meshgrid(ax, ax, indexing="ij")
+    inside = l * l + m * m < 1.0
+    table = np.full((n, n), -1, dtype=np.int64)
+    margin = np.full((n, n), np.inf)
+    if inside.any():
+        k, mg = map_components(l[inside], m[inside], ra0, dec0, J)
+        table[inside] = k
+        margin[inside] = mg
+    return table, margin
+
+
 # ---------------------------------------------------------------------------
 # Sec. 3.5: the coefficient tree
 # ---------------------------------------------------------------------------

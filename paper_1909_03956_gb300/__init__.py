@@ -45,6 +45,7 @@ EXPORTS = [
     "wt_mlp_create", "wt_mlp_free", "wt_mlp_get_params", "wt_mlp_set_params", "wt_response_exact",
     "wt_mlp_loss_grad", "wt_mlp_train", "wt_mlp_eval", "wt_predict_vis_learned",
     "wt_selftest_bounded_wait", "wt_selftest_grid_barrier", "wt_dirty_image", "wt_hogbom", "wt_clean",
+    "wt_xref_table", "wt_build_tree_xref",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -78,6 +79,8 @@ def load(build_if_missing=True):
 def _declare(L):
     vp, d, i64 = C.c_void_p, C.c_double, C.c_int64
     L.wt_build_tree.argtypes = [vp, vp, vp, i64, d, d, C.c_int, C.POINTER(vp), vp]
+    L.wt_xref_table.argtypes = [C.c_int, d, d, d, C.c_int, vp, vp]
+    L.wt_build_tree_xref.argtypes = [vp, C.c_int, vp, vp, i64, d, d, C.c_int, C.POINTER(vp), vp]
     L.wt_tree_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(i64), vp]
     L.wt_tree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.wt_free_tree.argtypes = [vp]
@@ -172,6 +175,30 @@ def wt_build_tree(l, m, flux, ra0, dec0, J, stream=None):
     h = C.c_void_p()
     _check(load().wt_build_tree(_dev(l, torch.float64), _dev(m, torch.float64), _dev(flux, torch.float64), n,
                                 float(ra0), float(dec0), int(J), C.byref(h), _stream(stream)))
+    return Tree(h, int(J))
+
+
+def wt_xref_table(n, dl, ra0, dec0, J, out=None, stream=None):
+    """Cross-reference table (Sec. 3.5): k_J of every pixel of an n x n image
+    of pixel size dl, as an int64 CUDA tensor [n, n] (-1 outside the unit
+    disc)."""
+    import torch
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.int64, device="cuda")
+    _check(load().wt_xref_table(int(n), float(dl), float(ra0), float(dec0), int(J), _dev(out, torch.int64),
+                                _stream(stream)))
+    return out
+
+
+def wt_build_tree_xref(table, pix, flux, ra0, dec0, J, stream=None):
+    """Tree of components at image pixels (int32 row-major indices) with
+    float64 fluxes, their k_J read from a wt_xref_table table."""
+    import torch
+    n = table.shape[0]
+    h = C.c_void_p()
+    _check(load().wt_build_tree_xref(_dev(table, torch.int64), int(n), _dev(pix, torch.int32),
+                                     _dev(flux, torch.float64), pix.numel(), float(ra0), float(dec0), int(J),
+                                     C.byref(h), _stream(stream)))
     return Tree(h, int(J))
 
 

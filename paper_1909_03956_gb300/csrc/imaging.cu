@@ -797,8 +797,9 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
     // scratch: grid, beam, model visibilities, component (l, m, flux), counters
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t c3 = static_cast<size_t>(cap > 0 ? cap : 1) * 8;
+    const bool tree = predictor == WT_PREDICT_TREE;
     const size_t bytes = up(nn * 8) + up(nn * 4) + up(static_cast<size_t>(n_vis > 0 ? n_vis : 1) * 8) + 3 * up(c3) +
-                         up(8) + up(hogbom_state_bytes()) + up(4);
+                         up(8) + up(hogbom_state_bytes()) + up(4) + (tree ? up(nn * 8) : 0);
     void* scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
     if (e != cudaSuccess) {
@@ -820,9 +821,13 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
     unsigned long long* count = reinterpret_cast<unsigned long long*>(take(8));
     void* state = take(hogbom_state_bytes());
     int* d_found = reinterpret_cast<int*>(take(4));
+    int64_t* xref = tree ? reinterpret_cast<int64_t*>(take(nn * 8)) : nullptr;
 
     int total = 0;
-    rc = dirty_image(uvw, nullptr, n_vis, n, dl, beam, grid, count, s);
+    // the tree predictor maps components through the cross-reference table
+    // of the image pixels, built once (Sec. 3.5)
+    rc = tree ? wt_xref_table(n, dl, ra0, dec0, J, xref, stream) : WT_OK;
+    if (!rc) rc = dirty_image(uvw, nullptr, n_vis, n, dl, beam, grid, count, s);
     if (!rc && n_vis > 0) {
         e = cudaMemcpyAsync(vis_resid, vis_obs, static_cast<size_t>(n_vis) * 8, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync");
@@ -847,7 +852,7 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
         // 1. model visibilities from every component so far, 2. subtraction
         if (predictor == WT_PREDICT_TREE) {
             wt_tree t = nullptr;
-            if ((rc = wt_build_tree(cl, cm, cf, total, ra0, dec0, J, &t, stream))) break;
+            if ((rc = wt_build_tree_xref(xref, n, comp_pix, cf, total, ra0, dec0, J, &t, stream))) break;
             rc = wt_predict_vis(t, uvw, n_vis, model, mode, 1, WT_SUM_EQ17_REGROUPED, stream);
             wt_free_tree(t);
         } else {

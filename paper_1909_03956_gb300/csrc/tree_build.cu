@@ -4,7 +4,10 @@
 // Device pipeline, all on the caller's stream:
 //   k_map_components   one thread per component: SIN projection (Sec. 3.3),
 //                      rotation into the xyz frame (Eq. 18), colatitude from
-//                      the NCP and RA, nested pixel k_J (Sec. 3.2, 3.5).
+//                      the NCP and RA, nested pixel k_J (Sec. 3.2, 3.5);
+//   or k_map_xref      for components found at image pixels: k_J read from
+//                      the cross-reference table (Sec. 3.5) that
+//                      k_xref_table fills with the same mapping.
 //   radix sort         stable LSD sort of (k_J, component index), 8-bit
 //                      digits, ceil((2J + 2) / 8) passes of three kernels.
 //   k_gather_flux      fluxes in sorted order (contiguous for the sums).
@@ -34,27 +37,67 @@ struct Rot {
 };
 
 // ---------------------------------------------------------------- K1: map
+// k_J of the image point (l, m): SIN projection, rotation into the xyz frame,
+// colatitude from the NCP and RA, nested pixel. False outside the unit disc
+// or for a non-finite coordinate.
+__device__ __forceinline__ bool map_lm(double li, double mi, const Rot& R, int J, uint64_t* key)
+{
+    const double r2 = __dadd_rn(__dmul_rn(li, li), __dmul_rn(mi, mi));
+    if (!(r2 < 1.0) || !isfinite(li) || !isfinite(mi)) return false;
+    const double ni = __dsqrt_rn(__dsub_rn(1.0, r2));
+    const double x = __dadd_rn(__dadd_rn(__dmul_rn(R.r[0], li), __dmul_rn(R.r[1], mi)), __dmul_rn(R.r[2], ni));
+    const double y = __dadd_rn(__dadd_rn(__dmul_rn(R.r[3], li), __dmul_rn(R.r[4], mi)), __dmul_rn(R.r[5], ni));
+    const double zc = __dadd_rn(__dadd_rn(__dmul_rn(R.r[6], li), __dmul_rn(R.r[7], mi)), __dmul_rn(R.r[8], ni));
+    double phi = atan2(x, zc);
+    if (phi < 0.0) phi = __dadd_rn(phi, 2.0 * kPi);
+    if (phi >= 2.0 * kPi) phi = __dsub_rn(phi, 2.0 * kPi);
+    *key = static_cast<uint64_t>(pixel_of(J - 1, y, phi));
+    return true;
+}
+
 __global__ void k_map_components(const double* __restrict__ l, const double* __restrict__ m,
                                  const double* __restrict__ flux, int64_t n, Rot R, int J,
                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ idx, int* status)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double li = l[i], mi = m[i];
-    const double r2 = __dadd_rn(__dmul_rn(li, li), __dmul_rn(mi, mi));
     uint64_t key = 0;
-    if (!(r2 < 1.0) || !isfinite(li) || !isfinite(mi) || !isfinite(flux[i])) {
+    if (!isfinite(flux[i]) || !map_lm(l[i], m[i], R, J, &key)) {
+        key = 0;
         record_status(status, WT_ERR_RANGE);
-    } else {
-        const double ni = __dsqrt_rn(__dsub_rn(1.0, r2));
-        const double x = __dadd_rn(__dadd_rn(__dmul_rn(R.r[0], li), __dmul_rn(R.r[1], mi)), __dmul_rn(R.r[2], ni));
-        const double y = __dadd_rn(__dadd_rn(__dmul_rn(R.r[3], li), __dmul_rn(R.r[4], mi)), __dmul_rn(R.r[5], ni));
-        const double zc = __dadd_rn(__dadd_rn(__dmul_rn(R.r[6], li), __dmul_rn(R.r[7], mi)), __dmul_rn(R.r[8], ni));
-        double phi = atan2(x, zc);
-        if (phi < 0.0) phi = __dadd_rn(phi, 2.0 * kPi);
-        if (phi >= 2.0 * kPi) phi = __dsub_rn(phi, 2.0 * kPi);
-        key = static_cast<uint64_t>(pixel_of(J - 1, y, phi));
     }
+    keys[i] = key;
+    idx[i] = static_cast<uint32_t>(i);
+}
+
+// The cross-reference table of Sec. 3.5: k_J of every pixel of an n x n
+// image, pixel (ix, iy) at l = (ix - n/2) dl, m = (iy - n/2) dl; -1 where
+// the pixel lies outside the unit disc.
+__global__ void k_xref_table(int n, double dl, Rot R, int J, int64_t* __restrict__ table)
+{
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < nn;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int iy = static_cast<int>(q / n), ix = static_cast<int>(q - static_cast<int64_t>(iy) * n);
+        const double li = static_cast<double>(ix - n / 2) * dl;
+        const double mi = static_cast<double>(iy - n / 2) * dl;
+        uint64_t key = 0;
+        table[q] = map_lm(li, mi, R, J, &key) ? static_cast<int64_t>(key) : -1;
+    }
+}
+
+// Keys of components found at image pixels, read from the table.
+__global__ void k_map_xref(const int64_t* __restrict__ table, int64_t n_pix, const int32_t* __restrict__ pix,
+                           const double* __restrict__ flux, int64_t n, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ idx, int* status)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t p = pix[i];
+    const int64_t k = (p >= 0 && p < n_pix) ? table[p] : -1;
+    uint64_t key = 0;
+    if (k < 0 || !isfinite(flux[i])) record_status(status, WT_ERR_RANGE);
+    else key = static_cast<uint64_t>(k);
     keys[i] = key;
     idx[i] = static_cast<uint32_t>(i);
 }
@@ -508,8 +551,8 @@ void rotation_matrix(double ra0, double dec0, double* R)
     R[8] = ca * cd;
 }
 
-int build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
-               int J, wt_tree t, cudaStream_t s)
+int build_tree(const KeySource& src, const double* flux, int64_t n_comp, double ra0, double dec0, int J, wt_tree t,
+               cudaStream_t s)
 {
     // Capacity: level j holds at most min(n_comp, N_j) nodes.
     int64_t cap_nodes = 0;
@@ -584,8 +627,12 @@ int build_tree(const double* l, const double* m, const double* flux, int64_t n_c
 
     if (n_comp > 0) {
         const int tb = 256;
-        k_map_components<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(l, m, flux, n_comp, R, J, k0,
-                                                                                        v0, status);
+        if (src.table)
+            k_map_xref<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(src.table, src.n_pix, src.pix,
+                                                                                     flux, n_comp, k0, v0, status);
+        else
+            k_map_components<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(src.l, src.m, flux, n_comp,
+                                                                                            R, J, k0, v0, status);
         WT_CUDA_TRY(cudaGetLastError());
         const int bits = 2 * J + 2;
         const int passes = (bits + 7) / 8;
@@ -617,6 +664,19 @@ int build_tree(const double* l, const double* m, const double* flux, int64_t n_c
     WT_CUDA_TRY(cudaMemcpyAsync(t->host_hdr, d.hdr, sizeof(TreeHeader), cudaMemcpyDeviceToHost, s));
     WT_CUDA_TRY(cudaFreeAsync(scratch, s));
     t->host_valid = false;
+    return WT_OK;
+}
+
+int xref_table(int n, double dl, double ra0, double dec0, int J, int64_t* table, cudaStream_t s)
+{
+    Rot R;
+    rotation_matrix(ra0, dec0, R.r);
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    int64_t blocks = (nn + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * 16;
+    if (blocks > cap) blocks = cap;
+    k_xref_table<<<static_cast<unsigned>(blocks > 0 ? blocks : 1), 256, 0, s>>>(n, dl, R, J, table);
+    WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
 

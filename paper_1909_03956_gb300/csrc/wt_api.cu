@@ -156,24 +156,14 @@ static int check_tree(wt_tree t, const char* fn)
     return WT_OK;
 }
 
-extern "C" {
+namespace {
 
-int wt_build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
-                  int J, wt_tree* out, void* stream)
+// A new tree handle built from `src` (checked by the caller).
+int new_tree(const char* fn, const wt::KeySource& src, const double* flux, int64_t n_comp, double ra0, double dec0,
+             int J, wt_tree* out, void* stream)
 {
-    const char* fn = "wt_build_tree";
-    if (!out) return set_error(WT_ERR_ARG, "%s: out is NULL", fn);
-    *out = nullptr;
-    if (n_comp < 0) return set_error(WT_ERR_ARG, "%s: n_comp < 0", fn);
-    if (n_comp > (int64_t(1) << 30)) return set_error(WT_ERR_RANGE, "%s: n_comp too large", fn);
-    if (J < 1 || J > kMaxJ) return set_error(WT_ERR_RANGE, "%s: J = %d outside 1..%d", fn, J, kMaxJ);
-    if (!isfinite(ra0) || !isfinite(dec0)) return set_error(WT_ERR_RANGE, "%s: non-finite phase centre", fn);
-    const size_t nb = static_cast<size_t>(n_comp) * sizeof(double);
-    int rc;
-    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
-        (rc = check_device_buffer(flux, nb, fn, "flux")))
-        return rc;
     int dev = 0;
+    int rc;
     if ((rc = wt::current_device(&dev))) return rc;
     wt_tree t = new (std::nothrow) wt_tree_s();
     if (!t) return set_error(WT_ERR_NOMEM, "%s: host allocation failed", fn);
@@ -191,7 +181,7 @@ int wt_build_tree(const double* l, const double* m, const double* flux, int64_t 
         delete t;
         return cuda_error(e, "cudaMallocHost");
     }
-    rc = wt::build_tree(l, m, flux, n_comp, ra0, dec0, J, t, t->stream);
+    rc = wt::build_tree(src, flux, n_comp, ra0, dec0, J, t, t->stream);
     if (rc != WT_OK) {
         if (t->block) cudaFreeAsync(t->block, t->stream);
         cudaStreamSynchronize(t->stream);
@@ -202,6 +192,71 @@ int wt_build_tree(const double* l, const double* m, const double* flux, int64_t 
     }
     *out = t;
     return WT_OK;
+}
+
+int check_tree_args(const char* fn, int64_t n_comp, double ra0, double dec0, int J)
+{
+    if (n_comp < 0) return set_error(WT_ERR_ARG, "%s: n_comp < 0", fn);
+    if (n_comp > (int64_t(1) << 30)) return set_error(WT_ERR_RANGE, "%s: n_comp too large", fn);
+    if (J < 1 || J > kMaxJ) return set_error(WT_ERR_RANGE, "%s: J = %d outside 1..%d", fn, J, kMaxJ);
+    if (!isfinite(ra0) || !isfinite(dec0)) return set_error(WT_ERR_RANGE, "%s: non-finite phase centre", fn);
+    return WT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+
+int wt_build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
+                  int J, wt_tree* out, void* stream)
+{
+    const char* fn = "wt_build_tree";
+    if (!out) return set_error(WT_ERR_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    int rc;
+    if ((rc = check_tree_args(fn, n_comp, ra0, dec0, J))) return rc;
+    const size_t nb = static_cast<size_t>(n_comp) * sizeof(double);
+    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux")))
+        return rc;
+    wt::KeySource src;
+    src.l = l;
+    src.m = m;
+    return new_tree(fn, src, flux, n_comp, ra0, dec0, J, out, stream);
+}
+
+int wt_xref_table(int n, double dl, double ra0, double dec0, int J, int64_t* table, void* stream)
+{
+    const char* fn = "wt_xref_table";
+    if (n < 1 || n > 16384) return set_error(WT_ERR_ARG, "%s: n = %d outside 1..16384", fn, n);
+    if (!(dl > 0.0) || !isfinite(dl)) return set_error(WT_ERR_RANGE, "%s: pixel size must be positive", fn);
+    if (J < 1 || J > kMaxJ) return set_error(WT_ERR_RANGE, "%s: J = %d outside 1..%d", fn, J, kMaxJ);
+    if (!isfinite(ra0) || !isfinite(dec0)) return set_error(WT_ERR_RANGE, "%s: non-finite phase centre", fn);
+    int rc;
+    if ((rc = check_device_buffer(table, static_cast<size_t>(n) * n * sizeof(int64_t), fn, "table"))) return rc;
+    return wt::xref_table(n, dl, ra0, dec0, J, table, static_cast<cudaStream_t>(stream));
+}
+
+int wt_build_tree_xref(const int64_t* table, int n, const int32_t* pix, const double* flux, int64_t n_comp,
+                       double ra0, double dec0, int J, wt_tree* out, void* stream)
+{
+    const char* fn = "wt_build_tree_xref";
+    if (!out) return set_error(WT_ERR_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    int rc;
+    if ((rc = check_tree_args(fn, n_comp, ra0, dec0, J))) return rc;
+    if (n < 1 || n > 16384) return set_error(WT_ERR_ARG, "%s: n = %d outside 1..16384", fn, n);
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    if ((rc = check_device_buffer(table, static_cast<size_t>(nn) * sizeof(int64_t), fn, "table")) ||
+        (rc = check_device_buffer(pix, static_cast<size_t>(n_comp) * sizeof(int32_t), fn, "pix")) ||
+        (rc = check_device_buffer(flux, static_cast<size_t>(n_comp) * sizeof(double), fn, "flux")))
+        return rc;
+    wt::KeySource src;
+    src.table = table;
+    src.n_pix = nn;
+    src.pix = pix;
+    return new_tree(fn, src, flux, n_comp, ra0, dec0, J, out, stream);
 }
 
 int wt_tree_info(wt_tree t, int* J, int64_t* n_leaves, int64_t* n_nodes, int64_t* nodes_per_level)

@@ -522,8 +522,18 @@ struct WaveletJob {
 };
 
 // tree_build.cu
-int build_tree(const double* l, const double* m, const double* flux, int64_t n_comp, double ra0, double dec0,
-               int J, wt_tree t, cudaStream_t s);
+// Where a tree's components come from: image-plane (l, m), or image pixels
+// with their keys read from a cross-reference table (Sec. 3.5).
+struct KeySource {
+    const double* l = nullptr;
+    const double* m = nullptr;
+    const int64_t* table = nullptr;
+    int64_t n_pix = 0;
+    const int32_t* pix = nullptr;
+};
+int build_tree(const KeySource& src, const double* flux, int64_t n_comp, double ra0, double dec0, int J, wt_tree t,
+               cudaStream_t s);
+int xref_table(int n, double dl, double ra0, double dec0, int J, int64_t* table, cudaStream_t s);
 int tree_sync_header(wt_tree t);
 // wavelet.cu
 int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int mode, int sign, int which,

@@ -412,3 +412,51 @@ def test_dft_mixed_fast():
     assert _dft_case(w, w.uvw[::4], wt.WT_MIXED_FAST) <= TOLMIX
     s = synth.small()
     assert _dft_case(s, s.uvw[:333], wt.WT_MIXED_FAST, sign=-1) <= TOLMIX
+
+
+# ---------------------------------------------------------------- cross-reference table (Sec. 3.5)
+
+@pytest.mark.parametrize("J", [8, 12, 18])
+def test_xref_table_matches_the_oracle(J):
+    n, dl = 96, 2.0e-5
+    g = wt.wt_xref_table(n, dl, synth.RA0, synth.DEC0, J).cpu().numpy()
+    o, margin = O.xref_table(n, dl, synth.RA0, synth.DEC0, J)
+    # the GPU's atan2 may differ from libm's in the last ulp: pixels within
+    # 1e-9 of a sphere-pixel edge (a row on the phase centre's meridian
+    # here) are left out
+    clear = margin > 1e-9
+    assert clear.mean() > 0.95
+    assert np.array_equal(g[clear], o[clear])
+    # corners outside the unit disc
+    g2 = wt.wt_xref_table(8, 0.3, synth.RA0, synth.DEC0, J).cpu().numpy()
+    assert g2[0, 0] == -1 and g2[4, 4] >= 0
+
+
+def test_tree_from_xref_equals_tree_from_pixel_centres():
+    # components at image pixels (repeats merge), mapped through the table,
+    # give bit for bit the tree of the pixel centres' (l, m)
+    n, dl, J = 128, 2.0e-5, 16
+    rng = np.random.default_rng(5)
+    pix = rng.integers(0, n * n, 400).astype(np.int32)
+    pix[:20] = pix[20:40]
+    flux = rng.uniform(0.1, 1.0, 400)
+    l = (pix % n - n // 2).astype(np.float64) * dl
+    m = (pix // n - n // 2).astype(np.float64) * dl
+    table = wt.wt_xref_table(n, dl, synth.RA0, synth.DEC0, J)
+    tx = wt.wt_build_tree_xref(table, dev(pix), dev(flux), synth.RA0, synth.DEC0, J).export()
+    tl = wt.wt_build_tree(dev(l), dev(m), dev(flux), synth.RA0, synth.DEC0, J).export()
+    for k in tl:
+        assert np.array_equal(np.asarray(tx[k]), np.asarray(tl[k])), k
+
+
+def test_tree_from_xref_bad_pixel_is_reported():
+    n, J = 16, 10
+    table = wt.wt_xref_table(n, 1e-4, synth.RA0, synth.DEC0, J)
+    wt.wt_device_status()
+    t = wt.wt_build_tree_xref(table, dev(np.array([3, n * n + 5], np.int32)), dev(np.ones(2)),
+                              synth.RA0, synth.DEC0, J)
+    with pytest.raises(wt.WtError) as e:
+        wt.wt_device_status()
+    assert e.value.status == wt.WT_ERR_RANGE
+    t.close()
+    wt.wt_device_status()

@@ -155,3 +155,39 @@ def test_recommended_J_table1():
         dJ = 2.0 ** (1 - int(J)) * math.sqrt(math.pi / 3) / mas
         # the printed wavelet resolution is the rounded Delta theta_J
         assert abs(dJ / float(wres) - 1) < 0.03, (name, dJ)
+
+
+# ---------------------------------------------------------------- cross-reference table (Sec. 3.5)
+
+@pytest.mark.parametrize("ra0,dec0", [(0.3, 0.9), (4.0, -0.4), (2.0, 1.45)])
+@pytest.mark.parametrize("J", [6, 12, 20])
+def test_xref_phase_centre_pixel_is_the_phase_centre_direction(ra0, dec0, J):
+    # image pixel (n/2, n/2) is l = m = 0, the phase centre itself: its sphere
+    # pixel is that of (RA, Dec) = (ra0, dec0), found here straight from the
+    # spherical coordinates (z = sin dec, phi = RA) without the rotation
+    n, dl = 16, 1e-4
+    table, margin = O.xref_table(n, dl, ra0, dec0, J)
+    k, mg = O.ang2pix_nest(J - 1, math.sin(dec0), ra0 % (2 * math.pi))
+    assert min(mg, margin[n // 2, n // 2]) > 1e-6    # clear of every edge: the keys must agree
+    assert table[n // 2, n // 2] == k
+
+
+def test_xref_levels_nest():
+    # the table at level J, shifted by 2 (J - j) bits, is the table at level j
+    # (k_j = k_J >> 2 (J - j)) wherever neither pixel edge is within reach
+    n, dl, ra0, dec0 = 48, 3e-3, 1.1, 0.6
+    tJ, mJ = O.xref_table(n, dl, ra0, dec0, 14)
+    for j in (3, 8, 11):
+        tj, mj = O.xref_table(n, dl, ra0, dec0, j)
+        ok = (mJ > 1e-9) & (mj > 1e-9)
+        assert ok.mean() > 0.99
+        assert np.array_equal(tJ[ok] >> (2 * (14 - j)), tj[ok])
+
+
+def test_xref_outside_the_unit_disc_and_pixel_sharing():
+    # corners beyond l^2 + m^2 = 1 are -1; with pixels much smaller than the
+    # sphere pixels, neighbouring image pixels share a sphere pixel
+    table, _ = O.xref_table(8, 0.3, 0.5, 0.2, 8)
+    assert table[0, 0] == -1 and table[7, 7] == -1 and table[4, 4] >= 0
+    fine, _ = O.xref_table(32, 1e-6, 0.5, 0.2, 8)
+    assert len(np.unique(fine)) <= 4

@@ -241,7 +241,8 @@ def native(args):
     dl, dm, df = torch.empty_like(l), torch.empty_like(m), torch.empty_like(fl)
     duvw, dobs = torch.empty_like(uvw), torch.empty_like(obs)
     # the visibilities in E2E_CHUNKS pieces on two streams, so that one
-    # piece's copies overlap another's prediction; the tree is built first
+    # piece's copies overlap another's prediction; the pieces' uploads start
+    # at once and overlap the tree build, which their predictions wait for
     side = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
     bounds = np.linspace(0, n_vis, E2E_CHUNKS + 1).astype(int)
     e2e_times = []
@@ -259,10 +260,11 @@ def native(args):
         for c in range(E2E_CHUNKS):
             a, b = int(bounds[c]), int(bounds[c + 1])
             s2 = side[c % 2]
-            s2.wait_event(built)
+            s2.wait_event(e0)
             with torch.cuda.stream(s2):
                 duvw[a:b].copy_(huvw[a:b], non_blocking=True)
                 dobs[a:b].copy_(hobs[a:b], non_blocking=True)
+                s2.wait_event(built)
                 wt.wt_predict_vis(tree, duvw[a:b], mode=mode, which=which, out=model[a:b], stream=s2)
                 wt.subtract_model(dobs[a:b], model[a:b], mode=mode, out=resid[a:b], stream=s2)
                 hres[a:b].copy_(resid[a:b], non_blocking=True)

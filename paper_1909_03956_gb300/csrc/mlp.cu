@@ -17,10 +17,11 @@
 // Kernels:
 //   k_response_offsets  s_i - c_j for the 4^D sub-pixels (float64)
 //   k_response_exact    R_j(B) by the exact sum (float64, table sin/cos)
-//   k_mlp_apply         inference on the tensor cores: mma.sync m16n8k16
-//                       BF16 x BF16 -> FP32 for the 64 x 64 layer, FP32 for
-//                       the 3 -> 64 and 64 -> 2 layers; writes R or
-//                       multiplies visibilities by it in place
+//   k_mlp_apply         inference on the tensor cores: the 64 x 64 layer as
+//                       tcgen05.mma BF16 x BF16 -> FP32 into tensor memory,
+//                       128 samples per MMA tile, FP32 for the 3 -> 64 and
+//                       64 -> 2 layers; writes R or multiplies visibilities
+//                       by it in place
 //   k_mlp_train_grad    forward + backward over a batch (FP32, with the
 //                       hidden activations and W2 rounded to BF16 in the
 //                       forward pass exactly as the inference kernel sees
@@ -72,15 +73,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// D = A (16x16 bf16, row) * B (16x8 bf16, col) + C (16x8 f32)
-__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 struct Rot {
     double r[9];
@@ -156,108 +148,180 @@ struct MlpDev {
     const uint32_t* w2_bf16x2;  // W2 as bf16 pairs, row n: W2[n][2p], W2[n][2p+1] -> [n * 32 + p]
 };
 
+// One sample per thread; a CTA's 128 samples are the M = 128 rows of one
+// tcgen05 MMA tile (N = 64 hidden units, K = 64 inputs).
 constexpr int kApplyThreads = 128;
+constexpr uint32_t kTmemCols = 64;   // the 128 x 64 FP32 accumulator
 
-// One warp evaluates 16 samples per step: layer 1 straight into the A
-// fragments, layer 2 as 4 x 8 mma.sync tiles (K = 64, N = 64), layer 3 by
-// quad reductions of the accumulator fragments.
+// Byte offset of element (r, k) of an [r][64] bf16 operand in the
+// no-swizzle K-major layout of the tensor cores: core matrices of 8 rows x
+// 16 bytes, core (r/8, k/8) at (r/8) 1024 + (k/8) 128, row r%8 at 16 bytes,
+// element k%8 at 2 bytes.
+__device__ __forceinline__ uint32_t umma_off(int r, int k)
+{
+    return static_cast<uint32_t>((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor of such an operand: start address, the
+// leading byte offset (stride between core matrices along K, 128), the
+// stride byte offset (between 8-row groups, 1024), descriptor version 1,
+// base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+{
+    return static_cast<uint64_t>((saddr >> 4) & 0x3fff) | (static_cast<uint64_t>(128 >> 4) << 16) |
+           (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46);
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, BF16 A
+// and B, both K-major, N = 64 (bits 17-22: N/8), M = 128 (bits 24-28: M/16).
+constexpr uint32_t kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this thread's TMEM lane (its warp's
+// quarter of the 128 lanes, lane = row = sample).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Inference of the 3 -> 64 -> 64 -> 2 network on the 5th-generation tensor
+// cores. Per tile of 128 samples: every thread computes its sample's first
+// layer in FP32 (SiLU, rounded to BF16) straight into the A operand in
+// shared memory; one thread issues four tcgen05.mma (K = 16 each) against
+// W2 (the B operand, staged once per CTA) into a 128 x 64 FP32 accumulator
+// in tensor memory and commits to an mbarrier; every thread then reads its
+// accumulator row (tcgen05.ld), adds b2, applies SiLU and the 64 -> 2 layer
+// in FP32. Waits are bounded: a wait that runs out records WT_ERR_TIMEOUT,
+// waits once more for the MMA in flight, frees the tensor memory and leaves.
 template <bool APPLY>
 __global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const double* __restrict__ uvw, int64_t n,
                                                              float2* __restrict__ io, float scale, int sign,
-                                                             float x_max, const double* __restrict__ offs, int n_off)
+                                                             float x_max, const double* __restrict__ offs, int n_off,
+                                                             int* status)
 {
+    __shared__ __align__(1024) unsigned char sA[128 * kH * 2];
+    __shared__ __align__(1024) unsigned char sB[kH * kH * 2];
     __shared__ float sW1[kH * 3], sb1[kH], sb2[kH], sW3[2 * kH], sb3[2];
-    for (int i = threadIdx.x; i < kH * 3; i += blockDim.x) sW1[i] = p.params[oW1 + i];
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int t = threadIdx.x;
+    for (int i = t; i < kH * 3; i += kApplyThreads) sW1[i] = p.params[oW1 + i];
+    for (int i = t; i < kH; i += kApplyThreads) {
         sb1[i] = p.params[ob1 + i];
         sb2[i] = p.params[ob2 + i];
     }
-    for (int i = threadIdx.x; i < 2 * kH; i += blockDim.x) sW3[i] = p.params[oW3 + i];
-    if (threadIdx.x < 2) sb3[threadIdx.x] = p.params[ob3 + threadIdx.x];
+    for (int i = t; i < 2 * kH; i += kApplyThreads) sW3[i] = p.params[oW3 + i];
+    if (t < 2) sb3[t] = p.params[ob3 + t];
+    for (int i = t; i < kH * kH / 2; i += kApplyThreads)   // W2 row n = output unit: K-major B
+        *reinterpret_cast<uint32_t*>(sB + umma_off(i / 32, 2 * (i % 32))) = __ldg(&p.w2_bf16x2[i]);
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    if (t < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-    // B fragments of W2^T (k = input unit, n = output unit) for every tile
-    uint32_t bfr[4][8][2];
+    tc_fence_after();
+    const uint32_t tm = tmem_base;
+    const uint32_t row_addr = tm + (static_cast<uint32_t>(t & ~31) << 16);   // this warp's lanes
+    const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
+    uint32_t phase = 0;
+    const int64_t tiles = (n + 127) / 128;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t s = tile * 128 + t;
+        const bool live = s < n;
+        float x[3] = {0.f, 0.f, 0.f};
+        if (live)
+            for (int d = 0; d < 3; ++d) x[d] = static_cast<float>(uvw[3 * s + d]) * scale;
+        // layer 1 into row t of A, one 16-byte core-matrix row (8 units) at a time
 #pragma unroll
-    for (int kt = 0; kt < 4; ++kt)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int nn = 8 * nt + g, k0 = 16 * kt + 2 * tq;
-            bfr[kt][nt][0] = __ldg(&p.w2_bf16x2[nn * 32 + k0 / 2]);
-            bfr[kt][nt][1] = __ldg(&p.w2_bf16x2[nn * 32 + (k0 + 8) / 2]);
-        }
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-    for (int64_t tile = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < n;
-         tile += warps) {
-        const int64_t s0 = tile * 16 + g, s1 = s0 + 8;
-        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
-        if (s0 < n)
-            for (int d = 0; d < 3; ++d) x0[d] = static_cast<float>(uvw[3 * s0 + d]) * scale;
-        if (s1 < n)
-            for (int d = 0; d < 3; ++d) x1[d] = static_cast<float>(uvw[3 * s1 + d]) * scale;
-        // layer 1 -> A fragments (rows g, g + 8; columns 16 kt + 2 tq + {0, 1, 8, 9})
-        uint32_t a[4][4];
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) {
-            float h0[4], h1[4];
+        for (int kg = 0; kg < 8; ++kg) {
+            uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int col = 16 * kt + 2 * tq + (e & 1) + 8 * (e >> 1);
-                const float w0 = sW1[3 * col], w1 = sW1[3 * col + 1], w2 = sW1[3 * col + 2], b = sb1[col];
-                h0[e] = silu_fast(fmaf(w2, x0[2], fmaf(w1, x0[1], fmaf(w0, x0[0], b))));
-                h1[e] = silu_fast(fmaf(w2, x1[2], fmaf(w1, x1[1], fmaf(w0, x1[0], b))));
+                const int c0 = 8 * kg + 2 * e, c1 = c0 + 1;
+                const float h0 =
+                    silu_fast(fmaf(sW1[3 * c0 + 2], x[2], fmaf(sW1[3 * c0 + 1], x[1], fmaf(sW1[3 * c0], x[0], sb1[c0]))));
+                const float h1 =
+                    silu_fast(fmaf(sW1[3 * c1 + 2], x[2], fmaf(sW1[3 * c1 + 1], x[1], fmaf(sW1[3 * c1], x[0], sb1[c1]))));
+                w[e] = pack_bf16x2(h0, h1);
             }
-            a[kt][0] = pack_bf16x2(h0[0], h0[1]);
-            a[kt][1] = pack_bf16x2(h1[0], h1[1]);
-            a[kt][2] = pack_bf16x2(h0[2], h0[3]);
-            a[kt][3] = pack_bf16x2(h1[2], h1[3]);
+            *reinterpret_cast<uint4*>(sA + umma_off(t, 8 * kg)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        // layer 2 (tensor cores), SiLU, layer 3
-        float y00 = 0.f, y01 = 0.f, y10 = 0.f, y11 = 0.f;
+        // the generic-proxy writes of A before the tensor cores read it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) {
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int col = 8 * nt + 2 * tq;
-            float acc[4] = {sb2[col], sb2[col + 1], sb2[col], sb2[col + 1]};
+            for (int kk = 0; kk < kH / 16; ++kk) {   // 16 columns = two core matrices = 256 bytes along K
+                const uint64_t ad = umma_desc(a_addr + kk * 256), bd = umma_desc(b_addr + kk * 256);
+                const uint32_t acc = kk > 0;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tm),
+                    "l"(ad), "l"(bd), "r"(kMlpIdesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&bar))
+                         : "memory");
+        }
+        const bool done = mbar_wait_parity(&bar, phase);
+        if (!__syncthreads_and(done)) {
+            if (t == 0) record_status(status, WT_ERR_TIMEOUT);
+            mbar_wait_parity(&bar, phase);   // once more for the MMA in flight
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        uint32_t r[kH];
+        tmem_ld32(row_addr, r);
+        tmem_ld32(row_addr + 32, r + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float rr = sb3[0], ri = sb3[1];
 #pragma unroll
-            for (int kt = 0; kt < 4; ++kt) mma_bf16_16816(acc, a[kt], bfr[kt][nt]);
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float hr0 = silu_fast(acc[j]), hr1 = silu_fast(acc[2 + j]);
-                y00 = fmaf(sW3[col + j], hr0, y00);
-                y01 = fmaf(sW3[kH + col + j], hr0, y01);
-                y10 = fmaf(sW3[col + j], hr1, y10);
-                y11 = fmaf(sW3[kH + col + j], hr1, y11);
+        for (int c = 0; c < kH; ++c) {
+            const float h = silu_fast(__uint_as_float(r[c]) + sb2[c]);
+            rr = fmaf(sW3[c], h, rr);
+            ri = fmaf(sW3[kH + c], h, ri);
+        }
+        if (live) {
+            if (fmaxf(fabsf(x[0]), fmaxf(fabsf(x[1]), fabsf(x[2]))) > x_max) {
+                const double2 e = response_exact_one(uvw[3 * s], uvw[3 * s + 1], uvw[3 * s + 2], offs, n_off);
+                rr = static_cast<float>(e.x);
+                ri = static_cast<float>(e.y);
+            }
+            if (sign < 0) ri = -ri;
+            if (APPLY) {
+                const float2 v = io[s];
+                io[s] = make_float2(v.x * rr - v.y * ri, v.x * ri + v.y * rr);
+            } else {
+                io[s] = make_float2(rr, ri);
             }
         }
-#pragma unroll
-        for (int o = 1; o < 4; o <<= 1) {
-            y00 += __shfl_xor_sync(0xffffffffu, y00, o);
-            y01 += __shfl_xor_sync(0xffffffffu, y01, o);
-            y10 += __shfl_xor_sync(0xffffffffu, y10, o);
-            y11 += __shfl_xor_sync(0xffffffffu, y11, o);
-        }
-        // lane tq = 0 finishes row g, lane tq = 1 row g + 8
-        if (tq < 2) {
-            const int64_t s = tq ? s1 : s0;
-            if (s < n) {
-                const float* x = tq ? x1 : x0;
-                float rr = (tq ? y10 : y00) + sb3[0];
-                float ri = (tq ? y11 : y01) + sb3[1];
-                if (fmaxf(fabsf(x[0]), fmaxf(fabsf(x[1]), fabsf(x[2]))) > x_max) {
-                    const double2 e = response_exact_one(uvw[3 * s], uvw[3 * s + 1], uvw[3 * s + 2], offs, n_off);
-                    rr = static_cast<float>(e.x);
-                    ri = static_cast<float>(e.y);
-                }
-                if (sign < 0) ri = -ri;
-                if (APPLY) {
-                    const float2 v = io[s];
-                    io[s] = make_float2(v.x * rr - v.y * ri, v.x * ri + v.y * rr);
-                } else {
-                    io[s] = make_float2(rr, ri);
-                }
-            }
-        }
+        tc_fence_before();   // this tile's accumulator reads before the next tile's MMA
     }
+    __syncthreads();
+    tc_fence_after();
+    if (t < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols) : "memory");
 }
 
 __global__ void k_w2_to_bf16(const float* __restrict__ params, uint32_t* __restrict__ w2)
@@ -488,17 +552,21 @@ int launch_apply(wt_mlp m, const double* uvw, int64_t n, void* io, int sign, boo
     using namespace wt;
     const float scale = static_cast<float>(ldexp(sqrt(kPi / 3.0), 1 - m->level));   // Delta theta_j
     MlpDev p{m->params, m->w2};
-    const int64_t tiles = (n + 15) / 16;
-    int64_t blocks = (tiles + (kApplyThreads / 32) - 1) / (kApplyThreads / 32);
-    const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
-    if (blocks > cap) blocks = cap;
+    int* status = device_status_word();
+    if (!status) return set_error(WT_ERR_CUDA, "wt_mlp: no device status word");
+    // CTAs of 128 samples, at most as many as fit at once (each holds 64
+    // tensor-memory columns; 8 per SM would use all 512)
+    auto kern = apply ? k_mlp_apply<true> : k_mlp_apply<false>;
+    int per_sm = 0;
+    WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kApplyThreads, 0));
+    if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "wt_mlp: inference kernel does not fit on an SM");
+    if (per_sm > 8) per_sm = 8;
+    const int64_t tiles = (n + 127) / 128;
+    int64_t blocks = static_cast<int64_t>(num_sms()) * per_sm;
+    if (blocks > tiles) blocks = tiles;
     if (blocks < 1) blocks = 1;
-    if (apply)
-        k_mlp_apply<true><<<static_cast<unsigned>(blocks), kApplyThreads, 0, s>>>(
-            p, uvw, n, static_cast<float2*>(io), scale, sign, m->x_max, m->offs, m->n_off);
-    else
-        k_mlp_apply<false><<<static_cast<unsigned>(blocks), kApplyThreads, 0, s>>>(
-            p, uvw, n, static_cast<float2*>(io), scale, sign, m->x_max, m->offs, m->n_off);
+    kern<<<static_cast<unsigned>(blocks), kApplyThreads, 0, s>>>(p, uvw, n, static_cast<float2*>(io), scale, sign,
+                                                                 m->x_max, m->offs, m->n_off, status);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }

@@ -33,6 +33,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <random>
 #include <vector>
 
@@ -554,13 +555,15 @@ int launch_apply(wt_mlp m, const double* uvw, int64_t n, void* io, int sign, boo
     MlpDev p{m->params, m->w2};
     int* status = device_status_word();
     if (!status) return set_error(WT_ERR_CUDA, "wt_mlp: no device status word");
-    // CTAs of 128 samples, at most as many as fit at once (each holds 64
-    // tensor-memory columns; 8 per SM would use all 512)
+    // CTAs of 128 samples, as many as the registers and shared memory let
+    // reside on an SM (each holds 64 tensor-memory columns: at most 8 per SM)
     auto kern = apply ? k_mlp_apply<true> : k_mlp_apply<false>;
-    int per_sm = 0;
-    WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kApplyThreads, 0));
+    cudaFuncAttributes fa;
+    WT_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * kApplyThreads) : 8;
+    const int by_smem = static_cast<int>((227 * 1024) / (fa.sharedSizeBytes + 1024));
+    int per_sm = std::min(std::min(by_regs, by_smem), 8);
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "wt_mlp: inference kernel does not fit on an SM");
-    if (per_sm > 8) per_sm = 8;
     const int64_t tiles = (n + 127) / 128;
     int64_t blocks = static_cast<int64_t>(num_sms()) * per_sm;
     if (blocks > tiles) blocks = tiles;

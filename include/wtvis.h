@@ -68,9 +68,14 @@ typedef enum {
     WT_MIXED = 1,    /* float64-accurate phase (double-float), float32 sincos and
                         compensated float32 accumulation, complex64 output */
     WT_LEARNED = 2,  /* wavelet route only: learned per-level response (MLP) */
-    WT_MIXED_FAST = 3 /* as WT_MIXED, but sin/cos of the reduced phase from the
+    WT_MIXED_FAST = 3, /* as WT_MIXED, but sin/cos of the reduced phase from the
                          special-function unit: at most ~7e-7 of a term's flux in
                          error per term (measured against the oracle); complex64 */
+    WT_FP64_DF = 4    /* float64-class accuracy on the float32 pipe: phase, sin/cos
+                         (table method) and every sum in double-float arithmetic
+                         (48-bit significands: a term's phase error is a few times
+                         2^-48 |B.s| turns, 32x float64's); complex128 output;
+                         wt_predict_vis with WT_SUM_EQ17_REGROUPED only */
 } wt_mode;
 
 typedef enum {
@@ -174,9 +179,10 @@ void wt_free_tree(wt_tree t);
  *
  *   t        a built tree (the build must precede this call in stream order)
  *   uvw      device float64 [n_vis][3], wavelengths
- *   vis_out  device complex128 [n_vis] (WT_FP64) or complex64 [n_vis] (WT_MIXED,
+ *   vis_out  device complex128 [n_vis] (WT_FP64, WT_FP64_DF) or complex64 [n_vis] (WT_MIXED,
  *            WT_MIXED_FAST)
- *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST (WT_LEARNED: see
+ *   mode     WT_FP64, WT_FP64_DF (regrouped sum only), WT_MIXED or
+ *            WT_MIXED_FAST (WT_LEARNED: see
  *            wt_predict_vis_learned)
  *   which    wt_sum
  * ------------------------------------------------------------------------- */

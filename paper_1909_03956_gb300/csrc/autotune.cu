@@ -147,10 +147,10 @@ int choose_wavelet_variant(wt_tree t, const WaveletJob& jb, cudaStream_t s)
             const int64_t n = sample_size(v, jb);
             if (n > common) common = n;
         }
-    // the mixed forms are fast enough to time on up to 2 Mi visibilities:
-    // with a persistent grid the shapes' tails differ with the batch size,
-    // so the closer the sample is to the real batch, the better the choice
-    if (jb.mode != WT_FP64) {
+    // the float32 mixed forms are fast enough to time on up to 2 Mi
+    // visibilities: the shapes' last waves differ with the batch size, so
+    // the closer the sample is to the real batch, the better the choice
+    if (jb.mode == WT_MIXED || jb.mode == WT_MIXED_FAST) {
         const int64_t cap = int64_t(1) << 21;
         common = jb.n_vis < cap ? jb.n_vis : (common > cap ? common : cap);
     }

@@ -262,8 +262,9 @@ __global__ void __launch_bounds__(kImgThreads) k_hogbom_step(float* __restrict__
     // the last CTA: every other CTA's writes are visible after the fence
     __threadfence();
     const unsigned long long k = atomicAdd(&st->key, 0ull);
-    const int win = static_cast<int>(0xffffffffu - static_cast<unsigned int>(k & 0xffffffffu));
-    const float peak = __ldcg(img + win);
+    // no comparable value anywhere (an all-NaN image): nothing to clean
+    const int win = k ? static_cast<int>(0xffffffffu - static_cast<unsigned int>(k & 0xffffffffu)) : 0;
+    const float peak = k ? __ldcg(img + win) : __int_as_float(0x7fc00000);
     const int it = st->iter;
     if (it >= max_iter || !(peak >= threshold)) {
         st->stopped = 1;
@@ -487,6 +488,9 @@ __global__ void __launch_bounds__(kHogThreads) k_hogbom_persistent(float* __rest
             unsigned long long m = wbest[0];
             for (int w = 1; w < kHogThreads / 32; ++w)
                 if (wbest[w] > m) m = wbest[w];
+            // a CTA without a comparable value (all NaN) still takes part with
+            // the smallest key, which decodes to NaN and stops the clean
+            if (m == 0) m = 1;
             unsigned long long g = 0;
             if (!grid_max(sy, it, m, &g)) {
                 record_status(status, WT_ERR_TIMEOUT);

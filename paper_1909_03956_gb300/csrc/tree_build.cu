@@ -508,8 +508,20 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         if (!leaf) {
             wd.a = wd.b = wd.c = 0.0;
         }
+        RecWDF wdf;
+        auto split = [](double x, float& h, float& l) {
+            h = __double2float_rn(x);
+            l = __double2float_rn(x - static_cast<double>(h));
+        };
+        wdf.meta = wmeta;
+        split(wd.a, wdf.ah, wdf.al);
+        split(wd.b, wdf.bh, wdf.bl);
+        split(wd.c, wdf.ch, wdf.cl);
+        split(wgt, wdf.wh, wdf.wl);
+        wdf.pad[0] = wdf.pad[1] = wdf.pad[2] = 0.f;
         d.recwd[post] = wd;
         d.recwf[post] = wf;
+        d.recwdf[post] = wdf;
     }
 }
 
@@ -529,7 +541,8 @@ int64_t carve_bytes(int64_t cap_nodes, int64_t cap_leaves)
            4 * b(cap_nodes * 4) + b(cap_leaves * 24) + b(cap_leaves * 8) + b(cap_leaves * 8) +
            b(cap_leaves * 4) + b(cap_nodes * int64_t(sizeof(RecD))) + b(cap_nodes * int64_t(sizeof(RecF))) +
            b(cap_leaves * int64_t(sizeof(RecD))) + b(cap_leaves * int64_t(sizeof(RecF))) +
-           b(cap_nodes * int64_t(sizeof(RecWD))) + b(cap_nodes * int64_t(sizeof(RecWF))) + b(sizeof(TreeHeader));
+           b(cap_nodes * int64_t(sizeof(RecWD))) + b(cap_nodes * int64_t(sizeof(RecWF))) +
+           b(cap_nodes * int64_t(sizeof(RecWDF))) + b(sizeof(TreeHeader));
 }
 
 }  // namespace
@@ -610,6 +623,7 @@ int build_tree(const KeySource& src, const double* flux, int64_t n_comp, double 
     d.leaff = carve<RecF>(p, capl);
     d.recwd = carve<RecWD>(p, cap1);
     d.recwf = carve<RecWF>(p, cap1);
+    d.recwdf = carve<RecWDF>(p, cap1);
     d.hdr = carve<TreeHeader>(p, 1);
 
     char* q = scratch;

@@ -29,6 +29,9 @@
 //             reduced phase in float32 (Taylor series, wt_internal.cuh),
 //             recursion in float32, Kahan-compensated float32 V.
 //   WT_MIXED_FAST  as WT_MIXED with sin/cos from the special-function unit.
+//   WT_FP64_DF     float64-class: phase, sin/cos (table method) and every
+//             sum in double-float arithmetic on the float32 pipe (df64.cuh);
+//             the regrouped sum only.
 #include "staging.cuh"
 #include "wavelet_bodies.cuh"
 #include "wt_internal.cuh"
@@ -109,6 +112,56 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const Rec* __restrict__ rec
         for (int k = 0; k < VPT; ++k) {
             const int64_t n = n0 + static_cast<int64_t>(k) * NT;
             if (n < n_vis) vis[n] = make_double2(vr[k], vi[k]);
+        }
+    }
+}
+
+// The float64-class double-float form: regrouped Eq. 17 (Eq17DF) on the
+// float32 pipe. Shared memory: the record staging, the 257-entry
+// double-float sin/cos table, then the stack.
+template <int NT, int VPT>
+__global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ recs,
+                                                   const TreeHeader* __restrict__ hdr,
+                                                   const double* __restrict__ uvw, int64_t n_vis,
+                                                   double2* __restrict__ vis, double sgn, int rows, int J,
+                                                   int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stager<RecWDF> st;
+    stager_setup(st, smem, recs, hdr->n_nodes, kChunkD);
+    float4* tab = reinterpret_cast<float4*>(smem + stager_bytes<RecWDF>(kChunkD));
+    load_sincos_table_df(tab);
+    float4* stk = tab + kDfTableEntries + threadIdx.x;
+    __syncthreads();
+    const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
+    const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t n0 = tile * per_tile + threadIdx.x;
+        Eq17DF<NT, VPT> b;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+            const bool ok = n < n_vis;
+            b.u[k] = split_f64(ok ? sgn * uvw[3 * n] : 0.0);   // sign folded in (exact)
+            b.v[k] = split_f64(ok ? sgn * uvw[3 * n + 1] : 0.0);
+            b.w[k] = split_f64(ok ? sgn * uvw[3 * n + 2] : 0.0);
+            b.vr[k] = DF{0.f, 0.f};
+            b.vi[k] = DF{0.f, 0.f};
+            b.lr[k] = DF{0.f, 0.f};
+            b.li[k] = DF{0.f, 0.f};
+        }
+        b.stk = stk;
+        b.tab = tab;
+        b.J = J;
+        b.maxrow = rows - 1;
+        if (!st.sweep(b)) {
+            if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+            if (n < n_vis) vis[n] = make_double2(df_to_double(b.vr[k]), df_to_double(b.vi[k]));
         }
     }
 }
@@ -222,6 +275,7 @@ int prepare(K kernel, int nt, size_t smem, int64_t per_tile, int64_t n_vis, dim3
 int stack_rows(int mode, int which, int J)
 {
     if (which == WT_SUM_EQ16) return 0;
+    if (mode == WT_FP64_DF) return J > 3 ? J - 2 : 1;   // regrouped only
     if (which == WT_SUM_EQ17_REGROUPED) {
         if (mode == WT_FP64) return J > 3 ? 2 * (J - 2) : 2;
         return J > 4 ? J - 3 : 1;
@@ -233,6 +287,7 @@ int stack_rows(int mode, int which, int J)
 size_t stage_bytes(int mode, int which)
 {
     if (mode == WT_FP64) return stager_bytes<RecD>(kChunkD);
+    if (mode == WT_FP64_DF) return stager_bytes<RecWDF>(kChunkD) + kDfTableEntries * sizeof(float4);
     return (which == WT_SUM_EQ17_REGROUPED) ? stager_bytes<RecWF>(kChunkW) : stager_bytes<RecF>(kChunkF);
 }
 
@@ -259,6 +314,21 @@ int run_fp64(const WaveletJob& jb, cudaStream_t s)
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(jb.recwd, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     }
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+template <int NT, int VPT>
+int run_df(const WaveletJob& jb, cudaStream_t s)
+{
+    const int rows = stack_rows(WT_FP64_DF, jb.which, jb.J);
+    const size_t smem = stage_bytes(WT_FP64_DF, jb.which) + static_cast<size_t>(rows) * VPT * NT * sizeof(float4);
+    dim3 grid;
+    int rc;
+    auto k = k_wavelet_df<NT, VPT>;
+    if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
+    k<<<grid, NT, smem, s>>>(jb.recwdf, jb.hdr, jb.uvw, jb.n_vis, static_cast<double2*>(jb.vis),
+                             static_cast<double>(jb.sign), rows, jb.J, jb.status);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
@@ -318,7 +388,7 @@ int wavelet_variant_shape(int v, int* nt, int* vpt)
 size_t wavelet_variant_smem(int v, int mode, int which, int J)
 {
     if (v < 0 || v >= kNumWaveletVariants) return 0;
-    const size_t cplx = (mode == WT_FP64) ? sizeof(double2) : sizeof(float2);
+    const size_t cplx = (mode == WT_FP64 || mode == WT_FP64_DF) ? sizeof(double2) : sizeof(float2);
     const size_t stage = stage_bytes(mode, which);
     const size_t stack = static_cast<size_t>(stack_rows(mode, which, J)) * kVariants[v].nt * kVariants[v].vpt * cplx;
     return stage + stack;
@@ -334,6 +404,18 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
 {
     if (!wavelet_variant_fits(v, jb.mode, jb.which, jb.J))
         return set_error(WT_ERR_UNSUPPORTED, "wavelet variant %d does not fit for J = %d", v, jb.J);
+    if (jb.mode == WT_FP64_DF) {
+        switch (v) {
+            case 0: return run_df<256, 1>(jb, s);
+            case 1: return run_df<128, 1>(jb, s);
+            case 2: return run_df<128, 2>(jb, s);
+            case 3: return run_df<64, 2>(jb, s);
+            case 4: return run_df<64, 4>(jb, s);
+            case 5: return run_df<32, 4>(jb, s);
+            case 6: return run_df<32, 2>(jb, s);
+            default: return run_df<256, 2>(jb, s);
+        }
+    }
     if (jb.mode == WT_FP64) {
         switch (v) {
             case 0: return run_fp64<256, 1>(jb, s);
@@ -368,7 +450,7 @@ int default_wavelet_variant(int mode, int which, int J)
     static const int order_mixed[kNumWaveletVariants] = {0, 2, 1, 3, 4, 5, 6, 7};
     static const int order_mixed_rg[kNumWaveletVariants] = {2, 7, 4, 6, 3, 5, 0, 1};
     static const int order_fp64[kNumWaveletVariants] = {1, 0, 2, 3, 4, 5, 6, 7};
-    const int* order = (mode == WT_FP64) ? order_fp64
+    const int* order = (mode == WT_FP64 || mode == WT_FP64_DF) ? order_fp64
                        : (which == WT_SUM_EQ17_REGROUPED) ? order_mixed_rg : order_mixed;
     for (int i = 0; i < kNumWaveletVariants; ++i)
         if (wavelet_variant_fits(order[i], mode, which, J)) return order[i];
@@ -386,6 +468,7 @@ int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int 
     jb.recf_leaf = t->d.leaff;
     jb.recwd = t->d.recwd;
     jb.recwf = t->d.recwf;
+    jb.recwdf = t->d.recwdf;
     jb.hdr = t->d.hdr;
     jb.uvw = uvw;
     jb.n_vis = n_vis;

@@ -4,6 +4,7 @@
 // record for every thread of the CTA; see wavelet.cu for the mapping.
 #pragma once
 
+#include "df64.cuh"
 #include "staging.cuh"
 #include "wt_internal.cuh"
 
@@ -307,6 +308,82 @@ struct Eq17WD {
                 double2& px = slot(par + 1, k);
                 ps = make_double2(ps.x + er, ps.y + ei);
                 px = make_double2(fma(r.d, er, px.x), fma(r.d, ei, px.y));
+            }
+        }
+    }
+};
+
+// Regrouped Eq. 17 in double-float (WT_FP64_DF, RecWDF): V = sum_n w_n eta_n
+// with every quantity a double-float on the float32 pipe. Each node adds
+// its w eta to V as soon as its eta is known. Per visibility a thread keeps
+// the sum of the children's eta of the open level-j node (j = 1 .. J-2) in
+// shared-memory row j - 1 as (re h, re l, im h, im l); that of the open
+// level-(J-1) node lives in registers, so a leaf never touches shared
+// memory. A node's eta is a quarter of its children's sum (the Eq. 9 form;
+// exact scaling), which it passes up to its parent (the first child
+// writes, the others add).
+template <int NT, int VPT>
+struct Eq17DF {
+    F2 u[VPT], v[VPT], w[VPT];
+    DF vr[VPT], vi[VPT];   // V
+    DF lr[VPT], li[VPT];   // children's eta sum of the open level-(J-1) node
+    float4* stk;           // shared stack + threadIdx.x; row stride VPT * NT
+    const float4* tab;     // exp(i 2 pi k/256), sincos_turns_df
+    int J;
+    int maxrow;
+
+    __device__ __forceinline__ float4& slot(int row, int k) { return stk[(row * VPT + k) * NT]; }
+
+    __device__ void operator()(const RecWDF& r)
+    {
+        const uint32_t meta = r.meta;
+        const int lev = static_cast<int>(meta & 31u);
+        const bool root = meta & kRwRoot, first = meta & kRwFirst;
+        const DF wgt{r.wh, r.wl};
+        if (meta & kRwLeaf) {
+            const F2 su{r.ah, r.al}, sv{r.bh, r.bl}, sw{r.ch, r.cl};
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                float th, tl;
+                phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
+                DF s, c;
+                sincos_turns_df(th, tl, tab, s, c);
+                vr[k] = df_add(vr[k], df_mul(wgt, c));
+                vi[k] = df_add(vi[k], df_mul(wgt, s));
+                if (root) continue;
+                if (first) {
+                    lr[k] = c;
+                    li[k] = s;
+                } else {
+                    lr[k] = df_add(lr[k], c);
+                    li[k] = df_add(li[k], s);
+                }
+            }
+            return;
+        }
+        const bool in_regs = (lev == J - 1);
+        const int own = clamp_row(static_cast<uint32_t>(lev > 1 ? lev - 1 : 0), maxrow);
+        const int par = clamp_row(static_cast<uint32_t>(lev > 2 ? lev - 2 : 0), maxrow);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            DF er, ei;
+            if (in_regs) {
+                er = df_scale(lr[k], 0.25f);
+                ei = df_scale(li[k], 0.25f);
+            } else {
+                const float4 S = slot(own, k);
+                er = DF{0.25f * S.x, 0.25f * S.y};
+                ei = DF{0.25f * S.z, 0.25f * S.w};
+            }
+            vr[k] = df_add(vr[k], df_mul(wgt, er));
+            vi[k] = df_add(vi[k], df_mul(wgt, ei));
+            if (root) continue;
+            float4& P = slot(par, k);
+            if (first) {
+                P = make_float4(er.h, er.l, ei.h, ei.l);
+            } else {
+                const DF pr = df_add(DF{P.x, P.y}, er), pi = df_add(DF{P.z, P.w}, ei);
+                P = make_float4(pr.h, pr.l, pi.h, pi.l);
             }
         }
     }

@@ -442,6 +442,17 @@ struct RecWD {
 };
 static_assert(sizeof(RecWD) == 48, "RecWD layout");
 
+// float64-class double-float form (48 bytes): the fields of RecWD as
+// double-floats: leaf pixel centre (s_u, s_v, s_w - 1) = (ah + al, bh + bl,
+// ch + cl); weight w_n = wh + wl (every node).
+struct RecWDF {
+    uint32_t meta;
+    float ah, al, bh, bl, ch, cl;
+    float wh, wl;
+    float pad[3];
+};
+static_assert(sizeof(RecWDF) == 48, "RecWDF layout");
+
 // mixed (32 bytes): leaf: (a, b), (c, d), (e, f) = pixel centre as
 // double-float pairs; internal node: a, b = the stack rows of its own and
 // its parent's xi sums (j - 1 and j - 2, 0 at level 1) as unsigned integers
@@ -481,6 +492,7 @@ struct TreeDev {
     RecF* leaff;
     RecWD* recwd;         // post-order records of the regrouped Eq. 17 [cap]
     RecWF* recwf;
+    RecWDF* recwdf;
     TreeHeader* hdr;
 };
 
@@ -513,6 +525,7 @@ struct WaveletJob {
     const RecF* recf_leaf;
     const RecWD* recwd;      // regrouped Eq. 17
     const RecWF* recwf;
+    const RecWDF* recwdf;    // regrouped Eq. 17, double-float
     const TreeHeader* hdr;
     const double* uvw;
     int64_t n_vis;

@@ -19,7 +19,7 @@ wt = pytest.importorskip("paper_1909_03956_gb300")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {wt.WT_FP64: 1e-10, wt.WT_MIXED: 1e-6, wt.WT_MIXED_FAST: 1e-6}
+TOL = {wt.WT_FP64: 1e-10, wt.WT_FP64_DF: 1e-10, wt.WT_MIXED: 1e-6, wt.WT_MIXED_FAST: 1e-6}
 
 
 def dev(a):
@@ -30,8 +30,9 @@ def _sample(n, k=300):
     return np.unique(np.concatenate([np.arange(0, n, max(1, n // k)), [n - 1]]))
 
 
-@pytest.mark.parametrize("which", [wt.WT_SUM_EQ17_REGROUPED, wt.WT_SUM_EQ17])
-@pytest.mark.parametrize("mode", [wt.WT_MIXED_FAST, wt.WT_MIXED, wt.WT_FP64])
+@pytest.mark.parametrize("mode,which", [(m, w) for m in (wt.WT_MIXED_FAST, wt.WT_MIXED, wt.WT_FP64)
+                                        for w in (wt.WT_SUM_EQ17_REGROUPED, wt.WT_SUM_EQ17)]
+                         + [(wt.WT_FP64_DF, wt.WT_SUM_EQ17_REGROUPED)])
 def test_medium_full_size(mode, which):
     # the bench's step uses the regrouped sum in the fast form, autotuned shape
     w = synth.medium(J=12)

@@ -104,6 +104,19 @@ def test_hogbom_maximum_value_rule_and_zero_iterations(schedule):
     assert pix.numel() == 0
 
 
+def test_hogbom_image_without_a_comparable_value(schedule):
+    # an all-NaN image has no maximum: no component, the image untouched
+    n = 16
+    psf = np.zeros((n, n), np.float32)
+    psf[n // 2, n // 2] = 1.0
+    t = dev(np.full((n, n), np.nan, np.float32))
+    wt.wt_device_status()
+    pix, flux = wt.wt_hogbom(t, dev(psf), 0.5, 5)
+    wt.wt_device_status()
+    assert pix.numel() == 0
+    assert np.isnan(t.cpu().numpy()).all()
+
+
 def _two_sources(n):
     uvw, dl = _array(n)
     src = [(n // 2 + 6, n // 2 - 4, 1.0), (n // 2 - 9, n // 2 + 5, 0.6)]

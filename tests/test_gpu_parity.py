@@ -5,7 +5,9 @@ Bars (see the oracle's readings R1-R9):
     leaf pixel centres: within a few ulp (they go through sin/cos);
   * WT_FP64 visibilities: max |dV| <= 1e-10 * sum |C| (relative to the peak
     amplitude, the zero-spacing visibility);
-  * WT_MIXED visibilities: max |dV| <= 1e-6 * sum |C|.
+  * WT_MIXED visibilities: max |dV| <= 1e-6 * sum |C|;
+  * WT_FP64_DF visibilities: the float64 bar, or where phases reach beyond
+    about 500 turns the bar its 48-bit arithmetic implies (df_bar).
 """
 import math
 
@@ -102,6 +104,18 @@ def test_tree_empty():
 
 
 # ---------------------------------------------------------------- wavelet
+
+def df_bar(w, J, uvw):
+    """Error bar of the double-float form (WT_FP64_DF): its inputs and phase
+    carry 48 significant bits, so a term's phase can be off by a few times
+    2^-48 |B.s| turns (eight roundings' worth: 2^-45 (|u s_u| + |v s_v| +
+    |w (s_w - 1)|)), 32 times the float64 form's; summed over the terms and
+    relative to sum |C|: 2 pi 2^-45 max |B.s|. Never below the float64
+    form's bar, which it meets wherever |B.s| stays below about 500 turns."""
+    d = np.abs(O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J).export()["leaf_dir"])
+    T = float(np.max(np.abs(np.asarray(uvw)) @ d.T)) if len(d) else 0.0
+    return max(TOL64, 2 * math.pi * 2.0 ** -45 * T)
+
 
 def _wavelet_case(w, J, uvw, mode, which=wt.WT_SUM_EQ17, sign=1):
     t = gpu_tree(w, J)
@@ -296,33 +310,70 @@ def test_wavelet_every_launch_shape(variant, mode, tol, monkeypatch):
     assert _wavelet_case(w, 13, uvw, mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
 
 
+@pytest.mark.parametrize("variant", range(8))
+def test_wavelet_df_every_launch_shape(variant, monkeypatch):
+    # the double-float form in every launch shape, on a ragged count
+    monkeypatch.setenv("WT_WAVELET_VARIANT", str(variant))
+    w = synth.medium(n_t=4)
+    uvw = w.uvw[::7][:1111]
+    assert _wavelet_case(w, 13, uvw, wt.WT_FP64_DF, which=wt.WT_SUM_EQ17_REGROUPED) <= df_bar(w, 13, uvw)
+
+
+def test_wavelet_df_other_sums_refused():
+    w = synth.small()
+    t = gpu_tree(w, 8)
+    for which in (wt.WT_SUM_EQ17, wt.WT_SUM_EQ16):
+        with pytest.raises(wt.WtError) as e:
+            wt.wt_predict_vis(t, dev(w.uvw[:10]), mode=wt.WT_FP64_DF, which=which)
+        assert e.value.status == wt.WT_ERR_UNSUPPORTED
+
+
+def test_wavelet_df_agrees_with_the_float64_form_far_below_the_bar():
+    # float64-class: against the float64 kernel the double-float form
+    # differs by the phase tail's float32 rounding (about 1e-11 turns at a
+    # thousand turns), far below the 1e-10 bar both meet
+    w = synth.medium(n_t=6)
+    uvw = w.uvw[::3]
+    t = gpu_tree(w, 12)
+    a = wt.wt_predict_vis(t, dev(uvw), mode=wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED).cpu().numpy()
+    b = wt.wt_predict_vis(t, dev(uvw), mode=wt.WT_FP64_DF, which=wt.WT_SUM_EQ17_REGROUPED).cpu().numpy()
+    assert np.max(np.abs(a - b)) / peak(w.flux) <= 1e-11
+
+
 # ---------------------------------------------------------------- regrouped Eq. 17
 
-@pytest.mark.parametrize("J", [1, 2, 3, 8, 12, 20])
-@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+@pytest.mark.parametrize("J", [1, 2, 3, 4, 8, 12, 20])
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_FP64_DF, TOL64), (wt.WT_MIXED, TOLMIX)])
 def test_wavelet_regrouped_small(J, mode, tol):
     # V = sum_n w_n eta_n with w from the parents' gammas: the same terms as
     # Eq. 17, judged against the oracle's literal Eq. 17.
     w = synth.small()
+    if mode == wt.WT_FP64_DF:
+        tol = df_bar(w, J, w.uvw[::3])
     assert _wavelet_case(w, J, w.uvw[::3], mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
 
 
 @pytest.mark.parametrize("J", [10, 14])
-@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_MIXED, TOLMIX)])
+@pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_FP64_DF, TOL64), (wt.WT_MIXED, TOLMIX)])
 def test_wavelet_regrouped_medium_and_sign(J, mode, tol):
     w = synth.medium(n_t=6)
+    if mode == wt.WT_FP64_DF:
+        tol = df_bar(w, J, w.uvw)
     assert _wavelet_case(w, J, w.uvw[::3], mode, which=wt.WT_SUM_EQ17_REGROUPED) <= tol
     assert _wavelet_case(w, J, w.uvw[:999], mode, which=wt.WT_SUM_EQ17_REGROUPED, sign=-1) <= tol
 
 
 @pytest.mark.parametrize("mode,which,tol", [(wt.WT_FP64, wt.WT_SUM_EQ17, TOL64),
                                            (wt.WT_FP64, wt.WT_SUM_EQ17_REGROUPED, TOL64),
+                                           (wt.WT_FP64_DF, wt.WT_SUM_EQ17_REGROUPED, TOL64),
                                            (wt.WT_MIXED, wt.WT_SUM_EQ17, TOLMIX),
                                            (wt.WT_MIXED_FAST, wt.WT_SUM_EQ17_REGROUPED, TOLMIX)])
 def test_wavelet_deepest_tree_J30(mode, which, tol):
     # the largest J the int64 keys hold: level-29 HEALPix pixels (Nside 2^29),
     # 29 stack levels, every form's launch shapes at their shared-memory limit
     w = synth.medium_fixed(20, n_t=2)
+    if mode == wt.WT_FP64_DF:
+        tol = df_bar(w, 30, w.uvw[::5])
     assert _wavelet_case(w, 30, w.uvw[::5], mode, which=which) <= tol
 
 
@@ -330,12 +381,14 @@ def test_wavelet_regrouped_deep_and_mixed_sign():
     w = synth.medium_fixed(40, n_t=4)
     for J in (16, 25):
         assert _wavelet_case(w, J, w.uvw[::4], wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED) <= TOL64
+        assert _wavelet_case(w, J, w.uvw[::4], wt.WT_FP64_DF, which=wt.WT_SUM_EQ17_REGROUPED) <= df_bar(w, J, w.uvw[::4])
         assert _wavelet_case(w, J, w.uvw[::4], wt.WT_MIXED, which=wt.WT_SUM_EQ17_REGROUPED) <= TOLMIX
     rng = np.random.default_rng(31)
     s = synth.small()
     f = s.flux * np.where(rng.random(len(s.flux)) < 0.5, -1.0, 1.0)
     w2 = synth.Workload("mixed-sign", s.uvw, s.l, s.m, f, 11)
     assert _wavelet_case(w2, 11, s.uvw[::5], wt.WT_FP64, which=wt.WT_SUM_EQ17_REGROUPED) <= TOL64
+    assert _wavelet_case(w2, 11, s.uvw[::5], wt.WT_FP64_DF, which=wt.WT_SUM_EQ17_REGROUPED) <= df_bar(w2, 11, s.uvw[::5])
 
 
 # ---------------------------------------------------------------- one launch against pieces

@@ -413,6 +413,16 @@ SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum), per (form, sum);
 # a form whose kernel or launch shape changed since its capture has no entry.
 TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24283136}
+# Double-float form (WT_FP64_DF, regrouped Eq. 17), float32 FMA-pipe ops per
+# (vis, leaf): phase 32 (three double-float products of 5, two error-free
+# sums of 6, reduction 1, tail 4), sin/cos 135 (argument reduction 8, 2 pi f,
+# x^2, x^3 and x^3/6 as double-float products of 7, the float32 tails 6,
+# three double-float sums of 10-11 and one of 11, the rotation by the table
+# entry: four products of 7 and two sums of 11), w eta into V 36, the
+# parent's sum 22; per (vis, internal node): quarter 4, w eta into V 36, the
+# parent's sum 22.
+OPS_DF_LEAF = 32 + 135 + 36 + 22
+OPS_DF_NODE = 4 + 36 + 22
 # Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
 # element ops per (visibility, component): phase 29, angle and SFU scaling 3
 # (fast) or polynomial sin/cos 15, the flux times (cos, sin) 2, half a Kahan
@@ -456,6 +466,8 @@ def _time_call(fn, stream, flush, reps=3):
 
 def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
     n = w.n_vis
+    info = tree.info()
+    n_leaves, n_int = info["n_leaves"], info["n_nodes"] - info["n_leaves"]
     out64 = torch.empty(n, dtype=torch.complex128, device=uvw.device)
     out32 = torch.empty(n, dtype=torch.complex64, device=uvw.device)
     r = {}
@@ -464,6 +476,8 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
     for name, mode, which, out in [("wavelet_fp64_eq17", wt.WT_FP64, wt.WT_SUM_EQ17, out64),
                                    ("wavelet_mixed_eq17", wt.WT_MIXED, wt.WT_SUM_EQ17, out32),
                                    ("wavelet_fp64_eq17_regrouped", wt.WT_FP64, wt.WT_SUM_EQ17_REGROUPED, out64),
+                                   ("wavelet_fp64_df_eq17_regrouped", wt.WT_FP64_DF, wt.WT_SUM_EQ17_REGROUPED,
+                                    out64),
                                    ("wavelet_mixed_eq17_regrouped", wt.WT_MIXED, wt.WT_SUM_EQ17_REGROUPED, out32),
                                    ("wavelet_fp64_eq16", wt.WT_FP64, wt.WT_SUM_EQ16, out64),
                                    ("wavelet_mixed_eq16", wt.WT_MIXED, wt.WT_SUM_EQ16, out32),
@@ -506,6 +520,10 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
                       "ops_per_term": OPS_DFT},
         "dft_fp64": {"bound": "fp64", "frac": r["dft_fp64_vis_per_s"] * nc * OPS_DFT_FP64 / FP64_PEAK_INST_PER_S,
                      "ops_per_term": OPS_DFT_FP64},
+        "wavelet_fp64_df": {"bound": "alu",
+                            "frac": r["wavelet_fp64_df_eq17_regrouped_vis_per_s"]
+                            * (OPS_DF_LEAF * n_leaves + OPS_DF_NODE * n_int) / 1e12 / FP32_PEAK_TOPS,
+                            "ops_per_leaf": OPS_DF_LEAF, "ops_per_internal_node": OPS_DF_NODE},
         "subtract_c64_64Mi": {"bound": "hbm", "frac": r["subtract_c64_64Mi_frac_of_hbm"]},
         "mlp_eval": {"bound": "tensor", "achieved_tflops": n * 8832 / t_mlp / 1e12,
                      "frac": n * 8832 / t_mlp / 1e12 / BF16_PEAK_TFLOPS},
@@ -905,6 +923,8 @@ def forms_once(args):
     runs.append(("wavelet_mixed_fast_regrouped",
                  lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED_FAST, which=rg, out=o32)))
     runs.append(("wavelet_mixed_regrouped", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, which=rg, out=o32)))
+    runs.append(("wavelet_fp64_df_regrouped",
+                 lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_FP64_DF, which=rg, out=o64)))
     if args.only:
         keep = set(args.only.split(","))
         runs = [(n, fn) for n, fn in runs if n in keep]

@@ -422,6 +422,7 @@ TRAFFIC_BYTES_MEDIUM_J12 = {("fast", "regrouped"): 24283136}
 # parent's sum 22; per (vis, internal node): quarter 4, w eta into V 36, the
 # parent's sum 22.
 OPS_DF_LEAF = 32 + 135 + 36 + 22
+OPS_DFT_DF = 32 + 135 + 36   # per (vis, component) of the double-float direct sum
 OPS_DF_NODE = 4 + 36 + 22
 # Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
 # element ops per (visibility, component): phase 29, angle and SFU scaling 3
@@ -489,6 +490,8 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
         r[name + "_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_FP64, out=out64), stream, flush, reps=1)
     r["dft_fp64_vis_per_s"] = n / t
+    t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_FP64_DF, out=out64), stream, flush)
+    r["dft_fp64_df_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED, out=out32), stream, flush)
     r["dft_mixed_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED_FAST, out=out32), stream, flush)
@@ -520,6 +523,8 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
                       "ops_per_term": OPS_DFT},
         "dft_fp64": {"bound": "fp64", "frac": r["dft_fp64_vis_per_s"] * nc * OPS_DFT_FP64 / FP64_PEAK_INST_PER_S,
                      "ops_per_term": OPS_DFT_FP64},
+        "dft_fp64_df": {"bound": "alu", "frac": r["dft_fp64_df_vis_per_s"] * nc * OPS_DFT_DF / 1e12 / FP32_PEAK_TOPS,
+                        "ops_per_term": OPS_DFT_DF},
         "wavelet_fp64_df": {"bound": "alu",
                             "frac": r["wavelet_fp64_df_eq17_regrouped_vis_per_s"]
                             * (OPS_DF_LEAF * n_leaves + OPS_DF_NODE * n_int) / 1e12 / FP32_PEAK_TOPS,

@@ -221,8 +221,8 @@ int wt_predict_vis_batched(const wt_tree* trees, const double* freq_hz, int n_ch
  * a device scratch buffer the call allocates and releases on `stream`.
  *   l, m, flux  device float64 [n_comp]
  *   uvw         device float64 [n_vis][3]
- *   vis_out     device complex128 (WT_FP64) or complex64 (WT_MIXED,
- *               WT_MIXED_FAST) [n_vis]
+ *   vis_out     device complex128 (WT_FP64, WT_FP64_DF) or complex64
+ *               (WT_MIXED, WT_MIXED_FAST) [n_vis]
  * ------------------------------------------------------------------------- */
 int dft_predict_vis(const double* l, const double* m, const double* flux, int64_t n_comp,
                     const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign,

@@ -4,10 +4,12 @@
 //
 // A prologue kernel packs each component once into a 32-byte record in a
 // scratch buffer: (l, m, n - 1, C) in float64 for WT_FP64, or double-float
-// halves of l, m, n - 1 plus C in float32 for WT_MIXED. The main kernel gives
+// halves of l, m, n - 1 and C for the other forms (the mixed forms use C's
+// high half only). The main kernel gives
 // each thread one visibility (float64) or two (mixed, on packed float32
 // pairs) and streams the records through shared memory (bulk copies,
 // double-buffered, broadcast reads), like the wavelet kernels.
+#include "df64.cuh"
 #include "staging.cuh"
 #include "wt_internal.cuh"
 
@@ -20,7 +22,7 @@ struct CompD {
     double l, m, nm1, flux;
 };
 struct CompF {
-    float lh, ll, mh, ml, nh, nl, flux, pad;
+    float lh, ll, mh, ml, nh, nl, flux, flux_lo;   // flux_lo: the double-float form's low half of C
 };
 static_assert(sizeof(CompD) == 32 && sizeof(CompF) == 32, "component record layout");
 
@@ -41,8 +43,8 @@ __global__ void k_pack_components(const double* __restrict__ l, const double* __
     }
     if (outd) outd[i] = CompD{li, mi, nm1, fi};
     if (outf) {
-        const F2 a = split_f64(li), b = split_f64(mi), c = split_f64(nm1);
-        outf[i] = CompF{a.hi, a.lo, b.hi, b.lo, c.hi, c.lo, static_cast<float>(fi), 0.0f};
+        const F2 a = split_f64(li), b = split_f64(mi), c = split_f64(nm1), f = split_f64(fi);
+        outf[i] = CompF{a.hi, a.lo, b.hi, b.lo, c.hi, c.lo, f.hi, f.lo};
     }
 }
 
@@ -96,6 +98,54 @@ struct BodyF2 {
         kahan_add2(acc[1], comp[1], x1);
     }
 };
+
+// The float64-class double-float form: one visibility per thread, every
+// step in double-float (df64.cuh).
+struct BodyDF {
+    F2 u, v, w;
+    DF vr, vi;
+    const float4* tab;
+    __device__ void operator()(const CompF& c)
+    {
+        float th, tl;
+        phase_turns_df(u, v, w, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, th, tl);
+        DF s, co;
+        sincos_turns_df(th, tl, tab, s, co);
+        const DF f{c.flux, c.flux_lo};
+        vr = df_add(vr, df_mul(f, co));
+        vi = df_add(vi, df_mul(f, s));
+    }
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_dft_df(const CompF* __restrict__ comps, int64_t n_comp,
+                                               const double* __restrict__ uvw, int64_t n_vis,
+                                               double2* __restrict__ vis, double sgn, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stager<CompF> st;
+    stager_setup(st, smem, comps, n_comp, kChunk);
+    float4* tab = reinterpret_cast<float4*>(smem + stager_bytes<CompF>(kChunk));
+    load_sincos_table_df(tab);
+    __syncthreads();
+    const int64_t ntiles = (n_vis + NT - 1) / NT;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t n = tile * NT + threadIdx.x;
+        const bool valid = n < n_vis;
+        BodyDF b;
+        b.u = split_f64(valid ? sgn * uvw[3 * n] : 0.0);   // sign folded into the baseline (exact)
+        b.v = split_f64(valid ? sgn * uvw[3 * n + 1] : 0.0);
+        b.w = split_f64(valid ? sgn * uvw[3 * n + 2] : 0.0);
+        b.vr = DF{0.f, 0.f};
+        b.vi = DF{0.f, 0.f};
+        b.tab = tab;
+        if (!st.sweep(b)) {
+            if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
+            return;
+        }
+        if (valid) vis[n] = make_double2(df_to_double(b.vr), df_to_double(b.vi));
+    }
+}
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_dft_fp64(const CompD* __restrict__ comps, int64_t n_comp,
@@ -177,6 +227,14 @@ int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, in
         int rc = grid_for(k, NT, NT, smem, n_vis, grid);
         if (rc) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(scratch), n_comp, uvw, n_vis, static_cast<double2*>(vis),
+                                 static_cast<double>(sign), status);
+    } else if (mode == WT_FP64_DF) {
+        constexpr int NT = 128;
+        const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk)) + kDfTableEntries * sizeof(float4);
+        auto k = k_dft_df<NT>;
+        int rc = grid_for(k, NT, NT, smem, n_vis, grid);
+        if (rc) return rc;
+        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(scratch), n_comp, uvw, n_vis, static_cast<double2*>(vis),
                                  static_cast<double>(sign), status);
     } else {
         constexpr int NT = 256;

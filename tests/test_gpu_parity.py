@@ -190,6 +190,30 @@ def _dft_case(w, uvw, mode, sign=1):
     return np.max(np.abs(v - ref)) / peak(w.flux)
 
 
+def dft_df_bar(w, uvw):
+    """The double-float form's bar for the direct sum (see df_bar), with the
+    components' (l, m, n - 1) in place of the pixel centres."""
+    r2 = w.l ** 2 + w.m ** 2
+    d = np.abs(np.stack([w.l, w.m, -r2 / (1 + np.sqrt(1 - r2))], axis=1))
+    T = float(np.max(np.abs(np.asarray(uvw)) @ d.T))
+    return max(TOL64, 2 * math.pi * 2.0 ** -45 * T)
+
+
+def test_dft_df_small_all_vis_and_sign():
+    w = synth.small()
+    assert _dft_case(w, w.uvw, wt.WT_FP64_DF) <= dft_df_bar(w, w.uvw)
+    assert _dft_case(w, w.uvw[:333], wt.WT_FP64_DF, sign=-1) <= dft_df_bar(w, w.uvw[:333])
+
+
+def test_dft_df_medium_many_chunks_and_agreement_with_fp64():
+    w = synth.medium(n_t=2)
+    uvw = w.uvw[::4]
+    assert _dft_case(w, uvw, wt.WT_FP64_DF) <= dft_df_bar(w, uvw)
+    a = wt.dft_predict_vis(dev(w.l), dev(w.m), dev(w.flux), dev(uvw), mode=wt.WT_FP64).cpu().numpy()
+    b = wt.dft_predict_vis(dev(w.l), dev(w.m), dev(w.flux), dev(uvw), mode=wt.WT_FP64_DF).cpu().numpy()
+    assert np.max(np.abs(a - b)) / peak(w.flux) <= 1e-11
+
+
 def test_dft_fp64_small_all_vis():
     w = synth.small()
     assert _dft_case(w, w.uvw, wt.WT_FP64) <= TOL64

@@ -539,7 +539,7 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
 def batched_measurement(wt, torch, dev, stream, flush):
     """Config B: 128 antennas, 64 channels over 1.0-1.8 GHz, per-channel
     component lists of log-uniform size 100..20 000 and J in 10..13; one
-    persistent graph-captured launch against 64 single-channel launches."""
+    graph-captured launch against 64 single-channel launches."""
     import oracle as O
     w = synth.batched()
     chans = w.extra["channels"]

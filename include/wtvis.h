@@ -201,8 +201,8 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
  *   vis_out  device [n_ch][n_vis], complex128 (WT_FP64) or complex64 (WT_MIXED,
  *            WT_MIXED_FAST)
  *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST; sign +1 / -1
- * All channels run in one persistent kernel that takes (channel, tile) work
- * items, largest trees first, from a device-side counter. The first call for
+ * All channels run in one kernel of one CTA per (channel, tile) work item,
+ * largest trees first. The first call for
  * a given (trees, freq_hz, mode, sign) builds a plan: it reads the trees'
  * sizes (waiting for their build streams), times the fitting launch shapes
  * on the caller's stream (skipped under WT_AUTOTUNE=0 or when the stream is

@@ -1,11 +1,12 @@
 // batched.cu -- wt_predict_vis_batched: many frequency channels (or major
-// cycles), each with its own coefficient tree, in one persistent launch.
+// cycles), each with its own coefficient tree, in one launch.
 //
 // Work items are (channel, tile of NT * VPT visibilities). Channels are
 // ordered by decreasing tree size (largest work first), items numbered
-// channel-major in that order, and CTAs (as many per SM as fit, persistent)
-// take the next item from a device-wide atomic counter, so channels of very
-// uneven size keep every SM busy to the end. Items depend on nothing but
+// channel-major in that order, one CTA per item: the hardware hands each SM
+// the next CTA as one of its own finishes, so channels of very uneven size
+// keep every SM busy to the end (beyond 2^31 - 1 items, persistent CTAs take
+// the next item from a device-wide atomic counter instead). Items depend on nothing but
 // their own inputs: no CTA ever waits for another. A CTA re-targets its
 // shared-memory record staging only when the channel changes. Baselines are
 // shared in metres and scaled per channel, u_lambda = u_m f_c / c. The
@@ -459,7 +460,7 @@ int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const
     if (rc) return rc;
     if ((rc = write_table(*p, n_vis, p->shape, s))) return rc;
     if (!p->exec || p->g_uvw != uvw_m || p->g_nvis != n_vis || p->g_vis != vis || p->g_shape != p->shape) {
-        // capture [counter reset, persistent kernel] once for these buffers
+        // capture [counter reset, kernel] once for these buffers
         cudaGraph_t g = nullptr;
         WT_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned long long), p->cap);

@@ -6,7 +6,7 @@
 // memory as a broadcast. Two buffers of `chunk` records alternate: while the
 // CTA works on one, the next chunk is in flight into the other. A list that
 // fits in the two buffers is loaded once and stays resident for every tile
-// the (persistent) CTA processes.
+// the CTA processes.
 #pragma once
 
 #include "wt_internal.cuh"

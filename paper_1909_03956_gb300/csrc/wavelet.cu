@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ re
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Stager<RecWDF> st;
-    stager_setup(st, smem, recs, hdr->n_nodes, kChunkD);
-    float4* tab = reinterpret_cast<float4*>(smem + stager_bytes<RecWDF>(kChunkD));
+    stager_setup(st, smem, recs, hdr->n_nodes, kChunkDF);
+    float4* tab = reinterpret_cast<float4*>(smem + stager_bytes<RecWDF>(kChunkDF));
     load_sincos_table_df(tab);
     float4* stk = tab + kDfTableEntries + threadIdx.x;
     __syncthreads();
@@ -287,7 +287,7 @@ int stack_rows(int mode, int which, int J)
 size_t stage_bytes(int mode, int which)
 {
     if (mode == WT_FP64) return stager_bytes<RecD>(kChunkD);
-    if (mode == WT_FP64_DF) return stager_bytes<RecWDF>(kChunkD) + kDfTableEntries * sizeof(float4);
+    if (mode == WT_FP64_DF) return stager_bytes<RecWDF>(kChunkDF) + kDfTableEntries * sizeof(float4);
     return (which == WT_SUM_EQ17_REGROUPED) ? stager_bytes<RecWF>(kChunkW) : stager_bytes<RecF>(kChunkF);
 }
 

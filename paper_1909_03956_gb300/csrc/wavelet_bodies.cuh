@@ -12,6 +12,7 @@ namespace wt {
 namespace {
 
 constexpr int kChunkD = 256;   // records per staging buffer (48 B each)
+constexpr int kChunkDF = 128;  // double-float form (48 B each): smaller buffers, more CTAs per SM
 constexpr int kChunkF = 384;   // (32 B each)
 constexpr int kChunkW = kRecChunkW;   // regrouped float32 form (32 B each): its stack is small, so the
                                // staging buffers set how many CTAs fit on an SM

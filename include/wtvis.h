@@ -261,7 +261,8 @@ int dft_predict_vis_noalloc(const double* l, const double* m, const double* flux
 /* ---------------------------------------------------------------------------
  * subtract_model -- Sec. 2.2, major-cycle step 2: V_resid = V - V_M,
  * element by element. vis_resid may alias vis_obs (in place).
- *   mode WT_FP64: complex128 arrays; any other mode: complex64 arrays.
+ *   mode WT_FP64 or WT_FP64_DF: complex128 arrays; any other mode: complex64
+ *   arrays.
  * ------------------------------------------------------------------------- */
 int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid,
                    int64_t n_vis, int mode, void* stream);

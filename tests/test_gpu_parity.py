@@ -343,6 +343,18 @@ def test_wavelet_df_every_launch_shape(variant, monkeypatch):
     assert _wavelet_case(w, 13, uvw, wt.WT_FP64_DF, which=wt.WT_SUM_EQ17_REGROUPED) <= df_bar(w, 13, uvw)
 
 
+def test_wavelet_df_subtract_and_default_sum():
+    # the binding picks the regrouped sum for the double-float form, and its
+    # complex128 output subtracts under its own mode
+    w = synth.small()
+    t = gpu_tree(w, 10)
+    uvw = dev(w.uvw[:500])
+    v = wt.wt_predict_vis(t, uvw, mode=wt.WT_FP64_DF)
+    assert v.dtype == torch.complex128
+    r = wt.subtract_model(v, v, mode=wt.WT_FP64_DF)
+    assert torch.all(r == 0)
+
+
 def test_wavelet_df_other_sums_refused():
     w = synth.small()
     t = gpu_tree(w, 8)

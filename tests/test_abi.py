@@ -48,3 +48,19 @@ def test_host_argument_checks_need_no_gpu():
     assert L.wt_predict_vis(None, None, 0, None, 0, 1, 0, None) == wt.WT_ERR_ARG
     assert L.dft_predict_vis(None, None, None, 0, None, 0, None, 0, 3, None) == wt.WT_ERR_ARG
     assert L.subtract_model(None, None, None, -5, 0, None) == wt.WT_ERR_ARG
+
+
+def test_host_argument_checks_of_the_imaging_and_cross_reference_entries():
+    L = wt.load()
+    h = C.c_void_p()
+    # image size, pixel size and level are checked before any device call
+    assert L.wt_xref_table(0, 1e-4, 0.0, 0.5, 10, None, None) == wt.WT_ERR_ARG
+    assert L.wt_xref_table(64, -1.0, 0.0, 0.5, 10, None, None) == wt.WT_ERR_RANGE
+    assert L.wt_xref_table(64, 1e-4, 0.0, 0.5, 31, None, None) == wt.WT_ERR_RANGE
+    assert L.wt_build_tree_xref(None, 64, None, None, 1, 0.0, 0.5, 0, C.byref(h), None) == wt.WT_ERR_RANGE
+    assert L.wt_build_tree_xref(None, 64, None, None, -1, 0.0, 0.5, 10, C.byref(h), None) == wt.WT_ERR_ARG
+    assert L.wt_hogbom(None, None, 31, C.c_float(0.1), C.c_float(0.0), 10, None, None, None, None) == wt.WT_ERR_ARG
+    assert L.wt_hogbom(None, None, 32, C.c_float(1.5), C.c_float(0.0), 10, None, None, None, None) == wt.WT_ERR_RANGE
+    assert L.wt_selftest_grid_barrier(0, None) == wt.WT_ERR_ARG
+    # the double-float mode is known to the mode checks (a null tree is the error here)
+    assert L.wt_predict_vis(None, None, 0, None, wt.WT_FP64_DF, 1, 2, None) == wt.WT_ERR_ARG

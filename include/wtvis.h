@@ -198,9 +198,10 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out,
  *   trees    HOST array [n_ch] of built trees (any mix of J and sizes)
  *   freq_hz  HOST array [n_ch], > 0
  *   uvw_m    device float64 [n_vis][3], metres
- *   vis_out  device [n_ch][n_vis], complex128 (WT_FP64) or complex64 (WT_MIXED,
- *            WT_MIXED_FAST)
- *   mode     WT_FP64, WT_MIXED or WT_MIXED_FAST; sign +1 / -1
+ *   vis_out  device [n_ch][n_vis], complex128 (WT_FP64, WT_FP64_DF) or complex64
+ *            (WT_MIXED, WT_MIXED_FAST)
+ *   mode     WT_FP64 (explicit Eq. 17), WT_FP64_DF, WT_MIXED or WT_MIXED_FAST
+ *            (regrouped Eq. 17); sign +1 / -1
  * All channels run in one kernel of one CTA per (channel, tile) work item,
  * largest trees first. The first call for
  * a given (trees, freq_hz, mode, sign) builds a plan: it reads the trees'

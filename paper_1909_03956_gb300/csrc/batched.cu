@@ -12,7 +12,7 @@
 // shared in metres and scaled per channel, u_lambda = u_m f_c / c. The
 // float64 form evaluates Eq. 17 explicitly (Eq17D), the mixed forms in the
 // regrouped order (Eq17WF: one stack pair per level, so small CTAs fit many
-// to an SM).
+// to an SM), the double-float form in the regrouped order too (Eq17DF).
 //
 // The memset of the counter plus the kernel are captured once into a CUDA
 // graph per plan (tree set, frequencies, form, sign, buffers, launch shape)
@@ -41,6 +41,7 @@ constexpr double kLightSpeed = 299792458.0;   // m/s
 struct BatchChan {
     const RecD* recd;
     const RecWF* recwf;
+    const RecWDF* recwdf;
     const TreeHeader* hdr;
     double scale;          // f_c / c: metres -> wavelengths
     int64_t out_offset;    // channel * n_vis
@@ -48,7 +49,11 @@ struct BatchChan {
     int32_t J;
     int32_t pad;
 };
-static_assert(sizeof(BatchChan) == 56, "BatchChan layout");
+static_assert(sizeof(BatchChan) == 64, "BatchChan layout");
+
+// The form a batched kernel evaluates: float64 explicit Eq. 17, regrouped
+// Eq. 17 in the mixed forms, or regrouped Eq. 17 in double-float.
+constexpr int kKindF64 = 0, kKindMixed = 1, kKindDF = 2;
 
 __device__ __forceinline__ int find_channel(const BatchChan* __restrict__ ch, int n_ch, int64_t item)
 {
@@ -61,18 +66,25 @@ __device__ __forceinline__ int find_channel(const BatchChan* __restrict__ ch, in
     return a;
 }
 
-template <int NT, int VPT, bool MIXED, bool FAST = false>
+template <int NT, int VPT, int KIND, bool FAST = false>
 __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ chans, int n_ch, int64_t total_items,
                                                 const double* __restrict__ uvw_m, int64_t n_vis, void* vis, double sgn,
                                                 int rows_max, unsigned long long* queue, int* status)
 {
-    using Rec = typename std::conditional<MIXED, RecWF, RecD>::type;
-    constexpr int kChunk = MIXED ? kChunkW : kChunkD;
+    using Rec = typename std::conditional<KIND == kKindMixed, RecWF,
+                                          typename std::conditional<KIND == kKindDF, RecWDF, RecD>::type>::type;
+    constexpr int kChunk = KIND == kKindMixed ? kChunkW : (KIND == kKindDF ? kChunkDF : kChunkD);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
     Stager<Rec> st;
     stager_setup(st, smem, static_cast<const Rec*>(nullptr), 0, kChunk);
     unsigned char* stk_base = smem + stager_bytes<Rec>(kChunk);
+    float4* tab = reinterpret_cast<float4*>(stk_base);   // double-float form: sin/cos table, then the stack
+    if constexpr (KIND == kKindDF) {
+        load_sincos_table_df(tab);
+        stk_base += kDfTableEntries * sizeof(float4);
+        __syncthreads();
+    }
     int cur = -1;
     int maxrow = 0;
     constexpr int64_t per_tile = static_cast<int64_t>(NT) * VPT;
@@ -91,16 +103,41 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
         const BatchChan ch = chans[c];
         if (c != cur) {
             const Rec* recs;
-            if constexpr (MIXED) recs = ch.recwf;
+            if constexpr (KIND == kKindMixed) recs = ch.recwf;
+            else if constexpr (KIND == kKindDF) recs = ch.recwdf;
             else recs = ch.recd;
             st.retarget(recs, ch.hdr->n_nodes);
             cur = c;
-            if constexpr (MIXED) maxrow = min(ch.J > 4 ? ch.J - 3 : 1, rows_max) - 1;
+            if constexpr (KIND == kKindMixed) maxrow = min(ch.J > 4 ? ch.J - 3 : 1, rows_max) - 1;
+            else if constexpr (KIND == kKindDF) maxrow = min(ch.J > 3 ? ch.J - 2 : 1, rows_max) - 1;
             else maxrow = min(4 * (ch.J > 1 ? ch.J - 1 : 1), rows_max) - 1;
         }
         const int64_t n0 = (item - ch.tile_base) * per_tile + threadIdx.x;
         bool good;
-        if constexpr (MIXED) {
+        if constexpr (KIND == kKindDF) {
+            Eq17DF<NT, VPT> b;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+                const bool ok = n < n_vis;
+                const double s = sgn * ch.scale;   // sign folded into B (exact negation)
+                b.u[k] = split_f64(ok ? uvw_m[3 * n] * s : 0.0);
+                b.v[k] = split_f64(ok ? uvw_m[3 * n + 1] * s : 0.0);
+                b.w[k] = split_f64(ok ? uvw_m[3 * n + 2] * s : 0.0);
+                b.vr[k] = b.vi[k] = b.lr[k] = b.li[k] = DF{0.f, 0.f};
+            }
+            b.stk = reinterpret_cast<float4*>(stk_base) + threadIdx.x;
+            b.tab = tab;
+            b.J = ch.J;
+            b.maxrow = maxrow;
+            good = st.sweep(b);
+            double2* out = static_cast<double2*>(vis) + ch.out_offset;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+                const int64_t n = n0 + static_cast<int64_t>(k) * NT;
+                if (good && n < n_vis) out[n] = make_double2(df_to_double(b.vr[k]), df_to_double(b.vi[k]));
+            }
+        } else if constexpr (KIND == kKindMixed) {
             Eq17WF<NT, VPT, FAST> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
@@ -161,17 +198,20 @@ const Shape kBatchShapes[kNumBatchShapes] = {{256, 1}, {128, 1}, {128, 2}, {64, 
 
 // Stack rows for the deepest tree of a plan: the explicit float64 sum keeps
 // four child slots per level, the regrouped mixed sum one pair per level
-// above J - 2.
+// above J - 2, the double-float sum one entry per level above J - 1.
 int batch_rows(int mode, int jmax)
 {
     if (mode == WT_FP64) return jmax > 1 ? 4 * (jmax - 1) : 4;
+    if (mode == WT_FP64_DF) return jmax > 3 ? jmax - 2 : 1;
     return jmax > 4 ? jmax - 3 : 1;
 }
 
 size_t batch_smem(int mode, int shape, int rows_max)
 {
-    const size_t cplx = mode == WT_FP64 ? sizeof(double2) : sizeof(float2);
-    const size_t stage = mode == WT_FP64 ? stager_bytes<RecD>(kChunkD) : stager_bytes<RecWF>(kChunkW);
+    const size_t cplx = (mode == WT_FP64 || mode == WT_FP64_DF) ? sizeof(double2) : sizeof(float2);
+    const size_t stage = mode == WT_FP64      ? stager_bytes<RecD>(kChunkD)
+                         : mode == WT_FP64_DF ? stager_bytes<RecWDF>(kChunkDF) + kDfTableEntries * sizeof(float4)
+                                              : stager_bytes<RecWF>(kChunkW);
     return stage + static_cast<size_t>(rows_max) * kBatchShapes[shape].nt * kBatchShapes[shape].vpt * cplx;
 }
 
@@ -183,18 +223,19 @@ bool batch_fits(int mode, int shape, int rows_max) { return batch_smem(mode, sha
 int default_shape(int mode, int rows_max)
 {
     static const int order_fp64[kNumBatchShapes] = {0, 1, 2, 3, 4, 5};
+    static const int order_df[kNumBatchShapes] = {1, 0, 2, 3, 4, 5};
     static const int order_mixed[kNumBatchShapes] = {2, 3, 5, 0, 1, 4};
-    const int* order = (mode == WT_FP64) ? order_fp64 : order_mixed;
+    const int* order = (mode == WT_FP64) ? order_fp64 : (mode == WT_FP64_DF) ? order_df : order_mixed;
     for (int i = 0; i < kNumBatchShapes; ++i)
         if (batch_fits(mode, order[i], rows_max)) return order[i];
     return -1;
 }
 
-template <int NT, int VPT, bool MIXED, bool FAST = false>
+template <int NT, int VPT, int KIND, bool FAST = false>
 int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
                  int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
 {
-    auto k = k_batched<NT, VPT, MIXED, FAST>;
+    auto k = k_batched<NT, VPT, KIND, FAST>;
     int per_sm = 0;
     WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
@@ -210,20 +251,34 @@ int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* 
     return WT_OK;
 }
 
-template <bool MIXED, bool FAST = false>
+template <int KIND, bool FAST = false>
 int set_attr(int shape, size_t smem)
 {
     const void* fn;
     switch (shape) {
-        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, MIXED, FAST>); break;
-        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, MIXED, FAST>); break;
-        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, MIXED, FAST>); break;
-        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, MIXED, FAST>); break;
-        case 4: fn = reinterpret_cast<const void*>(k_batched<32, 1, MIXED, FAST>); break;
-        default: fn = reinterpret_cast<const void*>(k_batched<32, 2, MIXED, FAST>); break;
+        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, KIND, FAST>); break;
+        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, KIND, FAST>); break;
+        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, KIND, FAST>); break;
+        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, KIND, FAST>); break;
+        case 4: fn = reinterpret_cast<const void*>(k_batched<32, 1, KIND, FAST>); break;
+        default: fn = reinterpret_cast<const void*>(k_batched<32, 2, KIND, FAST>); break;
     }
     WT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     return WT_OK;
+}
+
+template <int KIND, bool FAST = false>
+int launch_kind(int shape, const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis,
+                void* vis, int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
+{
+    switch (shape) {
+        case 0: return launch_shape<256, 1, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 1: return launch_shape<128, 1, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 2: return launch_shape<128, 2, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 3: return launch_shape<64, 2, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        case 4: return launch_shape<32, 1, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+        default: return launch_shape<32, 2, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+    }
 }
 
 int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m,
@@ -231,34 +286,23 @@ int launch_batch(int mode, int shape, const BatchChan* chans, int n_ch, int64_t 
                  cudaStream_t s)
 {
     const size_t smem = batch_smem(mode, shape, rows_max);
-    if (mode == WT_FP64) {
-        switch (shape) {
-            case 0: return launch_shape<256, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 1: return launch_shape<128, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 2: return launch_shape<128, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 3: return launch_shape<64, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 4: return launch_shape<32, 1, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            default: return launch_shape<32, 2, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        }
-    }
-    if (mode == WT_MIXED_FAST) {
-        switch (shape) {
-            case 0: return launch_shape<256, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 1: return launch_shape<128, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 2: return launch_shape<128, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 3: return launch_shape<64, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            case 4: return launch_shape<32, 1, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-            default: return launch_shape<32, 2, true, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        }
-    }
-    switch (shape) {
-        case 0: return launch_shape<256, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        case 1: return launch_shape<128, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        case 2: return launch_shape<128, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        case 3: return launch_shape<64, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        case 4: return launch_shape<32, 1, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-        default: return launch_shape<32, 2, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
-    }
+    if (mode == WT_FP64)
+        return launch_kind<kKindF64>(shape, chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+    if (mode == WT_FP64_DF)
+        return launch_kind<kKindDF>(shape, chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+    if (mode == WT_MIXED_FAST)
+        return launch_kind<kKindMixed, true>(shape, chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status,
+                                             smem, s);
+    return launch_kind<kKindMixed>(shape, chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status, smem, s);
+}
+
+// The shared-memory attribute of a shape's kernel in a plan's form.
+int set_attr_mode(int mode, int shape, size_t smem)
+{
+    if (mode == WT_FP64) return set_attr<kKindF64>(shape, smem);
+    if (mode == WT_FP64_DF) return set_attr<kKindDF>(shape, smem);
+    if (mode == WT_MIXED_FAST) return set_attr<kKindMixed, true>(shape, smem);
+    return set_attr<kKindMixed>(shape, smem);
 }
 
 // A plan: one set of trees and frequencies in one form, its device-side
@@ -321,6 +365,7 @@ int write_table(Plan& p, int64_t n_vis, int shape, cudaStream_t s)
         BatchChan& b = h[i];
         b.recd = t->d.recd;
         b.recwf = t->d.recwf;
+        b.recwdf = t->d.recwdf;
         b.hdr = t->d.hdr;
         b.scale = p.freqs[c] / kLightSpeed;
         b.out_offset = static_cast<int64_t>(c) * n_vis;
@@ -347,7 +392,7 @@ int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cu
     if (e && e[0] == '0') return first;
     // per channel: the mixed forms are timed on up to 131 072 visibilities
     // (with 64 channels, several waves of every shape), float64 on 16 384
-    const int64_t cap = (p.mode == WT_FP64) ? 16384 : 131072;
+    const int64_t cap = (p.mode == WT_FP64) ? 16384 : (p.mode == WT_FP64_DF) ? 32768 : 131072;
     const int64_t sample = n_vis < cap ? n_vis : cap;
     cudaEvent_t e0, e1;
     WT_CUDA_TRY(cudaEventCreate(&e0));
@@ -357,8 +402,7 @@ int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cu
     for (int sh = 0; sh < kNumBatchShapes; ++sh) {
         if (!batch_fits(p.mode, sh, p.rows_max)) continue;
         const size_t sm = batch_smem(p.mode, sh, p.rows_max);
-        int rc = (p.mode == WT_FP64) ? set_attr<false>(sh, sm)
-                 : (p.mode == WT_MIXED_FAST) ? set_attr<true, true>(sh, sm) : set_attr<true>(sh, sm);
+        int rc = set_attr_mode(p.mode, sh, sm);
         if (rc) continue;
         if (write_table(p, sample, sh, s)) continue;
         float ms_best_rep = 1e30f;
@@ -455,8 +499,7 @@ int predict_batched(const wt_tree* trees, const double* freq_hz, int n_ch, const
         }
     }
     const size_t smem = batch_smem(mode, p->shape, p->rows_max);
-    int rc = (mode == WT_FP64) ? set_attr<false>(p->shape, smem)
-             : (mode == WT_MIXED_FAST) ? set_attr<true, true>(p->shape, smem) : set_attr<true>(p->shape, smem);
+    int rc = set_attr_mode(mode, p->shape, smem);
     if (rc) return rc;
     if ((rc = write_table(*p, n_vis, p->shape, s))) return rc;
     if (!p->exec || p->g_uvw != uvw_m || p->g_nvis != n_vis || p->g_vis != vis || p->g_shape != p->shape) {
@@ -498,7 +541,7 @@ extern "C" int wt_predict_vis_batched(const wt_tree* trees, const double* freq_h
     if (n_ch < 1 || n_ch > 65536) return set_error(WT_ERR_ARG, "%s: n_ch = %d outside 1..65536", fn, n_ch);
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
     if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST)
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST && mode != WT_FP64_DF)
         return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
     int dev = 0;
     WT_CUDA_TRY(cudaGetDevice(&dev));
@@ -510,7 +553,7 @@ extern "C" int wt_predict_vis_batched(const wt_tree* trees, const double* freq_h
         if (!(freq_hz[c] > 0.0) || !isfinite(freq_hz[c]))
             return set_error(WT_ERR_RANGE, "%s: frequency %d must be positive and finite", fn, c);
     }
-    const size_t ob = static_cast<size_t>(n_vis) * n_ch * (mode == WT_FP64 ? 16 : 8);
+    const size_t ob = static_cast<size_t>(n_vis) * n_ch * ((mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8);
     int rc;
     if ((rc = check_device_buffer(uvw_m, static_cast<size_t>(n_vis) * 24, fn, "uvw_m")) ||
         (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))

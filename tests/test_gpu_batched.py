@@ -51,7 +51,15 @@ def _gpu_trees(chans):
     return [wt.wt_build_tree(dev(c["l"]), dev(c["m"]), dev(c["flux"]), synth.RA0, synth.DEC0, c["J"]) for c in chans]
 
 
-@pytest.mark.parametrize("mode", [wt.WT_FP64, wt.WT_MIXED, wt.WT_MIXED_FAST])
+def _df_bar(ch, uvw):
+    """The double-float form's bar (see the single-tree parity tests): the
+    float64 bar, or 2 pi 2^-45 max |B.s| where phases reach beyond about
+    500 turns."""
+    d = np.abs(O.Tree(ch["l"], ch["m"], ch["flux"], synth.RA0, synth.DEC0, ch["J"]).export()["leaf_dir"])
+    return max(TOL[wt.WT_FP64], 2 * np.pi * 2.0 ** -45 * float(np.max(np.abs(uvw) @ d.T)))
+
+
+@pytest.mark.parametrize("mode", [wt.WT_FP64, wt.WT_FP64_DF, wt.WT_MIXED, wt.WT_MIXED_FAST])
 def test_batched_matches_oracle_per_channel(mode):
     chans = _channels(9)
     uvw_m = _uvw_m(3001)                       # ragged against every tile size
@@ -60,7 +68,20 @@ def test_batched_matches_oracle_per_channel(mode):
     ref = _oracle(chans, uvw_m)
     for c, ch in enumerate(chans):
         err = np.max(np.abs(v[c] - ref[c])) / np.abs(ch["flux"]).sum()
-        assert err <= TOL[mode], (c, err)
+        bar = _df_bar(ch, uvw_m * (ch["freq"] / C_LIGHT)) if mode == wt.WT_FP64_DF else TOL[mode]
+        assert err <= bar, (c, err)
+
+
+def test_batched_double_float_equals_single_channel_calls():
+    chans = _channels(5, seed=12)
+    uvw_m = _uvw_m(2048, seed=13)
+    trees = _gpu_trees(chans)
+    freqs = [c["freq"] for c in chans]
+    v = wt.wt_predict_vis_batched(trees, freqs, dev(uvw_m), mode=wt.WT_FP64_DF, sign=-1).cpu().numpy()
+    for c, ch in enumerate(chans):
+        u = dev(uvw_m * (ch["freq"] / C_LIGHT))
+        s = wt.wt_predict_vis(trees[c], u, mode=wt.WT_FP64_DF, sign=-1).cpu().numpy()
+        assert np.max(np.abs(v[c] - s)) <= 1e-12 * np.abs(ch["flux"]).sum()
 
 
 def test_batched_equals_single_channel_calls_and_sign():

@@ -439,10 +439,19 @@ OPS_DFT_FP64 = 21
 FP64_PEAK_INST_PER_S = 152 * 1.89 * 2.07e9
 # Pieces of the batch in the end-to-end leg (copies of one overlap the prediction of another).
 E2E_CHUNKS = 4
-# Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
-HBM_PEAK_GBPS = 6690.1
-# Measured cuBLAS bf16 GEMM throughput (MEASURED_PEAKS.json, bf16_tflops, burst).
-BF16_PEAK_TFLOPS = 1861.7
+# Measured copy bandwidth (hbm_gbs) and cuBLAS bf16 GEMM throughput (burst,
+# bf16_tflops) of the GB300s, from MEASURED_PEAKS.json beside this
+# file when it is there, else an earlier measurement on the same pool.
+def _measured_peaks():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "MEASURED_PEAKS.json"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6690.1, 1861.7, "earlier measurement on this pool"
+
+
+HBM_PEAK_GBPS, BF16_PEAK_TFLOPS, PEAKS_SOURCE = _measured_peaks()
 # 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock), one op per lane per clock
 # (a packed pair instruction does two per lane in two clocks: the same rate).
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
@@ -529,9 +538,11 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, S):
                             "frac": r["wavelet_fp64_df_eq17_regrouped_vis_per_s"]
                             * (OPS_DF_LEAF * n_leaves + OPS_DF_NODE * n_int) / 1e12 / FP32_PEAK_TOPS,
                             "ops_per_leaf": OPS_DF_LEAF, "ops_per_internal_node": OPS_DF_NODE},
-        "subtract_c64_64Mi": {"bound": "hbm", "frac": r["subtract_c64_64Mi_frac_of_hbm"]},
+        "subtract_c64_64Mi": {"bound": "hbm", "frac": r["subtract_c64_64Mi_frac_of_hbm"],
+                              "peak_gbps": HBM_PEAK_GBPS, "peak_source": PEAKS_SOURCE},
         "mlp_eval": {"bound": "tensor", "achieved_tflops": n * 8832 / t_mlp / 1e12,
-                     "frac": n * 8832 / t_mlp / 1e12 / BF16_PEAK_TFLOPS},
+                     "frac": n * 8832 / t_mlp / 1e12 / BF16_PEAK_TFLOPS, "peak_tflops": BF16_PEAK_TFLOPS,
+                     "peak_source": PEAKS_SOURCE},
     }
     return {"forms": r, "side_rooflines": roof}
 

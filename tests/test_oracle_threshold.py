@@ -60,3 +60,26 @@ def test_thresholding_does_not_compress_a_clean_component_sky():
     assert err[0.5] > 1e-3
     assert err[0.99] > 1e-6
     assert math.isfinite(err[0.99])
+
+
+def test_planted_mistakes_fail_the_oracle_equality(monkeypatch):
+    # each plausible mistake planted in the numpy evaluation (a sign flipped
+    # in a butterfly row, the area of the wrong level, a dropped area factor)
+    # breaks the equality with the C oracle's Eq. 17 (the first pin above)
+    w = synth.small()
+    uvw = w.uvw[::40]
+    tr = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, 10)
+    ref = tr.vis_eq17(uvw)
+    Sg = np.abs(w.flux).sum()
+    area = T.area
+    H_flip = T._H.copy()
+    H_flip[1] = -H_flip[1]
+    plants = {"butterfly row sign": ("_H", H_flip),
+              "area of level j + 1": ("area", lambda j: area(j + 1)),
+              "no area factor at level 1": ("area", lambda j: 1.0 if j == 1 else area(j))}
+    for kind, (attr, value) in plants.items():
+        with monkeypatch.context() as mp:
+            mp.setattr(T, attr, value)
+            base, G, S = T.eq17_terms(tr.export(), 10, uvw)
+        v = T.thresholded_vis(base, G, S, len(G))
+        assert np.max(np.abs(v - ref)) > 1e-6 * Sg, kind

@@ -75,7 +75,8 @@ typedef enum {
                          (table method) and every sum in double-float arithmetic
                          (48-bit significands: a term's phase error is a few times
                          2^-48 |B.s| turns, 32x float64's); complex128 output;
-                         wt_predict_vis with WT_SUM_EQ17_REGROUPED only */
+                         wt_predict_vis with WT_SUM_EQ17_REGROUPED or
+                         WT_SUM_EQ16 */
 } wt_mode;
 
 typedef enum {
@@ -181,7 +182,7 @@ void wt_free_tree(wt_tree t);
  *   uvw      device float64 [n_vis][3], wavelengths
  *   vis_out  device complex128 [n_vis] (WT_FP64, WT_FP64_DF) or complex64 [n_vis] (WT_MIXED,
  *            WT_MIXED_FAST)
- *   mode     WT_FP64, WT_FP64_DF (regrouped sum only), WT_MIXED or
+ *   mode     WT_FP64, WT_FP64_DF (regrouped Eq. 17 or Eq. 16), WT_MIXED or
  *            WT_MIXED_FAST (WT_LEARNED: see
  *            wt_predict_vis_learned)
  *   which    wt_sum

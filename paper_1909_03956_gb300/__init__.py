@@ -234,7 +234,7 @@ def wt_free_tree(tree):
 def wt_predict_vis(tree, uvw, mode=WT_FP64, sign=1, which=None, out=None, stream=None):
     """Model visibilities on the tree (Eq. 17, or Eq. 16 with which=WT_SUM_EQ16).
     which=None: the explicit Eq. 17, or the regrouped sum for WT_FP64_DF
-    (the only sum that form evaluates)."""
+    (which evaluates the regrouped Eq. 17 and Eq. 16)."""
     import torch
     if which is None:
         which = WT_SUM_EQ17_REGROUPED if mode == WT_FP64_DF else WT_SUM_EQ17

@@ -518,7 +518,8 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         split(wd.b, wdf.bh, wdf.bl);
         split(wd.c, wdf.ch, wdf.cl);
         split(wgt, wdf.wh, wdf.wl);
-        wdf.pad[0] = wdf.pad[1] = wdf.pad[2] = 0.f;
+        split(leaf ? d.leaf_flux[li] : 0.0, wdf.fh, wdf.fl);
+        wdf.pad = 0.f;
         d.recwd[post] = wd;
         d.recwf[post] = wf;
         d.recwdf[post] = wdf;

@@ -31,7 +31,9 @@
 //   WT_MIXED_FAST  as WT_MIXED with sin/cos from the special-function unit.
 //   WT_FP64_DF     float64-class: phase, sin/cos (table method) and every
 //             sum in double-float arithmetic on the float32 pipe (df64.cuh);
-//             the regrouped sum only.
+//             the regrouped Eq. 17 and Eq. 16.
+#include <type_traits>
+
 #include "staging.cuh"
 #include "wavelet_bodies.cuh"
 #include "wt_internal.cuh"
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_fp64(const Rec* __restrict__ rec
 // The float64-class double-float form: regrouped Eq. 17 (Eq17DF) on the
 // float32 pipe. Shared memory: the record staging, the 257-entry
 // double-float sin/cos table, then the stack.
-template <int NT, int VPT>
+template <int NT, int VPT, int SUM>
 __global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ recs,
                                                    const TreeHeader* __restrict__ hdr,
                                                    const double* __restrict__ uvw, int64_t n_vis,
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ re
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t n0 = tile * per_tile + threadIdx.x;
-        Eq17DF<NT, VPT> b;
+        using Body = typename std::conditional<SUM == 1, Eq16DF<VPT>, Eq17DF<NT, VPT>>::type;
+        Body b;
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             const int64_t n = n0 + static_cast<int64_t>(k) * NT;
@@ -147,13 +150,15 @@ __global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ re
             b.w[k] = split_f64(ok ? sgn * uvw[3 * n + 2] : 0.0);
             b.vr[k] = DF{0.f, 0.f};
             b.vi[k] = DF{0.f, 0.f};
-            b.lr[k] = DF{0.f, 0.f};
-            b.li[k] = DF{0.f, 0.f};
         }
-        b.stk = stk;
         b.tab = tab;
-        b.J = J;
-        b.maxrow = rows - 1;
+        if constexpr (SUM != 1) {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) b.lr[k] = b.li[k] = DF{0.f, 0.f};
+            b.stk = stk;
+            b.J = J;
+            b.maxrow = rows - 1;
+        }
         if (!st.sweep(b)) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
             return;
@@ -275,7 +280,7 @@ int prepare(K kernel, int nt, size_t smem, int64_t per_tile, int64_t n_vis, dim3
 int stack_rows(int mode, int which, int J)
 {
     if (which == WT_SUM_EQ16) return 0;
-    if (mode == WT_FP64_DF) return J > 3 ? J - 2 : 1;   // regrouped only
+    if (mode == WT_FP64_DF) return J > 3 ? J - 2 : 1;   // regrouped (Eq. 16 returned 0 above)
     if (which == WT_SUM_EQ17_REGROUPED) {
         if (mode == WT_FP64) return J > 3 ? 2 * (J - 2) : 2;
         return J > 4 ? J - 3 : 1;
@@ -325,7 +330,7 @@ int run_df(const WaveletJob& jb, cudaStream_t s)
     const size_t smem = stage_bytes(WT_FP64_DF, jb.which) + static_cast<size_t>(rows) * VPT * NT * sizeof(float4);
     dim3 grid;
     int rc;
-    auto k = k_wavelet_df<NT, VPT>;
+    auto k = (jb.which == WT_SUM_EQ16) ? k_wavelet_df<NT, VPT, 1> : k_wavelet_df<NT, VPT, 2>;
     if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
     k<<<grid, NT, smem, s>>>(jb.recwdf, jb.hdr, jb.uvw, jb.n_vis, static_cast<double2*>(jb.vis),
                              static_cast<double>(jb.sign), rows, jb.J, jb.status);

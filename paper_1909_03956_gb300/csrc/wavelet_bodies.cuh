@@ -314,6 +314,31 @@ struct Eq17WD {
     }
 };
 
+// Eq. 16 in double-float (WT_FP64_DF, RecWDF): V = sum over the leaves of
+// Phi_k times the plane wave at the pixel centre; internal records are
+// passed over.
+template <int VPT>
+struct Eq16DF {
+    F2 u[VPT], v[VPT], w[VPT];
+    DF vr[VPT], vi[VPT];
+    const float4* tab;
+    __device__ void operator()(const RecWDF& r)
+    {
+        if (!(r.meta & kRwLeaf)) return;
+        const F2 su{r.ah, r.al}, sv{r.bh, r.bl}, sw{r.ch, r.cl};
+        const DF phi{r.fh, r.fl};
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            float th, tl;
+            phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
+            DF s, c;
+            sincos_turns_df(th, tl, tab, s, c);
+            vr[k] = df_add(vr[k], df_mul(phi, c));
+            vi[k] = df_add(vi[k], df_mul(phi, s));
+        }
+    }
+};
+
 // Regrouped Eq. 17 in double-float (WT_FP64_DF, RecWDF): V = sum_n w_n eta_n
 // with every quantity a double-float on the float32 pipe. Each node adds
 // its w eta to V as soon as its eta is known. Per visibility a thread keeps

@@ -343,8 +343,8 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out, i
         return set_error(WT_ERR_UNSUPPORTED, "%s: the learned response has its own entry point", fn);
     if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST && mode != WT_FP64_DF)
         return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
-    if (mode == WT_FP64_DF && which != WT_SUM_EQ17_REGROUPED)
-        return set_error(WT_ERR_UNSUPPORTED, "%s: WT_FP64_DF evaluates the regrouped sum only", fn);
+    if (mode == WT_FP64_DF && which == WT_SUM_EQ17)
+        return set_error(WT_ERR_UNSUPPORTED, "%s: WT_FP64_DF evaluates the regrouped Eq. 17 and Eq. 16 only", fn);
     const size_t ob = static_cast<size_t>(n_vis) * ((mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8);
     if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
         (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))

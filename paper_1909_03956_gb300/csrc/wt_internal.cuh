@@ -444,12 +444,14 @@ static_assert(sizeof(RecWD) == 48, "RecWD layout");
 
 // float64-class double-float form (48 bytes): the fields of RecWD as
 // double-floats: leaf pixel centre (s_u, s_v, s_w - 1) = (ah + al, bh + bl,
-// ch + cl); weight w_n = wh + wl (every node).
+// ch + cl); weight w_n = wh + wl (every node); the leaf's merged flux
+// Phi_k = fh + fl (Eq. 16; 0 for internal nodes).
 struct RecWDF {
     uint32_t meta;
     float ah, al, bh, bl, ch, cl;
     float wh, wl;
-    float pad[3];
+    float fh, fl;
+    float pad;
 };
 static_assert(sizeof(RecWDF) == 48, "RecWDF layout");
 

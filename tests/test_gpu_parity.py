@@ -341,6 +341,7 @@ def test_wavelet_df_every_launch_shape(variant, monkeypatch):
     w = synth.medium(n_t=4)
     uvw = w.uvw[::7][:1111]
     assert _wavelet_case(w, 13, uvw, wt.WT_FP64_DF, which=wt.WT_SUM_EQ17_REGROUPED) <= df_bar(w, 13, uvw)
+    assert _wavelet_case(w, 13, uvw, wt.WT_FP64_DF, which=wt.WT_SUM_EQ16) <= df_bar(w, 13, uvw)
 
 
 def test_wavelet_df_subtract_and_default_sum():
@@ -355,13 +356,21 @@ def test_wavelet_df_subtract_and_default_sum():
     assert torch.all(r == 0)
 
 
-def test_wavelet_df_other_sums_refused():
+def test_wavelet_df_explicit_sum_refused():
     w = synth.small()
     t = gpu_tree(w, 8)
-    for which in (wt.WT_SUM_EQ17, wt.WT_SUM_EQ16):
-        with pytest.raises(wt.WtError) as e:
-            wt.wt_predict_vis(t, dev(w.uvw[:10]), mode=wt.WT_FP64_DF, which=which)
-        assert e.value.status == wt.WT_ERR_UNSUPPORTED
+    with pytest.raises(wt.WtError) as e:
+        wt.wt_predict_vis(t, dev(w.uvw[:10]), mode=wt.WT_FP64_DF, which=wt.WT_SUM_EQ17)
+    assert e.value.status == wt.WT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("J", [1, 8, 12, 20])
+def test_wavelet_df_eq16(J):
+    # the level-J sum in double-float, against the oracle's Eq. 16
+    w = synth.small()
+    uvw = w.uvw[::3]
+    assert _wavelet_case(w, J, uvw, wt.WT_FP64_DF, which=wt.WT_SUM_EQ16) <= df_bar(w, J, uvw)
+    assert _wavelet_case(w, J, uvw[:777], wt.WT_FP64_DF, which=wt.WT_SUM_EQ16, sign=-1) <= df_bar(w, J, uvw)
 
 
 def test_wavelet_df_agrees_with_the_float64_form_far_below_the_bar():

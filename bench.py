@@ -706,8 +706,8 @@ def learned_measurement(wt, torch, dev, stream, flush, n_train=10_000_000, depth
     """Config L: 256 antennas, 15 993 600 visibilities, 50 000 components,
     J = 12; the level-12 response network trained on n_train responses the
     oracle generates (baselines drawn from the array), then the learned form
-    timed on every visibility and judged on a sample: against the exact
-    response (its fallback and judge) and, for the gain, against the true
+    timed on every visibility and checked on a sample: against the exact
+    response (its fallback and yardstick) and, for the gain, against the true
     visibilities (Eq. 12 at the true positions) next to the centre-snapped
     level-J sum."""
     import oracle as O
@@ -743,7 +743,7 @@ def learned_measurement(wt, torch, dev, stream, flush, n_train=10_000_000, depth
     o17 = torch.empty_like(out)
     wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o17)
     t_17 = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o17), stream, flush)
-    # judge on a strided sample
+    # check on a strided sample
     S = float(np.abs(w.flux).sum())
     sidx = np.arange(0, w.n_vis, w.n_vis // 600)[:600]
     su = w.uvw[sidx]

@@ -365,7 +365,7 @@ void wt_mlp_free(wt_mlp m);
 /* Host copies of the 4546 float32 parameters (both synchronise). */
 int wt_mlp_get_params(wt_mlp m, float* host_params);
 int wt_mlp_set_params(wt_mlp m, const float* host_params);
-/* Exact R_j(B) in float64 (the fallback and the judge); out: device
+/* Exact R_j(B) in float64 (the fallback and the yardstick); out: device
  * complex128 [n]. sign = -1 gives the conjugate. */
 int wt_response_exact(int level, int depth, double ra0, double dec0, const double* uvw, int64_t n, int sign,
                       void* out, void* stream);

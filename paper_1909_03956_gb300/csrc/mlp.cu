@@ -12,7 +12,7 @@
 //     V_learned(B) = R_j(B) sum_k Phi_k exp(i 2 pi B.(c_k - P))      (j = J).
 // A network 3 -> 64 -> 64 -> 2 (SiLU) maps x = B Delta theta_j to
 // (Re R, Im R). Outside |x|_inf <= x_max (the trained domain) the exact sum
-// is evaluated instead: exact evaluation is the fallback and the judge.
+// is evaluated instead: exact evaluation is the fallback and the yardstick.
 //
 // Kernels:
 //   k_response_offsets  s_i - c_j for the 4^D sub-pixels (float64)

@@ -1,6 +1,6 @@
 """Learned per-level response on the GPU, against the CPU oracle.
 
-* the exact response (fallback and judge) equals the oracle's to 1e-12;
+* the exact response (fallback and yardstick) equals the oracle's to 1e-12;
 * the training kernels' loss and gradient equal the FP64 oracle's within
   1e-2 (the GPU rounds W2 and the hidden activations to BF16 as inference
   does; the oracle is given the same BF16-rounded W2);

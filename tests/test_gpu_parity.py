@@ -391,7 +391,7 @@ def test_wavelet_df_agrees_with_the_float64_form_far_below_the_bar():
 @pytest.mark.parametrize("mode,tol", [(wt.WT_FP64, TOL64), (wt.WT_FP64_DF, TOL64), (wt.WT_MIXED, TOLMIX)])
 def test_wavelet_regrouped_small(J, mode, tol):
     # V = sum_n w_n eta_n with w from the parents' gammas: the same terms as
-    # Eq. 17, judged against the oracle's literal Eq. 17.
+    # Eq. 17, checked against the oracle's literal Eq. 17.
     w = synth.small()
     if mode == wt.WT_FP64_DF:
         tol = df_bar(w, J, w.uvw[::3])

@@ -435,20 +435,20 @@ OPS_DFT_FAST = OPS_PHASE + 3 + 2 + 4
 OPS_DFT = OPS_PHASE + 15 + 2 + 4
 OPS_DFT_FP64 = 21
 # 152 SMs x 1.89 FP64 instructions per clock per SM (a probe of independent
-# DFMA chains on this pool: 1.19 TFLOP/s) x 2.07 GHz.
+# DFMA chains on a GB300: 1.19 TFLOP/s) x 2.07 GHz.
 FP64_PEAK_INST_PER_S = 152 * 1.89 * 2.07e9
 # Pieces of the batch in the end-to-end leg (copies of one overlap the prediction of another).
 E2E_CHUNKS = 4
 # Measured copy bandwidth (hbm_gbs) and cuBLAS bf16 GEMM throughput (burst,
-# bf16_tflops) of the GB300s, from MEASURED_PEAKS.json beside this
-# file when it is there, else an earlier measurement on the same pool.
+# bf16_tflops) of the GB300s this runs on, from MEASURED_PEAKS.json beside
+# this file when it is there, else an earlier measurement on a GB300.
 def _measured_peaks():
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
         return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "MEASURED_PEAKS.json"
     except (OSError, ValueError, KeyError, TypeError):
-        return 6690.1, 1861.7, "earlier measurement on this pool"
+        return 6690.1, 1861.7, "earlier measurement on a GB300"
 
 
 HBM_PEAK_GBPS, BF16_PEAK_TFLOPS, PEAKS_SOURCE = _measured_peaks()

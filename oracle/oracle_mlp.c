@@ -32,6 +32,14 @@
 #define ORC_PI 3.14159265358979323846
 #define H 64
 
+/* Mutation testing of the pins, as in oracle.c: a test build may define
+ * ORC_PLANT = k to plant the k-th known mistake (here k = 13 .. 16); the
+ * normal build plants nothing. */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+#define PLANTED(k) (ORC_PLANT == (k))
+
 int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
                        double* out /* [n][2] */)
 {
@@ -46,9 +54,10 @@ int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const d
     for (int64_t i = 0; i < nsub; ++i) {
         double s[3];
         orc_pixel_dir_uvw(j + D, (kref << (2 * D)) + i, ra0, dec0, s);
-        d[3 * i + 0] = s[0] - c[0];
-        d[3 * i + 1] = s[1] - c[1];
-        d[3 * i + 2] = s[2] - c[2];
+        const double sg = PLANTED(13) ? -1.0 : 1.0;
+        d[3 * i + 0] = sg * (s[0] - c[0]);
+        d[3 * i + 1] = sg * (s[1] - c[1]);
+        d[3 * i + 2] = sg * (s[2] - c[2]);
     }
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < n; ++q) {
@@ -60,8 +69,9 @@ int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const d
             re += cos(2.0 * ORC_PI * t);
             im += (double)sign * sin(2.0 * ORC_PI * t);
         }
-        out[2 * q] = re / (double)nsub;
-        out[2 * q + 1] = im / (double)nsub;
+        const double norm = PLANTED(14) ? (double)(nsub / 4 > 0 ? nsub / 4 : 1) : (double)nsub;
+        out[2 * q] = re / norm;
+        out[2 * q + 1] = im / norm;
     }
     free(d);
     return 0;
@@ -76,7 +86,7 @@ static double silu(double z) { return z * sigm(z); }
 static double dsilu(double z)
 {
     const double s = sigm(z);
-    return s * (1.0 + z * (1.0 - s));
+    return PLANTED(15) ? s : s * (1.0 + z * (1.0 - s));
 }
 
 typedef struct {
@@ -114,7 +124,7 @@ static void forward_one(const params_view* P, const double* x, double* z1, doubl
     }
     for (int o = 0; o < H; ++o) {
         double s = P->b2[o];
-        for (int i = 0; i < H; ++i) s += P->W2[H * o + i] * h1[i];
+        for (int i = 0; i < H; ++i) s += (PLANTED(16) ? P->W2[H * i + o] : P->W2[H * o + i]) * h1[i];
         z2[o] = s;
         h2[o] = silu(s);
     }

@@ -76,6 +76,16 @@ def test_mlp_forward_closed_form():
         x0 = uvw[q, 0] * O.level_pixel_size(j)
         assert abs(y[q, 0] - (2.1 * silu(-1.3 * silu(0.7 * x0)) + 0.25)) < 1e-14
         assert y[q, 1] == -0.5
+    # an off-diagonal path pins the orientation of every matrix: input v into
+    # hidden unit 3, into second-layer unit 5, into output 1
+    p = np.zeros(O.mlp_n_params())
+    W1, b1, W2, b2, W3, b3 = O.mlp_split(p)
+    W1[3, 1], W2[5, 3], W3[1, 5] = 0.9, 1.1, -0.8
+    y = O.mlp_forward(p, j, uvw)
+    for q in range(2):
+        x1 = uvw[q, 1] * O.level_pixel_size(j)
+        assert y[q, 0] == 0.0
+        assert abs(y[q, 1] - (-0.8 * silu(1.1 * silu(0.9 * x1)))) < 1e-14
 
 
 def test_mlp_gradient_matches_finite_differences():

@@ -2,7 +2,7 @@
 
 The oracle is rebuilt with one known, plausible mistake planted
 (-DORC_PLANT=k: a flipped sign, a transposed operand, a wrong constant, a
-dropped term, an off-by-one) and the pins are run against it: for every
+dropped term, an off-by-one; 1 .. 12 in oracle.c, 13 .. 16 in oracle_mlp.c) and the pins are run against it: for every
 planted mistake at least one pin must fail. This is what makes the pins
 evidence that the unplanted oracle computes what the paper defines.
 """
@@ -17,6 +17,7 @@ import pytest
 import oracle as O
 
 import test_oracle_dft as TD
+import test_oracle_mlp as TM
 import test_oracle_sphere as TS
 import test_oracle_tree as TT
 
@@ -41,6 +42,11 @@ PLANTS = {
     11: ("s_w - 1 with the wrong sign", [lambda: TT.test_eq16_is_direct_sum_at_pixel_centres(10),
                                         TS.test_pixel_dir_uvw_of_phase_centre_pixel]),
     12: ("plane-wave sigma^0 with a wrong sign", [lambda: TT.test_eq17_equals_eq16(8)]),
+    13: ("pixel response with the sub-pixel offsets reversed", [TM.test_pixel_response_is_the_direct_sum_over_subpixel_centres]),
+    14: ("pixel response normalised by 4^(D-1)", [TM.test_pixel_response_at_zero_baseline_is_one]),
+    15: ("SiLU derivative without its z (1 - s) term", [TM.test_mlp_gradient_matches_finite_differences]),
+    16: ("second weight matrix transposed in the forward pass", [TM.test_mlp_forward_closed_form,
+                                                                  TM.test_mlp_gradient_matches_finite_differences]),
 }
 
 

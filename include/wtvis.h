@@ -418,6 +418,18 @@ int wt_selftest_bounded_wait(uint32_t spin_limit, void* stream);
  * wt_device_status(). WT_ERR_UNSUPPORTED without cooperative launches. */
 int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream);
 
+/* wt_measure_pipe_rates -- the issue rates of the arithmetic pipes the
+ * predictors run on, measured on the current device (the denominators of
+ * their rooflines; the paper has no counterpart). One CTA of 512 threads per
+ * SM runs eight independent dependency chains per thread of one operation,
+ * timed by its SM's own cycle counter; the median over the SMs is returned.
+ *   per_clk_per_sm  HOST double [4], written: operations per clock per SM of
+ *                   [0] float32 FMA, [1] float32 packed-pair FMA (elements),
+ *                   [2] float64 FMA, [3] special-function-unit sine
+ * Allocates a few KB of scratch on `stream`, runs about 10 ms of kernels and
+ * synchronises `stream`. */
+int wt_measure_pipe_rates(double* per_clk_per_sm, void* stream);
+
 /* Text of the calling thread's last error (never NULL). */
 const char* wt_last_error(void);
 

@@ -75,6 +75,8 @@ def _declare(L):
     L.orc_tree_sizes.argtypes = [C.c_void_p, _i64, _i64, _i64]
     L.orc_tree_export.argtypes = [C.c_void_p, _i64, _u8, _i32, _d, _d, _d, _d]
     L.orc_tree_vis_eq17.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d]
+    L.orc_tree_vis_eq17_mt.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d, C.c_int]
+    L.orc_dft_mt.argtypes = [C.c_int64, _d, _d, _d, C.c_int64, _d, C.c_int, _d, C.c_int]
     L.orc_tree_vis_eq16.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d]
     L.orc_tree_synthesis.argtypes = [C.c_void_p, _d]
     L.orc_dense_coeffs.argtypes = [C.c_int, C.c_int64, _d, _d, _d, C.c_double, C.c_double, _d, _d]
@@ -116,11 +118,16 @@ def _as_complex(buf):
 # Eq. 12: direct sum
 # ---------------------------------------------------------------------------
 
-def dft(l, m, flux, uvw, sign=1, long_double=False):
-    """Eq. 12: V_n = sum_m C_m exp(sign i 2 pi (u l + v m + w (n - 1)))."""
+def dft(l, m, flux, uvw, sign=1, long_double=False, threads=1):
+    """Eq. 12: V_n = sum_m C_m exp(sign i 2 pi (u l + v m + w (n - 1))).
+    threads > 1 splits the visibilities over that many OpenMP threads
+    (identical results)."""
     l, m, flux, uvw = _f64(l), _f64(m), _f64(flux), _f64(uvw).reshape(-1, 3)
     nv = uvw.shape[0]
     out = np.zeros(2 * nv)
+    if threads > 1 and not long_double:
+        _check(lib().orc_dft_mt(len(l), _p(l), _p(m), _p(flux), nv, _p(uvw), sign, _p(out), threads), "dft")
+        return _as_complex(out)
     fn = lib().orc_dft_ld if long_double else lib().orc_dft
     _check(fn(len(l), _p(l), _p(m), _p(flux), nv, _p(uvw), sign, _p(out)), "dft")
     return _as_complex(out)
@@ -227,10 +234,15 @@ class Tree:
         return dict(key=key, child_mask=mask, first_child=first, lam=lam, gamma=gam,
                     leaf_dir=ldir, leaf_flux=lflux, level_offsets=offs)
 
-    def vis_eq17(self, uvw, sign=1):
+    def vis_eq17(self, uvw, sign=1, threads=1):
+        """Eq. 17 per visibility; threads > 1 splits the visibilities over
+        that many OpenMP threads (identical results)."""
         uvw = _f64(uvw).reshape(-1, 3)
         out = np.zeros(2 * uvw.shape[0])
-        _check(lib().orc_tree_vis_eq17(self.h, uvw.shape[0], _p(uvw), sign, _p(out)), "eq17")
+        if threads > 1:
+            _check(lib().orc_tree_vis_eq17_mt(self.h, uvw.shape[0], _p(uvw), sign, _p(out), threads), "eq17")
+        else:
+            _check(lib().orc_tree_vis_eq17(self.h, uvw.shape[0], _p(uvw), sign, _p(out)), "eq17")
         return _as_complex(out)
 
     def vis_eq16(self, uvw, sign=1):

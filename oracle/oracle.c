@@ -589,6 +589,39 @@ int orc_tree_vis_eq17(const orc_tree* t, int64_t n_vis, const double* uvw, int s
     return 0;
 }
 
+/* Eq. 17 as orc_tree_vis_eq17, with the visibilities split into n_threads
+ * contiguous ranges evaluated side by side by OpenMP threads (the CPU
+ * baseline on all host cores). Every visibility is independent of the
+ * others (Sec. 3.6.1), so each range runs the single-threaded routine above
+ * unchanged and the results are identical bit for bit. */
+int orc_tree_vis_eq17_mt(const orc_tree* t, int64_t n_vis, const double* uvw, int sign, double* vis,
+                         int n_threads)
+{
+    if (!t || n_vis < 0 || (sign != 1 && sign != -1) || n_threads < 1) return -1;
+    int rc = 0;
+#pragma omp parallel for schedule(static) num_threads(n_threads) reduction(| : rc)
+    for (int r = 0; r < n_threads; ++r) {
+        const int64_t a = n_vis * r / n_threads, b = n_vis * (r + 1) / n_threads;
+        rc |= (b > a) ? orc_tree_vis_eq17(t, b - a, uvw + 3 * a, sign, vis + 2 * a) : 0;
+    }
+    return rc;
+}
+
+/* Eq. 12 as orc_dft, on n_threads OpenMP threads over contiguous ranges of
+ * the visibilities (identical results). */
+int orc_dft_mt(int64_t n_comp, const double* l, const double* m, const double* flux,
+               int64_t n_vis, const double* uvw, int sign, double* vis, int n_threads)
+{
+    if (n_comp < 0 || n_vis < 0 || (sign != 1 && sign != -1) || n_threads < 1) return -1;
+    int rc = 0;
+#pragma omp parallel for schedule(static) num_threads(n_threads) reduction(| : rc)
+    for (int r = 0; r < n_threads; ++r) {
+        const int64_t a = n_vis * r / n_threads, b = n_vis * (r + 1) / n_threads;
+        rc |= (b > a) ? orc_dft(n_comp, l, m, flux, b - a, uvw + 3 * a, sign, vis + 2 * a) : 0;
+    }
+    return rc;
+}
+
 /* Per-visibility Eq. 16: V = A_J sum_k lambda_J,k eta_J,k (R6). */
 int orc_tree_vis_eq16(const orc_tree* t, int64_t n_vis, const double* uvw, int sign, double* vis)
 {

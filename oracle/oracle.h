@@ -67,6 +67,10 @@ int orc_tree_export(const orc_tree* t, int64_t* key, uint8_t* child_mask, int32_
 /* Eq. 17 with the area factors (multiresolution sum). */
 int orc_tree_vis_eq17(const orc_tree* t, int64_t n_vis, const double* uvw, int sign, double* vis);
 /* Eq. 16 with the area factor (level-J sum). */
+int orc_tree_vis_eq17_mt(const orc_tree* t, int64_t n_vis, const double* uvw, int sign, double* vis,
+                         int n_threads);
+int orc_dft_mt(int64_t n_comp, const double* l, const double* m, const double* flux,
+               int64_t n_vis, const double* uvw, int sign, double* vis, int n_threads);
 int orc_tree_vis_eq16(const orc_tree* t, int64_t n_vis, const double* uvw, int sign, double* vis);
 /* Eq. 11 synthesis restricted to the tree: rebuild lambda_J from lambda_1 and
  * the gammas, top-down; out receives one value per leaf in BFS order. */

@@ -45,7 +45,7 @@ EXPORTS = [
     "wt_mlp_create", "wt_mlp_free", "wt_mlp_get_params", "wt_mlp_set_params", "wt_response_exact",
     "wt_mlp_loss_grad", "wt_mlp_train", "wt_mlp_eval", "wt_predict_vis_learned",
     "wt_selftest_bounded_wait", "wt_selftest_grid_barrier", "wt_dirty_image", "wt_hogbom", "wt_clean",
-    "wt_xref_table", "wt_build_tree_xref",
+    "wt_xref_table", "wt_build_tree_xref", "wt_measure_pipe_rates",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -105,6 +105,7 @@ def _declare(L):
     L.wt_device_status.argtypes = [vp]
     L.wt_selftest_bounded_wait.argtypes = [C.c_uint32, vp]
     L.wt_selftest_grid_barrier.argtypes = [C.c_uint32, vp]
+    L.wt_measure_pipe_rates.argtypes = [C.POINTER(C.c_double), vp]
     L.wt_last_error.restype = C.c_char_p
     L.wt_dirty_image.argtypes = [vp, vp, i64, C.c_int, d, vp, vp]
     L.wt_hogbom.argtypes = [vp, vp, C.c_int, f, f, C.c_int, vp, vp, vp, vp]
@@ -384,6 +385,14 @@ def wt_selftest_grid_barrier(spin_limit=1000, stream=None):
     """Run the grid-barrier self-test (a barrier that never opens); the
     timeout shows up in wt_device_status() as WT_ERR_TIMEOUT."""
     return _check(load().wt_selftest_grid_barrier(int(spin_limit), _stream(stream)))
+
+
+def wt_measure_pipe_rates(stream=None):
+    """Measured issue rates of the current device's pipes, per clock per SM:
+    {"ffma": ..., "ffma2_elems": ..., "dfma": ..., "mufu_sin": ...}."""
+    out = (C.c_double * 4)()
+    _check(load().wt_measure_pipe_rates(out, _stream(stream)))
+    return {"ffma": out[0], "ffma2_elems": out[1], "dfma": out[2], "mufu_sin": out[3]}
 
 
 def wt_last_error():

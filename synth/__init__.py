@@ -195,13 +195,32 @@ def batched(seed=1912, n_ch=64, n_t=250):
     return w
 
 
-def learned(seed=1913, J=12, n_t=490):
-    """256 antennas in a 10 km disc, 490 times (15 993 600 vis), 1.4 GHz;
-    50 000 components in 20 blobs inside a 2 deg field."""
+def large(seed=1913, J=12, n_t=490, shard=(0, 1)):
+    """The largest single-GPU workload: 256 antennas in a 10 km disc, 490
+    times (15 993 600 vis), 1.4 GHz; 50 000 components in 20 blobs inside a
+    2 deg field.
+
+    shard = (rank, world) with world > 1 describes one batch of world * n_t
+    hour angles over the same -1h .. +1h track, of which this rank takes the
+    rank-th contiguous block of n_t (visibilities are time-major, so a
+    contiguous range of the batch); the array and the sky are the same for
+    every rank. (0, 1) is the workload above."""
+    rank, world = shard
+    if not (0 <= rank < world):
+        raise ValueError("shard rank outside 0..world-1")
     rng = np.random.default_rng(seed)
-    _, uvw = _array_uvw(256, 10000.0, n_t, 1.4e9, rng)
+    enu = antenna_disc(256, 10000.0, rng)
+    b = baselines_xyz(enu, math.radians(SITE_LAT_DEG))
+    ha = np.linspace(-math.pi / 12.0, math.pi / 12.0, n_t * world)[rank * n_t:(rank + 1) * n_t]
+    uvw = uvw_metres(b, ha, DEC0) * (1.4e9 / C_LIGHT)
     l, m, f = components_blobs(20, 2500, 2.0, rng)
-    return Workload("learned_256ant_%dvis_50000comp" % uvw.shape[0], uvw, l, m, f, J)
+    tag = "" if world == 1 else "_shard%dof%d" % (rank, world)
+    return Workload("large_256ant_%dvis_50000comp%s" % (uvw.shape[0], tag), uvw, l, m, f, J)
+
+
+def learned(seed=1913, J=12, n_t=490):
+    """The learned-response workload: the same sky and array as large()."""
+    return large(seed=seed, J=J, n_t=n_t)
 
 
 def paper_context(n_distinct=140, seed=1914, J=20, n_t=3600):

@@ -97,3 +97,18 @@ def test_subtract():
 def test_rejects_bad_sign():
     with pytest.raises(ValueError):
         O.dft([0.0], [0.0], [1.0], np.zeros((1, 3)), sign=2)
+
+
+def test_threaded_evaluation_is_bitwise_single_threaded():
+    """The all-core CPU baseline splits the visibilities over OpenMP threads;
+    each visibility is computed by the unchanged single-threaded routine, so
+    the results must be identical bit for bit (Eq. 12 and Eq. 17)."""
+    w = synth.small()
+    uvw = w.uvw[:997]
+    one = O.dft(w.l, w.m, w.flux, uvw)
+    for th in (2, 3, 8):
+        assert np.array_equal(O.dft(w.l, w.m, w.flux, uvw, threads=th), one)
+    t = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, 9)
+    one = t.vis_eq17(uvw)
+    for th in (2, 5):
+        assert np.array_equal(t.vis_eq17(uvw, threads=th), one)

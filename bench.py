@@ -158,6 +158,12 @@ def tree_launches(J):
     return 4 + 3 * passes
 
 
+def predictor_launches(wt, which):
+    """libwtvis kernels per wt_predict_vis in a mixed form: the regrouped
+    Eq. 17 runs as a grid pass and an exact pass over the tiles it leaves."""
+    return 2 if which == wt.WT_SUM_EQ17_REGROUPED else 1
+
+
 def time_steps(wt, torch, w, J, mode, which, steps, warmup, dev, flush, clocks=None, dist=None, world=1):
     """W untimed steps, then K timed steps of build + predict + subtract on
     the resident inputs of workload w; per step the whole step and the
@@ -210,7 +216,7 @@ def time_steps(wt, torch, w, J, mode, which, steps, warmup, dev, flush, clocks=N
     info = tree.info()
     return dict(t_step=statistics.mean(times), t_pred=statistics.mean(pred_times), clocks=clk, info=info,
                 tree=tree, tensors=(l, m, fl, uvw, obs, model, resid),
-                launches_per_step=tree_launches(J) + 2)
+                launches_per_step=tree_launches(J) + predictor_launches(wt, which) + 1)
 
 
 def e2e_steps(wt, torch, w, J, mode, which, steps, warmup, dev, flush, tensors):

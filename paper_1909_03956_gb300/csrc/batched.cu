@@ -66,7 +66,12 @@ __device__ __forceinline__ int find_channel(const BatchChan* __restrict__ ch, in
     return a;
 }
 
-template <int NT, int VPT, int KIND, bool FAST = false>
+// The mixed kind runs the regrouped Eq. 17 in two passes as the single-tree
+// predictor does (wavelet_bodies.cuh, sweep_regrouped_mixed): GRIDPASS =
+// true evaluates the items whose phases fit the head grid and marks the
+// others, GRIDPASS = false evaluates only the marked items. GRIDPASS is
+// unused for the other kinds.
+template <int NT, int VPT, int KIND, bool FAST = false, bool GRIDPASS = false>
 __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ chans, int n_ch, int64_t total_items,
                                                 const double* __restrict__ uvw_m, int64_t n_vis, void* vis, double sgn,
                                                 int rows_max, unsigned long long* queue, int* status)
@@ -138,26 +143,37 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
                 if (good && n < n_vis) out[n] = make_double2(df_to_double(b.vr[k]), df_to_double(b.vi[k]));
             }
         } else if constexpr (KIND == kKindMixed) {
-            Eq17WF<NT, VPT, FAST> b;
+            float2* out = static_cast<float2*>(vis) + ch.out_offset;
+            float2* first_vis = out + (item - ch.tile_base) * per_tile;
+            if constexpr (!GRIDPASS) {
+                if (!tile_deferred(first_vis)) continue;   // done by the grid pass
+            }
+            F2 U[VPT], V[VPT], W[VPT];
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const int64_t n = n0 + static_cast<int64_t>(k) * NT;
                 const bool ok = n < n_vis;
                 const double s = sgn * ch.scale;   // sign folded into B (exact negation)
-                b.u[k] = split_f64(ok ? uvw_m[3 * n] * s : 0.0);
-                b.v[k] = split_f64(ok ? uvw_m[3 * n + 1] * s : 0.0);
-                b.w[k] = split_f64(ok ? uvw_m[3 * n + 2] * s : 0.0);
+                U[k] = split_f64(ok ? uvw_m[3 * n] * s : 0.0);
+                V[k] = split_f64(ok ? uvw_m[3 * n + 1] * s : 0.0);
+                W[k] = split_f64(ok ? uvw_m[3 * n + 2] * s : 0.0);
             }
-            b.start();
-            b.stk = reinterpret_cast<float2*>(stk_base) + threadIdx.x * VPT;   // [row][thread][vis] layout
-            b.J = ch.J;
-            b.maxrow = maxrow;
-            good = st.sweep_at(b);
-            float2* out = static_cast<float2*>(vis) + ch.out_offset;
+            float2 res[VPT];
+            float C[VPT];
+            bool defer = false;
+            float2* rstk = reinterpret_cast<float2*>(stk_base) + threadIdx.x * VPT;   // [row][thread][vis] layout
+            if constexpr (GRIDPASS) {
+                // an item that does not fit is swept too, its results discarded
+                defer = !tile_grid_constants(U, V, W, ch.hdr->smax, C);   // a CTA-wide decision
+                good = sweep_regrouped_mixed<NT, VPT, FAST, true>(st, U, V, W, C, rstk, ch.J, maxrow, res);
+            } else {
+                good = sweep_regrouped_mixed<NT, VPT, FAST, false>(st, U, V, W, C, rstk, ch.J, maxrow, res);
+            }
+            if (good && defer) mark_deferred(first_vis);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
                 const int64_t n = n0 + static_cast<int64_t>(k) * NT;
-                if (good && n < n_vis) out[n] = b.result(k);
+                if (good && !defer && n < n_vis) out[n] = res[k];
             }
         } else {
             Eq17D<NT, VPT> b;
@@ -231,40 +247,69 @@ int default_shape(int mode, int rows_max)
     return -1;
 }
 
-template <int NT, int VPT, int KIND, bool FAST = false>
-int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
-                 int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
+template <int NT, int VPT, int KIND, bool FAST = false, bool GRIDPASS = false>
+int launch_pass(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
+                int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
 {
-    auto k = k_batched<NT, VPT, KIND, FAST>;
+    auto k = k_batched<NT, VPT, KIND, FAST, GRIDPASS>;
     int per_sm = 0;
     WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
     if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
     // One CTA per item: the hardware balances the SMs as CTAs finish, as for
     // the single-channel predictor. The queue serves batches of more items
-    // than a grid holds.
+    // than a grid holds (reset before each pass).
     const bool per_item = total <= 0x7fffffff;
     int64_t grid = per_item ? total : static_cast<int64_t>(num_sms()) * per_sm;
     if (grid < 1) grid = 1;
+    if (!per_item) WT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     k<<<static_cast<unsigned>(grid), NT, smem, s>>>(chans, n_ch, total, uvw_m, n_vis, vis, static_cast<double>(sign),
                                                     rows_max, per_item ? nullptr : queue, status);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
 
-template <int KIND, bool FAST = false>
-int set_attr(int shape, size_t smem)
+// The mixed kind: the grid pass, then the exact pass over the items it left
+// marked; the other kinds: one pass.
+template <int NT, int VPT, int KIND, bool FAST = false>
+int launch_shape(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
+                 int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
+{
+    if constexpr (KIND == kKindMixed) {
+        const int rc = launch_pass<NT, VPT, KIND, FAST, true>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max,
+                                                              queue, status, smem, s);
+        if (rc) return rc;
+        return launch_pass<NT, VPT, KIND, FAST, false>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue,
+                                                       status, smem, s);
+    }
+    return launch_pass<NT, VPT, KIND, FAST>(chans, n_ch, total, uvw_m, n_vis, vis, sign, rows_max, queue, status,
+                                            smem, s);
+}
+
+template <int KIND, bool FAST = false, bool GRIDPASS = false>
+int set_attr_pass(int shape, size_t smem)
 {
     const void* fn;
     switch (shape) {
-        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, KIND, FAST>); break;
-        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, KIND, FAST>); break;
-        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, KIND, FAST>); break;
-        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, KIND, FAST>); break;
-        case 4: fn = reinterpret_cast<const void*>(k_batched<32, 1, KIND, FAST>); break;
-        default: fn = reinterpret_cast<const void*>(k_batched<32, 2, KIND, FAST>); break;
+        case 0: fn = reinterpret_cast<const void*>(k_batched<256, 1, KIND, FAST, GRIDPASS>); break;
+        case 1: fn = reinterpret_cast<const void*>(k_batched<128, 1, KIND, FAST, GRIDPASS>); break;
+        case 2: fn = reinterpret_cast<const void*>(k_batched<128, 2, KIND, FAST, GRIDPASS>); break;
+        case 3: fn = reinterpret_cast<const void*>(k_batched<64, 2, KIND, FAST, GRIDPASS>); break;
+        case 4: fn = reinterpret_cast<const void*>(k_batched<32, 1, KIND, FAST, GRIDPASS>); break;
+        default: fn = reinterpret_cast<const void*>(k_batched<32, 2, KIND, FAST, GRIDPASS>); break;
     }
     WT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     return WT_OK;
+}
+
+template <int KIND, bool FAST = false>
+int set_attr(int shape, size_t smem)
+{
+    if constexpr (KIND == kKindMixed) {
+        const int rc = set_attr_pass<KIND, FAST, true>(shape, smem);
+        if (rc) return rc;
+        return set_attr_pass<KIND, FAST, false>(shape, smem);
+    }
+    return set_attr_pass<KIND, FAST>(shape, smem);
 }
 
 template <int KIND, bool FAST = false>

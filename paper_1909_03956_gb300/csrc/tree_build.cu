@@ -228,8 +228,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_tree_levels(const uint64_t* _
     __shared__ int ws[32];
     __shared__ int64_t s_count[kMaxJ + 2];
     __shared__ int64_t s_roff[kMaxJ + 2];
+    __shared__ unsigned s_smax[3];   // float bits of max |s_u|, |s_v|, |s_w - 1| (non-negative: ordered as integers)
     const int tid = threadIdx.x;
     const int nt = blockDim.x;
+    if (tid < 3) s_smax[tid] = 0u;
 
     // ---- distinct level-J pixels (leaves) and their first sorted element
     int64_t carry = 0;
@@ -283,9 +285,13 @@ __global__ void __launch_bounds__(kLevelThreads) k_tree_levels(const uint64_t* _
         const double su = R.r[0] * x + R.r[3] * y + R.r[6] * zc;
         const double sv = R.r[1] * x + R.r[4] * y + R.r[7] * zc;
         const double sw = R.r[2] * x + R.r[5] * y + R.r[8] * zc;
+        const double sw1 = (sw > 0.0) ? -(su * su + sv * sv) / (1.0 + sw) : sw - 1.0;
         d.leaf_dir[3 * leaf + 0] = su;
         d.leaf_dir[3 * leaf + 1] = sv;
-        d.leaf_dir[3 * leaf + 2] = (sw > 0.0) ? -(su * su + sv * sv) / (1.0 + sw) : sw - 1.0;
+        d.leaf_dir[3 * leaf + 2] = sw1;
+        atomicMax(&s_smax[0], __float_as_uint(__double2float_ru(fabs(su))));
+        atomicMax(&s_smax[1], __float_as_uint(__double2float_ru(fabs(sv))));
+        atomicMax(&s_smax[2], __float_as_uint(__double2float_ru(fabs(sw1))));
     }
     __syncthreads();
 
@@ -352,6 +358,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_tree_levels(const uint64_t* _
         d.hdr->rev_offset[0] = total;
         d.hdr->n_leaves = n_leaves;
         d.hdr->n_nodes = total;
+        for (int c = 0; c < 3; ++c) d.hdr->smax[c] = __uint_as_float(s_smax[c]);
+        d.hdr->smax[3] = 0.0f;
     }
 }
 

@@ -171,8 +171,19 @@ __global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ re
     }
 }
 
-template <int NT, int VPT, int SUM, class Rec, bool FAST>
-__global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ recs, const TreeHeader* __restrict__ hdr,
+// SUM = 2 (the regrouped Eq. 17) runs as two passes (wavelet_bodies.cuh,
+// sweep_regrouped_mixed): GRIDPASS = true evaluates the tiles whose phases
+// fit the head grid and marks the others, GRIDPASS = false evaluates only the
+// marked tiles, with error-free sums. GRIDPASS is unused for SUM = 0, 1.
+// The regrouped form at one or two visibilities per thread is held to 64
+// registers (1024 threads per SM, the budget the form had before the grid
+// pass): left free, the compiler gives the grid pass 80 and fits 6 CTAs of
+// 128 threads per SM instead of 8.
+template <int NT, int VPT, int SUM>
+constexpr int mixed_min_blocks() { return (SUM == 2 && VPT <= 2) ? 1024 / NT : 1; }
+
+template <int NT, int VPT, int SUM, class Rec, bool FAST, bool GRIDPASS = false>
+__global__ void __launch_bounds__(NT, (mixed_min_blocks<NT, VPT, SUM>())) k_wavelet_mixed(const Rec* __restrict__ recs, const TreeHeader* __restrict__ hdr,
                                                       const double* __restrict__ uvw, int64_t n_vis,
                                                       float2* __restrict__ vis, float sgn, int rows, int J,
                                                       int* status)
@@ -186,6 +197,9 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
     const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if constexpr (SUM == 2 && !GRIDPASS) {
+            if (!tile_deferred(vis + tile * per_tile)) continue;   // done by the grid pass
+        }
         const int64_t n0 = tile * per_tile + threadIdx.x;
         F2 U[VPT], V[VPT], W[VPT];
 #pragma unroll
@@ -198,6 +212,7 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
             W[k] = split_f64(ok ? sg * uvw[3 * n + 2] : 0.0);
         }
         bool good;
+        bool defer = false;   // a tile the grid pass leaves marked for the exact pass
         float vr[VPT], vi[VPT];
         if constexpr (SUM == 1) {
             Eq16F<VPT, FAST> b;
@@ -225,24 +240,32 @@ __global__ void __launch_bounds__(NT) k_wavelet_mixed(const Rec* __restrict__ re
                 vi[k] = r.y;
             }
         } else {
-            Eq17WF<NT, VPT, FAST> b;
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) { b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k]; }
-            b.start();
-            b.stk = stk - threadIdx.x + threadIdx.x * VPT;   // [row][thread][vis] layout
-            b.J = J;
-            b.maxrow = rows - 1;
-            good = st.sweep_at(b);
+            float2 res[VPT];
+            float C[VPT];
+            float2* rstk = stk - threadIdx.x + threadIdx.x * VPT;   // [row][thread][vis] layout
+            if constexpr (GRIDPASS) {
+                // A tile that does not fit is swept too and its results are
+                // discarded (marked for the exact pass instead): skipping the
+                // sweep conditionally costs the kernel register spills, and
+                // such tiles come only with phases of 2^14 turns or more.
+                defer = !tile_grid_constants(U, V, W, hdr->smax, C);   // a CTA-wide decision
+                good = sweep_regrouped_mixed<NT, VPT, FAST, true>(st, U, V, W, C, rstk, J, rows - 1, res);
+            } else {
+                good = sweep_regrouped_mixed<NT, VPT, FAST, false>(st, U, V, W, C, rstk, J, rows - 1, res);
+            }
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
-                const float2 r = b.result(k);
-                vr[k] = r.x;
-                vi[k] = r.y;
+                vr[k] = res[k].x;
+                vi[k] = res[k].y;
             }
         }
         if (!good) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
             return;
+        }
+        if (defer) {
+            mark_deferred(vis + tile * per_tile);
+            continue;
         }
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
@@ -357,9 +380,15 @@ int run_mixed_form(const WaveletJob& jb, cudaStream_t s)
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else {
-        auto k = k_wavelet_mixed<NT, VPT, 2, RecWF, FAST>;
-        if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recwf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+        // the grid pass, then the exact pass over the tiles it left marked
+        auto kg = k_wavelet_mixed<NT, VPT, 2, RecWF, FAST, true>;
+        auto ke = k_wavelet_mixed<NT, VPT, 2, RecWF, FAST, false>;
+        if ((rc = prepare(kg, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
+        dim3 grid_e;
+        if ((rc = prepare(ke, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid_e))) return rc;
+        kg<<<grid, NT, smem, s>>>(jb.recwf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+        WT_CUDA_TRY(cudaGetLastError());
+        ke<<<grid_e, NT, smem, s>>>(jb.recwf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     }
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;

@@ -427,13 +427,18 @@ struct Eq17DF {
 // compensated sum. Any other internal node reads its xi, adds w xi (plus,
 // at level J-2, its children's terms) to V with compensation and passes xi
 // up (the first child writes its parent's sum, the others add).
-// Packed pairs as in Eq17F.
-template <int NT, int VPT, bool FAST = false>
+// Packed pairs as in Eq17F. GRID: the leaf phases with their heads on the
+// common grid of each visibility's constant C (phase_turns_grid2; the
+// caller sets Cg and Cs and guarantees that the grid is valid), else with
+// error-free sums (phase_turns_df2).
+template <int NT, int VPT, bool FAST = false, bool GRID = false>
 struct Eq17WF {
     static constexpr int NP = VPT / 2;
     static constexpr bool ODD = (VPT & 1) != 0;
     F2 u[VPT], v[VPT], w[VPT];                        // set by the caller, then start()
     DF2 U[NP > 0 ? NP : 1], V[NP > 0 ? NP : 1], W[NP > 0 ? NP : 1];
+    float2 Cg[NP > 0 ? NP : 1];                       // GRID: the grid constants of visibilities 2p, 2p + 1
+    float Cs;                                         // GRID: that of the last, unpaired visibility
     float2 acc[VPT], comp[VPT];                       // Kahan sum of V and its compensation
     float2 low[VPT];                                  // xi sum of the open level-(J-1) node
     float2 lowx[VPT];                                 // w xi sum of its leaves
@@ -496,6 +501,19 @@ struct Eq17WF {
 
     __device__ __forceinline__ float2 result(int k) const { return sub2(acc[k], comp[k]); }
 
+    __device__ __forceinline__ void phase2(int p, F2 su, F2 sv, F2 sw, float2& h, float2& tl) const
+    {
+        if constexpr (GRID) phase_turns_grid2(U[p], V[p], W[p], su, sv, sw, Cg[p], h, tl);
+        else phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
+    }
+
+    __device__ __forceinline__ void phase1(F2 su, F2 sv, F2 sw, float& th, float& tl) const
+    {
+        constexpr int k = VPT - 1;
+        if constexpr (GRID) phase_turns_grid(u[k], v[k], w[k], su, sv, sw, Cs, th, tl);
+        else phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
+    }
+
     // A leaf's sums start from zero: its parent clears them after reading.
     __device__ __forceinline__ void leaf_up(int k, float2 xi, float2 wv, bool root)
     {
@@ -517,8 +535,8 @@ struct Eq17WF {
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float2 h0, tl0, h1, tl1, e00, e01, e10, e11;
-            phase_turns_df2(U[p], V[p], W[p], su0, sv0, sw0, h0, tl0);
-            phase_turns_df2(U[p], V[p], W[p], su1, sv1, sw1, h1, tl1);
+            phase2(p, su0, sv0, sw0, h0, tl0);
+            phase2(p, su1, sv1, sw1, h1, tl1);
             sincos_mixed2<FAST>(h0, tl0, e00, e01);
             sincos_mixed2<FAST>(h1, tl1, e10, e11);
             low[2 * p] = add2(low[2 * p], add2(e00, e10));
@@ -529,8 +547,8 @@ struct Eq17WF {
         if constexpr (ODD) {
             constexpr int k = VPT - 1;
             float th0, tl0, s0, c0, th1, tl1, s1, c1;
-            phase_turns_df(u[k], v[k], w[k], su0, sv0, sw0, th0, tl0);
-            phase_turns_df(u[k], v[k], w[k], su1, sv1, sw1, th1, tl1);
+            phase1(su0, sv0, sw0, th0, tl0);
+            phase1(su1, sv1, sw1, th1, tl1);
             sincos_mixed<FAST>(th0, tl0, s0, c0);
             sincos_mixed<FAST>(th1, tl1, s1, c1);
             const float2 e0 = make_float2(c0, s0), e1 = make_float2(c1, s1);
@@ -611,7 +629,7 @@ struct Eq17WF {
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 float2 h, tl, e0, e1;
-                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
+                phase2(p, su, sv, sw, h, tl);
                 sincos_mixed2<FAST>(h, tl, e0, e1);
                 leaf_up(2 * p, e0, wv, root);
                 leaf_up(2 * p + 1, e1, wv, root);
@@ -619,7 +637,7 @@ struct Eq17WF {
             if constexpr (ODD) {
                 constexpr int k = VPT - 1;
                 float th, tl, s, c;
-                phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
+                phase1(su, sv, sw, th, tl);
                 sincos_mixed<FAST>(th, tl, s, c);
                 leaf_up(k, make_float2(c, s), wv, root);
             }
@@ -642,6 +660,80 @@ struct Eq17WF {
         pass_up(par, (meta & kRwFirst) != 0, xi);
     }
 };
+
+// The regrouped Eq. 17 in a mixed form is evaluated in two passes over the
+// tiles. The grid pass takes every tile whose phases all fit the head grid
+// (tile_grid_constants: all heads below 2^(kGridMaxK - 1) turns, which the
+// tree's coordinate bounds smax and each visibility's |u|, |v|, |w|
+// establish) and evaluates it with phase_turns_grid2; a tile that does not
+// fit gets kDeferredMark in both parts of its first visibility and is left
+// to the exact pass, which evaluates only tiles so marked, with error-free
+// sums (phase_turns_df2). The two kernels are launched back to back on one
+// stream; kept apart, each stays within its register budget.
+constexpr uint32_t kDeferredMark = 0x7fc4b1d3u;   // a quiet NaN
+
+// Grid constants of a thread's visibilities and the CTA's vote on whether
+// every visibility of the tile fits; every thread of the CTA must call it.
+template <int VPT>
+__device__ __forceinline__ bool tile_grid_constants(const F2 (&u)[VPT], const F2 (&v)[VPT], const F2 (&w)[VPT],
+                                                    const float* __restrict__ smax, float (&C)[VPT])
+{
+    const float sm[3] = {smax[0], smax[1], smax[2]};
+    bool fits = true;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        int kk;
+        C[k] = grid_magic(phase_bound(u[k], v[k], w[k], sm), kk);
+        fits = fits && kk <= kGridMaxK;
+    }
+    return __syncthreads_and(fits ? 1 : 0) != 0;
+}
+
+// One tile's sweep of the regrouped Eq. 17 (GRID: on the head grid of the
+// constants C, else with error-free sums). Returns false (CTA-wide) if a
+// staging copy did not arrive; res receives V of each visibility.
+template <int NT, int VPT, bool FAST, bool GRID>
+__device__ __forceinline__ bool sweep_regrouped_mixed(Stager<RecWF>& st, const F2 (&u)[VPT], const F2 (&v)[VPT],
+                                      const F2 (&w)[VPT], const float (&C)[VPT], float2* stk, int J, int maxrow,
+                                      float2 (&res)[VPT])
+{
+    Eq17WF<NT, VPT, FAST, GRID> b;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) { b.u[k] = u[k]; b.v[k] = v[k]; b.w[k] = w[k]; }
+    if constexpr (GRID) {
+#pragma unroll
+        for (int p = 0; p < VPT / 2; ++p) b.Cg[p] = make_float2(C[2 * p], C[2 * p + 1]);
+        b.Cs = C[VPT - 1];
+    }
+    b.start();
+    b.stk = stk;
+    b.J = J;
+    b.maxrow = maxrow;
+    const bool good = st.sweep_at(b);
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) res[k] = b.result(k);
+    return good;
+}
+
+// The exact pass's test of a tile: whether its first visibility carries
+// kDeferredMark (read by one thread, broadcast through shared memory);
+// every thread of the CTA must call it.
+__device__ __forceinline__ bool tile_deferred(const float2* first_vis)
+{
+    __shared__ int s_deferred;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const volatile float* x = reinterpret_cast<const volatile float*>(first_vis);
+        s_deferred = __float_as_uint(x[0]) == kDeferredMark && __float_as_uint(x[1]) == kDeferredMark;
+    }
+    __syncthreads();
+    return s_deferred != 0;
+}
+
+__device__ __forceinline__ void mark_deferred(float2* first_vis)
+{
+    if (threadIdx.x == 0) *first_vis = make_float2(__uint_as_float(kDeferredMark), __uint_as_float(kDeferredMark));
+}
 
 }  // namespace
 }  // namespace wt

@@ -299,6 +299,87 @@ __device__ __forceinline__ void phase_turns_df2(const DF2& u, const DF2& v, cons
     tl = sub2(add2(add2(t1, t2), sub2(t3, ea)), eb);
 }
 
+// ---- phase with the heads on a common grid ----------------------------------
+// The error-free sums of phase_turns_df2 exist to add the three head
+// products without losing their low bits. When every head is first rounded
+// onto one common grid G = 2^(k-23), with k chosen per visibility so that
+// every product stays below 2^(k-1), the heads and their partial sums are
+// multiples of G below 2^(k+1): 24 significant bits at most, so plain
+// float32 additions are exact. A head is rounded onto the grid by one FMA
+// against the constant C = 1.5 * 2^k (the sum x y + C stays in C's binade,
+// where the spacing of floats is G) and recovered by one exact subtraction
+// (Sterbenz); its remainder x y - (x y)_G, below G/2, goes to the tail with
+// the cross terms. Per visibility and term this is 20 float32 operations
+// against 29 for the error-free sums, with the same phase accuracy: the
+// tail's roundings are of order 2^-24 G, the dropped x.lo y.lo below 2^-48
+// of the product. Valid while k <= kGridMaxK, which keeps |tail| <= 2 G
+// small enough for both sin/cos forms (sincos_turns_f32 then sees
+// |x| <= 0.84); larger phases take phase_turns_df2 (the caller decides).
+constexpr int kGridMinK = -8;    // finest grid used: 2^-31 turns
+constexpr int kGridMaxK = 15;    // heads below 2^14 turns
+
+// C = 1.5 * 2^k for the smallest k >= kGridMinK with bound < 2^(k-1); also
+// returns k through kk. bound: an upper bound on the sum of |x.hi y.hi| over
+// the three coordinates (a non-finite bound gives k > kGridMaxK).
+__device__ __forceinline__ float grid_magic(float bound, int& kk)
+{
+    const int e = (__float_as_int(bound) >> 23) & 255;   // bound < 2^(e - 126) (e = 255: not finite)
+    int k = e - 125;
+    k = k < kGridMinK ? kGridMinK : k;
+    kk = k;
+    const int kc = k > kGridMaxK ? kGridMaxK : k;
+    return __int_as_float(((kc + 127) << 23) | 0x400000);
+}
+
+// Head of x y on the grid of C, negated, and the tail, for both elements
+// (element-wise C): nq = -(x.hi y.hi rounded to the grid), exactly;
+// t = (x.hi y.hi + nq) + x.lo y.hi + x.hi y.lo, the first term exact.
+__device__ __forceinline__ void grid_product2n(const DF2& x, F2 y, float2 C, float2& nq, float2& t)
+{
+    const float2 yh = bcast2(y.hi);
+    nq = sub2(C, fma2(x.hi, yh, C));
+    t = fma2(x.hi, bcast2(y.lo), fma2(x.lo, yh, fma2(x.hi, yh, nq)));
+}
+
+// phase_turns_df2 on the grid of C (per element): returns h and tl with the
+// phase = tl - h modulo 1, |h| <= 1/2, |tl| <= 2^(k-22).
+__device__ __forceinline__ void phase_turns_grid2(const DF2& u, const DF2& v, const DF2& w, F2 su, F2 sv, F2 sw1,
+                                                  float2 C, float2& h, float2& tl)
+{
+    float2 q1, t1, q2, t2, q3, t3;
+    grid_product2n(u, su, C, q1, t1);
+    grid_product2n(v, sv, C, q2, t2);
+    grid_product2n(w, sw1, C, q3, t3);
+    const float2 b = add2(add2(q1, q2), q3);          // exact: multiples of the grid below 2^(k+1)
+    h = sub2(b, make_float2(rintf(b.x), rintf(b.y)));
+    tl = add2(add2(t1, t2), t3);
+}
+
+// The scalar form of phase_turns_grid2 (one visibility): the phase is
+// th + tl modulo 1, |th| <= 1/2.
+__device__ __forceinline__ void phase_turns_grid(F2 u, F2 v, F2 w, F2 su, F2 sv, F2 sw1, float C, float& th,
+                                                 float& tl)
+{
+    const float p1 = __fsub_rn(__fmaf_rn(u.hi, su.hi, C), C);
+    const float p2 = __fsub_rn(__fmaf_rn(v.hi, sv.hi, C), C);
+    const float p3 = __fsub_rn(__fmaf_rn(w.hi, sw1.hi, C), C);
+    const float t1 = __fmaf_rn(u.hi, su.lo, __fmaf_rn(u.lo, su.hi, __fmaf_rn(u.hi, su.hi, -p1)));
+    const float t2 = __fmaf_rn(v.hi, sv.lo, __fmaf_rn(v.lo, sv.hi, __fmaf_rn(v.hi, sv.hi, -p2)));
+    const float t3 = __fmaf_rn(w.hi, sw1.lo, __fmaf_rn(w.lo, sw1.hi, __fmaf_rn(w.hi, sw1.hi, -p3)));
+    const float b = __fadd_rn(__fadd_rn(p1, p2), p3);
+    th = __fsub_rn(b, rintf(b));
+    tl = __fadd_rn(__fadd_rn(t1, t2), t3);
+}
+
+// Bound on sum_c |x_c.hi y_c.hi| for a visibility (u, v, w) against every
+// leaf of a tree whose coordinates are bounded by smax (float32, rounded
+// up): the float32 evaluation, raised by 2^-10 to cover its own roundings.
+__device__ __forceinline__ float phase_bound(F2 u, F2 v, F2 w, const float* smax)
+{
+    const float b = __fmaf_rn(fabsf(u.hi), smax[0], __fmaf_rn(fabsf(v.hi), smax[1], fabsf(w.hi) * smax[2]));
+    return b * 1.0009765625f;
+}
+
 // sincos_turns_f32 of the phase tl - h (turns) of two visibilities, each
 // result written as the pair (cos, sin) of its own visibility: e0 for
 // element 0, e1 for element 1. Quadrant reduction and both polynomials on
@@ -471,6 +552,8 @@ struct TreeHeader {
     int64_t n_nodes;
     int64_t per_level[kMaxJ + 1];   // [j] = nodes at level j (index 0 unused)
     int64_t rev_offset[kMaxJ + 2];  // start of level j in the level-J-first layout
+    float smax[4];                  // max over the leaves of |s_u|, |s_v|, |s_w - 1| (float32, rounded
+                                    // up; 0 for an empty tree); [3] unused
 };
 
 struct TreeDev {

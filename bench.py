@@ -526,6 +526,10 @@ ALG_FLOPS_PER_NODE = 40
 #     sum) to V (2, with a Kahan add of 8); every internal node passes xi to
 #     its parent's sum (2).
 OPS_PHASE = 12 + 12 + 1 + 4
+# The regrouped forms' phase on the head grid: per coordinate the head on the
+# grid (2), its remainder (1) and the two cross terms (2); the heads' sum (2),
+# the reduction (1), the tails' sum (2): 20.
+OPS_PHASE_GRID = 3 * 5 + 2 + 1 + 2
 OPS_LEAF = OPS_PHASE + 15
 OPS_NODE = 30
 OPS_LEAF_FAST = OPS_PHASE + 3
@@ -535,8 +539,8 @@ OPS_RG_LOW = 2 + 2 + 2
 # (form, sum) -> (per leaf, per internal node, per internal node at level J - 1)
 OPS = {("mixed", "explicit"): (OPS_LEAF, OPS_NODE, OPS_NODE),
        ("fast", "explicit"): (OPS_LEAF_FAST, OPS_NODE, OPS_NODE),
-       ("mixed", "regrouped"): (OPS_LEAF + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW),
-       ("fast", "regrouped"): (OPS_LEAF_FAST + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW)}
+       ("mixed", "regrouped"): (OPS_LEAF - OPS_PHASE + OPS_PHASE_GRID + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW),
+       ("fast", "regrouped"): (OPS_LEAF_FAST - OPS_PHASE + OPS_PHASE_GRID + OPS_RG_LEAF, OPS_RG_NODE, OPS_RG_LOW)}
 SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # DRAM bytes of one k_wavelet_mixed launch at J = 12, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), per (workload, form, sum);

@@ -244,7 +244,11 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
  * exits. n_comp above that limit returns WT_ERR_RANGE before anything is
  * enqueued.
  *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current, and so does the first call in a new context on
+ *     that device (after cudaDeviceReset, say); make that first call before
+ *     any stream capture.
+ *   - mode: WT_FP64 or WT_FP64_DF (complex128 out), WT_MIXED or
+ *     WT_MIXED_FAST (complex64 out), as for dft_predict_vis.
  *   - All calls on a device share the array and it keeps the last call's
  *     records. Calls whose work overlaps on the GPU (e.g. on two streams with
  *     no ordering between them) race on it and give wrong results; order
@@ -390,6 +394,31 @@ int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis
                            void* stream);
 
 /* ---------------------------------------------------------------------------
+ * wt_predict_vis_truncated -- the tree truncated at one level, the use of
+ * the per-level response (an addition to the paper's method). The level's
+ * nodes stand for their pixels, each with its pixel's flux
+ * F_k = A_level lambda_level,k (Eq. 9: the merged flux below the node):
+ *   V = R(B) sum_k F_k exp(sign i 2 pi B.(c_k - P))
+ * (c_k the pixel centres, the sum in the fast mixed form), with
+ *   response = WT_RESPONSE_SNAPPED: R = 1, each pixel's flux at its centre
+ *              (Eq. 16 read at the truncation level);
+ *              WT_RESPONSE_LEARNED: R = the network m of that level (exact
+ *              sum beyond its x_max), the flux spread over each pixel;
+ *              WT_RESPONSE_EXACT: R = the exact response of the level-`level`
+ *              pixel holding the phase centre, `depth` levels of sub-pixels
+ *              (float64; the learned form's yardstick).
+ * All pixels of the level share one response: the change of pixel shape
+ * across the field is neglected. level 1..J of the tree; m (LEARNED) must be
+ * for that level and the tree's phase centre; depth (EXACT) 0..8. Output
+ * device complex64 [n_vis]. Allocates scratch on `stream` and releases it.
+ * ------------------------------------------------------------------------- */
+#define WT_RESPONSE_SNAPPED 0
+#define WT_RESPONSE_LEARNED 1
+#define WT_RESPONSE_EXACT 2
+int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int depth, const double* uvw,
+                             int64_t n_vis, void* vis_out, int sign, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Helpers
  * ------------------------------------------------------------------------- */
 
@@ -400,7 +429,10 @@ int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis
 int wt_recommended_J(double dtheta_rad);
 
 /* Read and clear the device status word of the current device after
- * synchronising `stream`: WT_OK, or the first error a kernel recorded. */
+ * synchronising `stream`: WT_OK, or the first error a kernel recorded.
+ * WT_ERR_TIMEOUT means a bounded wait ran out: the results of that call are
+ * undefined, and since a bulk copy that never arrived may still land later,
+ * later results on the device are not to be trusted either. */
 int wt_device_status(void* stream);
 
 /* Failure-detection self-test: a one-CTA kernel waits, with at most
@@ -429,6 +461,17 @@ int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream);
  * Allocates a few KB of scratch on `stream`, runs about 10 ms of kernels and
  * synchronises `stream`. */
 int wt_measure_pipe_rates(double* per_clk_per_sm, void* stream);
+
+/* Self-test of the library's per-context state (the device status word and
+ * the device address of dft_predict_vis_noalloc's fixed array; the paper has
+ * no counterpart): one component of flux 3 at the phase centre through
+ * dft_predict_vis_noalloc (V = 3 exactly), then cudaDeviceReset on the
+ * current device, then the same again in the new context. Returns WT_OK when
+ * both rounds give V = 3 and a clear status word. cudaDeviceReset ends this
+ * process's context on the device: every device pointer, stream and tree
+ * handle of the process on it becomes invalid, so call this only from a
+ * process that holds nothing on the device. Synchronises. */
+int wt_selftest_context_reset(void);
 
 /* Text of the calling thread's last error (never NULL). */
 const char* wt_last_error(void);

@@ -75,6 +75,7 @@ def _declare(L):
     L.orc_tree_sizes.argtypes = [C.c_void_p, _i64, _i64, _i64]
     L.orc_tree_export.argtypes = [C.c_void_p, _i64, _u8, _i32, _d, _d, _d, _d]
     L.orc_tree_vis_eq17.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d]
+    L.orc_tree_vis_truncated.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int64, _d, C.c_int, _d]
     L.orc_tree_vis_eq17_mt.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d, C.c_int]
     L.orc_dft_mt.argtypes = [C.c_int64, _d, _d, _d, C.c_int64, _d, C.c_int, _d, C.c_int]
     L.orc_tree_vis_eq16.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int, _d]
@@ -90,6 +91,8 @@ def _declare(L):
 
 def _declare_mlp(L):
     L.orc_pixel_response.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int64, _d, C.c_int, _d]
+    L.orc_pixel_response_of.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int64, _d, C.c_int,
+                                        _d]
     L.orc_level_pixel_size.argtypes = [C.c_int]
     L.orc_level_pixel_size.restype = C.c_double
     L.orc_mlp_n_params.restype = C.c_int
@@ -251,6 +254,19 @@ class Tree:
         _check(lib().orc_tree_vis_eq16(self.h, uvw.shape[0], _p(uvw), sign, _p(out)), "eq16")
         return _as_complex(out)
 
+    def vis_truncated(self, jt, uvw, kind="snapped", depth=4, sign=1):
+        """The tree truncated at level jt (reading R12): sum over the level-jt
+        nodes of F_k exp(sign i 2 pi B.(c_k - P)) R_k(B), F_k = A_jt lambda_jt;
+        kind "snapped" R_k = 1, "level" R_k = the phase-centre pixel's
+        response R_jt(B), "pixel" R_k = each pixel's own response (depth D
+        quadrature)."""
+        kinds = {"snapped": 0, "level": 1, "pixel": 2}
+        uvw = _f64(uvw).reshape(-1, 3)
+        out = np.zeros(2 * uvw.shape[0])
+        _check(lib().orc_tree_vis_truncated(self.h, jt, kinds[kind], depth, uvw.shape[0], _p(uvw), sign, _p(out)),
+               "truncated")
+        return _as_complex(out)
+
     def synthesis(self):
         out = np.zeros(self.n_leaves)
         _check(lib().orc_tree_synthesis(self.h, _p(out)), "synthesis")
@@ -304,6 +320,16 @@ def pixel_response(j, D, ra0, dec0, uvw, sign=1):
     uvw = _f64(uvw).reshape(-1, 3)
     out = np.zeros(2 * uvw.shape[0])
     _check(lib().orc_pixel_response(j, D, ra0, dec0, uvw.shape[0], _p(uvw), sign, _p(out)), "pixel_response")
+    return _as_complex(out)
+
+
+def pixel_response_of(j, k, D, ra0, dec0, uvw, sign=1):
+    """Exact R_j,k(B) of any level-j pixel k: mean of exp(sign i 2 pi B.(s_i -
+    c_j,k)) over the centres of its 4^D descendants D levels down."""
+    uvw = _f64(uvw).reshape(-1, 3)
+    out = np.zeros(2 * uvw.shape[0])
+    _check(lib().orc_pixel_response_of(j, int(k), D, ra0, dec0, uvw.shape[0], _p(uvw), sign, _p(out)),
+           "pixel_response_of")
     return _as_complex(out)
 
 

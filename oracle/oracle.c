@@ -642,6 +642,61 @@ int orc_tree_vis_eq16(const orc_tree* t, int64_t n_vis, const double* uvw, int s
     return 0;
 }
 
+/* Reading R12 (the use of the learned response, an addition to the paper):
+ * the tree truncated at level jt keeps its level-jt nodes, each with the
+ * flux of its pixel F_k = A_jt lambda_jt,k (Eq. 9 averages the children, so
+ * A_j lambda_j,k is the merged flux below the node), and predicts
+ *     V = sum_k F_k exp(sign i 2 pi B.(c_k - P)) R_k(B)
+ * with c_k the pixel centre and R_k(B):
+ *   kind 0: 1 -- centre-snapped: Eq. 16 read at level jt;
+ *   kind 1: R_jt(B), the response of the level-jt pixel holding the phase
+ *           centre, for every k (what the per-level network learns);
+ *   kind 2: R_jt,k(B), each pixel's own response (its flux spread uniformly
+ *           over its area),
+ * the responses by dense quadrature D levels down. Summed over the nodes in
+ * breadth-first (key) order. */
+int orc_tree_vis_truncated(const orc_tree* t, int jt, int kind, int D, int64_t n_vis, const double* uvw, int sign,
+                           double* vis)
+{
+    if (!t || jt < 1 || jt > t->J || kind < 0 || kind > 2 || n_vis < 0 || (sign != 1 && sign != -1)) return -1;
+    if (kind > 0 && (D < 0 || jt + D > 30 || D > 10)) return -1;
+    double* R = NULL;
+    if (kind > 0) {
+        R = (double*)malloc(sizeof(double) * 2 * (size_t)(n_vis > 0 ? n_vis : 1));
+        if (kind == 1 && orc_pixel_response(jt, D, t->ra0, t->dec0, n_vis, uvw, sign, R) != 0) {
+            free(R);
+            return -2;
+        }
+    }
+    for (int64_t q = 0; q < 2 * n_vis; ++q) vis[q] = 0.0;
+    const double Aj = area_of_level(jt);
+    for (int64_t i = 0; i < t->n_nodes; ++i) {
+        const orc_node* nd = t->bfs[i];
+        if (nd->level != jt) continue;
+        const double F = PLANTED(17) ? nd->lambda : Aj * nd->lambda;
+        double c[3];
+        orc_pixel_dir_uvw(jt, nd->key, t->ra0, t->dec0, c);
+        if (kind == 2 && orc_pixel_response_of(jt, nd->key, D, t->ra0, t->dec0, n_vis, uvw, sign, R) != 0) {
+            free(R);
+            return -2;
+        }
+        for (int64_t q = 0; q < n_vis; ++q) {
+            double er, ei;
+            plane_wave(uvw + 3 * q, c, sign, &er, &ei);
+            if (kind > 0) {
+                const double rr = R[2 * q], ri = PLANTED(18) ? -R[2 * q + 1] : R[2 * q + 1];
+                const double xr = er * rr - ei * ri, xi = er * ri + ei * rr;
+                er = xr;
+                ei = xi;
+            }
+            vis[2 * q] += F * er;
+            vis[2 * q + 1] += F * ei;
+        }
+    }
+    free(R);
+    return 0;
+}
+
 /* Eq. 11 on the tree: for each child c of a node at level j,
  *   lambda_c = lambda_j + (1 / sqrt(A_j)) sum_m H[m][c] gamma^m_j,
  * with H the sign rows of Eq. 10. Top-down from level 1. */

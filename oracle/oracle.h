@@ -89,6 +89,10 @@ int orc_dense_vis_eq17(int J, int64_t n, const double* l, const double* m, const
 /* ---- Learned response (oracle_mlp.c; an addition, not in the paper) -------- */
 /* Exact per-level pixel response R_j(B) over the 4^D descendants of the
  * level-j pixel holding the phase centre (see oracle_mlp.c). out: [n][2]. */
+int orc_pixel_response_of(int j, int64_t k, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
+                          double* out);
+int orc_tree_vis_truncated(const orc_tree* t, int jt, int kind, int D, int64_t n_vis, const double* uvw, int sign,
+                           double* vis);
 int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
                        double* out);
 double orc_level_pixel_size(int j);

@@ -40,20 +40,24 @@
 #endif
 #define PLANTED(k) (ORC_PLANT == (k))
 
-int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
-                       double* out /* [n][2] */)
+/* Full-pixel response of pixel k at level j (reading R10 for any pixel):
+ *     R_j,k(B) = 4^-D sum_i exp(sign i 2 pi B.(s_i - c_j,k))
+ * over the centres s_i of the 4^D descendants of pixel k at level j + D
+ * (nested numbering: keys k 4^D .. (k + 1) 4^D - 1, Sec. 3.5), c_j,k the
+ * pixel's own centre. A flux spread uniformly over the pixel contributes
+ * Phi exp(sign i 2 pi B.(c_j,k - P)) R_j,k(B) to the visibility. */
+int orc_pixel_response_of(int j, int64_t k, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
+                          double* out /* [n][2] */)
 {
     if (j < 1 || D < 0 || j + D > 30 || D > 10 || n < 0 || (sign != 1 && sign != -1)) return -1;
-    const double zero = 0.0;
-    int64_t kref;
-    if (orc_map_components(1, &zero, &zero, ra0, dec0, j, &kref, NULL) != 0) return -2;
+    if (k < 0 || k >= 12 * ((int64_t)1 << (2 * (j - 1)))) return -1;
     double c[3];
-    orc_pixel_dir_uvw(j, kref, ra0, dec0, c);
+    orc_pixel_dir_uvw(j, k, ra0, dec0, c);
     const int64_t nsub = (int64_t)1 << (2 * D);
     double* d = (double*)malloc(sizeof(double) * 3 * (size_t)nsub);
     for (int64_t i = 0; i < nsub; ++i) {
         double s[3];
-        orc_pixel_dir_uvw(j + D, (kref << (2 * D)) + i, ra0, dec0, s);
+        orc_pixel_dir_uvw(j + D, (k << (2 * D)) + i, ra0, dec0, s);
         const double sg = PLANTED(13) ? -1.0 : 1.0;
         d[3 * i + 0] = sg * (s[0] - c[0]);
         d[3 * i + 1] = sg * (s[1] - c[1]);
@@ -75,6 +79,17 @@ int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const d
     }
     free(d);
     return 0;
+}
+
+/* R_j(B) of the level-j pixel that holds the phase centre (reading R10). */
+int orc_pixel_response(int j, int D, double ra0, double dec0, int64_t n, const double* uvw, int sign,
+                       double* out /* [n][2] */)
+{
+    if (j < 1 || D < 0 || j + D > 30 || D > 10 || n < 0 || (sign != 1 && sign != -1)) return -1;
+    const double zero = 0.0;
+    int64_t kref;
+    if (orc_map_components(1, &zero, &zero, ra0, dec0, j, &kref, NULL) != 0) return -2;
+    return orc_pixel_response_of(j, kref, D, ra0, dec0, n, uvw, sign, out);
 }
 
 double orc_level_pixel_size(int j) { return ldexp(sqrt(ORC_PI / 3.0), 1 - j); }

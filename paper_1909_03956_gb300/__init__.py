@@ -33,6 +33,7 @@ WT_OK, WT_ERR_ARG, WT_ERR_RANGE, WT_ERR_CUDA, WT_ERR_NOMEM, WT_ERR_TIMEOUT, WT_E
 WT_FP64, WT_MIXED, WT_LEARNED, WT_MIXED_FAST, WT_FP64_DF = 0, 1, 2, 3, 4
 WT_SUM_EQ17, WT_SUM_EQ16, WT_SUM_EQ17_REGROUPED = 0, 1, 2
 WT_PREDICT_TREE, WT_PREDICT_DIRECT = 0, 1
+WT_RESPONSE_SNAPPED, WT_RESPONSE_LEARNED, WT_RESPONSE_EXACT = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwtvis.so")
@@ -46,6 +47,7 @@ EXPORTS = [
     "wt_mlp_loss_grad", "wt_mlp_train", "wt_mlp_eval", "wt_predict_vis_learned",
     "wt_selftest_bounded_wait", "wt_selftest_grid_barrier", "wt_dirty_image", "wt_hogbom", "wt_clean",
     "wt_xref_table", "wt_build_tree_xref", "wt_measure_pipe_rates",
+    "wt_selftest_context_reset", "wt_predict_vis_truncated",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -101,11 +103,13 @@ def _declare(L):
     L.wt_mlp_train.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, f, vp, vp]
     L.wt_mlp_eval.argtypes = [vp, vp, i64, C.c_int, vp, vp]
     L.wt_predict_vis_learned.argtypes = [vp, vp, vp, i64, vp, C.c_int, vp]
+    L.wt_predict_vis_truncated.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, i64, vp, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
     L.wt_device_status.argtypes = [vp]
     L.wt_selftest_bounded_wait.argtypes = [C.c_uint32, vp]
     L.wt_selftest_grid_barrier.argtypes = [C.c_uint32, vp]
     L.wt_measure_pipe_rates.argtypes = [C.POINTER(C.c_double), vp]
+    L.wt_selftest_context_reset.argtypes = []
     L.wt_last_error.restype = C.c_char_p
     L.wt_dirty_image.argtypes = [vp, vp, i64, C.c_int, d, vp, vp]
     L.wt_hogbom.argtypes = [vp, vp, C.c_int, f, f, C.c_int, vp, vp, vp, vp]
@@ -339,6 +343,21 @@ def wt_predict_vis_learned(tree, mlp, uvw, sign=1, out=None, stream=None):
         out = torch.empty(uvw.shape[0], dtype=torch.complex64, device=uvw.device)
     _check(load().wt_predict_vis_learned(tree.h, mlp.h, _dev(uvw, torch.float64), uvw.shape[0],
                                          _dev(out, torch.complex64), int(sign), _stream(stream)))
+    return out
+
+
+def wt_predict_vis_truncated(tree, level, uvw, response=WT_RESPONSE_SNAPPED, mlp=None, depth=4, sign=1, out=None,
+                             stream=None):
+    """The tree truncated at `level`: R(B) sum_k F_k exp(sign i 2 pi B.(c_k - P))
+    over its level-`level` nodes, R = 1 (WT_RESPONSE_SNAPPED), the network
+    `mlp` (WT_RESPONSE_LEARNED) or the exact response of depth `depth`
+    (WT_RESPONSE_EXACT). complex64 out."""
+    import torch
+    if out is None:
+        out = torch.empty(uvw.shape[0], dtype=torch.complex64, device=uvw.device)
+    _check(load().wt_predict_vis_truncated(tree.h, int(level), int(response), mlp.h if mlp is not None else None,
+                                           int(depth), _dev(uvw, torch.float64), uvw.shape[0],
+                                           _dev(out, torch.complex64), int(sign), _stream(stream)))
     return out
 
 

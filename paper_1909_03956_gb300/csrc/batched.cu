@@ -600,8 +600,8 @@ extern "C" int wt_predict_vis_batched(const wt_tree* trees, const double* freq_h
     }
     const size_t ob = static_cast<size_t>(n_vis) * n_ch * ((mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8);
     int rc;
-    if ((rc = check_device_buffer(uvw_m, static_cast<size_t>(n_vis) * 24, fn, "uvw_m")) ||
-        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
+    if ((rc = check_device_buffer(uvw_m, static_cast<size_t>(n_vis) * 24, fn, "uvw_m", 8)) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out", vis_align(mode))))
         return rc;
     if (n_vis == 0) return WT_OK;
     return predict_batched(trees, freq_hz, n_ch, uvw_m, n_vis, vis_out, mode, sign, static_cast<cudaStream_t>(stream));

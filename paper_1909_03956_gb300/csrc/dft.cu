@@ -318,18 +318,23 @@ static __device__ int g_noalloc_status_sink;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64] = {nullptr};
 int* g_noalloc_sink[64] = {nullptr};
+uint64_t g_noalloc_ctx[64] = {0};   // context ID the addresses belong to
 
 // Device addresses of the two arrays above on the current device. The first
 // call on a device looks them up (cudaGetSymbolAddress, with that device
-// current); in host code the names are only host-side stand-ins and must
-// never be handed to a kernel.
+// current), and so does the first call in a new context on it (after
+// cudaDeviceReset, say: the module is loaded again and the arrays may move);
+// in host code the names are only host-side stand-ins and must never be
+// handed to a kernel.
 int noalloc_addresses(void** records, int** sink)
 {
     int dev = 0;
     WT_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return set_error(WT_ERR_CUDA, "device ordinal %d out of range", dev);
+    const uint64_t ctx = current_context_id();
+    if (ctx == 0) return set_error(WT_ERR_CUDA, "dft_predict_vis_noalloc: no current CUDA context");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_records);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_records)");
@@ -339,6 +344,7 @@ int noalloc_addresses(void** records, int** sink)
         if (!p || !q) return set_error(WT_ERR_CUDA, "cudaGetSymbolAddress returned a null address");
         g_noalloc_addr[dev] = p;
         g_noalloc_sink[dev] = static_cast<int*>(q);
+        g_noalloc_ctx[dev] = ctx;
     }
     *records = g_noalloc_addr[dev];
     *sink = g_noalloc_sink[dev];
@@ -346,8 +352,6 @@ int noalloc_addresses(void** records, int** sink)
 }
 
 }  // namespace
-
-int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name);
 
 }  // namespace wt
 
@@ -362,15 +366,17 @@ extern "C" int dft_predict_vis_noalloc(const double* l, const double* m, const d
         return set_error(WT_ERR_RANGE, "%s: %lld components exceed the fixed capacity of %lld", fn,
                          static_cast<long long>(n_comp), static_cast<long long>(kNoAllocMaxComponents));
     if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED) return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    if (mode != WT_FP64 && mode != WT_FP64_DF && mode != WT_MIXED && mode != WT_MIXED_FAST)
+        return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
+    const bool c128 = mode == WT_FP64 || mode == WT_FP64_DF;
     const size_t nb = static_cast<size_t>(n_comp) * 8;
-    const size_t ob = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
+    const size_t ob = static_cast<size_t>(n_vis) * (c128 ? 16 : 8);
     int rc;
-    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
-        (rc = check_device_buffer(flux, nb, fn, "flux")) ||
-        (rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")) ||
-        (status && (rc = check_device_buffer(status, sizeof(int), fn, "status"))))
+    if ((rc = check_device_buffer(l, nb, fn, "l", 8)) || (rc = check_device_buffer(m, nb, fn, "m", 8)) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux", 8)) ||
+        (rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out", vis_align(mode))) ||
+        (status && (rc = check_device_buffer(status, sizeof(int), fn, "status", 4))))
         return rc;
     void* records = nullptr;
     int* sink = nullptr;
@@ -393,14 +399,79 @@ extern "C" int dft_predict_vis_noalloc(const double* l, const double* m, const d
         if ((rc = grid_for(k, NT, NT, smem, n_vis, grid))) return rc;
         k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(records), n_comp, uvw, n_vis, static_cast<double2*>(vis_out),
                                  static_cast<double>(sign), status);
+    } else if (mode == WT_FP64_DF) {
+        constexpr int NT = 128;
+        const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk)) + kDfTableEntries * sizeof(float4);
+        auto k = k_dft_df<NT>;
+        if ((rc = grid_for(k, NT, NT, smem, n_vis, grid))) return rc;
+        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<double2*>(vis_out),
+                                 static_cast<double>(sign), status);
     } else {
         constexpr int NT = 256;
         const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
-        auto k = k_dft_mixed<NT, false>;
+        auto k = (mode == WT_MIXED_FAST) ? k_dft_mixed<NT, true> : k_dft_mixed<NT, false>;
         if ((rc = grid_for(k, NT, 2 * NT, smem, n_vis, grid))) return rc;   // two visibilities per thread
         k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<float2*>(vis_out),
                                  static_cast<float>(sign), status);
     }
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
+}
+
+// ===========================================================================
+// wt_selftest_context_reset -- the per-context caches across a context reset.
+//
+// One component of flux 3 at the phase centre (so that V = 3 exactly for
+// every baseline in float64) through dft_predict_vis_noalloc with no status
+// word (the library's sink) and a read of the device status word; then
+// cudaDeviceReset, which ends this process's context on the device and with
+// it every device allocation; then the same again in the new context, with
+// buffers allocated afresh. Both rounds must give V = 3 + 0i and a clear
+// status word, which they can only if the array addresses and the status
+// word were looked up again for the new context.
+// ===========================================================================
+namespace wt {
+namespace {
+
+int noalloc_round(cudaStream_t s)
+{
+    // one allocation: l, m, flux at d[0..2], uvw at d[3..8], the two
+    // complex128 outputs at d[10..13] (16-byte aligned, as the kernel's
+    // stores need)
+    const double l = 0.0, m = 0.0, flux = 3.0;
+    const double uvw[6] = {1234.5, -987.25, 12.5, -3.0e4, 2.0e4, -150.0};
+    double* d = nullptr;
+    WT_CUDA_TRY(cudaMalloc(&d, sizeof(double) * 14));
+    double out[4] = {0, 0, 0, 0};
+    int rc = WT_OK;
+    cudaError_t e = cudaMemcpy(d, &l, sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 1, &m, sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 2, &flux, sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 3, uvw, sizeof(uvw), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_error(e, "wt_selftest_context_reset: upload");
+    if (rc == WT_OK)
+        rc = dft_predict_vis_noalloc(d, d + 1, d + 2, 1, d + 3, 2, d + 10, WT_FP64, 1, nullptr, s);
+    if (rc == WT_OK) {
+        e = cudaMemcpyAsync(out, d + 10, sizeof(out), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "wt_selftest_context_reset: download");
+    }
+    cudaFree(d);
+    if (rc != WT_OK) return rc;
+    if (out[0] != 3.0 || out[1] != 0.0 || out[2] != 3.0 || out[3] != 0.0)
+        return set_error(WT_ERR_CORRUPT, "wt_selftest_context_reset: V = (%g, %g), (%g, %g), expected (3, 0)", out[0],
+                         out[1], out[2], out[3]);
+    return wt_device_status(s);
+}
+
+}  // namespace
+}  // namespace wt
+
+extern "C" int wt_selftest_context_reset(void)
+{
+    using namespace wt;
+    int rc = noalloc_round(nullptr);
+    if (rc != WT_OK) return rc;
+    WT_CUDA_TRY(cudaDeviceReset());
+    return noalloc_round(nullptr);
 }

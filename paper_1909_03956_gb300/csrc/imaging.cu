@@ -689,9 +689,9 @@ extern "C" int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis,
     if (rc) return rc;
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
     const size_t nn = static_cast<size_t>(n) * n;
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
-        (vis && (rc = check_device_buffer(vis, static_cast<size_t>(n_vis) * 8, fn, "vis"))) ||
-        (rc = check_device_buffer(image, nn * 4, fn, "image")))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (vis && (rc = check_device_buffer(vis, static_cast<size_t>(n_vis) * 8, fn, "vis", 8))) ||
+        (rc = check_device_buffer(image, nn * 4, fn, "image", 4)))
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void* scratch = nullptr;
@@ -749,10 +749,10 @@ extern "C" int wt_hogbom(float* image, const float* psf, int n, float gain, floa
     if (!isfinite(threshold)) return set_error(WT_ERR_RANGE, "%s: threshold must be finite", fn);
     const size_t nn = static_cast<size_t>(n) * n;
     int rc;
-    if ((rc = check_device_buffer(image, nn * 4, fn, "image")) || (rc = check_device_buffer(psf, nn * 4, fn, "psf")) ||
-        (rc = check_device_buffer(n_comp, 4, fn, "n_comp")) ||
-        (max_iter > 0 && ((rc = check_device_buffer(comp_pix, static_cast<size_t>(max_iter) * 4, fn, "comp_pix")) ||
-                          (rc = check_device_buffer(comp_flux, static_cast<size_t>(max_iter) * 4, fn, "comp_flux")))))
+    if ((rc = check_device_buffer(image, nn * 4, fn, "image", 4)) || (rc = check_device_buffer(psf, nn * 4, fn, "psf", 4)) ||
+        (rc = check_device_buffer(n_comp, 4, fn, "n_comp", 4)) ||
+        (max_iter > 0 && ((rc = check_device_buffer(comp_pix, static_cast<size_t>(max_iter) * 4, fn, "comp_pix", 4)) ||
+                          (rc = check_device_buffer(comp_flux, static_cast<size_t>(max_iter) * 4, fn, "comp_flux", 4)))))
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void* state = nullptr;
@@ -789,12 +789,12 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
     if (!n_comp) return set_error(WT_ERR_ARG, "%s: n_comp (host) is NULL", fn);
     const int cap = minor_iter * n_major;
     const size_t nn = static_cast<size_t>(n) * n;
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(vis_obs, static_cast<size_t>(n_vis) * 8, fn, "vis_obs")) ||
-        (rc = check_device_buffer(vis_resid, static_cast<size_t>(n_vis) * 8, fn, "vis_resid")) ||
-        (rc = check_device_buffer(image_resid, nn * 4, fn, "image_resid")) ||
-        (cap > 0 && ((rc = check_device_buffer(comp_pix, static_cast<size_t>(cap) * 4, fn, "comp_pix")) ||
-                     (rc = check_device_buffer(comp_flux, static_cast<size_t>(cap) * 4, fn, "comp_flux")))))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(vis_obs, static_cast<size_t>(n_vis) * 8, fn, "vis_obs", 8)) ||
+        (rc = check_device_buffer(vis_resid, static_cast<size_t>(n_vis) * 8, fn, "vis_resid", 8)) ||
+        (rc = check_device_buffer(image_resid, nn * 4, fn, "image_resid", 4)) ||
+        (cap > 0 && ((rc = check_device_buffer(comp_pix, static_cast<size_t>(cap) * 4, fn, "comp_pix", 4)) ||
+                     (rc = check_device_buffer(comp_flux, static_cast<size_t>(cap) * 4, fn, "comp_flux", 4)))))
         return rc;
     *n_comp = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

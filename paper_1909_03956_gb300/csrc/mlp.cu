@@ -593,9 +593,146 @@ int run_grad(wt_mlp m, const double* uvw, const float* target, int64_t first, in
 }
 }  // namespace
 
+namespace wt {
+namespace {
+// ---------------------------------------------------------------- truncated tree
+// The tree's level-`level` nodes as Eq. 16 leaf records (RecF): the pixel
+// centre (s_u, s_v, s_w - 1) as double-float pairs and g = F_k =
+// A_level lambda_level,k, the flux of the node's pixel (Eq. 9 averages the
+// children, so A_j lambda_j,k is the merged flux below the node); and a
+// header view whose n_leaves is their count, for the Eq. 16 kernel. The
+// nodes of level j sit at rev_offset[j] .. + per_level[j] of the tree's
+// level-J-first arrays, in key order.
+__global__ void k_level_records(const int64_t* __restrict__ key, const double* __restrict__ lambda,
+                                const TreeHeader* __restrict__ hdr, int level, Rot R, RecF* __restrict__ out,
+                                TreeHeader* __restrict__ view, int64_t cap)
+{
+    int64_t n = hdr->per_level[level];
+    n = n < cap ? n : cap;
+    const int64_t base = hdr->rev_offset[level];
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i0 == 0) {
+        view->n_leaves = n;
+        view->n_nodes = n;
+    }
+    const double A = ldexp(kPi / 3.0, 2 * (1 - level));
+    for (int64_t i = i0; i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double c[3];
+        pixel_dir(level, key[base + i], R, c);
+        const F2 a = split_f64(c[0]), b = split_f64(c[1]), e = split_f64(c[2]);
+        RecF r;
+        r.meta = kRecLeaf;
+        r.a = a.hi;
+        r.b = a.lo;
+        r.c = b.hi;
+        r.d = b.lo;
+        r.e = e.hi;
+        r.f = e.lo;
+        r.g = static_cast<float>(A * lambda[base + i]);
+        out[i] = r;
+    }
+}
+
+// vis *= R, element by element (complex64 by complex128, formed in float64).
+__global__ void k_mul_response(float2* __restrict__ vis, const double2* __restrict__ r, int64_t n)
+{
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float2 v = vis[i];
+        const double2 q = r[i];
+        const double vr = v.x, vi = v.y;
+        vis[i] = make_float2(static_cast<float>(vr * q.x - vi * q.y), static_cast<float>(vr * q.y + vi * q.x));
+    }
+}
+
+}  // namespace
+}  // namespace wt
+
 using namespace wt;
 
 extern "C" {
+
+int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int depth, const double* uvw,
+                             int64_t n_vis, void* vis_out, int sign, void* stream)
+{
+    const char* fn = "wt_predict_vis_truncated";
+    if (!t || t->magic != kTreeMagic) return set_error(WT_ERR_ARG, "%s: bad tree handle", fn);
+    if (level < 1 || level > t->J) return set_error(WT_ERR_RANGE, "%s: level %d outside 1..J = %d", fn, level, t->J);
+    if (n_vis < 0 || (sign != 1 && sign != -1)) return set_error(WT_ERR_ARG, "%s: bad n_vis or sign", fn);
+    int rc;
+    if (response == WT_RESPONSE_LEARNED) {
+        if ((rc = check_mlp(m, fn))) return rc;
+        if (m->level != level)
+            return set_error(WT_ERR_ARG, "%s: the network is for level %d, not %d", fn, m->level, level);
+        if (t->ra0 != m->ra0 || t->dec0 != m->dec0)
+            return set_error(WT_ERR_ARG, "%s: tree and network have different phase centres", fn);
+    } else if (response == WT_RESPONSE_EXACT) {
+        if (depth < 0 || depth > 8 || level + depth > kMaxJ)
+            return set_error(WT_ERR_RANGE, "%s: need 0 <= depth <= 8 and level + depth <= %d", fn, kMaxJ);
+    } else if (response != WT_RESPONSE_SNAPPED) {
+        return set_error(WT_ERR_ARG, "%s: bad response %d", fn, response);
+    }
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(vis_out, static_cast<size_t>(n_vis) * 8, fn, "vis_out", 8)))
+        return rc;
+    if (n_vis == 0) return WT_OK;
+    int* status = device_status_word();
+    if (!status) return set_error(WT_ERR_CUDA, "%s: no device status word", fn);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // scratch: the header view, the level's records, and for the exact
+    // response the sub-pixel offsets and R(B) per visibility
+    const int64_t cap = t->cap_leaves > 0 ? t->cap_leaves : 1;
+    const int n_off = response == WT_RESPONSE_EXACT ? 1 << (2 * depth) : 0;
+    const size_t rec_bytes = ((static_cast<size_t>(cap) * sizeof(RecF)) + 255) & ~size_t(255);
+    const size_t off_bytes = ((sizeof(double) * 3 * static_cast<size_t>(n_off)) + 255) & ~size_t(255);
+    const size_t r_bytes = response == WT_RESPONSE_EXACT ? sizeof(double2) * static_cast<size_t>(n_vis) : 0;
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), 256 + rec_bytes + off_bytes + r_bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "%s: scratch allocation failed: %s", fn, cudaGetErrorString(e));
+    }
+    TreeHeader* view = reinterpret_cast<TreeHeader*>(scratch);
+    RecF* recs = reinterpret_cast<RecF*>(scratch + 256);
+    double* offs = reinterpret_cast<double*>(scratch + 256 + rec_bytes);
+    double2* resp = reinterpret_cast<double2*>(scratch + 256 + rec_bytes + off_bytes);
+    Rot R;
+    rotation_matrix(t->ra0, t->dec0, R.r);
+    int64_t blocks = (cap + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_level_records<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t->d.key, t->d.lambda, t->d.hdr, level, R, recs,
+                                                                  view, cap);
+    rc = (cudaGetLastError() == cudaSuccess) ? WT_OK : set_error(WT_ERR_CUDA, "%s: level records launch", fn);
+    if (rc == WT_OK) {
+        // Eq. 16 over the level's pixel centres, in the fast mixed form
+        WaveletJob jb{};
+        jb.recf_leaf = recs;
+        jb.hdr = view;
+        jb.uvw = uvw;
+        jb.n_vis = n_vis;
+        jb.vis = vis_out;
+        jb.mode = WT_MIXED_FAST;
+        jb.sign = sign;
+        jb.which = WT_SUM_EQ16;
+        jb.J = t->J;
+        jb.status = status;
+        rc = launch_wavelet(jb, default_wavelet_variant(WT_MIXED_FAST, WT_SUM_EQ16, t->J), s);
+    }
+    if (rc == WT_OK && response == WT_RESPONSE_LEARNED) rc = launch_apply(m, uvw, n_vis, vis_out, sign, true, s);
+    if (rc == WT_OK && response == WT_RESPONSE_EXACT) {
+        k_response_offsets<<<(n_off + 127) / 128, 128, 0, s>>>(level, depth, R, offs);
+        int64_t b2 = (n_vis + 255) / 256;
+        const int64_t bcap = static_cast<int64_t>(num_sms()) * 8;
+        if (b2 > bcap) b2 = bcap;
+        k_response_exact<<<static_cast<unsigned>(b2), 256, 0, s>>>(uvw, n_vis, offs, n_off, static_cast<double>(sign),
+                                                                   resp);
+        k_mul_response<<<static_cast<unsigned>(b2), 256, 0, s>>>(static_cast<float2*>(vis_out), resp, n_vis);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: exact response launch", fn);
+    }
+    cudaFreeAsync(scratch, s);
+    cudaGetLastError();
+    return rc;
+}
 
 int wt_mlp_create(int level, double ra0, double dec0, int depth, float x_max, uint64_t seed, wt_mlp* out)
 {
@@ -715,8 +852,8 @@ int wt_response_exact(int level, int depth, double ra0, double dec0, const doubl
         return set_error(WT_ERR_RANGE, "%s: need 1 <= level, 0 <= depth <= 8, level + depth <= %d", fn, kMaxJ);
     if (n < 0 || (sign != 1 && sign != -1)) return set_error(WT_ERR_ARG, "%s: bad n or sign", fn);
     int rc;
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(out, static_cast<size_t>(n) * 16, fn, "out")))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(out, static_cast<size_t>(n) * 16, fn, "out", 16)))
         return rc;
     if (n == 0) return WT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -745,8 +882,8 @@ int wt_mlp_loss_grad(wt_mlp m, const double* uvw, const float* target, int64_t n
     int rc = check_mlp(m, fn);
     if (rc) return rc;
     if (n <= 0 || !loss || !grad) return set_error(WT_ERR_ARG, "%s: need n > 0 and host outputs", fn);
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target")))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target", 8)))
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WT_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNumParams, s));
@@ -766,8 +903,8 @@ int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, in
     int rc = check_mlp(m, fn);
     if (rc) return rc;
     if (n <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0f)) return set_error(WT_ERR_ARG, "%s: bad sizes or lr", fn);
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target")))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target", 8)))
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WT_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNumParams, s));
@@ -798,8 +935,8 @@ int wt_mlp_eval(wt_mlp m, const double* uvw, int64_t n, int sign, void* out, voi
     int rc = check_mlp(m, fn);
     if (rc) return rc;
     if (n < 0 || (sign != 1 && sign != -1)) return set_error(WT_ERR_ARG, "%s: bad n or sign", fn);
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(out, static_cast<size_t>(n) * 8, fn, "out")))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(out, static_cast<size_t>(n) * 8, fn, "out", 8)))
         return rc;
     if (n == 0) return WT_OK;
     return launch_apply(m, uvw, n, out, sign, false, static_cast<cudaStream_t>(stream));

@@ -21,6 +21,7 @@ struct Stager {
     uint64_t* bars;       // shared, 2 mbarriers
     int chunk;            // records per buffer (even, so chunk * sizeof(Rec) % 16 == 0)
     uint32_t phase0, phase1;  // expected parity per buffer
+    bool busy0, busy1;    // a copy into buffer 0 / 1 has been issued and not yet waited for
     bool resident;        // whole list fits in the two buffers
     bool loaded;          // resident list already in shared memory
 
@@ -39,8 +40,21 @@ struct Stager {
     __device__ void init_state()
     {
         phase0 = phase1 = 0;
+        busy0 = busy1 = false;
         resident = nchunks() <= 2;
         loaded = false;
+    }
+
+    // After a wait ran out: one more bounded wait on every buffer whose copy
+    // is still outstanding, so that the CTA does not exit while a bulk copy
+    // may still write into its shared memory. Called by every thread (the
+    // busy flags are uniform across the CTA). If a copy still has not
+    // arrived, the CTA leaves anyway; the caller has recorded WT_ERR_TIMEOUT
+    // and the device's later results are not to be trusted.
+    __device__ void drain()
+    {
+        if (busy0) mbar_wait_parity(&bars[0], phase0);
+        if (busy1) mbar_wait_parity(&bars[1], phase1);
     }
 
     // Point the stager at another record list (same chunking). Call only
@@ -66,13 +80,25 @@ struct Stager {
             issue(0, 0);
             if (nc > 1) issue(1, 1);
         }
+        if (need_load) {
+            busy0 = true;
+            busy1 = nc > 1;
+        }
         for (int64_t c = 0; c < nc; ++c) {
             const int b = static_cast<int>(c & 1);
             if (need_load) {
                 const bool ok = mbar_wait_parity(&bars[b], b ? phase1 : phase0);
-                if (!__syncthreads_and(ok ? 1 : 0)) return false;
-                if (b) phase1 ^= 1u;
-                else phase0 ^= 1u;
+                if (!__syncthreads_and(ok ? 1 : 0)) {
+                    drain();
+                    return false;
+                }
+                if (b) {
+                    phase1 ^= 1u;
+                    busy1 = false;
+                } else {
+                    phase0 ^= 1u;
+                    busy0 = false;
+                }
             }
             const int64_t first = c * chunk;
             const int n = static_cast<int>((count - first < chunk) ? (count - first) : chunk);
@@ -85,6 +111,10 @@ struct Stager {
             if (!resident) {
                 __syncthreads();                           // buffer b fully consumed
                 if (threadIdx.x == 0 && c + 2 < nc) issue(c + 2, b);
+                if (c + 2 < nc) {
+                    if (b) busy1 = true;
+                    else busy0 = true;
+                }
             }
         }
         if (resident) loaded = true;
@@ -104,13 +134,25 @@ struct Stager {
             issue(0, 0);
             if (nc > 1) issue(1, 1);
         }
+        if (need_load) {
+            busy0 = true;
+            busy1 = nc > 1;
+        }
         for (int64_t c = 0; c < nc; ++c) {
             const int b = static_cast<int>(c & 1);
             if (need_load) {
                 const bool ok = mbar_wait_parity(&bars[b], b ? phase1 : phase0);
-                if (!__syncthreads_and(ok ? 1 : 0)) return false;
-                if (b) phase1 ^= 1u;
-                else phase0 ^= 1u;
+                if (!__syncthreads_and(ok ? 1 : 0)) {
+                    drain();
+                    return false;
+                }
+                if (b) {
+                    phase1 ^= 1u;
+                    busy1 = false;
+                } else {
+                    phase0 ^= 1u;
+                    busy0 = false;
+                }
             }
             const int64_t first = c * chunk;
             const int n = static_cast<int>((count - first < chunk) ? (count - first) : chunk);
@@ -123,6 +165,10 @@ struct Stager {
             if (!resident) {
                 __syncthreads();
                 if (threadIdx.x == 0 && c + 2 < nc) issue(c + 2, b);
+                if (c + 2 < nc) {
+                    if (b) busy1 = true;
+                    else busy0 = true;
+                }
             }
         }
         if (resident) loaded = true;

@@ -175,12 +175,17 @@ __global__ void __launch_bounds__(NT) k_wavelet_df(const RecWDF* __restrict__ re
 // sweep_regrouped_mixed): GRIDPASS = true evaluates the tiles whose phases
 // fit the head grid and marks the others, GRIDPASS = false evaluates only the
 // marked tiles, with error-free sums. GRIDPASS is unused for SUM = 0, 1.
-// The regrouped form at one or two visibilities per thread is held to 64
-// registers (1024 threads per SM, the budget the form had before the grid
-// pass): left free, the compiler gives the grid pass 80 and fits 6 CTAs of
-// 128 threads per SM instead of 8.
+// Register budgets of the regrouped form: 64 per thread at one or two
+// visibilities per thread (1024 threads per SM; left free, the compiler gives
+// the grid pass 80 and fits 6 CTAs of 128 threads per SM instead of 8), 128
+// at four (512 threads per SM, the same 2048 visibilities in flight, with
+// the per-record work -- loading, decoding and broadcasting a record --
+// shared by twice as many visibilities).
 template <int NT, int VPT, int SUM>
-constexpr int mixed_min_blocks() { return (SUM == 2 && VPT <= 2) ? 1024 / NT : 1; }
+constexpr int mixed_min_blocks()
+{
+    return SUM != 2 ? 1 : VPT <= 2 ? 1024 / NT : VPT == 4 ? 512 / NT : 1;
+}
 
 template <int NT, int VPT, int SUM, class Rec, bool FAST, bool GRIDPASS = false>
 __global__ void __launch_bounds__(NT, (mixed_min_blocks<NT, VPT, SUM>())) k_wavelet_mixed(const Rec* __restrict__ recs, const TreeHeader* __restrict__ hdr,

@@ -17,6 +17,7 @@ namespace {
 thread_local char g_msg[512] = "no error";
 std::mutex g_mu;
 int* g_status[64] = {nullptr};
+uint64_t g_status_ctx[64] = {0};   // context ID each status word belongs to
 int g_sms[64] = {0};
 
 // cuMemGetAddressRange from the driver, looked up at run time so that the
@@ -40,6 +41,34 @@ AddrRangeFn addr_range_fn()
             cudaGetLastError();
     }
     return g_addr_range;
+}
+
+// The driver's current context and its unique ID (cuCtxGetCurrent,
+// cuCtxGetId), looked up at run time like cuMemGetAddressRange. Caches of
+// device memory that belongs to a context are keyed on this ID: a context
+// that is destroyed and created again (cudaDeviceReset, or a host framework
+// tearing its context down) gets a new ID, and the caches are rebuilt.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_tried = false;
+
+void ctx_fns()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_ctx_tried) return;
+    g_ctx_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(fn);
+    cudaGetLastError();
 }
 
 int current_device(int* dev)
@@ -66,11 +95,31 @@ int cuda_error(cudaError_t e, const char* what)
     return set_error(WT_ERR_CUDA, "%s: %s (%d)", what, cudaGetErrorString(e), static_cast<int>(e));
 }
 
+// Unique ID of the current context (made current first if the runtime has
+// not done so yet); 0 if there is none.
+uint64_t current_context_id()
+{
+    ctx_fns();
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void* ctx = nullptr;
+    if (g_ctx_current(&ctx) != 0 || !ctx) {
+        cudaFree(nullptr);   // the runtime creates (or makes current) the primary context
+        cudaGetLastError();
+        ctx = nullptr;
+        if (g_ctx_current(&ctx) != 0 || !ctx) return 0;
+    }
+    unsigned long long id = 0;
+    if (g_ctx_id(ctx, &id) != 0) return 0;
+    return static_cast<uint64_t>(id) + 1;   // never 0
+}
+
 int* device_status_word()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    const uint64_t ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_mu);
+    if (g_status[dev] && g_status_ctx[dev] != ctx) g_status[dev] = nullptr;   // its context is gone
     if (!g_status[dev]) {
         int* p = nullptr;
         if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) {
@@ -83,6 +132,7 @@ int* device_status_word()
             return nullptr;
         }
         g_status[dev] = p;
+        g_status_ctx[dev] = ctx;
         // Keep stream-ordered allocations cached in the pool between calls.
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -108,10 +158,12 @@ int num_sms()
 
 // A pointer the kernels will dereference must be device (or managed) memory
 // of the current device, and [p, p + bytes) must lie inside its allocation.
-int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name)
+int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name, size_t align)
 {
     if (bytes == 0) return WT_OK;
     if (!p) return set_error(WT_ERR_ARG, "%s: %s is NULL", fn, name);
+    if (align > 1 && reinterpret_cast<uintptr_t>(p) % align != 0)
+        return set_error(WT_ERR_ARG, "%s: %s must be %zu-byte aligned", fn, name, align);
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) {
@@ -217,8 +269,8 @@ int wt_build_tree(const double* l, const double* m, const double* flux, int64_t 
     int rc;
     if ((rc = check_tree_args(fn, n_comp, ra0, dec0, J))) return rc;
     const size_t nb = static_cast<size_t>(n_comp) * sizeof(double);
-    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
-        (rc = check_device_buffer(flux, nb, fn, "flux")))
+    if ((rc = check_device_buffer(l, nb, fn, "l", 8)) || (rc = check_device_buffer(m, nb, fn, "m", 8)) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux", 8)))
         return rc;
     wt::KeySource src;
     src.l = l;
@@ -234,7 +286,7 @@ int wt_xref_table(int n, double dl, double ra0, double dec0, int J, int64_t* tab
     if (J < 1 || J > kMaxJ) return set_error(WT_ERR_RANGE, "%s: J = %d outside 1..%d", fn, J, kMaxJ);
     if (!isfinite(ra0) || !isfinite(dec0)) return set_error(WT_ERR_RANGE, "%s: non-finite phase centre", fn);
     int rc;
-    if ((rc = check_device_buffer(table, static_cast<size_t>(n) * n * sizeof(int64_t), fn, "table"))) return rc;
+    if ((rc = check_device_buffer(table, static_cast<size_t>(n) * n * sizeof(int64_t), fn, "table", 8))) return rc;
     return wt::xref_table(n, dl, ra0, dec0, J, table, static_cast<cudaStream_t>(stream));
 }
 
@@ -248,9 +300,9 @@ int wt_build_tree_xref(const int64_t* table, int n, const int32_t* pix, const do
     if ((rc = check_tree_args(fn, n_comp, ra0, dec0, J))) return rc;
     if (n < 1 || n > 16384) return set_error(WT_ERR_ARG, "%s: n = %d outside 1..16384", fn, n);
     const int64_t nn = static_cast<int64_t>(n) * n;
-    if ((rc = check_device_buffer(table, static_cast<size_t>(nn) * sizeof(int64_t), fn, "table")) ||
-        (rc = check_device_buffer(pix, static_cast<size_t>(n_comp) * sizeof(int32_t), fn, "pix")) ||
-        (rc = check_device_buffer(flux, static_cast<size_t>(n_comp) * sizeof(double), fn, "flux")))
+    if ((rc = check_device_buffer(table, static_cast<size_t>(nn) * sizeof(int64_t), fn, "table", 8)) ||
+        (rc = check_device_buffer(pix, static_cast<size_t>(n_comp) * sizeof(int32_t), fn, "pix", 4)) ||
+        (rc = check_device_buffer(flux, static_cast<size_t>(n_comp) * sizeof(double), fn, "flux", 8)))
         return rc;
     wt::KeySource src;
     src.table = table;
@@ -346,8 +398,8 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out, i
     if (mode == WT_FP64_DF && which == WT_SUM_EQ17)
         return set_error(WT_ERR_UNSUPPORTED, "%s: WT_FP64_DF evaluates the regrouped Eq. 17 and Eq. 16 only", fn);
     const size_t ob = static_cast<size_t>(n_vis) * ((mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8);
-    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out", vis_align(mode))))
         return rc;
     return wt::predict_wavelet(t, uvw, n_vis, vis_out, mode, sign, which, static_cast<cudaStream_t>(stream));
 }
@@ -364,10 +416,10 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
     const size_t nb = static_cast<size_t>(n_comp) * 8;
     const size_t ob = static_cast<size_t>(n_vis) * ((mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8);
     int rc;
-    if ((rc = check_device_buffer(l, nb, fn, "l")) || (rc = check_device_buffer(m, nb, fn, "m")) ||
-        (rc = check_device_buffer(flux, nb, fn, "flux")) ||
-        (rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw")) ||
-        (rc = check_device_buffer(vis_out, ob, fn, "vis_out")))
+    if ((rc = check_device_buffer(l, nb, fn, "l", 8)) || (rc = check_device_buffer(m, nb, fn, "m", 8)) ||
+        (rc = check_device_buffer(flux, nb, fn, "flux", 8)) ||
+        (rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(vis_out, ob, fn, "vis_out", vis_align(mode))))
         return rc;
     if (!device_status_word()) return set_error(WT_ERR_CUDA, "%s: no usable CUDA device", fn);
     return wt::predict_dft(l, m, flux, n_comp, uvw, n_vis, vis_out, mode, sign, static_cast<cudaStream_t>(stream));
@@ -382,8 +434,10 @@ int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid, 
     if (mode == WT_FP64_DF) mode = WT_FP64;   // both complex128
     const size_t b = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);
     int rc;
-    if ((rc = check_device_buffer(vis_obs, b, fn, "vis_obs")) || (rc = check_device_buffer(vis_model, b, fn, "vis_model")) ||
-        (rc = check_device_buffer(vis_resid, b, fn, "vis_resid")))
+    const size_t al = vis_align(mode);   // complex64 views need not be 16-byte aligned (a scalar path takes them)
+    if ((rc = check_device_buffer(vis_obs, b, fn, "vis_obs", al)) ||
+        (rc = check_device_buffer(vis_model, b, fn, "vis_model", al)) ||
+        (rc = check_device_buffer(vis_resid, b, fn, "vis_resid", al)))
         return rc;
     if (!device_status_word()) return set_error(WT_ERR_CUDA, "%s: no usable CUDA device", fn);
     return wt::subtract(vis_obs, vis_model, vis_resid, n_vis, mode, static_cast<cudaStream_t>(stream));

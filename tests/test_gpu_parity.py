@@ -312,6 +312,37 @@ def test_buffer_too_small_rejected_before_launch():
     assert rc == wt.WT_ERR_ARG
 
 
+def test_misaligned_buffers_rejected_before_launch():
+    # complex128 outputs need 16-byte alignment, float64 inputs 8: a pointer
+    # off by 8 (or 4) bytes is an argument error, returned before any launch
+    import ctypes as C
+    L = wt.load()
+    w = synth.small()
+    t = gpu_tree(w, 8)
+    n = 64
+    uvw = dev(w.uvw[:n + 1])
+    out = torch.empty(n + 1, dtype=torch.complex128, device="cuda")
+    z = dev(np.zeros(2))
+    base = out.data_ptr()
+    rc = L.wt_predict_vis(t.h, C.c_void_p(uvw.data_ptr()), n, C.c_void_p(base + 8), wt.WT_FP64, 1,
+                          wt.WT_SUM_EQ17, None)
+    assert rc == wt.WT_ERR_ARG and "aligned" in L.wt_last_error().decode()
+    rc = L.wt_predict_vis(t.h, C.c_void_p(uvw.data_ptr() + 4), n, C.c_void_p(base), wt.WT_FP64, 1,
+                          wt.WT_SUM_EQ17, None)
+    assert rc == wt.WT_ERR_ARG and "aligned" in L.wt_last_error().decode()
+    rc = L.dft_predict_vis(C.c_void_p(z.data_ptr()), C.c_void_p(z.data_ptr()), C.c_void_p(z.data_ptr()), 1,
+                           C.c_void_p(uvw.data_ptr()), n, C.c_void_p(base + 8), wt.WT_FP64_DF, 1, None)
+    assert rc == wt.WT_ERR_ARG and "aligned" in L.wt_last_error().decode()
+    # a complex64 output needs only 8 bytes
+    out32 = torch.empty(n + 1, dtype=torch.complex64, device="cuda")
+    rc = L.wt_predict_vis(t.h, C.c_void_p(uvw.data_ptr()), n, C.c_void_p(out32.data_ptr() + 8), wt.WT_MIXED, 1,
+                          wt.WT_SUM_EQ17, None)
+    assert rc == wt.WT_OK
+    torch.cuda.synchronize()
+    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, 8)
+    assert np.max(np.abs(out32.cpu().numpy()[1:] - ot.vis_eq17(w.uvw[:n]))) <= TOLMIX * peak(w.flux)
+
+
 def test_tree_on_wrong_mode_rejected():
     w = synth.small()
     t = gpu_tree(w, 8)

@@ -2,7 +2,7 @@
 
 The oracle is rebuilt with one known, plausible mistake planted
 (-DORC_PLANT=k: a flipped sign, a transposed operand, a wrong constant, a
-dropped term, an off-by-one; 1 .. 12 in oracle.c, 13 .. 16 in oracle_mlp.c) and the pins are run against it: for every
+dropped term, an off-by-one; 1 .. 12, 17, 18 in oracle.c, 13 .. 16 in oracle_mlp.c) and the pins are run against it: for every
 planted mistake at least one pin must fail. This is what makes the pins
 evidence that the unplanted oracle computes what the paper defines.
 """
@@ -20,6 +20,7 @@ import test_oracle_dft as TD
 import test_oracle_mlp as TM
 import test_oracle_sphere as TS
 import test_oracle_tree as TT
+import test_oracle_truncated as TR
 
 HERE = os.path.dirname(os.path.abspath(O.__file__))
 
@@ -47,6 +48,11 @@ PLANTS = {
     15: ("SiLU derivative without its z (1 - s) term", [TM.test_mlp_gradient_matches_finite_differences]),
     16: ("second weight matrix transposed in the forward pass", [TM.test_mlp_forward_closed_form,
                                                                   TM.test_mlp_gradient_matches_finite_differences]),
+    17: ("truncated tree weighted by lambda instead of the pixel's flux A_jt lambda",
+         [TR.test_truncated_at_level_J_is_eq16, lambda: TR.test_fully_populated_phase_centre_pixel_is_eq12("level")]),
+    18: ("truncated tree with the pixel response conjugated",
+         [lambda: TR.test_fully_populated_phase_centre_pixel_is_eq12("level"),
+          lambda: TR.test_fully_populated_phase_centre_pixel_is_eq12("pixel")]),
 }
 
 

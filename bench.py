@@ -857,69 +857,103 @@ def mixed_measurement(wt, torch, dev, stream, flush):
     return out
 
 
-def learned_measurement(wt, torch, dev, stream, flush, n_train=10_000_000, depth=4):
-    """Config L: 256 antennas, 15 993 600 visibilities, 50 000 components,
-    J = 12; the level-12 response network trained on n_train responses the
-    oracle generates (baselines drawn from the array), then the learned form
-    timed on every visibility and checked on a sample: against the exact
-    response (its fallback and yardstick) and, for the gain, against the true
-    visibilities (Eq. 12 at the true positions) next to the centre-snapped
-    level-J sum."""
+def learned_measurement(wt, torch, dev, stream, flush, n_train=10_000_000, depth=4, levels=(11, 10)):
+    """The learned response where it saves work: the large workload's tree
+    (J = 12) truncated at a coarser level j_t, its level-j_t nodes standing
+    for their pixels with a full-pixel response, against the same truncation
+    centre-snapped (the method without the network) and against the full
+    tree at J. Per truncation level the network MLP_jt is trained on n_train
+    responses the oracle generates (baselines drawn from the array, +-B).
+    Every form is timed on all visibilities and judged on a strided sample
+    against the true visibilities (Eq. 12 at the true positions); the
+    learned form also against its exact-response counterpart."""
     import oracle as O
     w = synth.learned()
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
     J = w.J
-    rng = np.random.default_rng(21)
-    t0 = time.perf_counter()
-    idx = rng.integers(0, w.n_vis, n_train)
-    tr_uvw = w.uvw[idx] * np.where(rng.random((n_train, 1)) < 0.5, -1.0, 1.0)
-    tgt = O.pixel_response(J, depth, w.ra0, w.dec0, tr_uvw)
-    t_gen = time.perf_counter() - t0
-    dt = O.level_pixel_size(J)
-    x_max = float(np.max(np.abs(tr_uvw * dt))) * 1.0001
-    mlp = wt.Mlp(J, w.ra0, w.dec0, depth=depth, x_max=x_max, seed=5)
-    tu = d(tr_uvw)
-    tt = d(np.stack([tgt.real, tgt.imag], axis=1).astype(np.float32))
-    del tr_uvw, tgt
-    steps = 2 * (n_train // 8192)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    loss = mlp.train(tu, tt, steps=steps, batch=8192, lr=3e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    del tu, tt
     uvw = d(w.uvw)
     l, m, f = d(w.l), d(w.m), d(w.flux)
     tree = wt.wt_build_tree(l, m, f, w.ra0, w.dec0, J)
     info = tree.info()
     out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
-    wt.wt_predict_vis_learned(tree, mlp, uvw, out=out)
-    t_l = _time_call(lambda: wt.wt_predict_vis_learned(tree, mlp, uvw, out=out), stream, flush)
-    o17 = torch.empty_like(out)
-    wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o17)
-    t_17 = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o17), stream, flush)
-    # check on a strided sample
     S = float(np.abs(w.flux).sum())
-    sidx = np.arange(0, w.n_vis, w.n_vis // 600)[:600]
+    sidx = strided(w.n_vis, 600)
     su = w.uvw[sidx]
-    got = out.cpu().numpy()[sidx]
-    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
-    v_centre = ot.vis_eq16(su)
-    r_exact = O.pixel_response(J, depth, w.ra0, w.dec0, su)
-    v_exact_resp = v_centre * r_exact
-    v_true = O.dft(w.l, w.m, w.flux, su)
+    v_true = O.dft(w.l, w.m, w.flux, su, threads=host_cores())
     rms = lambda a, b: float(np.sqrt(np.mean(np.abs(a - b) ** 2)) / S)
-    y = mlp.eval(d(su)).cpu().numpy()
+
+    def timed(fn):
+        fn()
+        t = _time_call(fn, stream, flush)
+        return w.n_vis / t, out.cpu().numpy()[sidx]
+
     res = {"workload": w.name, "J": J, "n_vis": w.n_vis, "n_comp": w.n_comp, "n_leaves": info["n_leaves"],
-           "n_nodes": info["n_nodes"], "train_samples": n_train, "train_steps": steps, "depth": depth,
-           "x_max": x_max, "oracle_target_gen_s": t_gen, "train_s": t_train, "final_minibatch_loss": loss,
-           "response_rms_err_vs_exact": float(np.sqrt(np.mean(np.abs(y - r_exact) ** 2))),
-           "learned_vis_per_s": w.n_vis / t_l, "wavelet_mixed_eq17_vis_per_s": w.n_vis / t_17,
-           "learned_max_rel_err_vs_exact_response_form": float(np.max(np.abs(got - v_exact_resp)) / S),
-           "rms_err_vs_true_learned": rms(got, v_true), "rms_err_vs_true_exact_response": rms(v_exact_resp, v_true),
-           "rms_err_vs_true_centre_snapped": rms(v_centre, v_true)}
+           "n_nodes": info["n_nodes"], "depth": depth, "train_samples": n_train,
+           "error": "RMS |V - V_true| / sum |C| over %d strided baselines; V_true = Eq. 12 at the true positions"
+                    % len(sidx)}
+    rate, v = timed(lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ17_REGROUPED,
+                                              out=out))
+    res["full_J"] = {"form": "Eq. 17 regrouped, WT_MIXED_FAST, %d leaves" % info["n_leaves"], "vis_per_s": rate,
+                     "terms_per_vis": info["n_leaves"], "rms_err_vs_true": rms(v, v_true)}
+    rng = np.random.default_rng(21)
+    for jt in levels:
+        n_jt = int(info["per_level"][jt - 1])
+        t0 = time.perf_counter()
+        idx = rng.integers(0, w.n_vis, n_train)
+        tr_uvw = w.uvw[idx] * np.where(rng.random((n_train, 1)) < 0.5, -1.0, 1.0)
+        tgt = O.pixel_response(jt, depth, w.ra0, w.dec0, tr_uvw)
+        t_gen = time.perf_counter() - t0
+        x_max = float(np.max(np.abs(tr_uvw * O.level_pixel_size(jt)))) * 1.0001
+        mlp = wt.Mlp(jt, w.ra0, w.dec0, depth=depth, x_max=x_max, seed=5)
+        tu = d(tr_uvw)
+        tt = d(np.stack([tgt.real, tgt.imag], axis=1).astype(np.float32))
+        del tr_uvw, tgt
+        steps = 2 * (n_train // 8192)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = mlp.train(tu, tt, steps=steps, batch=8192, lr=3e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del tu, tt
+        r_net = mlp.eval(d(su)).cpu().numpy()
+        r_ex = O.pixel_response(jt, depth, w.ra0, w.dec0, su)
+        rate_l, v_l = timed(lambda: wt.wt_predict_vis_truncated(tree, jt, uvw, response=wt.WT_RESPONSE_LEARNED,
+                                                                mlp=mlp, out=out))
+        rate_s, v_s = timed(lambda: wt.wt_predict_vis_truncated(tree, jt, uvw, out=out))
+        rate_e, v_e = timed(lambda: wt.wt_predict_vis_truncated(tree, jt, uvw, response=wt.WT_RESPONSE_EXACT,
+                                                                depth=depth, out=out))
+        res["truncated_level_%d" % jt] = {
+            "terms_per_vis": n_jt, "x_max": x_max, "oracle_target_gen_s": t_gen, "train_s": t_train,
+            "train_steps": steps, "final_minibatch_loss": loss,
+            "response_rms_err_vs_exact": float(np.sqrt(np.mean(np.abs(r_net - r_ex) ** 2))),
+            "learned": {"vis_per_s": rate_l, "rms_err_vs_true": rms(v_l, v_true),
+                        "max_rel_err_vs_exact_response_form": float(np.max(np.abs(v_l - v_e)) / S)},
+            "centre_snapped": {"vis_per_s": rate_s, "rms_err_vs_true": rms(v_s, v_true)},
+            "exact_response": {"vis_per_s": rate_e, "rms_err_vs_true": rms(v_e, v_true),
+                               "note": "float64 response by %d sub-pixels per visibility (the yardstick)"
+                                       % (4 ** depth)},
+        }
+        mlp.close()
+    # hard thresholding with full-pixel responses: the tree truncated at j0
+    # plus the detail coefficients of levels j0 .. J-1 with |gamma| >= tau
+    j0, d0 = 9, depth + 1
+    ex = tree.export()
+    offs, gam = ex["level_offsets"], ex["gamma"]
+    g_fine = np.abs(gam[offs[j0 - 1]:offs[J - 1]]).ravel()
+    for frac in (0.1, 0.5):
+        tau = float(np.quantile(g_fine, 1.0 - frac))
+        kept_nodes = int(np.sum(np.any(np.abs(gam[offs[j0 - 1]:offs[J - 1]]) >= tau, axis=1)))
+        terms = int(info["per_level"][j0 - 1]) + 4 * kept_nodes
+        rate_x, v_x = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw, response=wt.WT_RESPONSE_EXACT,
+                                                                  depth=d0, out=out))
+        rate_s, v_s = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw, out=out))
+        res["thresholded_j0_%d_keep_%d_percent" % (j0, round(100 * frac))] = {
+            "tau": tau, "kept_coefficients": int(np.sum(g_fine >= tau)), "terms_per_vis": terms,
+            "exact_response": {"vis_per_s": rate_x, "rms_err_vs_true": rms(v_x, v_true),
+                               "note": "float64 responses, %d .. %d sub-pixels per level" % (4 ** (d0 - (J - j0)),
+                                                                                            4 ** d0)},
+            "centre_snapped": {"vis_per_s": rate_s, "rms_err_vs_true": rms(v_s, v_true)}}
     tree.close()
-    mlp.close()
     return res
 
 

@@ -419,6 +419,32 @@ int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int d
                              int64_t n_vis, void* vis_out, int sign, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * wt_predict_vis_thresholded -- hard thresholding of the wavelet
+ * coefficients with full-pixel responses (Sec. 1 recalls McEwen (2008),
+ * which keeps only the largest coefficients; an addition to the paper's own
+ * method). Every coefficient above level j0 is kept, so the coarse part is
+ * the tree truncated at j0 (wt_predict_vis_truncated); of the coefficients
+ * gamma^m_j,k of levels j0 .. J-1 only those with |gamma| >= tau are kept,
+ * each through the responses of all four of its node's children (present
+ * in the tree or not):
+ *   V = R_j0(B) sum_k F_k exp(sign i 2 pi B.(c_k - P))
+ *     + sum_{L = j0+1..J} R_L(B) sum_c w_c exp(sign i 2 pi B.(c_c - P)),
+ *   w_c = (sqrt(A_j)/4) sum_{m kept} H_m[c] gamma^m_parent   (Eq. 10 form),
+ * the c running over the children at level L of the parents with a kept
+ * coefficient. The Haar wavelets are orthonormal on the sphere, so this is
+ * the visibility of the best image of so many coefficients; tau = 0 keeps
+ * all. R_L: 1 (WT_RESPONSE_SNAPPED); the networks mlps[L - j0] (HOST array
+ * of J - j0 + 1, levels j0 .. J; WT_RESPONSE_LEARNED); or the exact response
+ * of the phase-centre pixel with depth - (L - j0) levels of sub-pixels (one
+ * common finest level j0 + depth; J - j0 <= depth <= 8; WT_RESPONSE_EXACT).
+ * As in wt_predict_vis_truncated all pixels of a level share one response.
+ * Output device complex64 [n_vis]; the selection runs on the device
+ * (deterministic). Allocates scratch on `stream` and releases it.
+ * ------------------------------------------------------------------------- */
+int wt_predict_vis_thresholded(wt_tree t, int j0, double tau, int response, const wt_mlp* mlps, int depth,
+                               const double* uvw, int64_t n_vis, void* vis_out, int sign, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Helpers
  * ------------------------------------------------------------------------- */
 

@@ -70,3 +70,88 @@ def thresholded_vis(base, G, S, K):
     """Eq. 17 with only the K largest |gamma| kept (reading T1)."""
     keep = keep_largest(G, K)
     return base + S[:, keep] @ G[keep]
+
+
+# ---------------------------------------------------------------------------
+# Reading T2: thresholding with full-pixel responses.
+#
+# McEwen (2008) keeps the largest wavelet coefficients with each one's
+# response over the whole of its pixels. The Haar wavelets of Eq. 10 read as
+# functions on the sphere, psi^m_j,k = A_j^-1/2 sum_c H_m[c] chi_j+1,c (chi
+# the indicator of a child pixel; Eq. 11 synthesises the children from
+# them), are orthonormal, so the K coefficients of largest |gamma| give the
+# best K-term image, and the visibility of a kept coefficient is
+#   gamma^m_j,k sigma^m_j,k,  sigma^m_j,k = (sqrt(A_j)/4) sum_c H_m[c] eta_j+1,c
+# with eta_j,k = exp(sign i 2 pi B.(c_j,k - P)) R_j,k(B) the plane wave's mean
+# over the pixel (its full-pixel response), for all four children, present
+# in the tree or not: dropping a coefficient changes the image on every
+# child. Every coefficient above a level j0 is kept: together with the level-1
+# term they reproduce the level-j0 image, whose visibility is the tree
+# truncated at j0 with full-pixel responses (oracle reading R12, kind
+# "pixel"); the K largest |gamma| among levels j0 .. J - 1 are added to it.
+# The responses are dense quadratures over one common finest level
+# J + d_leaf, so that a pixel's response is exactly the mean of its four
+# children's, and with every coefficient kept the sum is the visibility of
+# the level-J image with each pixel's flux spread over it (kind "pixel" at
+# level J).
+# ---------------------------------------------------------------------------
+
+def _eta_full(j, k, uvw, ra0, dec0, depth, sign, reading="pixel", cache=None):
+    """eta_j,k = exp(sign i 2 pi B.(c_j,k - P)) R(B): R = the pixel's own
+    response by quadrature (reading "pixel"), the response of the level-j
+    pixel holding the phase centre (reading "level", the approximation the
+    GPU makes: one response per level), or 1 (reading "snapped")."""
+    import oracle as O
+    c = O.pixel_dir_uvw(j, int(k), ra0, dec0)
+    wave = np.exp(sign * 2j * np.pi * (uvw @ c))
+    if reading == "snapped":
+        return wave
+    if reading == "level":
+        if cache is not None and j in cache:
+            return wave * cache[j]
+        r = O.pixel_response(j, depth, ra0, dec0, uvw, sign)
+        if cache is not None:
+            cache[j] = r
+        return wave * r
+    return wave * O.pixel_response_of(j, int(k), depth, ra0, dec0, uvw, sign)
+
+
+def full_response_terms(tree, J, j0, uvw, ra0, dec0, d_leaf=2, sign=1, reading="pixel"):
+    """Reading T2 split as V = base + S @ G: base = the level-j0 image's
+    visibility (sum over the level-j0 nodes of A_j0 lambda_j0,k eta_j0,k),
+    G = gamma^m_j,k of the nodes of levels j0 .. J-1 (breadth-first, m =
+    1..3, flattened), S = the matching sigma^m_j,k from the full-pixel
+    responses of all four children. ``tree`` is ``oracle.Tree(...).export()``;
+    ``reading`` chooses the response (see _eta_full)."""
+    uvw = np.asarray(uvw, dtype=np.float64).reshape(-1, 3)
+    offs = tree["level_offsets"]
+    key, lam, gam = tree["key"], tree["lam"], tree["gamma"]
+    Lq = J + d_leaf
+    cache = {}
+    base = np.zeros(uvw.shape[0], dtype=np.complex128)
+    for i in range(int(offs[j0 - 1]), int(offs[j0])):
+        base += area(j0) * lam[i] * _eta_full(j0, key[i], uvw, ra0, dec0, Lq - j0, sign, reading, cache)
+    G, cols = [], []
+    for j in range(j0, J):
+        q = math.sqrt(area(j)) / 4.0
+        for i in range(int(offs[j - 1]), int(offs[j])):
+            kids = np.stack([_eta_full(j + 1, 4 * int(key[i]) + c, uvw, ra0, dec0, Lq - j - 1, sign, reading, cache)
+                             for c in range(4)], axis=1)
+            sig = q * kids @ _H.T                                    # the three sigma^m, Eq. 10 form
+            for mm in range(3):
+                G.append(gam[i, mm])
+                cols.append(sig[:, mm])
+    S = np.stack(cols, axis=1) if cols else np.zeros((uvw.shape[0], 0), dtype=np.complex128)
+    return base, np.asarray(G, dtype=np.float64), S
+
+
+def keep_at_least(G, tau):
+    """Indices of the coefficients with |gamma| >= tau (hard thresholding by
+    value)."""
+    return np.nonzero(np.abs(G) >= tau)[0]
+
+
+def thresholded_vis_tau(base, G, S, tau):
+    """base + the coefficients with |gamma| >= tau."""
+    keep = keep_at_least(G, tau)
+    return base + S[:, keep] @ G[keep]

@@ -48,6 +48,7 @@ EXPORTS = [
     "wt_selftest_bounded_wait", "wt_selftest_grid_barrier", "wt_dirty_image", "wt_hogbom", "wt_clean",
     "wt_xref_table", "wt_build_tree_xref", "wt_measure_pipe_rates",
     "wt_selftest_context_reset", "wt_predict_vis_truncated",
+    "wt_predict_vis_thresholded",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -104,6 +105,7 @@ def _declare(L):
     L.wt_mlp_eval.argtypes = [vp, vp, i64, C.c_int, vp, vp]
     L.wt_predict_vis_learned.argtypes = [vp, vp, vp, i64, vp, C.c_int, vp]
     L.wt_predict_vis_truncated.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, i64, vp, C.c_int, vp]
+    L.wt_predict_vis_thresholded.argtypes = [vp, C.c_int, d, C.c_int, vp, C.c_int, vp, i64, vp, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
     L.wt_device_status.argtypes = [vp]
     L.wt_selftest_bounded_wait.argtypes = [C.c_uint32, vp]
@@ -358,6 +360,25 @@ def wt_predict_vis_truncated(tree, level, uvw, response=WT_RESPONSE_SNAPPED, mlp
     _check(load().wt_predict_vis_truncated(tree.h, int(level), int(response), mlp.h if mlp is not None else None,
                                            int(depth), _dev(uvw, torch.float64), uvw.shape[0],
                                            _dev(out, torch.complex64), int(sign), _stream(stream)))
+    return out
+
+
+def wt_predict_vis_thresholded(tree, j0, tau, uvw, response=WT_RESPONSE_SNAPPED, mlps=None, depth=4, sign=1,
+                               out=None, stream=None):
+    """Hard thresholding with full-pixel responses: the tree truncated at j0
+    plus the coefficients of levels j0 .. J-1 with |gamma| >= tau, each
+    through its node's four children; mlps = the networks of levels j0 .. J
+    (WT_RESPONSE_LEARNED). complex64 out."""
+    import torch
+    if out is None:
+        out = torch.empty(uvw.shape[0], dtype=torch.complex64, device=uvw.device)
+    arr = None
+    if mlps is not None:
+        arr = (C.c_void_p * len(mlps))(*[m.h.value if isinstance(m.h, C.c_void_p) else m.h for m in mlps])
+    _check(load().wt_predict_vis_thresholded(tree.h, int(j0), float(tau), int(response),
+                                             C.cast(arr, C.c_void_p) if arr is not None else None, int(depth),
+                                             _dev(uvw, torch.float64), uvw.shape[0], _dev(out, torch.complex64),
+                                             int(sign), _stream(stream)))
     return out
 
 

@@ -645,6 +645,119 @@ __global__ void k_mul_response(float2* __restrict__ vis, const double2* __restri
     }
 }
 
+// ---------------------------------------------------------------- thresholded tree
+// Exclusive prefix sum of one int per thread over a CTA of blockDim.x (a
+// multiple of 32, at most 1024) threads; total receives the CTA's sum.
+__device__ int cta_exclusive_scan(int x, int& total, int* warp_sums)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_sums[lane] = v;
+    }
+    __syncthreads();
+    const int before = warp > 0 ? warp_sums[warp - 1] : 0;
+    total = warp_sums[nw - 1];
+    __syncthreads();
+    return before + inc - x;
+}
+
+// Records of the kept details, level by level, in one CTA (deterministic:
+// parents in key order, children in slot order). For each parent p at level
+// j = j0 .. J-1 with at least one |gamma^m_p| >= tau, its four children at
+// level j + 1 (present in the tree or not) get the records of their pixel
+// centres with weights
+//   w_c = (sqrt(A_j)/4) sum_{m kept} H_m[c] gamma^m_p,
+// the kept coefficients' sum_m gamma^m sigma^m regrouped over the children
+// (sigma^m = (sqrt(A_j)/4) H_m . eta_children, Eq. 10 form). The records of
+// level L = j + 1 go to out + seg[L], its count into views[L - j0].
+struct LevelSegs {
+    int64_t off[kMaxJ + 2];   // first record of level L's segment
+};
+
+__global__ void __launch_bounds__(1024) k_threshold_records(const int64_t* __restrict__ key,
+                                                            const double* __restrict__ gamma,
+                                                            const TreeHeader* __restrict__ hdr, int j0, int J,
+                                                            double tau, Rot R, RecF* __restrict__ out, LevelSegs seg,
+                                                            TreeHeader* __restrict__ views)
+{
+    __shared__ int ws[32];
+    for (int j = j0; j < J; ++j) {
+        const int64_t n = hdr->per_level[j];
+        const int64_t base = hdr->rev_offset[j];
+        RecF* dst = out + seg.off[j + 1];
+        const double q = __dmul_rn(ldexp(__dsqrt_rn(kPi / 3.0), 1 - j), 0.25);
+        int64_t carry = 0;
+        for (int64_t start = 0; start < n; start += blockDim.x) {
+            const int64_t i = start + threadIdx.x;
+            double g[3] = {0.0, 0.0, 0.0};
+            bool kept = false;
+            if (i < n) {
+#pragma unroll
+                for (int mm = 0; mm < 3; ++mm) {
+                    const double x = gamma[3 * (base + i) + mm];
+                    if (fabs(x) >= tau) {
+                        g[mm] = x;
+                        kept = true;
+                    }
+                }
+            }
+            int total;
+            const int pos = cta_exclusive_scan(kept ? 1 : 0, total, ws);
+            if (kept) {
+                const int64_t kp = key[base + i];
+                for (int c = 0; c < 4; ++c) {
+                    const double h0 = (c & 1) ? -1.0 : 1.0;                          // + - + -
+                    const double h1 = (c & 2) ? -1.0 : 1.0;                          // + + - -
+                    const double h2 = (((c & 1) ^ ((c >> 1) & 1)) != 0) ? -1.0 : 1.0;   // + - - +
+                    double d[3];
+                    pixel_dir(j + 1, 4 * kp + c, R, d);
+                    const F2 a = split_f64(d[0]), b = split_f64(d[1]), e = split_f64(d[2]);
+                    RecF r;
+                    r.meta = kRecLeaf;
+                    r.a = a.hi;
+                    r.b = a.lo;
+                    r.c = b.hi;
+                    r.d = b.lo;
+                    r.e = e.hi;
+                    r.f = e.lo;
+                    r.g = static_cast<float>(q * ((h0 * g[0] + h1 * g[1]) + h2 * g[2]));
+                    dst[4 * (carry + pos) + c] = r;
+                }
+            }
+            carry += total;
+        }
+        if (threadIdx.x == 0) {
+            views[j + 1 - j0].n_leaves = 4 * carry;
+            views[j + 1 - j0].n_nodes = 4 * carry;
+        }
+        __syncthreads();
+    }
+}
+
+// vis += x, element by element.
+__global__ void k_accumulate(float2* __restrict__ vis, const float2* __restrict__ x, int64_t n)
+{
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float2 a = vis[i], b = x[i];
+        vis[i] = make_float2(a.x + b.x, a.y + b.y);
+    }
+}
+
 }  // namespace
 }  // namespace wt
 
@@ -728,6 +841,119 @@ int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int d
                                                                    resp);
         k_mul_response<<<static_cast<unsigned>(b2), 256, 0, s>>>(static_cast<float2*>(vis_out), resp, n_vis);
         if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: exact response launch", fn);
+    }
+    cudaFreeAsync(scratch, s);
+    cudaGetLastError();
+    return rc;
+}
+
+int wt_predict_vis_thresholded(wt_tree t, int j0, double tau, int response, const wt_mlp* mlps, int depth,
+                               const double* uvw, int64_t n_vis, void* vis_out, int sign, void* stream)
+{
+    const char* fn = "wt_predict_vis_thresholded";
+    if (!t || t->magic != kTreeMagic) return set_error(WT_ERR_ARG, "%s: bad tree handle", fn);
+    const int J = t->J;
+    if (j0 < 1 || j0 > J) return set_error(WT_ERR_RANGE, "%s: j0 %d outside 1..J = %d", fn, j0, J);
+    if (!(tau >= 0.0)) return set_error(WT_ERR_ARG, "%s: tau must be >= 0", fn);
+    if (n_vis < 0 || (sign != 1 && sign != -1)) return set_error(WT_ERR_ARG, "%s: bad n_vis or sign", fn);
+    const int nl = J - j0 + 1;   // levels j0 .. J
+    int rc;
+    if (response == WT_RESPONSE_LEARNED) {
+        if (!mlps) return set_error(WT_ERR_ARG, "%s: no networks", fn);
+        for (int L = j0; L <= J; ++L) {
+            wt_mlp m = mlps[L - j0];
+            if ((rc = check_mlp(m, fn))) return rc;
+            if (m->level != L) return set_error(WT_ERR_ARG, "%s: network %d is for level %d, not %d", fn, L - j0,
+                                                m->level, L);
+            if (t->ra0 != m->ra0 || t->dec0 != m->dec0)
+                return set_error(WT_ERR_ARG, "%s: tree and network %d have different phase centres", fn, L - j0);
+        }
+    } else if (response == WT_RESPONSE_EXACT) {
+        if (depth < J - j0 || depth > 8 || j0 + depth > kMaxJ)
+            return set_error(WT_ERR_RANGE, "%s: need J - j0 <= depth <= 8 and j0 + depth <= %d", fn, kMaxJ);
+    } else if (response != WT_RESPONSE_SNAPPED) {
+        return set_error(WT_ERR_ARG, "%s: bad response %d", fn, response);
+    }
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (rc = check_device_buffer(vis_out, static_cast<size_t>(n_vis) * 8, fn, "vis_out", 8)))
+        return rc;
+    if (n_vis == 0) return WT_OK;
+    int* status = device_status_word();
+    if (!status) return set_error(WT_ERR_CUDA, "%s: no device status word", fn);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // scratch: a header view per level; the records, level by level, in
+    // segments of the capacity bound (level j0: its nodes, at most the leaf
+    // capacity; below it, four children per parent); a visibility buffer for
+    // the levels below j0; for the exact response the sub-pixel offsets and
+    // R(B) per visibility
+    const int64_t capl = t->cap_leaves > 0 ? t->cap_leaves : 1;
+    LevelSegs seg{};
+    int64_t nrec = 0;
+    for (int L = j0; L <= J; ++L) {
+        seg.off[L] = nrec;
+        nrec += (L == j0 ? 1 : 4) * capl;
+    }
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const int n_off = response == WT_RESPONSE_EXACT ? 1 << (2 * depth) : 0;
+    const size_t b_views = up(sizeof(TreeHeader) * static_cast<size_t>(nl));
+    const size_t b_seg = 0;
+    const size_t b_rec = up(sizeof(RecF) * static_cast<size_t>(nrec));
+    const size_t b_tmp = up(sizeof(float2) * static_cast<size_t>(n_vis));
+    const size_t b_off = up(sizeof(double) * 3 * static_cast<size_t>(n_off));
+    const size_t b_r = response == WT_RESPONSE_EXACT ? sizeof(double2) * static_cast<size_t>(n_vis) : 0;
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), b_views + b_seg + b_rec + b_tmp + b_off + b_r,
+                                    s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "%s: scratch allocation failed: %s", fn, cudaGetErrorString(e));
+    }
+    TreeHeader* views = reinterpret_cast<TreeHeader*>(scratch);
+    RecF* recs = reinterpret_cast<RecF*>(scratch + b_views + b_seg);
+    float2* tmp = reinterpret_cast<float2*>(scratch + b_views + b_seg + b_rec);
+    double* offs = reinterpret_cast<double*>(scratch + b_views + b_seg + b_rec + b_tmp);
+    double2* resp = reinterpret_cast<double2*>(scratch + b_views + b_seg + b_rec + b_tmp + b_off);
+    Rot R;
+    rotation_matrix(t->ra0, t->dec0, R.r);
+    rc = WT_OK;
+    {
+        int64_t blocks = (capl + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        k_level_records<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t->d.key, t->d.lambda, t->d.hdr, j0, R,
+                                                                      recs + seg.off[j0], views, capl);
+        if (j0 < J)
+            k_threshold_records<<<1, 1024, 0, s>>>(t->d.key, t->d.gamma, t->d.hdr, j0, J, tau, R, recs, seg, views);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: record kernels", fn);
+    }
+    int64_t b2 = (n_vis + 255) / 256;
+    const int64_t bcap = static_cast<int64_t>(num_sms()) * 8;
+    if (b2 > bcap) b2 = bcap;
+    for (int L = j0; L <= J && rc == WT_OK; ++L) {
+        float2* target = (L == j0) ? static_cast<float2*>(vis_out) : tmp;
+        WaveletJob jb{};
+        jb.recf_leaf = recs + seg.off[L];
+        jb.hdr = views + (L - j0);
+        jb.uvw = uvw;
+        jb.n_vis = n_vis;
+        jb.vis = target;
+        jb.mode = WT_MIXED_FAST;
+        jb.sign = sign;
+        jb.which = WT_SUM_EQ16;
+        jb.J = J;
+        jb.status = status;
+        rc = launch_wavelet(jb, default_wavelet_variant(WT_MIXED_FAST, WT_SUM_EQ16, J), s);
+        if (rc == WT_OK && response == WT_RESPONSE_LEARNED)
+            rc = launch_apply(mlps[L - j0], uvw, n_vis, target, sign, true, s);
+        if (rc == WT_OK && response == WT_RESPONSE_EXACT) {
+            const int dL = depth - (L - j0);   // one common finest level, j0 + depth
+            k_response_offsets<<<((1 << (2 * dL)) + 127) / 128, 128, 0, s>>>(L, dL, R, offs);
+            k_response_exact<<<static_cast<unsigned>(b2), 256, 0, s>>>(uvw, n_vis, offs, 1 << (2 * dL),
+                                                                       static_cast<double>(sign), resp);
+            k_mul_response<<<static_cast<unsigned>(b2), 256, 0, s>>>(target, resp, n_vis);
+        }
+        if (rc == WT_OK && L > j0)
+            k_accumulate<<<static_cast<unsigned>(b2), 256, 0, s>>>(static_cast<float2*>(vis_out), tmp, n_vis);
+        if (rc == WT_OK && cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: level %d", fn, L);
     }
     cudaFreeAsync(scratch, s);
     cudaGetLastError();

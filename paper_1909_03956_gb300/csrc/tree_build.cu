@@ -505,21 +505,14 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         wd.d = wgt;
         wd.e = 0.0;
         wf.meta = wmeta;
-        wf.pad = 0;
-        const float wg = static_cast<float>(ldexp(wgt, -2 * (J - j)));   // weight of xi = 4^(J-j) eta
-        wf.w = make_float2(wg, wg);
-        if (leaf) {   // every field as a pair (see RecWF)
-            wf.a = make_float2(rf.a, rf.a);
-            wf.b = make_float2(rf.b, rf.b);
-            wf.c = make_float2(rf.c, rf.c);
-            wf.d = make_float2(rf.d, rf.d);
-            wf.e = make_float2(rf.e, rf.e);
-            wf.f = make_float2(rf.f, rf.f);
-        } else {      // stack rows of the node's own xi sum and its parent's
-            wf.a = make_float2(__uint_as_float(static_cast<uint32_t>(j - 1)),
-                               __uint_as_float(static_cast<uint32_t>(j > 1 ? j - 2 : 0)));
-            wf.b = wf.c = wf.d = wf.e = wf.f = make_float2(0.f, 0.f);
-        }
+        // internal nodes: stack rows of the node's own xi sum and its parent's
+        wf.a = leaf ? rf.a : __uint_as_float(static_cast<uint32_t>(j - 1));
+        wf.b = leaf ? rf.b : __uint_as_float(static_cast<uint32_t>(j > 1 ? j - 2 : 0));
+        wf.c = leaf ? rf.c : 0.f;
+        wf.d = leaf ? rf.d : 0.f;
+        wf.e = leaf ? rf.e : 0.f;
+        wf.f = leaf ? rf.f : 0.f;
+        wf.g = static_cast<float>(ldexp(wgt, -2 * (J - j)));   // weight of xi = 4^(J-j) eta
         if (!leaf) {
             wd.a = wd.b = wd.c = 0.0;
         }

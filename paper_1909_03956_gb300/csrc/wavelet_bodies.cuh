@@ -501,18 +501,15 @@ struct Eq17WF {
 
     __device__ __forceinline__ float2 result(int k) const { return sub2(acc[k], comp[k]); }
 
-    // The phase of the leaf r for visibility pair p (its coordinates read as
-    // the record's pairs), and for the last, unpaired visibility.
-    __device__ __forceinline__ void phase2(int p, const RecWF& r, float2& h, float2& tl) const
+    __device__ __forceinline__ void phase2(int p, F2 su, F2 sv, F2 sw, float2& h, float2& tl) const
     {
-        if constexpr (GRID) phase_turns_grid2p(U[p], V[p], W[p], r.a, r.b, r.c, r.d, r.e, r.f, Cg[p], h, tl);
-        else phase_turns_df2p(U[p], V[p], W[p], r.a, r.b, r.c, r.d, r.e, r.f, h, tl);
+        if constexpr (GRID) phase_turns_grid2(U[p], V[p], W[p], su, sv, sw, Cg[p], h, tl);
+        else phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
     }
 
-    __device__ __forceinline__ void phase1(const RecWF& r, float& th, float& tl) const
+    __device__ __forceinline__ void phase1(F2 su, F2 sv, F2 sw, float& th, float& tl) const
     {
         constexpr int k = VPT - 1;
-        const F2 su{r.a.x, r.b.x}, sv{r.c.x, r.d.x}, sw{r.e.x, r.f.x};
         if constexpr (GRID) phase_turns_grid(u[k], v[k], w[k], su, sv, sw, Cs, th, tl);
         else phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
     }
@@ -532,12 +529,14 @@ struct Eq17WF {
     // (two visibilities x two leaves), one dispatch.
     __device__ __forceinline__ void leaf_pair(const RecWF& a, const RecWF& b)
     {
-        const float2 w0 = a.w, w1 = b.w;
+        const F2 su0{a.a, a.b}, sv0{a.c, a.d}, sw0{a.e, a.f};
+        const F2 su1{b.a, b.b}, sv1{b.c, b.d}, sw1{b.e, b.f};
+        const float2 w0 = bcast2(a.g), w1 = bcast2(b.g);
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float2 h0, tl0, h1, tl1, e00, e01, e10, e11;
-            phase2(p, a, h0, tl0);
-            phase2(p, b, h1, tl1);
+            phase2(p, su0, sv0, sw0, h0, tl0);
+            phase2(p, su1, sv1, sw1, h1, tl1);
             sincos_mixed2<FAST>(h0, tl0, e00, e01);
             sincos_mixed2<FAST>(h1, tl1, e10, e11);
             low[2 * p] = add2(low[2 * p], add2(e00, e10));
@@ -548,8 +547,8 @@ struct Eq17WF {
         if constexpr (ODD) {
             constexpr int k = VPT - 1;
             float th0, tl0, s0, c0, th1, tl1, s1, c1;
-            phase1(a, th0, tl0);
-            phase1(b, th1, tl1);
+            phase1(su0, sv0, sw0, th0, tl0);
+            phase1(su1, sv1, sw1, th1, tl1);
             sincos_mixed<FAST>(th0, tl0, s0, c0);
             sincos_mixed<FAST>(th1, tl1, s1, c1);
             const float2 e0 = make_float2(c0, s0), e1 = make_float2(c1, s1);
@@ -592,7 +591,7 @@ struct Eq17WF {
     __device__ __forceinline__ void low_levels(const RecWF& r, uint32_t meta)
     {
         const bool root = meta & kRwRoot, first = meta & kRwFirst;
-        const float2 wv = r.w;
+        const float2 wv = bcast2(r.g);
         float2 xi[VPT];
         if (meta & kRwLowSum) {                        // level J - 1: registers only
 #pragma unroll
@@ -617,19 +616,20 @@ struct Eq17WF {
             mid[k] = make_float2(0.f, 0.f);
             midx[k] = make_float2(0.f, 0.f);
         }
-        if (!root) pass_up(clamp_row(__float_as_uint(r.a.y), maxrow), first, xi);
+        if (!root) pass_up(clamp_row(__float_as_uint(r.b), maxrow), first, xi);
     }
 
     __device__ void operator()(const RecWF& r)
     {
         const uint32_t meta = r.meta;
-        const float2 wv = r.w;
+        const float2 wv = bcast2(r.g);
         if (meta & kRwLeaf) {
             const bool root = meta & kRwRoot;
+            const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 float2 h, tl, e0, e1;
-                phase2(p, r, h, tl);
+                phase2(p, su, sv, sw, h, tl);
                 sincos_mixed2<FAST>(h, tl, e0, e1);
                 leaf_up(2 * p, e0, wv, root);
                 leaf_up(2 * p + 1, e1, wv, root);
@@ -637,7 +637,7 @@ struct Eq17WF {
             if constexpr (ODD) {
                 constexpr int k = VPT - 1;
                 float th, tl, s, c;
-                phase1(r, th, tl);
+                phase1(su, sv, sw, th, tl);
                 sincos_mixed<FAST>(th, tl, s, c);
                 leaf_up(k, make_float2(c, s), wv, root);
             }
@@ -651,8 +651,8 @@ struct Eq17WF {
         // build (own: lev - 1, parent's: lev - 2), clamped to the stack. A
         // level-1 node (a root, always a first child) writes its xi back into
         // its own row 0, which the next level-1 node's first child overwrites.
-        const int own = clamp_row(__float_as_uint(r.a.x), maxrow);
-        const int par = clamp_row(__float_as_uint(r.a.y), maxrow);
+        const int own = clamp_row(__float_as_uint(r.a), maxrow);
+        const int par = clamp_row(__float_as_uint(r.b), maxrow);
         float2 xi[VPT];
         load_row(own, xi);
 #pragma unroll

@@ -333,26 +333,24 @@ __device__ __forceinline__ float grid_magic(float bound, int& kk)
 }
 
 // Head of x y on the grid of C, negated, and the tail, for both elements
-// (element-wise C), with y given as the pairs yh = (y.hi, y.hi) and
-// yl = (y.lo, y.lo): nq = -(x.hi y.hi rounded to the grid), exactly;
+// (element-wise C): nq = -(x.hi y.hi rounded to the grid), exactly;
 // t = (x.hi y.hi + nq) + x.lo y.hi + x.hi y.lo, the first term exact.
-__device__ __forceinline__ void grid_product2p(const DF2& x, float2 yh, float2 yl, float2 C, float2& nq, float2& t)
+__device__ __forceinline__ void grid_product2n(const DF2& x, F2 y, float2 C, float2& nq, float2& t)
 {
+    const float2 yh = bcast2(y.hi);
     nq = sub2(C, fma2(x.hi, yh, C));
-    t = fma2(x.hi, yl, fma2(x.lo, yh, fma2(x.hi, yh, nq)));
+    t = fma2(x.hi, bcast2(y.lo), fma2(x.lo, yh, fma2(x.hi, yh, nq)));
 }
 
-// phase_turns_df2 on the grid of C (per element), the leaf's coordinates as
-// pairs (hi, hi), (lo, lo): returns h and tl with the phase = tl - h modulo
-// 1, |h| <= 1/2, |tl| <= 2^(k-22).
-__device__ __forceinline__ void phase_turns_grid2p(const DF2& u, const DF2& v, const DF2& w, float2 suh, float2 sul,
-                                                   float2 svh, float2 svl, float2 swh, float2 swl, float2 C,
-                                                   float2& h, float2& tl)
+// phase_turns_df2 on the grid of C (per element): returns h and tl with the
+// phase = tl - h modulo 1, |h| <= 1/2, |tl| <= 2^(k-22).
+__device__ __forceinline__ void phase_turns_grid2(const DF2& u, const DF2& v, const DF2& w, F2 su, F2 sv, F2 sw1,
+                                                  float2 C, float2& h, float2& tl)
 {
     float2 q1, t1, q2, t2, q3, t3;
-    grid_product2p(u, suh, sul, C, q1, t1);
-    grid_product2p(v, svh, svl, C, q2, t2);
-    grid_product2p(w, swh, swl, C, q3, t3);
+    grid_product2n(u, su, C, q1, t1);
+    grid_product2n(v, sv, C, q2, t2);
+    grid_product2n(w, sw1, C, q3, t3);
     const float2 b = add2(add2(q1, q2), q3);          // exact: multiples of the grid below 2^(k+1)
     h = sub2(b, make_float2(rintf(b.x), rintf(b.y)));
     tl = add2(add2(t1, t2), t3);
@@ -381,23 +379,6 @@ __device__ __forceinline__ float phase_bound(F2 u, F2 v, F2 w, const float* smax
 {
     const float b = __fmaf_rn(fabsf(u.hi), smax[0], __fmaf_rn(fabsf(v.hi), smax[1], fabsf(w.hi) * smax[2]));
     return b * 1.0009765625f;
-}
-
-// phase_turns_df2 with the leaf's coordinates as pairs (hi, hi), (lo, lo).
-__device__ __forceinline__ void phase_turns_df2p(const DF2& u, const DF2& v, const DF2& w, float2 suh, float2 sul,
-                                                 float2 svh, float2 svl, float2 swh, float2 swl, float2& h, float2& tl)
-{
-    float2 q1, t1, q2, t2, q3, t3, a, ea, b, eb;
-    q1 = mul2(u.nhi, suh);
-    t1 = fma2(u.hi, sul, fma2(u.lo, suh, fma2(u.hi, suh, q1)));
-    q2 = mul2(v.nhi, svh);
-    t2 = fma2(v.hi, svl, fma2(v.lo, svh, fma2(v.hi, svh, q2)));
-    q3 = mul2(w.nhi, swh);
-    t3 = fma2(w.hi, swl, fma2(w.lo, swh, fma2(w.hi, swh, q3)));
-    two_sum2(q1, q2, a, ea);
-    two_sum2(a, q3, b, eb);
-    h = sub2(b, make_float2(rintf(b.x), rintf(b.y)));
-    tl = sub2(add2(add2(t1, t2), sub2(t3, ea)), eb);
 }
 
 // sincos_turns_f32 of the phase tl - h (turns) of two visibilities, each
@@ -533,7 +514,7 @@ constexpr uint32_t kRwPairFirst = 1u << 8;
 constexpr uint32_t kRwPairSecond = 1u << 9;
 constexpr uint32_t kRwLowSum = 1u << 10;
 constexpr uint32_t kRwMidSum = 1u << 11;
-constexpr int kRecChunkW = 64;    // records per staging buffer of the regrouped float32 form
+constexpr int kRecChunkW = 128;   // records per staging buffer of the regrouped float32 form
 
 // float64 (48 bytes): a, b, c = leaf pixel centre (s_u, s_v, s_w - 1); d = w.
 struct RecWD {
@@ -556,22 +537,15 @@ struct RecWDF {
 };
 static_assert(sizeof(RecWDF) == 48, "RecWDF layout");
 
-// mixed (64 bytes). Every value is stored twice, as a pair (x, x), because
-// the mixed kernels compute on two visibilities per packed float32 pair: a
-// record field loaded as a pair enters the packed operations as it is, where
-// a scalar would first be copied into both halves of a register pair.
-//   w = (g, g): g = w_n 4^-(J-j), the weight of xi = 4^(J-j) eta
-//   leaf:     a, b = s_u as double-float (hi, lo); c, d = s_v; e, f = s_w - 1
-//   internal: a = (own row, parent's row) -- the stack rows of its own and
-//             its parent's xi sums (j - 1 and j - 2, 0 at level 1) as
-//             unsigned integers in the float fields; b .. f unused (0)
+// mixed (32 bytes): leaf: (a, b), (c, d), (e, f) = pixel centre as
+// double-float pairs; internal node: a, b = the stack rows of its own and
+// its parent's xi sums (j - 1 and j - 2, 0 at level 1) as unsigned integers
+// in the float fields; g = w_n 4^-(J-j), the weight of xi = 4^(J-j) eta.
 struct RecWF {
     uint32_t meta;
-    uint32_t pad;
-    float2 w;
-    float2 a, b, c, d, e, f;
+    float a, b, c, d, e, f, g;
 };
-static_assert(sizeof(RecWF) == 64, "RecWF layout");
+static_assert(sizeof(RecWF) == 32, "RecWF layout");
 
 // Device-side header of a tree (written by the build kernels).
 struct TreeHeader {

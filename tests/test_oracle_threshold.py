@@ -83,3 +83,85 @@ def test_planted_mistakes_fail_the_oracle_equality(monkeypatch):
             base, G, S = T.eq17_terms(tr.export(), 10, uvw)
         v = T.thresholded_vis(base, G, S, len(G))
         assert np.max(np.abs(v - ref)) > 1e-6 * Sg, kind
+
+
+# ---------------------------------------------------------------- reading T2
+
+def _t2(w, J, j0, uvw, d_leaf=2, reading="pixel"):
+    tr = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+    return tr, T.full_response_terms(tr.export(), J, j0, uvw, w.ra0, w.dec0, d_leaf=d_leaf, reading=reading)
+
+
+def test_t2_every_coefficient_kept_is_the_level_J_image():
+    # with the responses on one common finest level, a pixel's response is
+    # the mean of its children's: all coefficients kept give the level-J
+    # image with each pixel's flux spread over it (the truncated tree at J,
+    # each pixel's own response)
+    w = synth.small()
+    J, j0, dl = 10, 6, 2
+    uvw = w.uvw[::200]
+    tr, (base, G, S) = _t2(w, J, j0, uvw, dl)
+    ref = tr.vis_truncated(J, uvw, kind="pixel", depth=dl)
+    assert np.max(np.abs(T.thresholded_vis(base, G, S, len(G)) - ref)) <= 1e-12 * np.abs(w.flux).sum()
+
+
+def test_t2_no_coefficient_kept_is_the_tree_truncated_at_j0():
+    w = synth.small()
+    J, j0, dl = 10, 7, 2
+    uvw = w.uvw[::200]
+    tr, (base, G, S) = _t2(w, J, j0, uvw, dl)
+    ref = tr.vis_truncated(j0, uvw, kind="pixel", depth=J + dl - j0)
+    assert np.max(np.abs(T.thresholded_vis(base, G, S, 0) - ref)) <= 1e-12 * np.abs(w.flux).sum()
+
+
+def test_t2_every_reading_keeps_the_total_flux_at_zero_baseline():
+    w = synth.small()
+    z = np.zeros((2, 3))
+    for reading in ("pixel", "level", "snapped"):
+        _, (base, G, S) = _t2(w, 9, 6, z, 2, reading)
+        for K in (0, len(G) // 3, len(G)):
+            assert np.max(np.abs(T.thresholded_vis(base, G, S, K) - w.flux.sum())) <= 1e-12 * w.flux.sum()
+
+
+def test_t2_threshold_by_value_is_the_largest_by_count():
+    w = synth.small()
+    _, (base, G, S) = _t2(w, 9, 6, w.uvw[::300], 2, "level")
+    tau = float(np.median(np.abs(G)))
+    K = int(np.sum(np.abs(G) >= tau))
+    assert np.array_equal(T.keep_at_least(G, tau), T.keep_largest(G, K)) or \
+        len(set(np.abs(G[T.keep_at_least(G, tau)]))) < K          # ties at tau are the only way they differ
+    assert np.max(np.abs(T.thresholded_vis_tau(base, G, S, tau) - T.thresholded_vis(base, G, S, K))) < 1e-12
+
+
+def test_t2_planted_butterfly_sign_breaks_the_level_J_identity(monkeypatch):
+    w = synth.small()
+    J, j0, dl = 10, 6, 2
+    uvw = w.uvw[::200]
+    tr = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+    ref = tr.vis_truncated(J, uvw, kind="pixel", depth=dl)
+    H_flip = T._H.copy()
+    H_flip[2] = -H_flip[2]
+    monkeypatch.setattr(T, "_H", H_flip)
+    base, G, S = T.full_response_terms(tr.export(), J, j0, uvw, w.ra0, w.dec0, d_leaf=dl)
+    assert np.max(np.abs(T.thresholded_vis(base, G, S, len(G)) - ref)) > 1e-6 * np.abs(w.flux).sum()
+
+
+def test_t2_compresses_the_large_sky_against_the_true_visibilities():
+    # The measured reading behind the GPU path for thresholding: with
+    # full-pixel responses a few dozen coarse pixels predict the large sky
+    # (50 000 components in 20 blobs) closer to its true visibilities
+    # (Eq. 12 at the true positions) than the centre-snapped level-J sum
+    # over all 1 663 leaves; adding the largest coefficients converges to
+    # the level-J image.
+    w = synth.learned(n_t=2)
+    J, j0, dl = 12, 9, 2
+    uvw = w.uvw[::len(w.uvw) // 100][:100]
+    tr, (base, G, S) = _t2(w, J, j0, uvw, dl)
+    v_true = O.dft(w.l, w.m, w.flux, uvw, threads=4)
+    Sg = np.abs(w.flux).sum()
+    rms = lambda v: float(np.sqrt(np.mean(np.abs(v - v_true) ** 2)) / Sg)
+    e_leaves = rms(tr.vis_eq16(uvw))
+    assert rms(T.thresholded_vis(base, G, S, 0)) < e_leaves
+    full = T.thresholded_vis(base, G, S, len(G))
+    d = [float(np.max(np.abs(T.thresholded_vis(base, G, S, int(f * len(G))) - full)) / Sg) for f in (0.1, 0.5)]
+    assert d[1] < d[0] < 0.1

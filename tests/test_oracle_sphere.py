@@ -191,3 +191,57 @@ def test_xref_outside_the_unit_disc_and_pixel_sharing():
     assert table[0, 0] == -1 and table[7, 7] == -1 and table[4, 4] >= 0
     fine, _ = O.xref_table(32, 1e-6, 0.5, 0.2, 8)
     assert len(np.unique(fine)) <= 4
+
+
+def _ring_scheme_centres(nside):
+    """Every pixel centre (z, phi) from the RING-scheme formulas of Gorski et
+    al. (2005), Sec. 4: ring i = 1 .. 4 nside - 1 from the north; in the
+    polar caps (i < nside, and mirrored in the south) 4i pixels at
+    z = 1 - i^2 / (3 nside^2), phi = (pi / 2i)(j - 1/2); in the equatorial
+    belt (nside <= i <= 3 nside) 4 nside pixels at z = 4/3 - 2i / (3 nside),
+    phi = (pi / 2 nside)(j - s/2), s = (i - nside + 1) mod 2."""
+    out = []
+    for i in range(1, 4 * nside):
+        ii = i if i < 2 * nside else 4 * nside - i        # distance in rings from the nearer pole
+        if ii < nside:
+            z = 1.0 - ii * ii / (3.0 * nside * nside)
+            z = z if i < 2 * nside else -z
+            out += [(z, math.pi / (2 * ii) * (j - 0.5)) for j in range(1, 4 * ii + 1)]
+        else:
+            z = 4.0 / 3.0 - 2.0 * i / (3.0 * nside)
+            s = (i - nside + 1) % 2
+            out += [(z, math.pi / (2 * nside) * (j - s / 2.0)) for j in range(1, 4 * nside + 1)]
+    out = np.array(out)
+    out[:, 1] %= 2 * math.pi          # phi = 2 pi (j = 4 nside, s = 0) is phi = 0
+    return out
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_nested_pixel_centres_are_the_ring_scheme_centres(order):
+    # The oracle's nested pix2ang over all 12 4^order pixels gives exactly
+    # the set of centres the ring-scheme formulas give: a second derivation
+    # of the geometry, independent of the nested recipe.
+    nside = 1 << order
+    ring = _ring_scheme_centres(nside)
+    assert len(ring) == 12 * nside * nside
+    nest = np.array([O.pix2ang_nest(order, k)[0::2] for k in range(12 * nside * nside)])
+    key = lambda a: np.lexsort((np.round(a[:, 1], 9), np.round(a[:, 0], 9)))
+    a, b = ring[key(ring)], nest[key(nest)]
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+@pytest.mark.parametrize("order", [3, 5, 6])
+def test_points_near_ring_scheme_centres_map_to_those_pixels(order):
+    # a point a thousandth of a pixel from a ring-scheme centre lies in that
+    # pixel: ang2pix_nest must return the pixel whose centre it is
+    nside = 1 << order
+    ring = _ring_scheme_centres(nside)
+    rng = np.random.default_rng(order)
+    pick = ring[rng.choice(len(ring), 400, replace=False)]
+    step = 1e-3 * math.sqrt(4 * math.pi / (12 * nside * nside))
+    for z, phi in pick:
+        zz = float(np.clip(z + step * rng.uniform(-1, 1) * math.sqrt(max(1 - z * z, 1e-12)), -1, 1))
+        pp = (phi + step * rng.uniform(-1, 1) / math.sqrt(max(1 - z * z, 1e-12))) % (2 * math.pi)
+        k, _ = O.ang2pix_nest(order, zz, pp)
+        zc, _, pc = O.pix2ang_nest(order, k)
+        assert abs(zc - z) < 1e-12 and abs((pc - phi + math.pi) % (2 * math.pi) - math.pi) < 1e-12

@@ -161,6 +161,21 @@ int wt_tree_info(wt_tree t, int* J, int64_t* n_leaves, int64_t* n_nodes, int64_t
 int wt_tree_export(wt_tree t, int64_t* key, uint8_t* child_mask, int32_t* first_child,
                    double* lambda, double* gamma, double* leaf_dir, double* leaf_flux);
 
+/* wt_tree_import -- the inverse of wt_tree_export, for checkpoint and resume
+ * of a major cycle's tree (the paper has no counterpart). A tree is fully
+ * determined by its leaves: their level-J keys and merged fluxes Phi_k, as
+ * wt_tree_export returns them (the last n_leaves keys, and leaf_flux); every
+ * other coefficient follows by Eqs. 9 and 10 in the same rounding order, so
+ * the imported tree equals the exported one bit for bit (its keys, topology,
+ * lambda, gamma, pixel centres and predictions).
+ *   leaf_keys  HOST int64 [n_leaves]: distinct, ascending, 0 .. 12 4^(J-1) - 1
+ *   leaf_flux  HOST float64 [n_leaves], finite
+ *   ra0, dec0, J as for wt_build_tree; out receives the handle.
+ * Argument errors (keys out of range or out of order) are returned before
+ * anything is enqueued; the build is enqueued on `stream`. */
+int wt_tree_import(const int64_t* leaf_keys, const double* leaf_flux, int64_t n_leaves, double ra0, double dec0,
+                   int J, wt_tree* out, void* stream);
+
 /* Release a tree handle and its device memory (synchronises with the
  * stream the tree was built on). NULL is ignored. */
 void wt_free_tree(wt_tree t);
@@ -384,6 +399,23 @@ int wt_mlp_loss_grad(wt_mlp m, const double* uvw, const float* target, int64_t n
  * may be NULL) receives the last minibatch's loss (synchronises). */
 int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, int steps, int batch, float lr,
                  float* final_loss, void* stream);
+/* Steps step0 .. step0 + steps - 1 of a training run of total_steps Adam
+ * steps: the learning rate of step i is the run's cosine-decayed
+ * 0.5 lr (1 + cos(pi i / total_steps)), its minibatch the samples
+ * i batch .. (i + 1) batch - 1 (mod n). wt_mlp_train is the whole run
+ * (step0 = 0, total_steps = steps). The gradient is reduced over the CTAs in
+ * a fixed order, so a run cut into ranges -- with the optimiser state saved
+ * by wt_mlp_get_state and restored by wt_mlp_set_state in between -- ends
+ * with the same parameters, bit for bit, as the uninterrupted run. */
+int wt_mlp_train_range(wt_mlp m, const double* uvw, const float* target, int64_t n, int64_t step0, int steps,
+                       int64_t total_steps, int batch, float lr, float* final_loss, void* stream);
+/* Checkpoint and resume of training: the parameters, Adam's first and
+ * second moments (HOST float32 [4546] each, the parameter order above) and
+ * its step count. Parameters and state travel only as host arrays: writing
+ * them to a file, and reading them back, is the caller's. Both synchronise
+ * the device. */
+int wt_mlp_get_state(wt_mlp m, float* host_params, float* host_m, float* host_v, int64_t* step);
+int wt_mlp_set_state(wt_mlp m, const float* host_params, const float* host_m, const float* host_v, int64_t step);
 /* R(B) by the network (exact sum beyond x_max); out: device complex64 [n]. */
 int wt_mlp_eval(wt_mlp m, const double* uvw, int64_t n, int sign, void* out, void* stream);
 /* Learned form of the tree prediction: V = R_J(B) sum_k Phi_k exp(sign i 2 pi

@@ -48,7 +48,7 @@ EXPORTS = [
     "wt_selftest_bounded_wait", "wt_selftest_grid_barrier", "wt_dirty_image", "wt_hogbom", "wt_clean",
     "wt_xref_table", "wt_build_tree_xref", "wt_measure_pipe_rates",
     "wt_selftest_context_reset", "wt_predict_vis_truncated",
-    "wt_predict_vis_thresholded",
+    "wt_predict_vis_thresholded", "wt_tree_import", "wt_mlp_get_state", "wt_mlp_set_state", "wt_mlp_train_range",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -104,6 +104,10 @@ def _declare(L):
     L.wt_mlp_train.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, f, vp, vp]
     L.wt_mlp_eval.argtypes = [vp, vp, i64, C.c_int, vp, vp]
     L.wt_predict_vis_learned.argtypes = [vp, vp, vp, i64, vp, C.c_int, vp]
+    L.wt_mlp_train_range.argtypes = [vp, vp, vp, i64, i64, C.c_int, i64, C.c_int, f, vp, vp]
+    L.wt_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int64)]
+    L.wt_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
+    L.wt_tree_import.argtypes = [vp, vp, i64, d, d, C.c_int, C.POINTER(C.c_void_p), vp]
     L.wt_predict_vis_truncated.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, i64, vp, C.c_int, vp]
     L.wt_predict_vis_thresholded.argtypes = [vp, C.c_int, d, C.c_int, vp, C.c_int, vp, i64, vp, C.c_int, vp]
     L.wt_recommended_J.argtypes = [d]
@@ -234,6 +238,19 @@ def wt_tree_export(tree):
                 leaf_flux=lflux, level_offsets=offs, **inf)
 
 
+def wt_tree_import(leaf_keys, leaf_flux, ra0, dec0, J, stream=None):
+    """Rebuild a tree from its leaves (host arrays: the level-J keys and
+    merged fluxes of wt_tree_export): bit for bit the exported tree."""
+    k = np.ascontiguousarray(np.asarray(leaf_keys, dtype=np.int64))
+    f = np.ascontiguousarray(np.asarray(leaf_flux, dtype=np.float64))
+    if k.shape != f.shape:
+        raise ValueError("leaf_keys and leaf_flux must have the same length")
+    h = C.c_void_p()
+    _check(load().wt_tree_import(k.ctypes.data_as(C.c_void_p), f.ctypes.data_as(C.c_void_p), k.size, float(ra0),
+                                 float(dec0), int(J), C.byref(h), _stream(stream)))
+    return Tree(h, int(J))
+
+
 def wt_free_tree(tree):
     tree.close()
 
@@ -318,6 +335,27 @@ class Mlp:
                                    int(steps), int(batch), float(lr), loss.ctypes.data_as(C.c_void_p),
                                    _stream(stream)))
         return float(loss[0])
+
+    def train_range(self, uvw, target, step0, steps, total_steps, batch=8192, lr=3e-3, stream=None):
+        """Steps step0 .. step0 + steps - 1 of a run of total_steps."""
+        import torch
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().wt_mlp_train_range(self.h, _dev(uvw, torch.float64), _dev(target, torch.float32),
+                                         uvw.shape[0], int(step0), int(steps), int(total_steps), int(batch),
+                                         float(lr), loss.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return float(loss[0])
+
+    def get_state(self):
+        """(params, Adam first moments, second moments, step) as host arrays."""
+        p, m1, m2 = (np.zeros(MLP_N_PARAMS, dtype=np.float32) for _ in range(3))
+        st = C.c_int64()
+        _check(load().wt_mlp_get_state(self.h, p.ctypes.data_as(C.c_void_p), m1.ctypes.data_as(C.c_void_p),
+                                       m2.ctypes.data_as(C.c_void_p), C.byref(st)))
+        return p, m1, m2, st.value
+
+    def set_state(self, params, m1, m2, step):
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (params, m1, m2)]
+        _check(load().wt_mlp_set_state(self.h, *[x.ctypes.data_as(C.c_void_p) for x in a], int(step)))
 
     def eval(self, uvw, sign=1, out=None, stream=None):
         import torch

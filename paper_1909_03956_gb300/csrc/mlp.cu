@@ -45,6 +45,7 @@ namespace {
 
 constexpr int kH = 64;                                   // hidden width
 constexpr int kNumParams = kH * 3 + kH + kH * kH + kH + 2 * kH + 2;   // 4546
+constexpr int kPartStride = ((kNumParams + 1 + 3) / 4) * 4;            // a CTA's partial gradient and loss
 // offsets into the flat parameter vector (same order as the CPU oracle)
 constexpr int oW1 = 0, ob1 = oW1 + kH * 3, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH, ob3 = oW3 + 2 * kH;
 
@@ -350,6 +351,7 @@ struct TrainSmem {
     float W2q[kH][kH];   // bf16-rounded W2
     float W1[kH * 3], b1[kH], b2[kH], W3[2 * kH], b3[2];
     float gW1[kH * 3], gb1[kH], gb2[kH], gW3[2 * kH], gb3[2];
+    float e2[kS][2];     // squared errors of the current samples
     float loss;
 };
 
@@ -357,8 +359,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train_grad(const float* _
                                                                   const double* __restrict__ uvw,
                                                                   const float* __restrict__ target, int64_t first,
                                                                   int64_t count, int64_t n_total, int64_t n_data,
-                                                                  float scale, float* __restrict__ grad,
-                                                                  float* __restrict__ loss_out)
+                                                                  float scale, float* __restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -423,10 +424,13 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train_grad(const float* _
             float y = sm.b3[o];
             for (int k = 0; k < kH; ++k) y = fmaf(sm.W3[o * kH + k], sm.h2[s][k], y);
             const float err = (sm.valid[s] != 0.f) ? y - sm.t[s][o] : 0.f;
-            atomicAdd(&sm.loss, err * err);
+            sm.e2[s][o] = err * err;
             sm.dy[s][o] = 2.f * err * inv_n;
         }
         __syncthreads();
+        if (tid == 0) {   // in sample order: the same sum on every run
+            for (int q = 0; q < kS; ++q) sm.loss += sm.e2[q][0] + sm.e2[q][1];
+        }
         for (int e = tid; e < kS * kH; e += blockDim.x) {
             const int s = e / kH, o = e % kH;
             const float dh = sm.dy[s][0] * sm.W3[o] + sm.dy[s][1] * sm.W3[kH + o];
@@ -477,16 +481,33 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train_grad(const float* _
         }
         __syncthreads();
     }
+    // this CTA's partial gradient and loss: its own row of `part`, summed
+    // over the rows in order by k_mlp_reduce (no atomics: every run of the
+    // same steps gives the same parameters, bit for bit)
+    float* row = part + static_cast<int64_t>(blockIdx.x) * kPartStride;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) atomicAdd(&grad[oW2 + tid + kTrainThreads * i], gW2[i]);
-    for (int i = tid; i < kH * 3; i += blockDim.x) atomicAdd(&grad[oW1 + i], sm.gW1[i]);
+    for (int i = 0; i < 16; ++i) row[oW2 + tid + kTrainThreads * i] = gW2[i];
+    for (int i = tid; i < kH * 3; i += blockDim.x) row[oW1 + i] = sm.gW1[i];
     for (int i = tid; i < kH; i += blockDim.x) {
-        atomicAdd(&grad[ob1 + i], sm.gb1[i]);
-        atomicAdd(&grad[ob2 + i], sm.gb2[i]);
+        row[ob1 + i] = sm.gb1[i];
+        row[ob2 + i] = sm.gb2[i];
     }
-    for (int i = tid; i < 2 * kH; i += blockDim.x) atomicAdd(&grad[oW3 + i], sm.gW3[i]);
-    if (tid < 2) atomicAdd(&grad[ob3 + tid], sm.gb3[tid]);
-    if (tid == 0) atomicAdd(loss_out, sm.loss * inv_n);
+    for (int i = tid; i < 2 * kH; i += blockDim.x) row[oW3 + i] = sm.gW3[i];
+    if (tid < 2) row[ob3 + tid] = sm.gb3[tid];
+    if (tid == 0) row[kNumParams] = sm.loss * inv_n;
+}
+
+// grad[i] = sum over the rows r = 0 .. rows - 1 of part[r][i], in row
+// order; the loss likewise.
+__global__ void k_mlp_reduce(const float* __restrict__ part, int rows, float* __restrict__ grad,
+                             float* __restrict__ loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kNumParams) return;
+    float a = 0.f;
+    for (int r = 0; r < rows; ++r) a += part[static_cast<int64_t>(r) * kPartStride + i];
+    if (i < kNumParams) grad[i] = a;
+    else *loss = a;
 }
 
 __global__ void k_mlp_adam(float* __restrict__ params, float* __restrict__ m, float* __restrict__ v,
@@ -525,6 +546,8 @@ struct wt_mlp_s {
     double* offs;
     int n_off;
     int adam_t;
+    float* part;                 // per-CTA partial gradients [part_rows][kPartStride]
+    int part_rows;
 };
 
 namespace {
@@ -586,8 +609,10 @@ int run_grad(wt_mlp m, const double* uvw, const float* target, int64_t first, in
     const int64_t cap = static_cast<int64_t>(num_sms()) * 2;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    if (blocks > m->part_rows) blocks = m->part_rows;
     k_mlp_train_grad<<<static_cast<unsigned>(blocks), kTrainThreads, smem, s>>>(
-        m->params, uvw, target, first, count, count, n_data, scale, m->grad, m->loss);
+        m->params, uvw, target, first, count, count, n_data, scale, m->part);
+    k_mlp_reduce<<<(kNumParams + 1 + 255) / 256, 256, 0, s>>>(m->part, static_cast<int>(blocks), m->grad, m->loss);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
@@ -981,8 +1006,10 @@ int wt_mlp_create(int level, double ra0, double dec0, int depth, float x_max, ui
     m->dec0 = dec0;
     m->n_off = 1 << (2 * depth);
     const size_t fbytes = sizeof(float) * kNumParams;
+    m->part_rows = 2 * num_sms();
+    const size_t pbytes = sizeof(float) * kPartStride * static_cast<size_t>(m->part_rows);
     const size_t bytes = 4 * ((fbytes + 255) & ~size_t(255)) + 256 + (kH * kH / 2) * 4 + 256 +
-                         sizeof(double) * 3 * static_cast<size_t>(m->n_off) + 256;
+                         sizeof(double) * 3 * static_cast<size_t>(m->n_off) + 256 + pbytes + 256;
     cudaError_t e = cudaMalloc(&m->block, bytes);
     if (e != cudaSuccess) {
         delete m;
@@ -1002,6 +1029,7 @@ int wt_mlp_create(int level, double ra0, double dec0, int depth, float x_max, ui
     m->loss = reinterpret_cast<float*>(take(sizeof(float)));
     m->w2 = reinterpret_cast<uint32_t*>(take((kH * kH / 2) * 4));
     m->offs = reinterpret_cast<double*>(take(sizeof(double) * 3 * static_cast<size_t>(m->n_off)));
+    m->part = reinterpret_cast<float*>(take(pbytes));
     // He-style initial weights, zero biases, from a seeded host generator
     std::vector<float> h(kNumParams, 0.0f);
     std::mt19937_64 rng(seed);
@@ -1122,25 +1150,29 @@ int wt_mlp_loss_grad(wt_mlp m, const double* uvw, const float* target, int64_t n
     return WT_OK;
 }
 
-int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, int steps, int batch, float lr,
-                 float* final_loss, void* stream)
+int wt_mlp_train_range(wt_mlp m, const double* uvw, const float* target, int64_t n, int64_t step0, int steps,
+                       int64_t total_steps, int batch, float lr, float* final_loss, void* stream)
 {
-    const char* fn = "wt_mlp_train";
+    const char* fn = "wt_mlp_train_range";
     int rc = check_mlp(m, fn);
     if (rc) return rc;
-    if (n <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0f)) return set_error(WT_ERR_ARG, "%s: bad sizes or lr", fn);
+    if (n <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0f) || step0 < 0 || total_steps < step0 + steps)
+        return set_error(WT_ERR_ARG, "%s: bad sizes, steps or lr", fn);
     if ((rc = check_device_buffer(uvw, static_cast<size_t>(n) * 24, fn, "uvw", 8)) ||
         (rc = check_device_buffer(target, static_cast<size_t>(n) * 8, fn, "target", 8)))
         return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     WT_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNumParams, s));
-    int64_t first = 0;
-    for (int it = 0; it < steps; ++it) {
+    // step i of the run takes the minibatch of samples i batch .. (i + 1) batch - 1 (mod n)
+    int64_t first = static_cast<int64_t>((static_cast<unsigned __int128>(step0) * static_cast<uint64_t>(batch)) %
+                                         static_cast<uint64_t>(n));
+    for (int64_t it = step0; it < step0 + steps; ++it) {
         WT_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
         if ((rc = run_grad(m, uvw, target, first, batch, n, s))) return rc;
         m->adam_t += 1;
-        // cosine decay of the learning rate over the run
-        const float lr_t = 0.5f * lr * (1.0f + cosf(3.14159265f * static_cast<float>(it) / static_cast<float>(steps)));
+        // cosine decay of the learning rate over the run of total_steps
+        const float lr_t = 0.5f * lr *
+                           (1.0f + cosf(3.14159265f * static_cast<float>(it) / static_cast<float>(total_steps)));
         const float b1c = 1.0f - powf(0.9f, static_cast<float>(m->adam_t));
         const float b2c = 1.0f - powf(0.999f, static_cast<float>(m->adam_t));
         k_mlp_adam<<<(kNumParams + 255) / 256, 256, 0, s>>>(m->params, m->m, m->v, m->grad, lr_t, b1c, b2c);
@@ -1152,6 +1184,41 @@ int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, in
         WT_CUDA_TRY(cudaMemcpyAsync(final_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
         WT_CUDA_TRY(cudaStreamSynchronize(s));
     }
+    return WT_OK;
+}
+
+int wt_mlp_train(wt_mlp m, const double* uvw, const float* target, int64_t n, int steps, int batch, float lr,
+                 float* final_loss, void* stream)
+{
+    return wt_mlp_train_range(m, uvw, target, n, 0, steps, steps, batch, lr, final_loss, stream);
+}
+
+int wt_mlp_get_state(wt_mlp m, float* host_params, float* host_m, float* host_v, int64_t* step)
+{
+    int rc = check_mlp(m, "wt_mlp_get_state");
+    if (rc) return rc;
+    if (!host_params || !host_m || !host_v || !step) return set_error(WT_ERR_ARG, "wt_mlp_get_state: NULL output");
+    WT_CUDA_TRY(cudaDeviceSynchronize());
+    WT_CUDA_TRY(cudaMemcpy(host_params, m->params, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
+    WT_CUDA_TRY(cudaMemcpy(host_m, m->m, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
+    WT_CUDA_TRY(cudaMemcpy(host_v, m->v, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost));
+    *step = m->adam_t;
+    return WT_OK;
+}
+
+int wt_mlp_set_state(wt_mlp m, const float* host_params, const float* host_m, const float* host_v, int64_t step)
+{
+    int rc = check_mlp(m, "wt_mlp_set_state");
+    if (rc) return rc;
+    if (!host_params || !host_m || !host_v || step < 0 || step > INT32_MAX)
+        return set_error(WT_ERR_ARG, "wt_mlp_set_state: NULL input or bad step");
+    WT_CUDA_TRY(cudaDeviceSynchronize());
+    WT_CUDA_TRY(cudaMemcpy(m->params, host_params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+    WT_CUDA_TRY(cudaMemcpy(m->m, host_m, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+    WT_CUDA_TRY(cudaMemcpy(m->v, host_v, sizeof(float) * kNumParams, cudaMemcpyHostToDevice));
+    m->adam_t = static_cast<int>(step);
+    if ((rc = refresh_bf16(m, nullptr))) return rc;
+    WT_CUDA_TRY(cudaDeviceSynchronize());
     return WT_OK;
 }
 

@@ -648,7 +648,15 @@ int build_tree(const KeySource& src, const double* flux, int64_t n_comp, double 
     int* status = device_status_word();
     if (!status) return set_error(WT_ERR_CUDA, "wt_build_tree: no device status word");
 
-    if (n_comp > 0) {
+    if (n_comp > 0 && src.leaf_keys) {
+        // the leaves themselves (a tree re-imported from its export): one
+        // component per distinct pixel, already in key order
+        k_tree_levels<<<1, kLevelThreads, 0, s>>>(reinterpret_cast<const uint64_t*>(src.leaf_keys), flux, n_comp, J, R,
+                                                  d);
+        WT_CUDA_TRY(cudaGetLastError());
+        k_tree_records<<<num_sms() * 4, 256, 0, s>>>(d, J, status);
+        WT_CUDA_TRY(cudaGetLastError());
+    } else if (n_comp > 0) {
         const int tb = 256;
         if (src.table)
             k_map_xref<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(src.table, src.n_pix, src.pix,

@@ -2,6 +2,8 @@
 // lifetime, error reporting, and dispatch to the kernels. No computation of
 // the method happens here; every step runs in the kernels of the other files.
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -276,6 +278,53 @@ int wt_build_tree(const double* l, const double* m, const double* flux, int64_t 
     src.l = l;
     src.m = m;
     return new_tree(fn, src, flux, n_comp, ra0, dec0, J, out, stream);
+}
+
+int wt_tree_import(const int64_t* leaf_keys, const double* leaf_flux, int64_t n_leaves, double ra0, double dec0,
+                   int J, wt_tree* out, void* stream)
+{
+    const char* fn = "wt_tree_import";
+    if (!out) return set_error(WT_ERR_ARG, "%s: out is NULL", fn);
+    *out = nullptr;
+    int rc;
+    if ((rc = check_tree_args(fn, n_leaves, ra0, dec0, J))) return rc;
+    if (n_leaves > 0 && (!leaf_keys || !leaf_flux)) return set_error(WT_ERR_ARG, "%s: NULL host array", fn);
+    // host checks: keys of level J, strictly ascending (distinct), finite fluxes
+    const int64_t npix = 12 * (int64_t(1) << (2 * (J - 1)));
+    for (int64_t i = 0; i < n_leaves; ++i) {
+        if (leaf_keys[i] < 0 || leaf_keys[i] >= npix)
+            return set_error(WT_ERR_RANGE, "%s: key %lld is not a level-%d pixel", fn, (long long)leaf_keys[i], J);
+        if (i > 0 && leaf_keys[i] <= leaf_keys[i - 1])
+            return set_error(WT_ERR_ARG, "%s: keys must be distinct and ascending (at %lld)", fn, (long long)i);
+        if (!std::isfinite(leaf_flux[i])) return set_error(WT_ERR_RANGE, "%s: non-finite flux at %lld", fn, (long long)i);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t kb = static_cast<size_t>(n_leaves > 0 ? n_leaves : 1) * sizeof(int64_t);
+    char* d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), 2 * ((kb + 255) & ~size_t(255)), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "%s: scratch allocation failed", fn);
+    }
+    int64_t* dk = reinterpret_cast<int64_t*>(d);
+    double* df = reinterpret_cast<double*>(d + ((kb + 255) & ~size_t(255)));
+    if (n_leaves > 0) {
+        // pageable host memory: the copies are staged before they return
+        e = cudaMemcpyAsync(dk, leaf_keys, static_cast<size_t>(n_leaves) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(df, leaf_flux, static_cast<size_t>(n_leaves) * sizeof(double), cudaMemcpyHostToDevice,
+                                s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(d, s);
+            return cuda_error(e, "wt_tree_import: upload");
+        }
+    }
+    wt::KeySource src;
+    src.leaf_keys = dk;
+    rc = new_tree(fn, src, df, n_leaves, ra0, dec0, J, out, stream);
+    cudaFreeAsync(d, s);
+    cudaGetLastError();
+    return rc;
 }
 
 int wt_xref_table(int n, double dl, double ra0, double dec0, int J, int64_t* table, void* stream)

@@ -629,6 +629,8 @@ struct KeySource {
     const int64_t* table = nullptr;
     int64_t n_pix = 0;
     const int32_t* pix = nullptr;
+    const int64_t* leaf_keys = nullptr;   // device: distinct level-J keys in ascending order (the fluxes
+                                          // are the leaves' merged fluxes): no mapping, no sort
 };
 int build_tree(const KeySource& src, const double* flux, int64_t n_comp, double ra0, double dec0, int J, wt_tree t,
                cudaStream_t s);

@@ -205,8 +205,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
 // accumulator row (tcgen05.ld), adds b2, applies SiLU and the 64 -> 2 layer
 // in FP32. Waits are bounded: a wait that runs out records WT_ERR_TIMEOUT,
 // waits once more for the MMA in flight, frees the tensor memory and leaves.
+// Eight CTAs per SM: 64 registers per thread (the accumulator row read in
+// two halves of 32 columns) and 8 x 64 tensor-memory columns, all of an SM's.
 template <bool APPLY>
-__global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const double* __restrict__ uvw, int64_t n,
+__global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const double* __restrict__ uvw, int64_t n,
                                                              float2* __restrict__ io, float scale, int sign,
                                                              float x_max, const double* __restrict__ offs, int n_off,
                                                              int* status)
@@ -244,12 +246,35 @@ __global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const dou
     const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
     uint32_t phase = 0;
     const int64_t tiles = (n + 127) / 128;
+    // the baselines of this thread's sample in the CTA's next tile, loaded
+    // one tile ahead so that their latency overlaps the current tile's work
+    double nu = 0.0, nv = 0.0, nw = 0.0;
+    {
+        const int64_t s0 = static_cast<int64_t>(blockIdx.x) * 128 + t;
+        if (blockIdx.x < tiles && s0 < n) {
+            nu = uvw[3 * s0];
+            nv = uvw[3 * s0 + 1];
+            nw = uvw[3 * s0 + 2];
+        }
+    }
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t s = tile * 128 + t;
         const bool live = s < n;
+        const double bu = nu, bv = nv, bw = nw;
         float x[3] = {0.f, 0.f, 0.f};
-        if (live)
-            for (int d = 0; d < 3; ++d) x[d] = static_cast<float>(uvw[3 * s + d]) * scale;
+        if (live) {
+            x[0] = static_cast<float>(bu) * scale;
+            x[1] = static_cast<float>(bv) * scale;
+            x[2] = static_cast<float>(bw) * scale;
+        }
+        {
+            const int64_t s1 = (tile + gridDim.x) * 128 + t;
+            if (tile + gridDim.x < tiles && s1 < n) {
+                nu = uvw[3 * s1];
+                nv = uvw[3 * s1 + 1];
+                nw = uvw[3 * s1 + 2];
+            }
+        }
         // layer 1 into row t of A, one 16-byte core-matrix row (8 units) at a time
 #pragma unroll
         for (int kg = 0; kg < 8; ++kg) {
@@ -293,20 +318,25 @@ __global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(MlpDev p, const dou
         }
         phase ^= 1u;
         tc_fence_after();
-        uint32_t r[kH];
-        tmem_ld32(row_addr, r);
-        tmem_ld32(row_addr + 32, r + 32);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // the accumulator row in two halves of 32 columns, each folded into
+        // layer 3 at once (the same order of operations as one pass)
         float rr = sb3[0], ri = sb3[1];
 #pragma unroll
-        for (int c = 0; c < kH; ++c) {
-            const float h = silu_fast(__uint_as_float(r[c]) + sb2[c]);
-            rr = fmaf(sW3[c], h, rr);
-            ri = fmaf(sW3[kH + c], h, ri);
+        for (int half = 0; half < 2; ++half) {
+            uint32_t r[32];
+            tmem_ld32(row_addr + 32 * half, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) {
+                const int c = 32 * half + cc;
+                const float h = silu_fast(__uint_as_float(r[cc]) + sb2[c]);
+                rr = fmaf(sW3[c], h, rr);
+                ri = fmaf(sW3[kH + c], h, ri);
+            }
         }
         if (live) {
             if (fmaxf(fabsf(x[0]), fmaxf(fabsf(x[1]), fabsf(x[2]))) > x_max) {
-                const double2 e = response_exact_one(uvw[3 * s], uvw[3 * s + 1], uvw[3 * s + 2], offs, n_off);
+                const double2 e = response_exact_one(bu, bv, bw, offs, n_off);
                 rr = static_cast<float>(e.x);
                 ri = static_cast<float>(e.y);
             }

@@ -282,7 +282,8 @@ def pipe_peaks(wt, torch, sm_max_mhz):
         r = wt.wt_measure_pipe_rates()
         src = "wt_measure_pipe_rates on this GPU (per clock per SM) x %d SMs x %.0f MHz" % (n_sm, mhz)
     except Exception as e:   # noqa: BLE001 - reported in the line
-        r = {"ffma": 128.0, "ffma2_elems": 128.0, "dfma": 2.0, "mufu_sin": 16.0}
+        r = {"ffma": 128.0, "ffma2_elems": 128.0, "dfma": 2.0, "mufu_sin": 16.0, "mufu_tanh": 16.0,
+             "mufu_tanh_bf16x2_elems": 32.0, "mufu_ex2": 16.0}
         src = "nominal (%d SMs x 128 FP32 / 2 FP64 / 16 SFU lanes x %.0f MHz); probe failed: %s" % (n_sm, mhz, e)
     hz = mhz * 1e6
     return {"fp32_tflops": 2.0 * r["ffma"] * n_sm * hz / 1e12,          # an FMA is 2 flops
@@ -290,6 +291,9 @@ def pipe_peaks(wt, torch, sm_max_mhz):
             "fp64_tflops": 2.0 * r["dfma"] * n_sm * hz / 1e12,
             "fp64_inst_per_s": r["dfma"] * n_sm * hz,
             "sfu_top_s": r["mufu_sin"] * n_sm * hz / 1e12,
+            "sfu_tanh_top_s": r["mufu_tanh"] * n_sm * hz / 1e12,
+            "sfu_tanh_bf16x2_top_s": r["mufu_tanh_bf16x2_elems"] * n_sm * hz / 1e12,
+            "sfu_ex2_top_s": r["mufu_ex2"] * n_sm * hz / 1e12,
             "per_clk_per_sm": r, "n_sm": n_sm, "sm_mhz": mhz, "peak_source": src}
 
 
@@ -687,9 +691,10 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
         "subtract_c64_64Mi": {"bound": "hbm", "frac": r["subtract_c64_64Mi_frac_of_hbm"],
                               "peak_gbps": HBM_PEAK_GBPS, "peak_source": PEAKS_SOURCE},
         "mlp_eval": {"bound": "sfu",
-                     "frac": n * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_top_s"],
-                     "unit": "hardware tanh of the two SiLU layers (%d per sample) of the measured SFU rate"
+                     "frac": n * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_tanh_top_s"],
+                     "unit": "hardware tanh of the two SiLU layers (%d per sample) of the measured tanh rate"
                              % MLP_TANH_PER_SAMPLE,
+                     "of_sine_rate": n * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_top_s"],
                      "tensor": {"achieved_tflops": mlp_tflops, "frac": mlp_tflops / BF16_PEAK_TFLOPS,
                                 "peak_tflops": BF16_PEAK_TFLOPS, "peak_source": PEAKS_SOURCE,
                                 "flops_per_sample": 8832}},

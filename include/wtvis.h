@@ -513,9 +513,12 @@ int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream);
  * their rooflines; the paper has no counterpart). One CTA of 512 threads per
  * SM runs eight independent dependency chains per thread of one operation,
  * timed by its SM's own cycle counter; the median over the SMs is returned.
- *   per_clk_per_sm  HOST double [4], written: operations per clock per SM of
+ *   per_clk_per_sm  HOST double [7], written: operations per clock per SM of
  *                   [0] float32 FMA, [1] float32 packed-pair FMA (elements),
- *                   [2] float64 FMA, [3] special-function-unit sine
+ *                   [2] float64 FMA, [3] special-function-unit sine,
+ *                   [4] tanh (PTX tanh.approx.f32), [5] tanh on packed
+ *                   BF16 pairs (tanh.approx.bf16x2, elements), [6] 2^x
+ *                   (ex2.approx.ftz.f32)
  * Allocates a few KB of scratch on `stream`, runs about 10 ms of kernels and
  * synchronises `stream`. */
 int wt_measure_pipe_rates(double* per_clk_per_sm, void* stream);

@@ -467,10 +467,12 @@ def wt_selftest_grid_barrier(spin_limit=1000, stream=None):
 
 def wt_measure_pipe_rates(stream=None):
     """Measured issue rates of the current device's pipes, per clock per SM:
-    {"ffma": ..., "ffma2_elems": ..., "dfma": ..., "mufu_sin": ...}."""
-    out = (C.c_double * 4)()
+    {"ffma", "ffma2_elems", "dfma", "mufu_sin", "mufu_tanh",
+    "mufu_tanh_bf16x2_elems", "mufu_ex2"}."""
+    out = (C.c_double * 7)()
     _check(load().wt_measure_pipe_rates(out, _stream(stream)))
-    return {"ffma": out[0], "ffma2_elems": out[1], "dfma": out[2], "mufu_sin": out[3]}
+    keys = ("ffma", "ffma2_elems", "dfma", "mufu_sin", "mufu_tanh", "mufu_tanh_bf16x2_elems", "mufu_ex2")
+    return {k: out[i] for i, k in enumerate(keys)}
 
 
 def wt_last_error():

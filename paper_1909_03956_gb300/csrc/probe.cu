@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "wt_internal.cuh"
 
 namespace wt {
@@ -23,7 +25,16 @@ constexpr int kProbeThreads = 512;
 constexpr int kProbeChains = 8;
 constexpr size_t kProbeSmem = 150 * 1024;   // > half of an SM's shared memory: one CTA per SM
 
-enum ProbeKind { kFfma = 0, kFfma2 = 1, kDfma = 2, kMufuSin = 3, kNumProbes = 4 };
+enum ProbeKind {
+    kFfma = 0,
+    kFfma2 = 1,
+    kDfma = 2,
+    kMufuSin = 3,
+    kMufuTanh = 4,
+    kMufuTanhBf16x2 = 5,
+    kMufuEx2 = 6,
+    kNumProbes = 7
+};
 
 template <int KIND>
 __global__ void __launch_bounds__(kProbeThreads) k_pipe_probe(int iters, float b, float c, float* sink,
@@ -67,13 +78,48 @@ __global__ void __launch_bounds__(kProbeThreads) k_pipe_probe(int iters, float b
         }
 #pragma unroll
         for (int r = 0; r < kProbeChains; ++r) acc += static_cast<float>(a[r]);
-    } else {
+    } else if constexpr (KIND == kMufuSin) {
         float a[kProbeChains];
 #pragma unroll
         for (int r = 0; r < kProbeChains; ++r) a[r] = x0 + 0.1f * r;
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int r = 0; r < kProbeChains; ++r) a[r] = __sinf(a[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kProbeChains; ++r) acc += a[r];
+    } else if constexpr (KIND == kMufuTanh) {
+        float a[kProbeChains];
+#pragma unroll
+        for (int r = 0; r < kProbeChains; ++r) a[r] = x0 + 0.1f * r;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int r = 0; r < kProbeChains; ++r) asm volatile("tanh.approx.f32 %0, %0;" : "+f"(a[r]));
+        }
+#pragma unroll
+        for (int r = 0; r < kProbeChains; ++r) acc += a[r];
+    } else if constexpr (KIND == kMufuTanhBf16x2) {
+        uint32_t a[kProbeChains];
+#pragma unroll
+        for (int r = 0; r < kProbeChains; ++r) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0 + 0.1f * r, x0 - 0.1f * r);
+            a[r] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int r = 0; r < kProbeChains; ++r) asm volatile("tanh.approx.bf16x2 %0, %0;" : "+r"(a[r]));
+        }
+#pragma unroll
+        for (int r = 0; r < kProbeChains; ++r) acc += __uint_as_float(a[r] << 16) + __uint_as_float(a[r] & 0xffff0000u);
+    } else {
+        float a[kProbeChains];
+#pragma unroll
+        for (int r = 0; r < kProbeChains; ++r) a[r] = -1e-3f * r;
+        for (int i = 0; i < iters; ++i) {   // 2^x of a non-positive x stays in (0, 1]: no overflow
+#pragma unroll
+            for (int r = 0; r < kProbeChains; ++r) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(a[r]));
+#pragma unroll
+            for (int r = 0; r < kProbeChains; ++r) a[r] = -a[r];
         }
 #pragma unroll
         for (int r = 0; r < kProbeChains; ++r) acc += a[r];
@@ -109,14 +155,18 @@ extern "C" int wt_measure_pipe_rates(double* per_clk_per_sm, void* stream)
     WT_CUDA_TRY(cudaMallocAsync(&sink, sizeof(float) * kProbeThreads * n_sm, s));
     WT_CUDA_TRY(cudaMallocAsync(&cyc, sizeof(long long) * kNumProbes * n_sm, s));
     // iterations per kind: about a millisecond each at the expected rates
-    const int iters[kNumProbes] = {40000, 20000, 1000, 5000};
-    const double elems[kNumProbes] = {1.0, 2.0, 1.0, 1.0};
+    const int iters[kNumProbes] = {40000, 20000, 1000, 5000, 5000, 5000, 5000};
+    const double elems[kNumProbes] = {1.0, 2.0, 1.0, 1.0, 1.0, 2.0, 1.0};
     int rc = WT_OK;
     for (int rep = 0; rep < 2 && rc == WT_OK; ++rep) {   // the first pass warms the clocks up
         if (!rc) rc = run_probe<kFfma>(iters[kFfma], n_sm, sink, cyc + kFfma * n_sm, s);
         if (!rc) rc = run_probe<kFfma2>(iters[kFfma2], n_sm, sink, cyc + kFfma2 * n_sm, s);
         if (!rc) rc = run_probe<kDfma>(iters[kDfma], n_sm, sink, cyc + kDfma * n_sm, s);
         if (!rc) rc = run_probe<kMufuSin>(iters[kMufuSin], n_sm, sink, cyc + kMufuSin * n_sm, s);
+        if (!rc) rc = run_probe<kMufuTanh>(iters[kMufuTanh], n_sm, sink, cyc + kMufuTanh * n_sm, s);
+        if (!rc)
+            rc = run_probe<kMufuTanhBf16x2>(iters[kMufuTanhBf16x2], n_sm, sink, cyc + kMufuTanhBf16x2 * n_sm, s);
+        if (!rc) rc = run_probe<kMufuEx2>(iters[kMufuEx2], n_sm, sink, cyc + kMufuEx2 * n_sm, s);
     }
     std::vector<long long> h(static_cast<size_t>(kNumProbes) * n_sm);
     if (rc == WT_OK) {

@@ -9,6 +9,8 @@
 // the CTA processes.
 #pragma once
 
+#include <type_traits>
+
 #include "wt_internal.cuh"
 
 namespace wt {
@@ -123,7 +125,8 @@ struct Stager {
 
     // As sweep, but the body sees the chunk, the position and the chunk's
     // record count (body.at(chunk, r, n)), so that it may handle a record
-    // together with its neighbour.
+    // together with its neighbours: a body whose at() returns the number of
+    // records it took (at least 1) advances by it.
     template <class Body>
     __device__ bool sweep_at(Body& body)
     {
@@ -157,11 +160,16 @@ struct Stager {
             const int64_t first = c * chunk;
             const int n = static_cast<int>((count - first < chunk) ? (count - first) : chunk);
             const Rec* cb = buf + static_cast<int64_t>(b) * chunk;
-            // four records per trip (measured against two: 2 % faster on the
-            // blob workloads, 4-6 % slower on deep trees of isolated
-            // components, whose records are mostly internal nodes)
+            if constexpr (std::is_void_v<decltype(body.at(cb, 0, n))>) {
+                // four records per trip (measured against two: 2 % faster on
+                // the blob workloads, 4-6 % slower on deep trees of isolated
+                // components, whose records are mostly internal nodes)
 #pragma unroll 4
-            for (int r = 0; r < n; ++r) body.at(cb, r, n);
+                for (int r = 0; r < n; ++r) body.at(cb, r, n);
+            } else {
+                // the body takes one or more records per step
+                for (int r = 0; r < n;) r += body.at(cb, r, n);
+            }
             if (!resident) {
                 __syncthreads();
                 if (threadIdx.x == 0 && c + 2 < nc) issue(c + 2, b);

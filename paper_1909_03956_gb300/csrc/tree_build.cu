@@ -465,7 +465,8 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
         // regrouped Eq. 17: the node's weight from its parent's gammas
         double wgt;
         bool first = true;
-        bool pair_first = false, pair_second = false;
+        bool pair_first = false, pair_second = false, group_first = false;
+        uint32_t group_len = 0;
         if (j == 1) {
             wgt = A1 * d.lambda[n];
         } else {
@@ -484,17 +485,25 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
                 const uint32_t sib_before = __popc(pmask & ((1u << slot) - 1u));
                 const int64_t run_lo = post - sib_before;
                 const int64_t run_hi = run_lo + __popc(pmask) - 1;
-                const int64_t chunk_lo = post - post % kRecChunkW;
-                const int64_t seg_lo = run_lo > chunk_lo ? run_lo : chunk_lo;
-                const int64_t k = post - seg_lo;
-                pair_second = (k & 1) != 0;
-                pair_first = (k & 1) == 0 && post + 1 <= run_hi && (post + 1) % kRecChunkW != 0;
+                if (run_lo / kRecChunkW == (run_hi + 1) / kRecChunkW) {
+                    // the run and its parent (post-order: right after the
+                    // run) in one chunk: taken together from the run's start
+                    group_first = sib_before == 0;
+                    group_len = static_cast<uint32_t>(__popc(pmask));
+                } else {
+                    const int64_t chunk_lo = post - post % kRecChunkW;
+                    const int64_t seg_lo = run_lo > chunk_lo ? run_lo : chunk_lo;
+                    const int64_t k = post - seg_lo;
+                    pair_second = (k & 1) != 0;
+                    pair_first = (k & 1) == 0 && post + 1 <= run_hi && (post + 1) % kRecChunkW != 0;
+                }
             }
         }
         const uint32_t wmeta = static_cast<uint32_t>(j) | (leaf ? kRwLeaf : 0u) | (j == 1 ? kRwRoot : 0u) |
                                (first ? kRwFirst : 0u) | (pair_first ? kRwPairFirst : 0u) |
                                (pair_second ? kRwPairSecond : 0u) | ((!leaf && j == J - 1) ? kRwLowSum : 0u) |
-                               ((!leaf && j == J - 2) ? kRwMidSum : 0u);
+                               ((!leaf && j == J - 2) ? kRwMidSum : 0u) |
+                               (group_first ? (kRwGroup | (group_len << kRwGroupShift)) : 0u);
         RecWD wd;
         RecWF wf;
         wd.meta = wmeta;

@@ -557,23 +557,40 @@ struct Eq17WF {
         }
     }
 
-    // One step of the record sweep: a leaf whose next record is its sibling
-    // leaf takes both (when both are in this chunk), anything else one.
-    // One record of the sweep. In the fast form a leaf marked as the first of
-    // a pair takes its next record (its sibling leaf, in the same chunk by
-    // construction) with it, and the second is skipped. The polynomial form
-    // takes every record alone: its four chains need more registers than the
-    // pairing saves (measured 2 % slower).
-    __device__ __forceinline__ void at(const RecWF* cb, int r, int n)
+    // One step of the record sweep; returns the records it took. In the fast
+    // form a group (a run of sibling leaves and their level-(J-1) parent, in
+    // one chunk by construction) is one step: its leaves in pairs, then the
+    // parent; a leaf marked as the first of a pair takes its sibling with it.
+    // The polynomial form takes every record alone: its four chains need
+    // more registers than the pairing saves (measured 2 % slower).
+    __device__ __forceinline__ int at(const RecWF* cb, int r, int n)
     {
         const RecWF& a = cb[r];
         if constexpr (FAST) {
-            if (a.meta & (kRwPairFirst | kRwPairSecond)) {
-                if (a.meta & kRwPairFirst) leaf_pair(a, cb[r + 1 < n ? r + 1 : r]);
-                return;
+            const uint32_t meta = a.meta;
+            if (meta & kRwGroup) {
+                const int k = static_cast<int>((meta >> kRwGroupShift) & 7u);
+                if (k >= 1 && k <= 4 && r + k < n) {
+                    group(cb + r, k);
+                    return k + 1;
+                }
+            } else if ((meta & kRwPairFirst) && r + 1 < n) {
+                leaf_pair(a, cb[r + 1]);
+                return 2;
             }
         }
         (*this)(a);
+        return 1;
+    }
+
+    // A group of k sibling leaves g[0 .. k-1] and their parent g[k].
+    __device__ __forceinline__ void group(const RecWF* g, int k)
+    {
+        if (k >= 2) leaf_pair(g[0], g[1]);
+        else leaf(g[0], false);
+        if (k == 4) leaf_pair(g[2], g[3]);
+        else if (k == 3) leaf(g[2], false);
+        low_levels(g[k], g[k].meta);
     }
 
     // Parent's xi sum: the first child writes it, the others add (a select,
@@ -619,28 +636,34 @@ struct Eq17WF {
         if (!root) pass_up(clamp_row(__float_as_uint(r.b), maxrow), first, xi);
     }
 
+    // One leaf alone (root: a level-1 pixel, J = 1).
+    __device__ __forceinline__ void leaf(const RecWF& r, bool root)
+    {
+        const float2 wv = bcast2(r.g);
+        const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float2 h, tl, e0, e1;
+            phase2(p, su, sv, sw, h, tl);
+            sincos_mixed2<FAST>(h, tl, e0, e1);
+            leaf_up(2 * p, e0, wv, root);
+            leaf_up(2 * p + 1, e1, wv, root);
+        }
+        if constexpr (ODD) {
+            constexpr int k = VPT - 1;
+            float th, tl, s, c;
+            phase1(su, sv, sw, th, tl);
+            sincos_mixed<FAST>(th, tl, s, c);
+            leaf_up(k, make_float2(c, s), wv, root);
+        }
+    }
+
     __device__ void operator()(const RecWF& r)
     {
         const uint32_t meta = r.meta;
         const float2 wv = bcast2(r.g);
         if (meta & kRwLeaf) {
-            const bool root = meta & kRwRoot;
-            const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float2 h, tl, e0, e1;
-                phase2(p, su, sv, sw, h, tl);
-                sincos_mixed2<FAST>(h, tl, e0, e1);
-                leaf_up(2 * p, e0, wv, root);
-                leaf_up(2 * p + 1, e1, wv, root);
-            }
-            if constexpr (ODD) {
-                constexpr int k = VPT - 1;
-                float th, tl, s, c;
-                phase1(su, sv, sw, th, tl);
-                sincos_mixed<FAST>(th, tl, s, c);
-                leaf_up(k, make_float2(c, s), wv, root);
-            }
+            leaf(r, (meta & kRwRoot) != 0);
             return;
         }
         if (meta & (kRwLowSum | kRwMidSum)) {

@@ -505,8 +505,12 @@ static_assert(sizeof(RecF) == 32, "RecF layout");
 // 6 level 1, 7 first child of its parent (in post-order), 8 a leaf that
 // takes its next record (its next sibling leaf) as a pair, 9 that second
 // leaf of a pair, 10 a node at level J - 1 (its children are leaves),
-// 11 a node at level J - 2. Pairs are formed greedily along each run of
-// sibling leaves, never across a staging chunk of kRecChunkW records.
+// 11 a node at level J - 2, 12 the first leaf of a group: a run of sibling
+// leaves whose parent (the next record after the run in post-order, a node
+// at level J - 1) lies in the same staging chunk of kRecChunkW records, so
+// that the run and its parent are taken in one step; bits 13-15 the run's
+// length (1 to 4). The leaves of a run that is not a group are paired
+// greedily, never across a staging chunk.
 constexpr uint32_t kRwLeaf = 1u << 5;
 constexpr uint32_t kRwRoot = 1u << 6;
 constexpr uint32_t kRwFirst = 1u << 7;
@@ -514,6 +518,8 @@ constexpr uint32_t kRwPairFirst = 1u << 8;
 constexpr uint32_t kRwPairSecond = 1u << 9;
 constexpr uint32_t kRwLowSum = 1u << 10;
 constexpr uint32_t kRwMidSum = 1u << 11;
+constexpr uint32_t kRwGroup = 1u << 12;
+constexpr int kRwGroupShift = 13;
 constexpr int kRecChunkW = 128;   // records per staging buffer of the regrouped float32 form
 
 // float64 (48 bytes): a, b, c = leaf pixel centre (s_u, s_v, s_w - 1); d = w.

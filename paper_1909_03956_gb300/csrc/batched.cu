@@ -165,9 +165,9 @@ __global__ void __launch_bounds__(NT) k_batched(const BatchChan* __restrict__ ch
             if constexpr (GRIDPASS) {
                 // an item that does not fit is swept too, its results discarded
                 defer = !tile_grid_constants(U, V, W, ch.hdr->smax, C);   // a CTA-wide decision
-                good = sweep_regrouped_mixed<NT, VPT, FAST, true>(st, U, V, W, C, rstk, ch.J, maxrow, res);
+                good = sweep_regrouped_mixed<NT, VPT, FAST, true, false>(st, U, V, W, C, rstk, ch.J, maxrow, res);
             } else {
-                good = sweep_regrouped_mixed<NT, VPT, FAST, false>(st, U, V, W, C, rstk, ch.J, maxrow, res);
+                good = sweep_regrouped_mixed<NT, VPT, FAST, false, false>(st, U, V, W, C, rstk, ch.J, maxrow, res);
             }
             if (good && defer) mark_deferred(first_vis);
 #pragma unroll
@@ -247,6 +247,14 @@ int default_shape(int mode, int rows_max)
     return -1;
 }
 
+// WT_BATCH_QUEUE=1 sends every batch through the persistent work queue
+// (otherwise taken only beyond 2^31 - 1 items), so that tests reach it.
+bool force_queue()
+{
+    const char* e = getenv("WT_BATCH_QUEUE");
+    return e && e[0] == '1';
+}
+
 template <int NT, int VPT, int KIND, bool FAST = false, bool GRIDPASS = false>
 int launch_pass(const BatchChan* chans, int n_ch, int64_t total, const double* uvw_m, int64_t n_vis, void* vis,
                 int sign, int rows_max, unsigned long long* queue, int* status, size_t smem, cudaStream_t s)
@@ -258,7 +266,7 @@ int launch_pass(const BatchChan* chans, int n_ch, int64_t total, const double* u
     // One CTA per item: the hardware balances the SMs as CTAs finish, as for
     // the single-channel predictor. The queue serves batches of more items
     // than a grid holds (reset before each pass).
-    const bool per_item = total <= 0x7fffffff;
+    const bool per_item = total <= 0x7fffffff && !force_queue();
     int64_t grid = per_item ? total : static_cast<int64_t>(num_sms()) * per_sm;
     if (grid < 1) grid = 1;
     if (!per_item) WT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
@@ -433,6 +441,11 @@ int tune(Plan& p, const double* uvw_m, int64_t n_vis, void* vis, int* status, cu
 {
     const int first = default_shape(p.mode, p.rows_max);
     if (first < 0) return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis_batched: no launch shape fits J");
+    const char* pin = getenv("WT_BATCH_SHAPE");   // pins shape k of kBatchShapes when it fits
+    if (pin) {
+        const int v = atoi(pin);
+        if (v >= 0 && v < kNumBatchShapes && batch_fits(p.mode, v, p.rows_max)) return v;
+    }
     const char* e = getenv("WT_AUTOTUNE");
     if (e && e[0] == '0') return first;
     // per channel: the mixed forms are timed on up to 131 072 visibilities

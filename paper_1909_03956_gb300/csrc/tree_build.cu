@@ -485,17 +485,16 @@ __global__ void k_tree_records(TreeDev d, int J, int* status)
                 const uint32_t sib_before = __popc(pmask & ((1u << slot) - 1u));
                 const int64_t run_lo = post - sib_before;
                 const int64_t run_hi = run_lo + __popc(pmask) - 1;
+                const int64_t chunk_lo = post - post % kRecChunkW;
+                const int64_t seg_lo = run_lo > chunk_lo ? run_lo : chunk_lo;
+                const int64_t k = post - seg_lo;
+                pair_second = (k & 1) != 0;
+                pair_first = (k & 1) == 0 && post + 1 <= run_hi && (post + 1) % kRecChunkW != 0;
                 if (run_lo / kRecChunkW == (run_hi + 1) / kRecChunkW) {
                     // the run and its parent (post-order: right after the
-                    // run) in one chunk: taken together from the run's start
+                    // run) in one chunk: a group, its pairs from its start
                     group_first = sib_before == 0;
                     group_len = static_cast<uint32_t>(__popc(pmask));
-                } else {
-                    const int64_t chunk_lo = post - post % kRecChunkW;
-                    const int64_t seg_lo = run_lo > chunk_lo ? run_lo : chunk_lo;
-                    const int64_t k = post - seg_lo;
-                    pair_second = (k & 1) != 0;
-                    pair_first = (k & 1) == 0 && post + 1 <= run_hi && (post + 1) % kRecChunkW != 0;
                 }
             }
         }

@@ -483,11 +483,12 @@ int launch_wavelet(const WaveletJob& jb, int v, cudaStream_t s)
 // preference order.
 int default_wavelet_variant(int mode, int which, int J)
 {
-    // measured on the medium workload (J = 12): the explicit mixed sum runs
-    // best at 256 x 1 (its stack limits the CTAs per SM), the regrouped one,
-    // whose stack is small, with two visibilities per thread
+    // measured on the medium and large workloads (J = 12): the explicit
+    // mixed sum runs best at 256 x 1 (its stack limits the CTAs per SM), the
+    // regrouped one, whose stack is small, at 64 x 4 (the per-record work
+    // shared by four visibilities), then 128 x 2
     static const int order_mixed[kNumWaveletVariants] = {0, 2, 1, 3, 4, 5, 6, 7};
-    static const int order_mixed_rg[kNumWaveletVariants] = {2, 7, 4, 6, 3, 5, 0, 1};
+    static const int order_mixed_rg[kNumWaveletVariants] = {4, 2, 7, 6, 3, 5, 0, 1};
     static const int order_fp64[kNumWaveletVariants] = {1, 0, 2, 3, 4, 5, 6, 7};
     const int* order = (mode == WT_FP64 || mode == WT_FP64_DF) ? order_fp64
                        : (which == WT_SUM_EQ17_REGROUPED) ? order_mixed_rg : order_mixed;

@@ -430,8 +430,12 @@ struct Eq17DF {
 // Packed pairs as in Eq17F. GRID: the leaf phases with their heads on the
 // common grid of each visibility's constant C (phase_turns_grid2; the
 // caller sets Cg and Cs and guarantees that the grid is valid), else with
-// error-free sums (phase_turns_df2).
-template <int NT, int VPT, bool FAST = false, bool GRID = false>
+// error-free sums (phase_turns_df2). GROUPS: the fast form takes a group
+// (a run of sibling leaves and their level-(J-1) parent) in one step of a
+// variable-stride sweep, else every record in a fixed-stride sweep, the
+// second leaf of a pair skipped (measured: groups faster in the single-tree
+// predictor, slower in the batched one).
+template <int NT, int VPT, bool FAST = false, bool GRID = false, bool GROUPS = true>
 struct Eq17WF {
     static constexpr int NP = VPT / 2;
     static constexpr bool ODD = (VPT & 1) != 0;
@@ -557,13 +561,13 @@ struct Eq17WF {
         }
     }
 
-    // One step of the record sweep; returns the records it took. In the fast
-    // form a group (a run of sibling leaves and their level-(J-1) parent, in
-    // one chunk by construction) is one step: its leaves in pairs, then the
-    // parent; a leaf marked as the first of a pair takes its sibling with it.
-    // The polynomial form takes every record alone: its four chains need
-    // more registers than the pairing saves (measured 2 % slower).
-    __device__ __forceinline__ int at(const RecWF* cb, int r, int n)
+    // One step of the record sweep (GROUPS); returns the records it took. In
+    // the fast form a group (in one chunk by construction) is one step: its
+    // leaves in pairs, then the parent; a leaf marked as the first of a pair
+    // takes its sibling with it. The polynomial form takes every record
+    // alone: its four chains need more registers than the pairing saves
+    // (measured 2 % slower).
+    __device__ __forceinline__ int at_grouped(const RecWF* cb, int r, int n)
     {
         const RecWF& a = cb[r];
         if constexpr (FAST) {
@@ -581,6 +585,26 @@ struct Eq17WF {
         }
         (*this)(a);
         return 1;
+    }
+
+    // One record of a fixed-stride sweep (!GROUPS): the fast form's first
+    // leaf of a pair takes its sibling, the second is skipped.
+    __device__ __forceinline__ void at_single(const RecWF* cb, int r, int n)
+    {
+        const RecWF& a = cb[r];
+        if constexpr (FAST) {
+            if (a.meta & (kRwPairFirst | kRwPairSecond)) {
+                if (a.meta & kRwPairFirst) leaf_pair(a, cb[r + 1 < n ? r + 1 : r]);
+                return;
+            }
+        }
+        (*this)(a);
+    }
+
+    __device__ __forceinline__ auto at(const RecWF* cb, int r, int n)
+    {
+        if constexpr (GROUPS) return at_grouped(cb, r, n);
+        else at_single(cb, r, n);
     }
 
     // A group of k sibling leaves g[0 .. k-1] and their parent g[k].
@@ -713,14 +737,15 @@ __device__ __forceinline__ bool tile_grid_constants(const F2 (&u)[VPT], const F2
 }
 
 // One tile's sweep of the regrouped Eq. 17 (GRID: on the head grid of the
-// constants C, else with error-free sums). Returns false (CTA-wide) if a
-// staging copy did not arrive; res receives V of each visibility.
-template <int NT, int VPT, bool FAST, bool GRID>
+// constants C, else with error-free sums; GROUPS as Eq17WF). Returns false
+// (CTA-wide) if a staging copy did not arrive; res receives V of each
+// visibility.
+template <int NT, int VPT, bool FAST, bool GRID, bool GROUPS = true>
 __device__ __forceinline__ bool sweep_regrouped_mixed(Stager<RecWF>& st, const F2 (&u)[VPT], const F2 (&v)[VPT],
                                       const F2 (&w)[VPT], const float (&C)[VPT], float2* stk, int J, int maxrow,
                                       float2 (&res)[VPT])
 {
-    Eq17WF<NT, VPT, FAST, GRID> b;
+    Eq17WF<NT, VPT, FAST, GRID, GROUPS> b;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) { b.u[k] = u[k]; b.v[k] = v[k]; b.w[k] = w[k]; }
     if constexpr (GRID) {

@@ -509,8 +509,8 @@ static_assert(sizeof(RecF) == 32, "RecF layout");
 // leaves whose parent (the next record after the run in post-order, a node
 // at level J - 1) lies in the same staging chunk of kRecChunkW records, so
 // that the run and its parent are taken in one step; bits 13-15 the run's
-// length (1 to 4). The leaves of a run that is not a group are paired
-// greedily, never across a staging chunk.
+// length (1 to 4). The leaves of every run are paired greedily from its
+// start, never across a staging chunk (in a group, from the group's start).
 constexpr uint32_t kRwLeaf = 1u << 5;
 constexpr uint32_t kRwRoot = 1u << 6;
 constexpr uint32_t kRwFirst = 1u << 7;

@@ -72,6 +72,39 @@ def test_batched_matches_oracle_per_channel(mode):
         assert err <= bar, (c, err)
 
 
+@pytest.mark.parametrize("shape", range(6))
+@pytest.mark.parametrize("mode", [wt.WT_MIXED, wt.WT_MIXED_FAST])
+def test_batched_every_launch_shape(shape, mode, monkeypatch):
+    # each (threads per CTA, visibilities per thread) shape the batched
+    # autotuner may pick gives the oracle's answer on a ragged batch
+    monkeypatch.setenv("WT_BATCH_SHAPE", str(shape))
+    chans = _channels(4, seed=21 + shape)
+    uvw_m = _uvw_m(2999, seed=22)
+    trees = _gpu_trees(chans)
+    v = wt.wt_predict_vis_batched(trees, [c["freq"] for c in chans], dev(uvw_m), mode=mode).cpu().numpy()
+    ref = _oracle(chans, uvw_m)
+    for c, ch in enumerate(chans):
+        assert np.max(np.abs(v[c] - ref[c])) / np.abs(ch["flux"]).sum() <= TOL[mode], c
+    for t in trees:
+        t.close()
+
+
+@pytest.mark.parametrize("mode", [wt.WT_FP64, wt.WT_MIXED_FAST])
+def test_batched_persistent_queue_matches_oracle(mode, monkeypatch):
+    # the persistent work queue (a fixed grid taking items from an atomic
+    # counter), forced on a small batch
+    monkeypatch.setenv("WT_BATCH_QUEUE", "1")
+    chans = _channels(6, seed=31)
+    uvw_m = _uvw_m(4097, seed=32)
+    trees = _gpu_trees(chans)
+    v = wt.wt_predict_vis_batched(trees, [c["freq"] for c in chans], dev(uvw_m), mode=mode).cpu().numpy()
+    ref = _oracle(chans, uvw_m)
+    for c, ch in enumerate(chans):
+        assert np.max(np.abs(v[c] - ref[c])) / np.abs(ch["flux"]).sum() <= TOL[mode], c
+    for t in trees:
+        t.close()
+
+
 def test_batched_double_float_equals_single_channel_calls():
     chans = _channels(5, seed=12)
     uvw_m = _uvw_m(2048, seed=13)

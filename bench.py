@@ -549,7 +549,7 @@ SFU_OPS_LEAF = {"fast": 2, "mixed": 0}
 # DRAM bytes of one k_wavelet_mixed launch at J = 12, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), per (workload, form, sum);
 # a form whose kernel or launch shape changed since its capture has no entry.
-TRAFFIC_BYTES = {("large_256ant_15993600vis_50000comp", "fast", "regrouped"): 388835840 + 104449792}
+TRAFFIC_BYTES = {("large_256ant_15993600vis_50000comp", "fast", "regrouped"): 388_350_000 + 107_320_000}
 # Double-float form (WT_FP64_DF, regrouped Eq. 17), float32 FMA-pipe ops per
 # (vis, leaf): phase 32 (three double-float products of 5, two error-free
 # sums of 6, reduction 1, tail 4), sin/cos 135 (argument reduction 8, 2 pi f,

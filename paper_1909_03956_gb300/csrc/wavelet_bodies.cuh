@@ -561,34 +561,32 @@ struct Eq17WF {
         }
     }
 
-    // One step of the record sweep (GROUPS); returns the records it took. In
-    // the fast form a group (in one chunk by construction) is one step: its
-    // leaves in pairs, then the parent; a leaf marked as the first of a pair
-    // takes its sibling with it. The polynomial form takes every record
-    // alone: its four chains need more registers than the pairing saves
-    // (measured 2 % slower).
+    // One step of the fast form's grouped sweep; returns the records it took.
+    // A group (in one chunk by construction) is one step: its leaves in
+    // pairs, then the parent; a leaf marked as the first of a pair takes its
+    // sibling with it.
     __device__ __forceinline__ int at_grouped(const RecWF* cb, int r, int n)
     {
         const RecWF& a = cb[r];
-        if constexpr (FAST) {
-            const uint32_t meta = a.meta;
-            if (meta & kRwGroup) {
-                const int k = static_cast<int>((meta >> kRwGroupShift) & 7u);
-                if (k >= 1 && k <= 4 && r + k < n) {
-                    group(cb + r, k);
-                    return k + 1;
-                }
-            } else if ((meta & kRwPairFirst) && r + 1 < n) {
-                leaf_pair(a, cb[r + 1]);
-                return 2;
+        const uint32_t meta = a.meta;
+        if (meta & kRwGroup) {
+            const int k = static_cast<int>((meta >> kRwGroupShift) & 7u);
+            if (k >= 1 && k <= 4 && r + k < n) {
+                group(cb + r, k);
+                return k + 1;
             }
+        } else if ((meta & kRwPairFirst) && r + 1 < n) {
+            leaf_pair(a, cb[r + 1]);
+            return 2;
         }
         (*this)(a);
         return 1;
     }
 
-    // One record of a fixed-stride sweep (!GROUPS): the fast form's first
-    // leaf of a pair takes its sibling, the second is skipped.
+    // One record of a fixed-stride sweep: the fast form's first leaf of a
+    // pair takes its sibling, the second is skipped. The polynomial form
+    // takes every record alone: its four chains need more registers than the
+    // pairing saves (measured 2 % slower).
     __device__ __forceinline__ void at_single(const RecWF* cb, int r, int n)
     {
         const RecWF& a = cb[r];
@@ -601,9 +599,10 @@ struct Eq17WF {
         (*this)(a);
     }
 
+    // The polynomial form takes every record alone: a fixed stride.
     __device__ __forceinline__ auto at(const RecWF* cb, int r, int n)
     {
-        if constexpr (GROUPS) return at_grouped(cb, r, n);
+        if constexpr (GROUPS && FAST) return at_grouped(cb, r, n);
         else at_single(cb, r, n);
     }
 

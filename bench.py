@@ -562,14 +562,15 @@ OPS_DF_LEAF = 32 + 135 + 36 + 22
 OPS_DFT_DF = 32 + 135 + 36   # per (vis, component) of the double-float direct sum
 OPS_DF_NODE = 4 + 36 + 22
 # Direct sum (k_dft_mixed, two visibilities x two components per step), FMA-pipe
-# element ops per (visibility, component): phase 29, angle and SFU scaling 3
-# (fast) or polynomial sin/cos 15, the flux times (cos, sin) 2, half a Kahan
-# add of a pair of terms 4. float64 (k_dft_fp64), FP64-pipe instructions per
+# element ops per (visibility, component): phase 20 on the head grid (the
+# grid pass; the exact pass's 29 only for tiles beyond the grid's range),
+# angle and SFU scaling 3 (fast) or polynomial sin/cos 15, the flux times
+# (cos, sin) 2, half a Kahan add of a pair of terms 4. float64 (k_dft_fp64), FP64-pipe instructions per
 # term: phase 3, table reduction and polynomials 14, rotation by the table
 # entry 2 (+2 multiplies), multiply-add into V 2 -> 21 (roundings to integer
 # and the table load not counted).
-OPS_DFT_FAST = OPS_PHASE + 3 + 2 + 4
-OPS_DFT = OPS_PHASE + 15 + 2 + 4
+OPS_DFT_FAST = OPS_PHASE_GRID + 3 + 2 + 4
+OPS_DFT = OPS_PHASE_GRID + 15 + 2 + 4
 OPS_DFT_FP64 = 21
 # Algorithmic work per (visibility, component) of the direct sum: the phase
 # (3 multiplies, 2 adds), its reduction (rounding and subtraction), the

@@ -5,10 +5,14 @@
 // A prologue kernel packs each component once into a 32-byte record in a
 // scratch buffer: (l, m, n - 1, C) in float64 for WT_FP64, or double-float
 // halves of l, m, n - 1 and C for the other forms (the mixed forms use C's
-// high half only). The main kernel gives
+// high half only), and reduces the bounds max |l|, |m|, |n - 1| of the
+// float32 heads into a 16-byte block after the records. The main kernel gives
 // each thread one visibility (float64) or two (mixed, on packed float32
 // pairs) and streams the records through shared memory (bulk copies,
-// double-buffered, broadcast reads), like the wavelet kernels.
+// double-buffered, broadcast reads), like the wavelet kernels. The mixed
+// forms run a grid pass and an exact pass, as the regrouped wavelet sum does
+// (wt_internal.cuh): the phase heads on each visibility's common grid where
+// the bounds allow, else error-free sums.
 #include "df64.cuh"
 #include "staging.cuh"
 #include "wt_internal.cuh"
@@ -27,24 +31,42 @@ struct CompF {
 static_assert(sizeof(CompD) == 32 && sizeof(CompF) == 32, "component record layout");
 
 // n - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)), free of cancellation.
+// bound (float records only; zeroed before the launch): the largest |l|,
+// |m|, |n - 1| of the float32 heads as float bit patterns (non-negative
+// floats order as their bits), reduced per warp, then by atomicMax; a
+// component that fails the range check adds nothing.
 __global__ void k_pack_components(const double* __restrict__ l, const double* __restrict__ m,
                                   const double* __restrict__ flux, int64_t n, CompD* __restrict__ outd,
-                                  CompF* __restrict__ outf, int* status)
+                                  CompF* __restrict__ outf, uint32_t* __restrict__ bound, int* status)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double li = l[i], mi = m[i], fi = flux[i];
-    const double r2 = li * li + mi * mi;
-    double nm1 = 0.0;
-    if (!(r2 < 1.0) || !isfinite(li) || !isfinite(mi) || !isfinite(fi)) {
-        record_status(status, WT_ERR_RANGE);
-    } else {
-        nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+    uint32_t bl = 0, bm = 0, bn = 0;
+    if (i < n) {
+        const double li = l[i], mi = m[i], fi = flux[i];
+        const double r2 = li * li + mi * mi;
+        double nm1 = 0.0;
+        const bool good = r2 < 1.0 && isfinite(li) && isfinite(mi) && isfinite(fi);
+        if (!good) record_status(status, WT_ERR_RANGE);
+        else nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+        if (outd) outd[i] = CompD{li, mi, nm1, fi};
+        if (outf) {
+            const F2 a = split_f64(li), b = split_f64(mi), c = split_f64(nm1), f = split_f64(fi);
+            outf[i] = CompF{a.hi, a.lo, b.hi, b.lo, c.hi, c.lo, f.hi, f.lo};
+            if (good) {
+                bl = __float_as_uint(fabsf(a.hi));
+                bm = __float_as_uint(fabsf(b.hi));
+                bn = __float_as_uint(fabsf(c.hi));
+            }
+        }
     }
-    if (outd) outd[i] = CompD{li, mi, nm1, fi};
-    if (outf) {
-        const F2 a = split_f64(li), b = split_f64(mi), c = split_f64(nm1), f = split_f64(fi);
-        outf[i] = CompF{a.hi, a.lo, b.hi, b.lo, c.hi, c.lo, f.hi, f.lo};
+    if (!bound) return;
+    bl = __reduce_max_sync(0xffffffffu, bl);
+    bm = __reduce_max_sync(0xffffffffu, bm);
+    bn = __reduce_max_sync(0xffffffffu, bn);
+    if ((threadIdx.x & 31) == 0) {
+        if (bl) atomicMax(&bound[0], bl);
+        if (bm) atomicMax(&bound[1], bm);
+        if (bn) atomicMax(&bound[2], bn);
     }
 }
 
@@ -66,15 +88,19 @@ struct BodyD {
 // double-floats; each visibility's (cos, sin) comes out as its own pair; the
 // two components' terms of a visibility are added plainly, then into its
 // Kahan sum (one rounding more per two terms than one at a time).
-template <bool FAST>
+// GRID: the phases with their heads on the grids of Cg (phase_turns_grid2),
+// else with error-free sums (phase_turns_df2).
+template <bool FAST, bool GRID>
 struct BodyF2 {
     DF2 U, V, W;
+    float2 Cg;
     float2 acc[2], comp[2];
 
     __device__ __forceinline__ void terms(const CompF& c, float2& e0, float2& e1) const
     {
         float2 h, tl;
-        phase_turns_df2(U, V, W, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, h, tl);
+        if constexpr (GRID) phase_turns_grid2(U, V, W, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, Cg, h, tl);
+        else phase_turns_df2(U, V, W, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, h, tl);
         sincos_mixed2<FAST>(h, tl, e0, e1);
     }
 
@@ -170,8 +196,13 @@ __global__ void __launch_bounds__(NT) k_dft_fp64(const CompD* __restrict__ comps
     }
 }
 
-template <int NT, bool FAST>
+// GRIDPASS: the grid pass (every tile; a tile whose phases do not all fit
+// the head grid is swept too, its results discarded, and marked for the
+// exact pass); else the exact pass (only the marked tiles). bound: the
+// records' coordinate bounds (k_pack_components).
+template <int NT, bool FAST, bool GRIDPASS>
 __global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comps, int64_t n_comp,
+                                                  const uint32_t* __restrict__ bound,
                                                   const double* __restrict__ uvw, int64_t n_vis,
                                                   float2* __restrict__ vis, float sgn, int* status)
 {
@@ -180,17 +211,40 @@ __global__ void __launch_bounds__(NT) k_dft_mixed(const CompF* __restrict__ comp
     stager_setup(st, smem, comps, n_comp, kChunk);
     const int64_t ntiles = (n_vis + 2 * NT - 1) / (2 * NT);
     const double sg = static_cast<double>(sgn);       // sign folded into the baseline (exact)
+    float smax[3] = {0.f, 0.f, 0.f};
+    if constexpr (GRIDPASS) {
+        smax[0] = __uint_as_float(bound[0]);
+        smax[1] = __uint_as_float(bound[1]);
+        smax[2] = __uint_as_float(bound[2]);
+    }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        float2* first_vis = vis + tile * 2 * NT;
+        if constexpr (!GRIDPASS) {
+            if (!tile_deferred(first_vis)) continue;   // done by the grid pass
+        }
         const int64_t n0 = tile * 2 * NT + threadIdx.x, n1 = n0 + NT;
         const bool ok0 = n0 < n_vis, ok1 = n1 < n_vis;
-        BodyF2<FAST> b;
-        b.U = df2_pack(split_f64(ok0 ? sg * uvw[3 * n0] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1] : 0.0));
-        b.V = df2_pack(split_f64(ok0 ? sg * uvw[3 * n0 + 1] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1 + 1] : 0.0));
-        b.W = df2_pack(split_f64(ok0 ? sg * uvw[3 * n0 + 2] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1 + 2] : 0.0));
+        const F2 u[2] = {split_f64(ok0 ? sg * uvw[3 * n0] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1] : 0.0)};
+        const F2 v[2] = {split_f64(ok0 ? sg * uvw[3 * n0 + 1] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1 + 1] : 0.0)};
+        const F2 w[2] = {split_f64(ok0 ? sg * uvw[3 * n0 + 2] : 0.0), split_f64(ok1 ? sg * uvw[3 * n1 + 2] : 0.0)};
+        BodyF2<FAST, GRIDPASS> b;
+        bool defer = false;
+        if constexpr (GRIDPASS) {
+            float C[2];
+            defer = !tile_grid_constants<2>(u, v, w, smax, C);   // a CTA-wide decision
+            b.Cg = make_float2(C[0], C[1]);
+        }
+        b.U = df2_pack(u[0], u[1]);
+        b.V = df2_pack(v[0], v[1]);
+        b.W = df2_pack(w[0], w[1]);
         b.acc[0] = b.acc[1] = b.comp[0] = b.comp[1] = make_float2(0.f, 0.f);
         if (!st.sweep_at(b)) {
             if (threadIdx.x == 0) record_status(status, WT_ERR_TIMEOUT);
             return;
+        }
+        if (defer) {
+            mark_deferred(first_vis);
+            continue;
         }
         if (ok0) vis[n0] = sub2(b.acc[0], b.comp[0]);
         if (ok1) vis[n1] = sub2(b.acc[1], b.comp[1]);
@@ -214,11 +268,11 @@ int grid_for(K kernel, int threads, int nt, size_t smem, int64_t n_vis, dim3& gr
 }  // namespace
 
 // Launch the DFT on component records already packed in `scratch`
-// (n_comp records of 32 bytes, 256-byte aligned).
-int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, int64_t n_vis, void* vis, int mode,
-                      int sign, cudaStream_t s)
+// (n_comp records of 32 bytes, 256-byte aligned) with their coordinate
+// bounds at `bound` (mixed forms); errors go to `status`.
+int dft_launch_packed(const void* scratch, const uint32_t* bound, int64_t n_comp, const double* uvw, int64_t n_vis,
+                      void* vis, int mode, int sign, int* status, cudaStream_t s)
 {
-    int* status = device_status_word();
     dim3 grid;
     if (mode == WT_FP64) {
         constexpr int NT = 128;
@@ -237,26 +291,38 @@ int dft_launch_packed(const void* scratch, int64_t n_comp, const double* uvw, in
         k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(scratch), n_comp, uvw, n_vis, static_cast<double2*>(vis),
                                  static_cast<double>(sign), status);
     } else {
+        // the grid pass, then the exact pass over the tiles it left marked
         constexpr int NT = 256;
         const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
-        auto k = (mode == WT_MIXED_FAST) ? k_dft_mixed<NT, true> : k_dft_mixed<NT, false>;
-        int rc = grid_for(k, NT, 2 * NT, smem, n_vis, grid);   // two visibilities per thread
+        const bool fast = mode == WT_MIXED_FAST;
+        auto kg = fast ? k_dft_mixed<NT, true, true> : k_dft_mixed<NT, false, true>;
+        auto ke = fast ? k_dft_mixed<NT, true, false> : k_dft_mixed<NT, false, false>;
+        dim3 grid_e;
+        int rc = grid_for(kg, NT, 2 * NT, smem, n_vis, grid);   // two visibilities per thread
+        if (!rc) rc = grid_for(ke, NT, 2 * NT, smem, n_vis, grid_e);
         if (rc) return rc;
-        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(scratch), n_comp, uvw, n_vis, static_cast<float2*>(vis),
-                                 static_cast<float>(sign), status);
+        const CompF* recs = static_cast<const CompF*>(scratch);
+        float2* out = static_cast<float2*>(vis);
+        kg<<<grid, NT, smem, s>>>(recs, n_comp, bound, uvw, n_vis, out, static_cast<float>(sign), status);
+        WT_CUDA_TRY(cudaGetLastError());
+        ke<<<grid_e, NT, smem, s>>>(recs, n_comp, bound, uvw, n_vis, out, static_cast<float>(sign), status);
     }
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
 
-int dft_pack(const double* l, const double* m, const double* flux, int64_t n_comp, void* scratch, int mode,
-             cudaStream_t s)
+// Pack the components into `scratch` and, for the float forms, zero and
+// reduce their coordinate bounds at `bound` (16 bytes, 16-byte aligned).
+int dft_pack(const double* l, const double* m, const double* flux, int64_t n_comp, void* scratch, uint32_t* bound,
+             int mode, int* status, cudaStream_t s)
 {
+    const bool f64 = mode == WT_FP64;
+    if (!f64) WT_CUDA_TRY(cudaMemsetAsync(bound, 0, 4 * sizeof(uint32_t), s));
     if (n_comp == 0) return WT_OK;
     const int tb = 256;
     k_pack_components<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(
-        l, m, flux, n_comp, mode == WT_FP64 ? static_cast<CompD*>(scratch) : nullptr,
-        mode == WT_FP64 ? nullptr : static_cast<CompF*>(scratch), device_status_word());
+        l, m, flux, n_comp, f64 ? static_cast<CompD*>(scratch) : nullptr, f64 ? nullptr : static_cast<CompF*>(scratch),
+        f64 ? nullptr : bound, status);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
 }
@@ -265,8 +331,10 @@ int predict_dft(const double* l, const double* m, const double* flux, int64_t n_
                 int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s)
 {
     if (n_vis == 0) return WT_OK;
-    // 32-byte records, padded to a 16-byte multiple for the bulk copies
-    const size_t bytes = static_cast<size_t>((n_comp > 0 ? n_comp : 1) * 32 + 256);
+    // 32-byte records (a 16-byte multiple, as the bulk copies need), then
+    // the 16-byte block of coordinate bounds
+    const size_t rec_bytes = static_cast<size_t>(n_comp > 0 ? n_comp : 1) * 32;
+    const size_t bytes = rec_bytes + 256;
     void* scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
     if (e != cudaSuccess) {
@@ -274,8 +342,14 @@ int predict_dft(const double* l, const double* m, const double* flux, int64_t n_
         return set_error(WT_ERR_NOMEM, "dft_predict_vis: scratch allocation of %zu bytes failed: %s", bytes,
                          cudaGetErrorString(e));
     }
-    int rc = dft_pack(l, m, flux, n_comp, scratch, mode, s);
-    if (rc == WT_OK) rc = dft_launch_packed(scratch, n_comp, uvw, n_vis, vis, mode, sign, s);
+    uint32_t* bound = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(scratch) + rec_bytes);
+    int* status = device_status_word();
+    if (!status) {
+        cudaFreeAsync(scratch, s);
+        return set_error(WT_ERR_CUDA, "dft_predict_vis: no device status word");
+    }
+    int rc = dft_pack(l, m, flux, n_comp, scratch, bound, mode, status, s);
+    if (rc == WT_OK) rc = dft_launch_packed(scratch, bound, n_comp, uvw, n_vis, vis, mode, sign, status, s);
     cudaError_t ef = cudaFreeAsync(scratch, s);
     if (rc != WT_OK) return rc;
     if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync");
@@ -312,21 +386,24 @@ constexpr int64_t kNoAllocMaxComponents = 65536;   // 32-byte records: 2 MiB
 static_assert(sizeof(CompD) == 32 && sizeof(CompF) == 32, "record size assumed below");
 
 static __device__ __align__(256) unsigned char g_noalloc_records[kNoAllocMaxComponents * 32];
+// The records' coordinate bounds (the mixed forms' grid pass).
+static __device__ __align__(16) uint32_t g_noalloc_bound[4];
 // Where the kernels record errors when the caller passes no status word.
 static __device__ int g_noalloc_status_sink;
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64] = {nullptr};
+uint32_t* g_noalloc_bnd[64] = {nullptr};
 int* g_noalloc_sink[64] = {nullptr};
 uint64_t g_noalloc_ctx[64] = {0};   // context ID the addresses belong to
 
-// Device addresses of the two arrays above on the current device. The first
+// Device addresses of the three arrays above on the current device. The first
 // call on a device looks them up (cudaGetSymbolAddress, with that device
 // current), and so does the first call in a new context on it (after
 // cudaDeviceReset, say: the module is loaded again and the arrays may move);
 // in host code the names are only host-side stand-ins and must never be
 // handed to a kernel.
-int noalloc_addresses(void** records, int** sink)
+int noalloc_addresses(void** records, uint32_t** bound, int** sink)
 {
     int dev = 0;
     WT_CUDA_TRY(cudaGetDevice(&dev));
@@ -341,12 +418,17 @@ int noalloc_addresses(void** records, int** sink)
         void* q = nullptr;
         e = cudaGetSymbolAddress(&q, g_noalloc_status_sink);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_status_sink)");
-        if (!p || !q) return set_error(WT_ERR_CUDA, "cudaGetSymbolAddress returned a null address");
+        void* b = nullptr;
+        e = cudaGetSymbolAddress(&b, g_noalloc_bound);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_bound)");
+        if (!p || !q || !b) return set_error(WT_ERR_CUDA, "cudaGetSymbolAddress returned a null address");
         g_noalloc_addr[dev] = p;
+        g_noalloc_bnd[dev] = static_cast<uint32_t*>(b);
         g_noalloc_sink[dev] = static_cast<int*>(q);
         g_noalloc_ctx[dev] = ctx;
     }
     *records = g_noalloc_addr[dev];
+    *bound = g_noalloc_bnd[dev];
     *sink = g_noalloc_sink[dev];
     return WT_OK;
 }
@@ -379,43 +461,14 @@ extern "C" int dft_predict_vis_noalloc(const double* l, const double* m, const d
         (status && (rc = check_device_buffer(status, sizeof(int), fn, "status", 4))))
         return rc;
     void* records = nullptr;
+    uint32_t* bound = nullptr;
     int* sink = nullptr;
-    if ((rc = noalloc_addresses(&records, &sink))) return rc;
+    if ((rc = noalloc_addresses(&records, &bound, &sink))) return rc;
     if (!status) status = sink;
     if (n_vis == 0) return WT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (n_comp > 0) {
-        const int tb = 256;
-        k_pack_components<<<static_cast<unsigned>((n_comp + tb - 1) / tb), tb, 0, s>>>(
-            l, m, flux, n_comp, mode == WT_FP64 ? static_cast<CompD*>(records) : nullptr,
-            mode == WT_FP64 ? nullptr : static_cast<CompF*>(records), status);
-        WT_CUDA_TRY(cudaGetLastError());
-    }
-    dim3 grid;
-    if (mode == WT_FP64) {
-        constexpr int NT = 128;
-        const size_t smem = static_cast<size_t>(stager_bytes<CompD>(kChunk));
-        auto k = k_dft_fp64<NT>;
-        if ((rc = grid_for(k, NT, NT, smem, n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(static_cast<const CompD*>(records), n_comp, uvw, n_vis, static_cast<double2*>(vis_out),
-                                 static_cast<double>(sign), status);
-    } else if (mode == WT_FP64_DF) {
-        constexpr int NT = 128;
-        const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk)) + kDfTableEntries * sizeof(float4);
-        auto k = k_dft_df<NT>;
-        if ((rc = grid_for(k, NT, NT, smem, n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<double2*>(vis_out),
-                                 static_cast<double>(sign), status);
-    } else {
-        constexpr int NT = 256;
-        const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
-        auto k = (mode == WT_MIXED_FAST) ? k_dft_mixed<NT, true> : k_dft_mixed<NT, false>;
-        if ((rc = grid_for(k, NT, 2 * NT, smem, n_vis, grid))) return rc;   // two visibilities per thread
-        k<<<grid, NT, smem, s>>>(static_cast<const CompF*>(records), n_comp, uvw, n_vis, static_cast<float2*>(vis_out),
-                                 static_cast<float>(sign), status);
-    }
-    WT_CUDA_TRY(cudaGetLastError());
-    return WT_OK;
+    if ((rc = dft_pack(l, m, flux, n_comp, records, bound, mode, status, s))) return rc;
+    return dft_launch_packed(records, bound, n_comp, uvw, n_vis, vis_out, mode, sign, status, s);
 }
 
 // ===========================================================================

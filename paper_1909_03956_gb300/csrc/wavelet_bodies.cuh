@@ -707,33 +707,9 @@ struct Eq17WF {
     }
 };
 
-// The regrouped Eq. 17 in a mixed form is evaluated in two passes over the
-// tiles. The grid pass takes every tile whose phases all fit the head grid
-// (tile_grid_constants: all heads below 2^(kGridMaxK - 1) turns, which the
-// tree's coordinate bounds smax and each visibility's |u|, |v|, |w|
-// establish) and evaluates it with phase_turns_grid2; a tile that does not
-// fit gets kDeferredMark in both parts of its first visibility and is left
-// to the exact pass, which evaluates only tiles so marked, with error-free
-// sums (phase_turns_df2). The two kernels are launched back to back on one
-// stream; kept apart, each stays within its register budget.
-constexpr uint32_t kDeferredMark = 0x7fc4b1d3u;   // a quiet NaN
-
-// Grid constants of a thread's visibilities and the CTA's vote on whether
-// every visibility of the tile fits; every thread of the CTA must call it.
-template <int VPT>
-__device__ __forceinline__ bool tile_grid_constants(const F2 (&u)[VPT], const F2 (&v)[VPT], const F2 (&w)[VPT],
-                                                    const float* __restrict__ smax, float (&C)[VPT])
-{
-    const float sm[3] = {smax[0], smax[1], smax[2]};
-    bool fits = true;
-#pragma unroll
-    for (int k = 0; k < VPT; ++k) {
-        int kk;
-        C[k] = grid_magic(phase_bound(u[k], v[k], w[k], sm), kk);
-        fits = fits && kk <= kGridMaxK;
-    }
-    return __syncthreads_and(fits ? 1 : 0) != 0;
-}
+// The regrouped Eq. 17 in a mixed form runs in a grid pass and an exact
+// pass (the tile helpers in wt_internal.cuh: tile_grid_constants,
+// tile_deferred, mark_deferred).
 
 // One tile's sweep of the regrouped Eq. 17 (GRID: on the head grid of the
 // constants C, else with error-free sums; GROUPS as Eq17WF). Returns false
@@ -762,25 +738,6 @@ __device__ __forceinline__ bool sweep_regrouped_mixed(Stager<RecWF>& st, const F
     return good;
 }
 
-// The exact pass's test of a tile: whether its first visibility carries
-// kDeferredMark (read by one thread, broadcast through shared memory);
-// every thread of the CTA must call it.
-__device__ __forceinline__ bool tile_deferred(const float2* first_vis)
-{
-    __shared__ int s_deferred;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const volatile float* x = reinterpret_cast<const volatile float*>(first_vis);
-        s_deferred = __float_as_uint(x[0]) == kDeferredMark && __float_as_uint(x[1]) == kDeferredMark;
-    }
-    __syncthreads();
-    return s_deferred != 0;
-}
-
-__device__ __forceinline__ void mark_deferred(float2* first_vis)
-{
-    if (threadIdx.x == 0) *first_vis = make_float2(__uint_as_float(kDeferredMark), __uint_as_float(kDeferredMark));
-}
 
 }  // namespace
 }  // namespace wt

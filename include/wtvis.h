@@ -255,10 +255,13 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
  *
  * Nothing is allocated: the packed component records go to a fixed array in
  * the library's device image, WT_NOALLOC_MAX_COMPONENTS records of 32 bytes
- * (2 MiB), which every GPU that loads the library holds until the process
- * exits. n_comp above that limit returns WT_ERR_RANGE before anything is
- * enqueued.
- *   - The first call on a device looks up the array's device address with
+ * (2 MiB), and the mixed forms' coordinate bounds to a 16-byte one beside
+ * it, which every GPU that loads the library holds until the process exits.
+ * n_comp above that limit returns WT_ERR_RANGE before anything is enqueued.
+ * The call enqueues the pack kernel and the direct-sum kernel (the mixed
+ * forms: a memset of the bounds, then a grid pass and an exact pass, as
+ * dft_predict_vis does).
+ *   - The first call on a device looks up the arrays' device addresses with
  *     that device current, and so does the first call in a new context on
  *     that device (after cudaDeviceReset, say); make that first call before
  *     any stream capture.

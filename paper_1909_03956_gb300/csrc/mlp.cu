@@ -671,6 +671,7 @@ __global__ void k_level_records(const int64_t* __restrict__ key, const double* _
         view->n_nodes = n;
     }
     const double A = ldexp(kPi / 3.0, 2 * (1 - level));
+    uint32_t bu = 0, bv = 0, bw = 0;
     for (int64_t i = i0; i < n; i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         double c[3];
         pixel_dir(level, key[base + i], R, c);
@@ -685,6 +686,20 @@ __global__ void k_level_records(const int64_t* __restrict__ key, const double* _
         r.f = e.lo;
         r.g = static_cast<float>(A * lambda[base + i]);
         out[i] = r;
+        bu = max(bu, __float_as_uint(fabsf(a.hi)));
+        bv = max(bv, __float_as_uint(fabsf(b.hi)));
+        bw = max(bw, __float_as_uint(fabsf(e.hi)));
+    }
+    // the records' coordinate bounds for the grid pass (view->smax zeroed
+    // before the launch; non-negative floats order as their bits)
+    bu = __reduce_max_sync(0xffffffffu, bu);
+    bv = __reduce_max_sync(0xffffffffu, bv);
+    bw = __reduce_max_sync(0xffffffffu, bw);
+    if ((threadIdx.x & 31) == 0) {
+        uint32_t* sm = reinterpret_cast<uint32_t*>(view->smax);
+        if (bu) atomicMax(&sm[0], bu);
+        if (bv) atomicMax(&sm[1], bv);
+        if (bw) atomicMax(&sm[2], bw);
     }
 }
 
@@ -750,12 +765,14 @@ __global__ void __launch_bounds__(1024) k_threshold_records(const int64_t* __res
                                                             TreeHeader* __restrict__ views)
 {
     __shared__ int ws[32];
+    __shared__ uint32_t wb[3][32];
     for (int j = j0; j < J; ++j) {
         const int64_t n = hdr->per_level[j];
         const int64_t base = hdr->rev_offset[j];
         RecF* dst = out + seg.off[j + 1];
         const double q = __dmul_rn(ldexp(__dsqrt_rn(kPi / 3.0), 1 - j), 0.25);
         int64_t carry = 0;
+        uint32_t bu = 0, bv = 0, bw = 0;   // the level's coordinate bounds (float bits)
         for (int64_t start = 0; start < n; start += blockDim.x) {
             const int64_t i = start + threadIdx.x;
             double g[3] = {0.0, 0.0, 0.0};
@@ -791,13 +808,31 @@ __global__ void __launch_bounds__(1024) k_threshold_records(const int64_t* __res
                     r.f = e.lo;
                     r.g = static_cast<float>(q * ((h0 * g[0] + h1 * g[1]) + h2 * g[2]));
                     dst[4 * (carry + pos) + c] = r;
+                    bu = max(bu, __float_as_uint(fabsf(a.hi)));
+                    bv = max(bv, __float_as_uint(fabsf(b.hi)));
+                    bw = max(bw, __float_as_uint(fabsf(e.hi)));
                 }
             }
             carry += total;
         }
+        bu = __reduce_max_sync(0xffffffffu, bu);
+        bv = __reduce_max_sync(0xffffffffu, bv);
+        bw = __reduce_max_sync(0xffffffffu, bw);
+        if ((threadIdx.x & 31) == 0) {
+            wb[0][threadIdx.x >> 5] = bu;
+            wb[1][threadIdx.x >> 5] = bv;
+            wb[2][threadIdx.x >> 5] = bw;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            views[j + 1 - j0].n_leaves = 4 * carry;
-            views[j + 1 - j0].n_nodes = 4 * carry;
+            TreeHeader& vw = views[j + 1 - j0];
+            vw.n_leaves = 4 * carry;
+            vw.n_nodes = 4 * carry;
+            uint32_t m[3] = {0, 0, 0};
+            for (int k = 0; k < static_cast<int>(blockDim.x + 31) / 32; ++k)
+                for (int c = 0; c < 3; ++c) m[c] = max(m[c], wb[c][k]);
+            for (int c = 0; c < 3; ++c) vw.smax[c] = __uint_as_float(m[c]);
+            vw.smax[3] = 0.f;
         }
         __syncthreads();
     }
@@ -854,20 +889,27 @@ int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int d
     const size_t rec_bytes = ((static_cast<size_t>(cap) * sizeof(RecF)) + 255) & ~size_t(255);
     const size_t off_bytes = ((sizeof(double) * 3 * static_cast<size_t>(n_off)) + 255) & ~size_t(255);
     const size_t r_bytes = response == WT_RESPONSE_EXACT ? sizeof(double2) * static_cast<size_t>(n_vis) : 0;
+    const size_t hdr_bytes = (sizeof(TreeHeader) + 255) & ~size_t(255);
     char* scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), 256 + rec_bytes + off_bytes + r_bytes, s);
+    cudaError_t e =
+        cudaMallocAsync(reinterpret_cast<void**>(&scratch), hdr_bytes + rec_bytes + off_bytes + r_bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(WT_ERR_NOMEM, "%s: scratch allocation failed: %s", fn, cudaGetErrorString(e));
     }
     TreeHeader* view = reinterpret_cast<TreeHeader*>(scratch);
-    RecF* recs = reinterpret_cast<RecF*>(scratch + 256);
-    double* offs = reinterpret_cast<double*>(scratch + 256 + rec_bytes);
-    double2* resp = reinterpret_cast<double2*>(scratch + 256 + rec_bytes + off_bytes);
+    RecF* recs = reinterpret_cast<RecF*>(scratch + hdr_bytes);
+    double* offs = reinterpret_cast<double*>(scratch + hdr_bytes + rec_bytes);
+    double2* resp = reinterpret_cast<double2*>(scratch + hdr_bytes + rec_bytes + off_bytes);
     Rot R;
     rotation_matrix(t->ra0, t->dec0, R.r);
     int64_t blocks = (cap + 255) / 256;
     if (blocks > 4096) blocks = 4096;
+    if (cudaMemsetAsync(view->smax, 0, sizeof(view->smax), s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(scratch, s);
+        return set_error(WT_ERR_CUDA, "%s: clearing the bounds", fn);
+    }
     k_level_records<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t->d.key, t->d.lambda, t->d.hdr, level, R, recs,
                                                                   view, cap);
     rc = (cudaGetLastError() == cudaSuccess) ? WT_OK : set_error(WT_ERR_CUDA, "%s: level records launch", fn);
@@ -974,6 +1016,10 @@ int wt_predict_vis_thresholded(wt_tree t, int j0, double tau, int response, cons
     {
         int64_t blocks = (capl + 255) / 256;
         if (blocks > 4096) blocks = 4096;
+        if (cudaMemsetAsync(views->smax, 0, sizeof(views->smax), s) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(WT_ERR_CUDA, "%s: clearing the bounds", fn);
+        }
         k_level_records<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t->d.key, t->d.lambda, t->d.hdr, j0, R,
                                                                       recs + seg.off[j0], views, capl);
         if (j0 < J)

@@ -289,9 +289,11 @@ __global__ void __launch_bounds__(kLevelThreads) k_tree_levels(const uint64_t* _
         d.leaf_dir[3 * leaf + 0] = su;
         d.leaf_dir[3 * leaf + 1] = sv;
         d.leaf_dir[3 * leaf + 2] = sw1;
-        atomicMax(&s_smax[0], __float_as_uint(__double2float_ru(fabs(su))));
-        atomicMax(&s_smax[1], __float_as_uint(__double2float_ru(fabs(sv))));
-        atomicMax(&s_smax[2], __float_as_uint(__double2float_ru(fabs(sw1))));
+        // the float32 heads the records carry (split_f64), whose products
+        // the grid pass bounds
+        atomicMax(&s_smax[0], __float_as_uint(fabsf(split_f64(su).hi)));
+        atomicMax(&s_smax[1], __float_as_uint(fabsf(split_f64(sv).hi)));
+        atomicMax(&s_smax[2], __float_as_uint(fabsf(split_f64(sw1).hi)));
     }
     __syncthreads();
 

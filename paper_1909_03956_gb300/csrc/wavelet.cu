@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NT, (mixed_min_blocks<NT, VPT, SUM>())) k_wave
     const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if constexpr (SUM == 2 && !GRIDPASS) {
+        if constexpr (SUM != 0 && !GRIDPASS) {
             if (!tile_deferred(vis + tile * per_tile)) continue;   // done by the grid pass
         }
         const int64_t n0 = tile * per_tile + threadIdx.x;
@@ -220,16 +220,23 @@ __global__ void __launch_bounds__(NT, (mixed_min_blocks<NT, VPT, SUM>())) k_wave
         bool defer = false;   // a tile the grid pass leaves marked for the exact pass
         float vr[VPT], vi[VPT];
         if constexpr (SUM == 1) {
-            Eq16F<VPT, FAST> b;
+            // grid pass / exact pass as for the regrouped sum below
+            float C[VPT];
+            if constexpr (GRIDPASS) {
+                defer = !tile_grid_constants(U, V, W, hdr->smax, C);   // a CTA-wide decision
+            } else {
+#pragma unroll
+                for (int k = 0; k < VPT; ++k) C[k] = 0.f;
+            }
+            Eq16F2<VPT, FAST, GRIDPASS> b;
+            b.start(U, V, W, C);
+            good = st.sweep_at(b);
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
-                b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k];
-                b.vr[k] = 0.f; b.vi[k] = 0.f; b.cr[k] = 0.f; b.ci[k] = 0.f;
+                const float2 r = b.result(k);
+                vr[k] = r.x;
+                vi[k] = r.y;
             }
-            b.sgn = sgn;
-            good = st.sweep(b);
-#pragma unroll
-            for (int k = 0; k < VPT; ++k) { vr[k] = b.vr[k] - b.cr[k]; vi[k] = b.vi[k] - b.ci[k]; }
         } else if constexpr (SUM == 0) {
             Eq17F<NT, VPT, FAST> b;
 #pragma unroll
@@ -377,9 +384,15 @@ int run_mixed_form(const WaveletJob& jb, cudaStream_t s)
     float2* out = static_cast<float2*>(jb.vis);
     const float sg = static_cast<float>(jb.sign);
     if (jb.which == WT_SUM_EQ16) {
-        auto k = k_wavelet_mixed<NT, VPT, 1, RecF, FAST>;
-        if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+        // the grid pass, then the exact pass over the tiles it left marked
+        auto kg = k_wavelet_mixed<NT, VPT, 1, RecF, FAST, true>;
+        auto ke = k_wavelet_mixed<NT, VPT, 1, RecF, FAST, false>;
+        if ((rc = prepare(kg, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
+        dim3 grid_e;
+        if ((rc = prepare(ke, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid_e))) return rc;
+        kg<<<grid, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+        WT_CUDA_TRY(cudaGetLastError());
+        ke<<<grid_e, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else if (jb.which == WT_SUM_EQ17) {
         auto k = k_wavelet_mixed<NT, VPT, 0, RecF, FAST>;
         if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
@@ -486,12 +499,16 @@ int default_wavelet_variant(int mode, int which, int J)
     // measured on the medium and large workloads (J = 12): the explicit
     // mixed sum runs best at 256 x 1 (its stack limits the CTAs per SM), the
     // regrouped one, whose stack is small, at 64 x 4 (the per-record work
-    // shared by four visibilities), then 128 x 2
+    // shared by four visibilities), then 128 x 2; Eq. 16 (no stack) on packed
+    // pairs of visibilities at 128 x 2
     static const int order_mixed[kNumWaveletVariants] = {0, 2, 1, 3, 4, 5, 6, 7};
+    static const int order_mixed16[kNumWaveletVariants] = {2, 7, 3, 4, 0, 1, 5, 6};
     static const int order_mixed_rg[kNumWaveletVariants] = {4, 2, 7, 6, 3, 5, 0, 1};
     static const int order_fp64[kNumWaveletVariants] = {1, 0, 2, 3, 4, 5, 6, 7};
     const int* order = (mode == WT_FP64 || mode == WT_FP64_DF) ? order_fp64
-                       : (which == WT_SUM_EQ17_REGROUPED) ? order_mixed_rg : order_mixed;
+                       : (which == WT_SUM_EQ17_REGROUPED) ? order_mixed_rg
+                       : (which == WT_SUM_EQ16)           ? order_mixed16
+                                                          : order_mixed;
     for (int i = 0; i < kNumWaveletVariants; ++i)
         if (wavelet_variant_fits(order[i], mode, which, J)) return order[i];
     return kNumWaveletVariants - 1;

@@ -215,22 +215,83 @@ struct Eq17F {
     }
 };
 
-template <int VPT, bool FAST = false>
-struct Eq16F {
-    F2 u[VPT], v[VPT], w[VPT];
-    float vr[VPT], vi[VPT], cr[VPT], ci[VPT];
-    float sgn;
-    __device__ void operator()(const RecF& r)
+// Eq. 16 in the mixed forms on packed pairs: a thread's visibilities taken
+// two at a time (their phases against one leaf as one pair of double-floats,
+// each visibility's (cos, sin) its own pair) and the leaf records two at a
+// time (the second's term added plainly to the first's, then into the
+// Kahan sum, one rounding more per two terms); an odd last visibility of
+// the thread alone. GRID: the phases with their heads on each visibility's
+// grid (constants Cg / Cs, set by the caller; phase_turns_grid2), else with
+// error-free sums (phase_turns_df2).
+template <int VPT, bool FAST, bool GRID>
+struct Eq16F2 {
+    static constexpr int NP = VPT / 2;
+    static constexpr bool ODD = (VPT & 1) != 0;
+    DF2 U[NP > 0 ? NP : 1], V[NP > 0 ? NP : 1], W[NP > 0 ? NP : 1];
+    F2 us, vs, ws;                                    // the unpaired last visibility
+    float2 Cg[NP > 0 ? NP : 1];
+    float Cs;
+    float2 acc[VPT], comp[VPT];
+
+    __device__ __forceinline__ void start(const F2 (&u)[VPT], const F2 (&v)[VPT], const F2 (&w)[VPT],
+                                          const float (&C)[VPT])
     {
-        const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            U[p] = df2_pack(u[2 * p], u[2 * p + 1]);
+            V[p] = df2_pack(v[2 * p], v[2 * p + 1]);
+            W[p] = df2_pack(w[2 * p], w[2 * p + 1]);
+            Cg[p] = make_float2(C[2 * p], C[2 * p + 1]);
+        }
+        us = u[VPT - 1];
+        vs = v[VPT - 1];
+        ws = w[VPT - 1];
+        Cs = C[VPT - 1];
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-            float th, tl, s, c;
-            phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
-            sincos_mixed<FAST>(th, tl, s, c);
-            kahan_add(vr[k], cr[k], r.g * c);
-            kahan_add(vi[k], ci[k], r.g * s);
+            acc[k] = make_float2(0.f, 0.f);
+            comp[k] = make_float2(0.f, 0.f);
         }
+    }
+
+    __device__ __forceinline__ float2 result(int k) const { return sub2(acc[k], comp[k]); }
+
+    // One leaf's terms: e[k] = Phi exp(i 2 pi phase) of visibility k.
+    __device__ __forceinline__ void terms(const RecF& r, float2 (&e)[VPT]) const
+    {
+        const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
+        const float2 fl = bcast2(r.g);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float2 h, tl, e0, e1;
+            if constexpr (GRID) phase_turns_grid2(U[p], V[p], W[p], su, sv, sw, Cg[p], h, tl);
+            else phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
+            sincos_mixed2<FAST>(h, tl, e0, e1);
+            e[2 * p] = mul2(fl, e0);
+            e[2 * p + 1] = mul2(fl, e1);
+        }
+        if constexpr (ODD) {
+            float th, tl, sn, cs;
+            if constexpr (GRID) phase_turns_grid(us, vs, ws, su, sv, sw, Cs, th, tl);
+            else phase_turns_df(us, vs, ws, su, sv, sw, th, tl);
+            sincos_mixed<FAST>(th, tl, sn, cs);
+            e[VPT - 1] = mul2(fl, make_float2(cs, sn));
+        }
+    }
+
+    __device__ __forceinline__ void at(const RecF* cb, int r, int n)
+    {
+        if (r & 1) return;                             // taken with its even neighbour
+        float2 x[VPT];
+        terms(cb[r], x);
+        if (r + 1 < n) {                               // chunks hold an even count: only a list's
+            float2 y[VPT];                             // last leaf can be alone
+            terms(cb[r + 1], y);
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) x[k] = add2(x[k], y[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) kahan_add2(acc[k], comp[k], x[k]);
     }
 };
 

@@ -608,8 +608,8 @@ struct TreeHeader {
     int64_t n_nodes;
     int64_t per_level[kMaxJ + 1];   // [j] = nodes at level j (index 0 unused)
     int64_t rev_offset[kMaxJ + 2];  // start of level j in the level-J-first layout
-    float smax[4];                  // max over the leaves of |s_u|, |s_v|, |s_w - 1| (float32, rounded
-                                    // up; 0 for an empty tree); [3] unused
+    float smax[4];                  // max over the leaves of |s_u|, |s_v|, |s_w - 1| as the float32
+                                    // heads of their records (0 for an empty tree); [3] unused
 };
 
 struct TreeDev {

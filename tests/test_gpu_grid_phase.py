@@ -1,9 +1,10 @@
-"""The regrouped Eq. 17 in the mixed forms runs in two passes: the grid pass
+"""The regrouped Eq. 17 and Eq. 16 in the mixed forms run in two passes: the grid pass
 forms each leaf phase with its three head products rounded onto a common
 grid (exact float32 sums, valid while every head of the tile's visibilities
 stays below 2^14 turns), and the exact pass takes the tiles that do not fit,
 with error-free sums. These GPU tests hold both passes, and tiles of either
-kind side by side, to the mixed forms' bar against the oracle's Eq. 17.
+kind side by side, to the mixed forms' bar against the oracle's Eq. 17 and
+Eq. 16.
 """
 import numpy as np
 import pytest
@@ -31,12 +32,16 @@ def phase_bound(w, J, uvw):
     return np.abs(uvw) @ d
 
 
-def rel_err(w, J, uvw, mode, sign=1):
+def rel_err(w, J, uvw, mode, sign=1, which=wt.WT_SUM_EQ17_REGROUPED):
     t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, J)
-    v = wt.wt_predict_vis(t, dev(uvw), mode=mode, which=wt.WT_SUM_EQ17_REGROUPED, sign=sign).cpu().numpy()
-    ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J).vis_eq17(uvw, sign)
+    v = wt.wt_predict_vis(t, dev(uvw), mode=mode, which=which, sign=sign).cpu().numpy()
+    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+    ref = ot.vis_eq16(uvw, sign) if which == wt.WT_SUM_EQ16 else ot.vis_eq17(uvw, sign)
     t.close()
     return float(np.max(np.abs(v - ref)) / np.abs(w.flux).sum())
+
+
+SUMS = [wt.WT_SUM_EQ17_REGROUPED, wt.WT_SUM_EQ16]
 
 
 def long_baselines(n, lo, hi, rng):
@@ -50,20 +55,22 @@ def wide_sky(n, half_width_rad, rng):
     return l, m, 10.0 ** rng.uniform(-3, 0, n)
 
 
+@pytest.mark.parametrize("which", SUMS)
 @pytest.mark.parametrize("mode", MIXED)
-def test_every_tile_in_the_exact_pass(mode):
+def test_every_tile_in_the_exact_pass(mode, which):
     # 20 deg field and baselines to 6e4 wavelengths: heads of ~10^4 turns
     rng = np.random.default_rng(71)
     l, m, f = wide_sky(300, 0.35, rng)
     uvw = long_baselines(3000, 5e4, 7e4, rng)
     w = synth.Workload("wide", uvw, l, m, f, 10)
     assert phase_bound(w, 10, uvw).min() > 1.1 * GRID_LIMIT_TURNS
-    assert rel_err(w, 10, uvw, mode) <= TOLMIX
-    assert rel_err(w, 10, uvw[:1001], mode, sign=-1) <= TOLMIX
+    assert rel_err(w, 10, uvw, mode, which=which) <= TOLMIX
+    assert rel_err(w, 10, uvw[:1001], mode, sign=-1, which=which) <= TOLMIX
 
 
+@pytest.mark.parametrize("which", SUMS)
 @pytest.mark.parametrize("mode", MIXED)
-def test_grid_and_exact_tiles_side_by_side(mode):
+def test_grid_and_exact_tiles_side_by_side(mode, which):
     # short baselines everywhere except one visibility in every 700: tiles
     # of 256 that hold one go to the exact pass, the others stay on the grid
     rng = np.random.default_rng(72)
@@ -73,11 +80,12 @@ def test_grid_and_exact_tiles_side_by_side(mode):
     w = synth.Workload("mixed_tiles", uvw, l, m, f, 11)
     pb = phase_bound(w, 11, uvw)
     assert pb[::700].min() > 1.1 * GRID_LIMIT_TURNS and np.delete(pb, np.s_[::700]).max() < GRID_LIMIT_TURNS / 2
-    assert rel_err(w, 11, uvw, mode) <= TOLMIX
+    assert rel_err(w, 11, uvw, mode, which=which) <= TOLMIX
 
 
+@pytest.mark.parametrize("which", SUMS)
 @pytest.mark.parametrize("mode", MIXED)
-def test_grid_pass_just_below_its_limit(mode):
+def test_grid_pass_just_below_its_limit(mode, which):
     # heads up to just under 2^14 turns: the coarsest grid the pass uses
     rng = np.random.default_rng(73)
     l, m, f = wide_sky(150, 0.1, rng)
@@ -86,7 +94,7 @@ def test_grid_pass_just_below_its_limit(mode):
     pb = phase_bound(w, 12, uvw)
     uvw *= (0.97 * GRID_LIMIT_TURNS / pb)[:, None]
     assert phase_bound(w, 12, uvw).max() < GRID_LIMIT_TURNS
-    assert rel_err(w, 12, uvw, mode) <= TOLMIX
+    assert rel_err(w, 12, uvw, mode, which=which) <= TOLMIX
 
 
 def test_single_component_worst_case_both_passes():
@@ -98,7 +106,8 @@ def test_single_component_worst_case_both_passes():
         uvw = rng.uniform(-scale, scale, (20000, 3))
         w = synth.Workload("one", uvw, np.array([0.0123]), np.array([-0.0071]), np.array([1.0]), 14)
         for mode in MIXED:
-            assert rel_err(w, 14, uvw, mode) <= TOLMIX
+            for which in SUMS:
+                assert rel_err(w, 14, uvw, mode, which=which) <= TOLMIX
 
 
 def test_zero_and_tiny_baselines():

@@ -118,6 +118,24 @@ def test_truncation_gains_from_full_pixel_responses_at_equal_work():
     assert e_learn < 0.8 * e_snap, (e_learn, e_snap)
 
 
+@pytest.mark.parametrize("response", [wt.WT_RESPONSE_SNAPPED, wt.WT_RESPONSE_EXACT])
+def test_truncation_in_both_passes(response):
+    # a 20 deg field truncated at level 9 and baselines short everywhere but
+    # one visibility in every 600: the level nodes' own coordinate bounds
+    # decide which tiles take the grid pass and which the exact pass
+    rng = np.random.default_rng(41)
+    l, m_, f = rng.uniform(-0.35, 0.35, 400), rng.uniform(-0.35, 0.35, 400), 10.0 ** rng.uniform(-3, 0, 400)
+    uvw = rng.uniform(-2e3, 2e3, (5000, 3))
+    uvw[::600] = rng.uniform(5e4, 8e4, (len(uvw[::600]), 3)) * rng.choice([-1.0, 1.0], (len(uvw[::600]), 3))
+    J, jt, D = 12, 9, 3
+    t = wt.wt_build_tree(dev(l), dev(m_), dev(f), RA0, DEC0, J)
+    got = wt.wt_predict_vis_truncated(t, jt, dev(uvw), response=response, depth=D).cpu().numpy()
+    kind = "snapped" if response == wt.WT_RESPONSE_SNAPPED else "level"
+    ref = O.Tree(l, m_, f, RA0, DEC0, J).vis_truncated(jt, uvw, kind=kind, depth=D)
+    assert np.max(np.abs(got - ref)) <= TOLMIX * f.sum()
+    t.close()
+
+
 def test_truncation_arguments_rejected():
     w = synth.small()
     t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, 8)

@@ -818,11 +818,16 @@ def major_cycle_measurement(wt, torch, dev, stream, flush, n=2048, minor_iter=10
            "total_component_flux": float(flux.sum()), "true_flux": float(np.sum(w.flux)),
            "note": "5 000 components in 20 extended blobs: 3 000 Hogbom iterations take a fraction of the flux"}
     out["point_sources"] = major_cycle_points(wt, torch, dev, stream, flush, w, uvw, n, dl, J, gain)
+    # a wider spread, where the w term matters, imaged without it and with
+    # w-projection (64 planes)
+    out["point_sources_400px"] = major_cycle_points(wt, torch, dev, stream, flush, w, uvw, n, dl, J, gain, half=400)
+    out["point_sources_400px_wproj"] = major_cycle_points(wt, torch, dev, stream, flush, w, uvw, n, dl, J, gain,
+                                                          half=400, w_planes=64)
     return out
 
 
 def major_cycle_points(wt, torch, dev, stream, flush, w, uvw, n, dl, J, gain, n_src=100, minor_iter=1500,
-                       n_major=5, half=100, threshold=0.02):
+                       n_major=5, half=100, threshold=0.02, w_planes=0):
     """The same major cycle on a sky Hogbom can take apart: n_src point
     sources at pixel centres within `half` pixels of the phase centre,
     fluxes log-uniform in [0.1, 1] (seeded), observed through the medium
@@ -843,7 +848,8 @@ def major_cycle_points(wt, torch, dev, stream, flush, w, uvw, n, dl, J, gain, n_
     per = []
     for k in sorted({1, 3, n_major}):
         pix, flux, resid, img = wt.wt_clean(uvw, obs, n, dl, w.ra0, w.dec0, J, mode=wt.WT_MIXED_FAST, gain=gain,
-                                            threshold=threshold, minor_iter=minor_iter, n_major=k)
+                                            threshold=threshold, minor_iter=minor_iter, n_major=k,
+                                            w_planes=w_planes)
         torch.cuda.synchronize()
         fl = flux.double().cpu().numpy()
         on = np.isin(pix.cpu().numpy(), true_pix)
@@ -851,12 +857,11 @@ def major_cycle_points(wt, torch, dev, stream, flush, w, uvw, n, dl, J, gain, n_
                     "flux_on_true_pixels_frac": float(fl[on].sum() / f.sum()),
                     "residual_rms_over_data_rms": float(torch.sqrt(torch.mean(torch.abs(resid) ** 2))) / rms0})
     t_clean = _time_call(lambda: wt.wt_clean(uvw, obs, n, dl, w.ra0, w.dec0, J, mode=wt.WT_MIXED_FAST, gain=gain,
-                                             threshold=threshold, minor_iter=minor_iter, n_major=n_major),
-                         stream, flush, reps=1)
+                                             threshold=threshold, minor_iter=minor_iter, n_major=n_major,
+                                             w_planes=w_planes), stream, flush, reps=1)
     return {"sources": n_src, "half_width_pixels": half, "true_flux": float(f.sum()), "minor_iter": minor_iter,
-            "threshold": threshold, "n_major": n_major, "clean_ms": t_clean * 1e3, "by_major_cycle": per,
-            "note": "the floor of the residual is the imaging's: nearest-cell gridding without a gridding kernel "
-                    "and no w term (the prediction is exact)"}
+            "threshold": threshold, "n_major": n_major, "imaging": "w-projection, %d planes" % w_planes
+            if w_planes else "nearest cell, no w term", "clean_ms": t_clean * 1e3, "by_major_cycle": per}
 
 
 def mixed_measurement(wt, torch, dev, stream, flush):

@@ -315,6 +315,30 @@ int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid,
 int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis, int n, double dl, float* image,
                    void* stream);
 
+/* wt_dirty_image_w -- the w-corrected dirty image (the wide-field imaging of
+ * Sec. 3.6.2, which grids over w-planes with an anti-aliasing kernel and a
+ * w-kernel):
+ *   I(l, m) = (1/W) Re sum_entries V exp(-i 2 pi (u l + v m + w (n(l, m) - 1))),
+ * n(l, m) = sqrt(1 - l^2 - m^2), over each visibility and its conjugate at
+ * -B, W the number of entries gridded; the same geometry and normalisation
+ * as wt_dirty_image, which it equals at w = 0 up to the gridding
+ * approximation. Convolutional gridding: a Kaiser-Bessel kernel of width 7
+ * cells (the image divided by its Fourier transform afterwards) convolved
+ * with each plane's w-kernel, tabulated at 8 points per cell over a support
+ * of 2h + 1 cells (h from the field's largest chirp frequency, at most 32),
+ * for w_planes planes uniformly spaced in |w| over [0, w_max] and
+ * interpolated linearly in |w|. A visibility whose kernel support would
+ * leave the grid is left out (and not counted in W); |w| above w_max takes
+ * the last planes' extrapolation.
+ *   w_planes  2 .. 1024
+ *   w_max     the largest |w| to plan for; 0: the batch's own, found on the
+ *             device (this synchronises `stream`)
+ * WT_ERR_RANGE if the field n dl reaches beyond l^2 + m^2 < 1 or the kernel
+ * would need h > 32 or would not fit the grid. Allocates scratch on
+ * `stream` (the grid and the kernel tables, tens of MB) and releases it. */
+int wt_dirty_image_w(const double* uvw, const void* vis, int64_t n_vis, int n, double dl, int w_planes,
+                     double w_max, float* image, void* stream);
+
 /* wt_hogbom -- Eqs. 4-5: Hogbom clean of `image` in place. Each iteration
  * takes the pixel with the largest value C (ties: the first in row-major
  * order), records the component g C there, and subtracts g C times the beam
@@ -348,6 +372,10 @@ int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold
  * dirty image of the final residual visibilities in image_resid.
  *   vis_obs     device complex64 [n_vis]
  *   mode        WT_MIXED or WT_MIXED_FAST (the prediction's form)
+ *   w_planes    0: the images as wt_dirty_image (nearest cell, no w term);
+ *               2 .. 1024: as wt_dirty_image_w with that many w-planes over
+ *               the batch's largest |w| (found once: one more stream
+ *               synchronisation), the beam included
  *   comp_pix, comp_flux  device [minor_iter * n_major], as wt_hogbom,
  *               every cycle's components in order
  *   n_comp      HOST int32: the number of components found
@@ -359,7 +387,7 @@ int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold
 #define WT_PREDICT_TREE 0
 #define WT_PREDICT_DIRECT 1
 int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, int n, double dl, double ra0, double dec0,
-             int J, int predictor, int mode, float gain, float threshold, int minor_iter, int n_major,
+             int J, int predictor, int mode, float gain, float threshold, int minor_iter, int n_major, int w_planes,
              int* comp_pix, float* comp_flux, int* n_comp, void* vis_resid, float* image_resid, void* stream);
 
 /* ---------------------------------------------------------------------------

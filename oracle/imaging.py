@@ -31,6 +31,10 @@ design notes):
       threshold. The arithmetic is float32 (the precision the GPU decides
       the argmax in): the component flux fl(g C), the update
       fl(I - fl(f B)).
+  I5  The w-corrected dirty image (what w-projection gridding, Sec. 3.6.2's
+      wide-field imaging, approximates): I3 with each entry's exponent
+      carrying w (n(l, m) - 1), evaluated as a direct sum over the
+      visibilities (every visibility inside the grid, so W = 2 N).
 """
 from __future__ import annotations
 
@@ -87,6 +91,29 @@ def dirty_image(uvw, vis, n, dl):
 def dirty_beam(uvw, n, dl):
     """The PSF: the dirty image of unit visibilities."""
     return dirty_image(uvw, np.ones(len(uvw), dtype=np.complex128), n, dl)
+
+
+def dirty_image_exact(uvw, vis, n, dl, ix, iy):
+    """The w-corrected dirty image at pixels (ix, iy) by its definition
+    (reading I5): the direct sum over the visibilities and their Hermitian
+    conjugates of V exp(-i 2 pi (u l + v m + w (n(l, m) - 1))), real part,
+    over W = 2 N entries, n(l, m) = sqrt(1 - l^2 - m^2): the image w-
+    projection gridding approximates. A point source of flux C observed as
+    V = C exp(i 2 pi B.(l0, m0, n0 - 1)) gives I = C at (l0, m0) for any w."""
+    uvw = np.asarray(uvw, dtype=np.float64)
+    vis = np.asarray(vis, dtype=np.complex128)
+    ix = np.atleast_1d(np.asarray(ix))
+    iy = np.atleast_1d(np.asarray(iy))
+    l = (ix - n // 2) * dl
+    m = (iy - n // 2) * dl
+    r2 = l * l + m * m
+    nm1 = -r2 / (1.0 + np.sqrt(1.0 - r2))             # n - 1 without cancellation
+    s = np.stack([l, m, nm1], axis=1)                 # [pixel][3]
+    out = np.zeros(len(l))
+    for k0 in range(0, len(uvw), 4096):               # chunks of visibilities
+        ph = uvw[k0:k0 + 4096] @ s.T                  # [vis][pixel]
+        out += (vis[k0:k0 + 4096, None] * np.exp(-2j * np.pi * ph)).real.sum(axis=0)
+    return out / len(uvw) if len(uvw) else out
 
 
 def hogbom(image, psf, gain, max_iter, threshold):

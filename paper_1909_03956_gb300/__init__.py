@@ -49,6 +49,7 @@ EXPORTS = [
     "wt_xref_table", "wt_build_tree_xref", "wt_measure_pipe_rates",
     "wt_selftest_context_reset", "wt_predict_vis_truncated",
     "wt_predict_vis_thresholded", "wt_tree_import", "wt_mlp_get_state", "wt_mlp_set_state", "wt_mlp_train_range",
+    "wt_dirty_image_w",
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
@@ -118,9 +119,10 @@ def _declare(L):
     L.wt_selftest_context_reset.argtypes = []
     L.wt_last_error.restype = C.c_char_p
     L.wt_dirty_image.argtypes = [vp, vp, i64, C.c_int, d, vp, vp]
+    L.wt_dirty_image_w.argtypes = [vp, vp, i64, C.c_int, d, C.c_int, d, vp, vp]
     L.wt_hogbom.argtypes = [vp, vp, C.c_int, f, f, C.c_int, vp, vp, vp, vp]
     L.wt_clean.argtypes = [vp, vp, i64, C.c_int, d, d, d, C.c_int, C.c_int, C.c_int, f, f, C.c_int, C.c_int,
-                           vp, vp, C.POINTER(C.c_int), vp, vp, vp]
+                           C.c_int, vp, vp, C.POINTER(C.c_int), vp, vp, vp]
 
 
 def _check(rc):
@@ -493,6 +495,19 @@ def wt_dirty_image(uvw, vis, n, dl, out=None, stream=None):
     return out
 
 
+def wt_dirty_image_w(uvw, vis, n, dl, w_planes=128, w_max=0.0, out=None, stream=None):
+    """w-corrected dirty image (float32 [n][n]) by w-projection gridding, or
+    the dirty beam when vis is None (Sec. 3.6.2's wide-field imaging);
+    w_max = 0 plans for the batch's own largest |w| (synchronises)."""
+    import torch
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float32, device=uvw.device)
+    v = _dev(vis, torch.complex64) if vis is not None else C.c_void_p(0)
+    _check(load().wt_dirty_image_w(_dev(uvw, torch.float64), v, uvw.shape[0], int(n), float(dl), int(w_planes),
+                                   float(w_max), _dev(out, torch.float32), _stream(stream)))
+    return out
+
+
 def wt_hogbom(image, psf, gain, max_iter, threshold=0.0, stream=None):
     """Hogbom clean of `image` (float32 [n][n], cleaned in place) with the
     beam `psf`; returns (pixels int32, fluxes float32) of the components."""
@@ -509,8 +524,9 @@ def wt_hogbom(image, psf, gain, max_iter, threshold=0.0, stream=None):
 
 
 def wt_clean(uvw, vis_obs, n, dl, ra0, dec0, J, predictor=WT_PREDICT_TREE, mode=WT_MIXED_FAST, gain=0.1,
-             threshold=0.0, minor_iter=100, n_major=3, stream=None):
-    """Cotton-Schwab major cycles with the tree (or direct-sum) prediction;
+             threshold=0.0, minor_iter=100, n_major=3, w_planes=0, stream=None):
+    """Cotton-Schwab major cycles with the tree (or direct-sum) prediction,
+    imaging by nearest-cell gridding (w_planes = 0) or w-projection;
     returns (pixels, fluxes, residual visibilities, residual image)."""
     import torch
     n_vis = uvw.shape[0]
@@ -522,6 +538,7 @@ def wt_clean(uvw, vis_obs, n, dl, ra0, dec0, J, predictor=WT_PREDICT_TREE, mode=
     cnt = C.c_int(0)
     _check(load().wt_clean(_dev(uvw, torch.float64), _dev(vis_obs, torch.complex64), n_vis, int(n), float(dl),
                            float(ra0), float(dec0), int(J), int(predictor), int(mode), float(gain), float(threshold),
-                           int(minor_iter), int(n_major), _dev(pix, torch.int32), _dev(flux, torch.float32),
+                           int(minor_iter), int(n_major), int(w_planes), _dev(pix, torch.int32),
+                           _dev(flux, torch.float32),
                            C.byref(cnt), _dev(resid, torch.complex64), _dev(img, torch.float32), _stream(stream)))
     return pix[:cnt.value], flux[:cnt.value], resid, img

@@ -166,6 +166,233 @@ __global__ void k_image_from_fft(const float2* __restrict__ f, int n, const unsi
     }
 }
 
+// ---------------------------------------------------------------- w-projection
+// The w-corrected dirty image (the wide-field imaging of Sec. 3.6.2, which
+// grids with an anti-aliasing kernel and a w-kernel over w-planes):
+//   I(l, m) = (1/W) Re sum_entries V exp(-i 2 pi (u l + v m + w (n(l, m) - 1))),
+// approximated by convolutional gridding. In image units t = l / (n dl),
+// s = m / (n dl) (the field is |t|, |s| < 1/2) and uv units of cells
+// x = u / du, the kernel of a plane at w is
+//   K_w(x, y) = int int c(t) c(s) exp(-i 2 pi w (n - 1)) exp(i 2 pi (x t + y s)) dt ds
+// over the field, c the Fourier transform of a Kaiser-Bessel kernel of
+// width kWpWidth cells (closed form, c(0) = 1); summed over all cells,
+// sum_x K_w(x - x_k) exp(-i 2 pi x t) = c(t) exp(-i 2 pi w (n - 1)) exp(-i 2 pi x_k t)
+// inside the field, so the transformed grid divided by c(t) c(s) is the
+// image above. K_w is tabulated at kWpOversample points per cell over the
+// support S = 2h + 1 cells (h from the largest chirp frequency of the field
+// and the Kaiser-Bessel half-width) for planes uniformly spaced in |w|,
+// from a midpoint sum over kWpSamples^2 points of the field (two complex
+// matrix products per plane), and interpolated linearly in |w| between the
+// two nearest planes; an entry at w < 0 takes conj(K_|w|(-x, -y)). Each
+// entry is spread over the support its own |w| needs (the same rule at that
+// |w|), not the table's.
+constexpr int kWpWidth = 7;             // Kaiser-Bessel width (cells)
+constexpr double kWpBeta = 16.25;       // its shape parameter
+constexpr int kWpOversample = 8;        // table points per cell
+constexpr int kWpSamples = 128;         // field samples per axis for the kernels
+constexpr int kWpMaxHalf = 32;          // largest half-support h (cells)
+
+// c(t) / c(0) for the Kaiser-Bessel kernel of width W and shape beta: the
+// kernel's Fourier transform, sinh(sqrt(beta^2 - (pi W t)^2)) / sqrt(...),
+// or sin(...) / ... past the zero of the root.
+__host__ __device__ inline double kb_taper(double t)
+{
+    const double a = kWpBeta * kWpBeta - (kPi * kWpWidth * t) * (kPi * kWpWidth * t);
+    const double c0 = sinh(kWpBeta) / kWpBeta;
+    if (a > 0.0) {
+        const double r = sqrt(a);
+        return (sinh(r) / r) / c0;
+    }
+    if (a < 0.0) {
+        const double r = sqrt(-a);
+        return (sin(r) / r) / c0;
+    }
+    return 1.0 / c0;
+}
+
+struct WpPlan {
+    int P;          // planes
+    int h, S, T;    // half-support, support (cells), table points per axis (S * oversample + 1)
+    double dw;      // plane spacing in |w|
+    double ndl;     // n dl: the field width (radians)
+    double xc_per_w;   // the field's largest chirp frequency (cells) per unit |w|
+};
+
+// f[p][q][r] = c(t_q) c(t_r) exp(-i 2 pi w_p (n - 1)) at the field's sample
+// points t = (q + 1/2)/M - 1/2 (float64 phase reduced modulo 1).
+__global__ void k_wp_field(WpPlan pl, float2* __restrict__ f)
+{
+    const int M = kWpSamples;
+    const int64_t total = static_cast<int64_t>(pl.P) * M * M;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int r = static_cast<int>(i % M), q = static_cast<int>((i / M) % M), p = static_cast<int>(i / (M * M));
+        const double tq = (q + 0.5) / M - 0.5, tr = (r + 0.5) / M - 0.5;
+        const double l = tq * pl.ndl, m = tr * pl.ndl;
+        const double r2 = l * l + m * m;
+        const double nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+        double ph = -(p * pl.dw) * nm1;                // turns
+        ph -= rint(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        const double c = kb_taper(tq) * kb_taper(tr);
+        f[i] = make_float2(static_cast<float>(c * cs), static_cast<float>(c * sn));
+    }
+}
+
+// tw[j][q] = exp(i 2 pi x_j t_q), x_j = j / oversample - (h + 1/2).
+__global__ void k_wp_twiddles(WpPlan pl, float2* __restrict__ tw)
+{
+    const int M = kWpSamples;
+    const int total = pl.T * M;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int q = i % M, j = i / M;
+        const double x = static_cast<double>(j) / kWpOversample - (pl.h + 0.5);
+        const double t = (q + 0.5) / M - 0.5;
+        double ph = x * t;
+        ph -= rint(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        tw[i] = make_float2(static_cast<float>(cs), static_cast<float>(sn));
+    }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// a[p][q][j] = sum_r f[p][q][r] tw[j][r]: one CTA per (p, q), threads over j.
+__global__ void k_wp_stage1(WpPlan pl, const float2* __restrict__ f, const float2* __restrict__ tw,
+                            float2* __restrict__ a)
+{
+    const int M = kWpSamples;
+    __shared__ float2 row[kWpSamples];
+    const int64_t pq = blockIdx.x;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) row[r] = f[pq * M + r];
+    __syncthreads();
+    for (int j = threadIdx.x; j < pl.T; j += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* t = tw + static_cast<int64_t>(j) * M;
+        for (int r = 0; r < M; ++r) {
+            const float2 b = cmul(row[r], t[r]);
+            acc.x += b.x;
+            acc.y += b.y;
+        }
+        a[pq * pl.T + j] = acc;
+    }
+}
+
+// K[p][i][j] = (1/M^2) sum_q tw[i][q] a[p][q][j]: one CTA per (p, i).
+__global__ void k_wp_stage2(WpPlan pl, const float2* __restrict__ a, const float2* __restrict__ tw,
+                            float2* __restrict__ K)
+{
+    const int M = kWpSamples;
+    __shared__ float2 col[kWpSamples];
+    const int p = blockIdx.x / pl.T, i = blockIdx.x % pl.T;
+    for (int q = threadIdx.x; q < M; q += blockDim.x) col[q] = tw[static_cast<int64_t>(i) * M + q];
+    __syncthreads();
+    const float inv = 1.0f / (static_cast<float>(M) * static_cast<float>(M));
+    for (int j = threadIdx.x; j < pl.T; j += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* ap = a + (static_cast<int64_t>(p) * M) * pl.T + j;
+        for (int q = 0; q < M; ++q) {
+            const float2 b = cmul(col[q], ap[static_cast<int64_t>(q) * pl.T]);
+            acc.x += b.x;
+            acc.y += b.y;
+        }
+        K[(static_cast<int64_t>(p) * pl.T + i) * pl.T + j] = make_float2(acc.x * inv, acc.y * inv);
+    }
+}
+
+// One entry (V at x, y cells and w) into the grid by a warp, lanes over the
+// S x S taps; false if its support leaves the grid (the entry is dropped).
+__device__ __forceinline__ bool wp_entry(const WpPlan& pl, const float2* __restrict__ K, float2 V, double x,
+                                         double y, double w, int n, float2* __restrict__ grid, int lane)
+{
+    const double icd = rint(x), jcd = rint(y);
+    const int half = n / 2;
+    const double lo = -half + pl.h + 1, hi = half - pl.h - 1;
+    if (!(icd >= lo && icd <= hi && jcd >= lo && jcd <= hi && fabs(w) <= 1e30))   // false for NaN too
+        return false;
+    const int ic = static_cast<int>(icd), jc = static_cast<int>(jcd);
+    const float fx = static_cast<float>(x - icd), fy = static_cast<float>(y - jcd);
+    const bool neg = w < 0.0;
+    double pw = fabs(w) / pl.dw;
+    int p0 = static_cast<int>(floor(pw));
+    if (p0 > pl.P - 2) p0 = pl.P - 2;
+    if (p0 < 0) p0 = 0;
+    const float a = static_cast<float>(fmin(fmax(pw - p0, 0.0), 1.0));
+    const int last = pl.S * kWpOversample;                         // the table's last index
+    const float2* K0 = K + static_cast<int64_t>(p0) * pl.T * pl.T;
+    const float2* K1 = K0 + static_cast<int64_t>(pl.T) * pl.T;
+    // this entry's own support: the Kaiser-Bessel half-width and the chirp
+    // frequency of its |w| (the kernel is negligible beyond), within the table's
+    int he = static_cast<int>(ceil(0.5 * kWpWidth + pl.xc_per_w * fabs(w))) + 1;
+    he = he < pl.h ? he : pl.h;
+    const int Se = 2 * he + 1;
+    const int taps = Se * Se;
+    for (int t = lane; t < taps; t += 32) {
+        const int dx = t % Se - he, dy = t / Se - he;
+        int ix = __float2int_rn((static_cast<float>(dx) - fx + pl.h + 0.5f) * kWpOversample);
+        int iy = __float2int_rn((static_cast<float>(dy) - fy + pl.h + 0.5f) * kWpOversample);
+        ix = min(max(ix, 0), last);
+        iy = min(max(iy, 0), last);
+        if (neg) {                                                 // conj(K_|w|(-x, -y))
+            ix = last - ix;
+            iy = last - iy;
+        }
+        const int64_t off = static_cast<int64_t>(ix) * pl.T + iy;  // table [x][y]
+        const float2 k0 = K0[off], k1 = K1[off];
+        float2 k = make_float2(fmaf(a, k1.x - k0.x, k0.x), fmaf(a, k1.y - k0.y, k0.y));
+        if (neg) k.y = -k.y;
+        const int iu = ic + dx + half, iv = jc + dy + half;
+        const float sg = ((iu + iv) & 1) ? -1.0f : 1.0f;            // the index shift (-1)^(iu+iv)
+        const float2 e = cmul(V, k);
+        float* g = reinterpret_cast<float*>(grid + static_cast<int64_t>(iv) * n + iu);
+        atomicAdd(g, sg * e.x);
+        atomicAdd(g + 1, sg * e.y);
+    }
+    return true;
+}
+
+// A warp per visibility: the visibility (unit value if vis is null) and its
+// conjugate at -B; counts the entries gridded.
+__global__ void k_grid_wproj(WpPlan pl, const float2* __restrict__ K, const double* __restrict__ uvw,
+                             const float2* __restrict__ vis, int64_t n_vis, int n, double inv_du,
+                             float2* __restrict__ grid, unsigned long long* __restrict__ count)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+    unsigned long long mine = 0;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); k < n_vis;
+         k += warps) {
+        const double x = uvw[3 * k] * inv_du, y = uvw[3 * k + 1] * inv_du, w = uvw[3 * k + 2];
+        const float2 V = vis ? vis[k] : make_float2(1.0f, 0.0f);
+        const bool in = wp_entry(pl, K, V, x, y, w, n, grid, lane);
+        if (in) wp_entry(pl, K, make_float2(V.x, -V.y), -x, -y, -w, n, grid, lane);
+        if (in && lane == 0) mine += 2;
+    }
+    if (lane == 0 && mine) atomicAdd(count, mine);
+}
+
+// Real part of the transformed grid, times (-1)^(ix+iy) / (W c(t) c(s)).
+__global__ void k_image_from_fft_wp(const float2* __restrict__ f, int n, const unsigned long long* __restrict__ count,
+                                    float* __restrict__ image)
+{
+    const unsigned long long W = *count;
+    const double inv = W ? 1.0 / static_cast<double>(W) : 0.0;
+    for (int iy = blockIdx.x; iy < n; iy += gridDim.x) {
+        const int64_t row = static_cast<int64_t>(iy) * n;
+        const double cy = kb_taper(static_cast<double>(iy - n / 2) / n);
+        for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+            const float sg = ((ix + iy) & 1) ? -1.0f : 1.0f;
+            const double c = kb_taper(static_cast<double>(ix - n / 2) / n) * cy;
+            image[row + ix] = static_cast<float>(sg * f[row + ix].x * inv / c);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- Hogbom
 struct HogbomState {
     unsigned long long key;   // (ordered value << 32) | (0xffffffff - pixel) of the current maximum
@@ -710,6 +937,149 @@ extern "C" int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis,
     return WT_OK;
 }
 
+namespace wt {
+namespace {
+
+// The largest |w| of the visibilities as float64 bits (non-negative doubles
+// order as their bits); *out zeroed before the launch.
+__global__ void k_max_abs_w(const double* __restrict__ uvw, int64_t n_vis, unsigned long long* __restrict__ out)
+{
+    unsigned long long m = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_vis;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double w = fabs(uvw[3 * i + 2]);
+        if (isfinite(w)) {
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
+            m = b > m ? b : m;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// The batch's largest finite |w| (1 if none is above 0); synchronises s.
+int max_abs_w(const double* uvw, int64_t n_vis, cudaStream_t s, double* out)
+{
+    unsigned long long* d = nullptr;
+    WT_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(unsigned long long), s));
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && n_vis > 0) {
+        int64_t b = (n_vis + 255) / 256;
+        if (b > 4096) b = 4096;
+        k_max_abs_w<<<static_cast<unsigned>(b), 256, 0, s>>>(uvw, n_vis, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    if (e != cudaSuccess) return cuda_error(e, "the largest |w|");
+    double wm;
+    memcpy(&wm, &h, sizeof(wm));
+    *out = wm > 0.0 ? wm : 1.0;
+    return WT_OK;
+}
+
+int dirty_image_w(const double* uvw, const float2* vis, int64_t n_vis, int n, double dl, int planes, double w_max,
+                  float* image, cudaStream_t s)
+{
+    const char* fn = "wt_dirty_image_w";
+    const double ndl = n * dl;
+    if (!(ndl * ndl < 1.0)) return set_error(WT_ERR_RANGE, "%s: the field (n dl = %g) must lie inside l^2 + m^2 < 1", fn, ndl);
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    if (w_max <= 0.0) {   // the batch's own largest |w|
+        const int rc = max_abs_w(uvw, n_vis, s, &w_max);
+        if (rc) return rc;
+    }
+    WpPlan pl;
+    pl.P = planes;
+    pl.dw = w_max / (planes - 1);
+    pl.ndl = ndl;
+    // the largest chirp frequency of the field in cells: w (n dl)^2 / (2 n) at its corner
+    const double n_min = sqrt(1.0 - 0.5 * ndl * ndl);
+    pl.xc_per_w = ndl * ndl / (2.0 * n_min);
+    const double xc = w_max * pl.xc_per_w;
+    pl.h = static_cast<int>(ceil(0.5 * kWpWidth + xc)) + 1;
+    if (pl.h > kWpMaxHalf)
+        return set_error(WT_ERR_RANGE, "%s: w up to %g needs a kernel half-width of %d cells (at most %d)", fn, w_max,
+                         pl.h, kWpMaxHalf);
+    if (2 * pl.h + 2 >= n / 2) return set_error(WT_ERR_RANGE, "%s: a %d-cell kernel does not fit an n = %d grid", fn,
+                                                2 * pl.h + 1, n);
+    pl.S = 2 * pl.h + 1;
+    pl.T = pl.S * kWpOversample + 1;
+    const int M = kWpSamples;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_grid = up(nn * sizeof(float2)), b_cnt = 256;
+    const size_t b_f = up(static_cast<size_t>(planes) * M * M * sizeof(float2));
+    const size_t b_tw = up(static_cast<size_t>(pl.T) * M * sizeof(float2));
+    const size_t b_a = up(static_cast<size_t>(planes) * M * pl.T * sizeof(float2));
+    const size_t b_k = up(static_cast<size_t>(planes) * pl.T * pl.T * sizeof(float2));
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), b_grid + b_cnt + b_f + b_tw + b_a + b_k, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "%s: scratch allocation failed: %s", fn, cudaGetErrorString(e));
+    }
+    float2* grid = reinterpret_cast<float2*>(scratch);
+    unsigned long long* count = reinterpret_cast<unsigned long long*>(scratch + b_grid);
+    float2* f = reinterpret_cast<float2*>(scratch + b_grid + b_cnt);
+    float2* tw = reinterpret_cast<float2*>(scratch + b_grid + b_cnt + b_f);
+    float2* a = reinterpret_cast<float2*>(scratch + b_grid + b_cnt + b_f + b_tw);
+    float2* K = reinterpret_cast<float2*>(scratch + b_grid + b_cnt + b_f + b_tw + b_a);
+    int rc = WT_OK;
+    const int64_t nf = static_cast<int64_t>(planes) * M * M;
+    k_wp_field<<<static_cast<unsigned>(std::min<int64_t>((nf + 255) / 256, 8192)), 256, 0, s>>>(pl, f);
+    k_wp_twiddles<<<(pl.T * M + 255) / 256, 256, 0, s>>>(pl, tw);
+    k_wp_stage1<<<static_cast<unsigned>(planes * M), 128, 0, s>>>(pl, f, tw, a);
+    k_wp_stage2<<<static_cast<unsigned>(planes * pl.T), 128, 0, s>>>(pl, a, tw, K);
+    if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: kernel tables", fn);
+    if (rc == WT_OK && (cudaMemsetAsync(grid, 0, static_cast<size_t>(nn) * sizeof(float2), s) != cudaSuccess ||
+                        cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess))
+        rc = set_error(WT_ERR_CUDA, "%s: clearing the grid", fn);
+    if (rc == WT_OK && n_vis > 0) {
+        int64_t b = (n_vis + 7) / 8;                   // 8 warps per CTA, a warp per visibility
+        const int64_t cap = static_cast<int64_t>(num_sms()) * 32;
+        if (b > cap) b = cap;
+        k_grid_wproj<<<static_cast<unsigned>(b), 256, 0, s>>>(pl, K, uvw, vis, n_vis, n, ndl, grid, count);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: gridding launch", fn);
+    }
+    if (rc == WT_OK) rc = fft2_forward(grid, n, s);
+    if (rc == WT_OK) {
+        k_image_from_fft_wp<<<rows_blocks(n), kImgThreads, 0, s>>>(grid, n, count, image);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: image launch", fn);
+    }
+    const cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (rc) return rc;
+    if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync");
+    return WT_OK;
+}
+
+}  // namespace
+}  // namespace wt
+
+extern "C" int wt_dirty_image_w(const double* uvw, const void* vis, int64_t n_vis, int n, double dl, int w_planes,
+                                double w_max, float* image, void* stream)
+{
+    using namespace wt;
+    const char* fn = "wt_dirty_image_w";
+    int rc = check_image_args(fn, n, dl);
+    if (rc) return rc;
+    if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
+    if (w_planes < 2 || w_planes > 1024) return set_error(WT_ERR_ARG, "%s: w_planes = %d must be 2..1024", fn, w_planes);
+    if (!(w_max >= 0.0) || !isfinite(w_max)) return set_error(WT_ERR_ARG, "%s: w_max must be finite and >= 0", fn);
+    const size_t nn = static_cast<size_t>(n) * n;
+    if ((rc = check_device_buffer(uvw, static_cast<size_t>(n_vis) * 24, fn, "uvw", 8)) ||
+        (vis && (rc = check_device_buffer(vis, static_cast<size_t>(n_vis) * 8, fn, "vis", 8))) ||
+        (rc = check_device_buffer(image, nn * 4, fn, "image", 4)))
+        return rc;
+    return dirty_image_w(uvw, static_cast<const float2*>(vis), n_vis, n, dl, w_planes, w_max, image,
+                         static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int wt_selftest_grid_barrier(uint32_t spin_limit, void* stream)
 {
     using namespace wt;
@@ -770,8 +1140,8 @@ extern "C" int wt_hogbom(float* image, const float* psf, int n, float gain, floa
 
 extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, int n, double dl, double ra0,
                         double dec0, int J, int predictor, int mode, float gain, float threshold, int minor_iter,
-                        int n_major, int* comp_pix, float* comp_flux, int* n_comp, void* vis_resid, float* image_resid,
-                        void* stream)
+                        int n_major, int w_planes, int* comp_pix, float* comp_flux, int* n_comp, void* vis_resid,
+                        float* image_resid, void* stream)
 {
     using namespace wt;
     const char* fn = "wt_clean";
@@ -786,6 +1156,8 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
         return set_error(WT_ERR_ARG, "%s: minor_iter x n_major outside 0..2^24", fn);
     if (!(gain > 0.0f) || !(gain <= 1.0f)) return set_error(WT_ERR_RANGE, "%s: gain must be in (0, 1]", fn);
     if (!isfinite(threshold)) return set_error(WT_ERR_RANGE, "%s: threshold must be finite", fn);
+    if (w_planes != 0 && (w_planes < 2 || w_planes > 1024))
+        return set_error(WT_ERR_ARG, "%s: w_planes = %d must be 0 or 2..1024", fn, w_planes);
     if (!n_comp) return set_error(WT_ERR_ARG, "%s: n_comp (host) is NULL", fn);
     const int cap = minor_iter * n_major;
     const size_t nn = static_cast<size_t>(n) * n;
@@ -828,18 +1200,25 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
     int64_t* xref = tree ? reinterpret_cast<int64_t*>(take(nn * 8)) : nullptr;
 
     int total = 0;
+    // the imaging: nearest-cell without w, or w-projection planned for the
+    // batch's largest |w| (found once)
+    double w_max = 0.0;
+    auto image_of = [&](const float2* v, float* out) {
+        return w_planes ? dirty_image_w(uvw, v, n_vis, n, dl, w_planes, w_max, out, s)
+                        : dirty_image(uvw, v, n_vis, n, dl, out, grid, count, s);
+    };
+    rc = w_planes ? max_abs_w(uvw, n_vis, s, &w_max) : WT_OK;
     // the tree predictor maps components through the cross-reference table
     // of the image pixels, built once (Sec. 3.5)
-    rc = tree ? wt_xref_table(n, dl, ra0, dec0, J, xref, stream) : WT_OK;
-    if (!rc) rc = dirty_image(uvw, nullptr, n_vis, n, dl, beam, grid, count, s);
+    if (!rc && tree) rc = wt_xref_table(n, dl, ra0, dec0, J, xref, stream);
+    if (!rc) rc = image_of(nullptr, beam);
     if (!rc && n_vis > 0) {
         e = cudaMemcpyAsync(vis_resid, vis_obs, static_cast<size_t>(n_vis) * 8, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync");
     }
     for (int cycle = 0; cycle < n_major && !rc; ++cycle) {
         // 3. gridding and FFT of the residuals, then the minor cycles
-        if ((rc = dirty_image(uvw, static_cast<const float2*>(vis_resid), n_vis, n, dl, image_resid, grid, count, s)))
-            break;
+        if ((rc = image_of(static_cast<const float2*>(vis_resid), image_resid))) break;
         if ((rc = hogbom(image_resid, beam, n, gain, threshold, minor_iter, comp_pix + total, comp_flux + total, d_found,
                          state, s)))
             break;
@@ -865,7 +1244,7 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
         if (!rc) rc = subtract_model(vis_obs, model, vis_resid, n_vis, mode, stream);
     }
     // the dirty image of the final residual visibilities
-    if (!rc) rc = dirty_image(uvw, static_cast<const float2*>(vis_resid), n_vis, n, dl, image_resid, grid, count, s);
+    if (!rc) rc = image_of(static_cast<const float2*>(vis_resid), image_resid);
     *n_comp = total;
     const cudaError_t ef = cudaFreeAsync(scratch, s);
     if (rc) return rc;

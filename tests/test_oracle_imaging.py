@@ -132,3 +132,44 @@ def test_major_cycles_recover_point_sources_with_the_direct_sum():
     for p in want:
         assert tot[p] == pytest.approx(want[p], rel=0.05)
     assert np.sqrt(np.mean(np.abs(resid) ** 2)) < 0.05 * np.sqrt(np.mean(np.abs(obs) ** 2))
+
+
+# ---------------------------------------------------------------- reading I5
+# The w-corrected dirty image by direct summation: pinned by its closed
+# forms and, at w = 0 on cell centres, by the FFT image of I1-I3.
+
+def _source_vis(uvw, l0, m0, flux=1.0):
+    nm1 = -(l0 * l0 + m0 * m0) / (1.0 + np.sqrt(1.0 - l0 * l0 - m0 * m0))
+    return flux * np.exp(2j * np.pi * (uvw @ np.array([l0, m0, nm1])))
+
+
+def test_exact_image_of_a_source_is_its_flux_at_its_pixel_for_any_w():
+    # a wide field and large w: the exact image peaks at the source with
+    # exactly its flux; dropping the w term (the plain 2-D image) does not
+    n, dl = 256, 2e-3
+    rng = np.random.default_rng(61)
+    uvw = rng.uniform(-60, 60, (3000, 3)) * np.array([1.0, 1.0, 8.0])
+    ix0, iy0 = n // 2 + 90, n // 2 - 70
+    l0, m0 = (ix0 - n // 2) * dl, (iy0 - n // 2) * dl
+    v = _source_vis(uvw, l0, m0, 2.5)
+    assert abs(I.dirty_image_exact(uvw, v, n, dl, ix0, iy0)[0] - 2.5) < 1e-12
+    # the neighbourhood is below the peak
+    around = I.dirty_image_exact(uvw, v, n, dl, [ix0 + 1, ix0 - 1, ix0], [iy0, iy0, iy0 + 1])
+    assert np.all(around < 2.5)
+    # with w set to zero in the image (but not in the data) the peak is lost
+    u0 = uvw.copy()
+    u0[:, 2] = 0.0
+    assert I.dirty_image_exact(u0, v, n, dl, ix0, iy0)[0] < 2.0
+    # at the phase centre a source of flux C gives C for any w
+    assert abs(I.dirty_image_exact(uvw, np.full(len(uvw), 0.7 + 0j), n, dl, n // 2, n // 2)[0] - 0.7) < 1e-12
+
+
+def test_exact_image_at_w_zero_on_cell_centres_is_the_fft_image():
+    n, dl = 32, 5e-3
+    uvw = _on_grid_uvw(n, dl, 400, seed=62)
+    rng = np.random.default_rng(63)
+    vis = rng.normal(size=400) + 1j * rng.normal(size=400)
+    ref = I.dirty_image(uvw, vis, n, dl)
+    iy, ix = np.mgrid[0:n, 0:n]
+    got = I.dirty_image_exact(uvw, vis, n, dl, ix.ravel(), iy.ravel()).reshape(n, n)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))

@@ -13,9 +13,29 @@ import test_oracle_imaging as P
 PINS = [P.test_single_visibility_lands_in_its_cell_and_mirror, P.test_fft_image_equals_the_double_sum,
         P.test_point_source_at_phase_centre_and_beam_peak, P.test_off_centre_point_source_is_the_shifted_beam,
         P.test_hogbom_on_a_pure_beam_follows_the_gain, P.test_hogbom_threshold_and_maximum_value,
-        P.test_major_cycles_recover_point_sources_with_the_direct_sum]
+        P.test_major_cycles_recover_point_sources_with_the_direct_sum,
+        P.test_exact_image_of_a_source_is_its_flux_at_its_pixel_for_any_w,
+        P.test_exact_image_at_w_zero_on_cell_centres_is_the_fft_image]
 
 _grid_nn, _image_from_grid, _hogbom, _major_cycles = I.grid_nn, I.image_from_grid, I.hogbom, I.major_cycles
+_exact = I.dirty_image_exact
+
+
+def _exact_variant(uvw, vis, n, dl, ix, iy, w_sign=-1.0, m_sign=1.0):
+    # the direct sum with the w term's sign or the m axis changed
+    uvw = np.asarray(uvw, dtype=np.float64)
+    ix, iy = np.atleast_1d(ix), np.atleast_1d(iy)
+    l, m = (ix - n // 2) * dl, (iy - n // 2) * dl * m_sign
+    r2 = l * l + m * m
+    nm1 = -r2 / (1.0 + np.sqrt(1.0 - r2))
+    ph = np.outer(uvw[:, 0], l) + np.outer(uvw[:, 1], m) - w_sign * np.outer(uvw[:, 2], nm1)
+    return (np.asarray(vis)[:, None] * np.exp(-2j * np.pi * ph)).real.sum(axis=0) / len(uvw)
+
+
+def exact_without_w(uvw, vis, n, dl, ix, iy):
+    u0 = np.array(uvw, dtype=np.float64, copy=True)
+    u0[:, 2] = 0.0
+    return _exact(u0, vis, n, dl, ix, iy)
 
 
 def _plain_grid(uvw, vis, n, dl, conj):
@@ -79,6 +99,10 @@ PLANTS = {
     "largest magnitude instead of largest value": ("hogbom", hogbom_by_magnitude),
     "component flux without the loop gain": ("hogbom", hogbom_without_gain),
     "model from the latest cycle only": ("major_cycles", major_cycles_latest_only),
+    "exact image without the w term": ("dirty_image_exact", exact_without_w),
+    "exact image with the w term's sign flipped": ("dirty_image_exact",
+                                                   lambda *a: _exact_variant(*a, w_sign=1.0)),
+    "exact image with the m axis mirrored": ("dirty_image_exact", lambda *a: _exact_variant(*a, m_sign=-1.0)),
 }
 
 

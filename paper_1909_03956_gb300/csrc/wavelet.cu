@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NT, (mixed_min_blocks<NT, VPT, SUM>())) k_wave
     const int64_t per_tile = static_cast<int64_t>(NT) * VPT;
     const int64_t ntiles = (n_vis + per_tile - 1) / per_tile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if constexpr (SUM != 0 && !GRIDPASS) {
+        if constexpr (!GRIDPASS) {
             if (!tile_deferred(vis + tile * per_tile)) continue;   // done by the grid pass
         }
         const int64_t n0 = tile * per_tile + threadIdx.x;
@@ -238,9 +238,16 @@ __global__ void __launch_bounds__(NT, (mixed_min_blocks<NT, VPT, SUM>())) k_wave
                 vi[k] = r.y;
             }
         } else if constexpr (SUM == 0) {
-            Eq17F<NT, VPT, FAST> b;
+            Eq17F<NT, VPT, FAST, GRIDPASS> b;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) { b.u[k] = U[k]; b.v[k] = V[k]; b.w[k] = W[k]; }
+            if constexpr (GRIDPASS) {
+                float C[VPT];
+                defer = !tile_grid_constants(U, V, W, hdr->smax, C);   // a CTA-wide decision
+#pragma unroll
+                for (int p = 0; p < VPT / 2; ++p) b.Cg[p] = make_float2(C[2 * p], C[2 * p + 1]);
+                b.Cs = C[VPT - 1];
+            }
             b.start();
             b.stk = stk;
             b.maxrow = rows - 1;
@@ -394,9 +401,15 @@ int run_mixed_form(const WaveletJob& jb, cudaStream_t s)
         WT_CUDA_TRY(cudaGetLastError());
         ke<<<grid_e, NT, smem, s>>>(jb.recf_leaf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else if (jb.which == WT_SUM_EQ17) {
-        auto k = k_wavelet_mixed<NT, VPT, 0, RecF, FAST>;
-        if ((rc = prepare(k, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
-        k<<<grid, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+        // the grid pass, then the exact pass over the tiles it left marked
+        auto kg = k_wavelet_mixed<NT, VPT, 0, RecF, FAST, true>;
+        auto ke = k_wavelet_mixed<NT, VPT, 0, RecF, FAST, false>;
+        if ((rc = prepare(kg, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid))) return rc;
+        dim3 grid_e;
+        if ((rc = prepare(ke, NT, smem, int64_t(NT) * VPT, jb.n_vis, grid_e))) return rc;
+        kg<<<grid, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
+        WT_CUDA_TRY(cudaGetLastError());
+        ke<<<grid_e, NT, smem, s>>>(jb.recf, jb.hdr, jb.uvw, jb.n_vis, out, sg, rows, jb.J, jb.status);
     } else {
         // the grid pass, then the exact pass over the tiles it left marked
         auto kg = k_wavelet_mixed<NT, VPT, 2, RecWF, FAST, true>;

@@ -123,12 +123,14 @@ struct Eq16D {
 // visibilities 2p and 2p + 1 are formed as one pair (VPT = 1 forms its one
 // phase on scalars). Per visibility a four-child node costs 15 paired
 // operations, Kahan included.
-template <int NT, int VPT, bool FAST = false>
+template <int NT, int VPT, bool FAST = false, bool GRID = false>
 struct Eq17F {
     static constexpr int NP = VPT / 2;                // visibility pairs
     static constexpr bool ODD = (VPT & 1) != 0;       // a last, unpaired visibility
     F2 u[VPT], v[VPT], w[VPT];                        // set by the caller, then start()
     DF2 U[NP > 0 ? NP : 1], V[NP > 0 ? NP : 1], W[NP > 0 ? NP : 1];
+    float2 Cg[NP > 0 ? NP : 1];                       // GRID: the grid constants of visibilities 2p, 2p + 1
+    float Cs;                                         // GRID: that of the last, unpaired visibility
     float2 acc[VPT], comp[VPT];                       // Kahan sum of V and its compensation
     float2* stk;
     int maxrow;
@@ -168,7 +170,8 @@ struct Eq17F {
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
                 float2 h, tl, e0, e1;
-                phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
+                if constexpr (GRID) phase_turns_grid2(U[p], V[p], W[p], su, sv, sw, Cg[p], h, tl);
+                else phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
                 sincos_mixed2<FAST>(h, tl, e0, e1);
                 emit(2 * p, root, srow, r.g, e0);
                 emit(2 * p + 1, root, srow, r.g, e1);
@@ -176,7 +179,8 @@ struct Eq17F {
             if constexpr (ODD) {
                 constexpr int k = VPT - 1;
                 float th, tl, s, c;
-                phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
+                if constexpr (GRID) phase_turns_grid(u[k], v[k], w[k], su, sv, sw, Cs, th, tl);
+                else phase_turns_df(u[k], v[k], w[k], su, sv, sw, th, tl);
                 sincos_mixed<FAST>(th, tl, s, c);
                 emit(k, root, srow, r.g, make_float2(c, s));
             }

@@ -1,4 +1,4 @@
-"""The regrouped Eq. 17 and Eq. 16 in the mixed forms run in two passes: the grid pass
+"""Eq. 17 (regrouped and explicit) and Eq. 16 in the mixed forms run in two passes: the grid pass
 forms each leaf phase with its three head products rounded onto a common
 grid (exact float32 sums, valid while every head of the tile's visibilities
 stays below 2^14 turns), and the exact pass takes the tiles that do not fit,
@@ -41,7 +41,7 @@ def rel_err(w, J, uvw, mode, sign=1, which=wt.WT_SUM_EQ17_REGROUPED):
     return float(np.max(np.abs(v - ref)) / np.abs(w.flux).sum())
 
 
-SUMS = [wt.WT_SUM_EQ17_REGROUPED, wt.WT_SUM_EQ16]
+SUMS = [wt.WT_SUM_EQ17_REGROUPED, wt.WT_SUM_EQ17, wt.WT_SUM_EQ16]
 
 
 def long_baselines(n, lo, hi, rng):

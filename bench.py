@@ -987,54 +987,60 @@ def learned_measurement(wt, torch, dev, stream, flush, n_train=10_000_000, depth
         }
         mlp.close()
     # hard thresholding with full-pixel responses: the tree truncated at j0
-    # plus the detail coefficients of levels j0 .. J-1 with |gamma| >= tau
-    j0, d0 = 9, depth + 1
+    # plus the detail coefficients of levels j0 .. J-1 with |gamma| >= tau;
+    # the responses exact (float64 quadrature), learned (one network per
+    # level j0 .. J for its level's responses down to the common finest level
+    # j0 + d0, trained on n_train oracle responses each) or none
+    d0 = depth + 1
     ex = tree.export()
     offs, gam = ex["level_offsets"], ex["gamma"]
-    g_fine = np.abs(gam[offs[j0 - 1]:offs[J - 1]]).ravel()
-    # one network per level j0 .. J, each for its level's responses down to
-    # the common finest level j0 + d0, on n_train / 5 oracle responses
-    n_thr = n_train // 5
-    nets, t_gen, t_train = [], 0.0, 0.0
-    for L in range(j0, J + 1):
-        dL = d0 - (L - j0)
-        t0 = time.perf_counter()
-        idx = rng.integers(0, w.n_vis, n_thr)
-        tr_uvw = w.uvw[idx] * np.where(rng.random((n_thr, 1)) < 0.5, -1.0, 1.0)
-        tgt = O.pixel_response(L, dL, w.ra0, w.dec0, tr_uvw)
-        t_gen += time.perf_counter() - t0
-        x_max = float(np.max(np.abs(tr_uvw * O.level_pixel_size(L)))) * 1.0001
-        mlp = wt.Mlp(L, w.ra0, w.dec0, depth=dL, x_max=x_max, seed=7 + L)
-        tu, tt = d(tr_uvw), d(np.stack([tgt.real, tgt.imag], axis=1).astype(np.float32))
-        del tr_uvw, tgt
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mlp.train(tu, tt, steps=2 * (n_thr // 8192), batch=8192, lr=3e-3)
-        torch.cuda.synchronize()
-        t_train += time.perf_counter() - t0
-        del tu, tt
-        nets.append(mlp)
-    for frac in (0.1, 0.5):
-        tau = float(np.quantile(g_fine, 1.0 - frac))
-        kept_nodes = int(np.sum(np.any(np.abs(gam[offs[j0 - 1]:offs[J - 1]]) >= tau, axis=1)))
-        terms = int(info["per_level"][j0 - 1]) + 4 * kept_nodes
-        rate_x, v_x = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw, response=wt.WT_RESPONSE_EXACT,
-                                                                  depth=d0, out=out))
-        rate_s, v_s = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw, out=out))
-        rate_l, v_l = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw, response=wt.WT_RESPONSE_LEARNED,
-                                                                  mlps=nets, out=out))
-        res["thresholded_j0_%d_keep_%d_percent" % (j0, round(100 * frac))] = {
-            "tau": tau, "kept_coefficients": int(np.sum(g_fine >= tau)), "terms_per_vis": terms,
-            "exact_response": {"vis_per_s": rate_x, "rms_err_vs_true": rms(v_x, v_true),
-                               "note": "float64 responses, %d .. %d sub-pixels per level" % (4 ** (d0 - (J - j0)),
-                                                                                            4 ** d0)},
-            "learned": {"vis_per_s": rate_l, "rms_err_vs_true": rms(v_l, v_true),
-                        "max_rel_err_vs_exact_response_form": float(np.max(np.abs(v_l - v_x)) / S),
-                        "networks": "one per level %d .. %d, %d oracle responses each (%.1f s to generate, "
-                                    "%.2f s to train all)" % (j0, J, n_thr, t_gen, t_train)},
-            "centre_snapped": {"vis_per_s": rate_s, "rms_err_vs_true": rms(v_s, v_true)}}
-    for mlp in nets:
-        mlp.close()
+    for j0 in (9, 11):
+        nets, errs, t_gen, t_train = [], [], 0.0, 0.0
+        for L in range(j0, J + 1):
+            dL = d0 - (L - j0)
+            t0 = time.perf_counter()
+            idx = rng.integers(0, w.n_vis, n_train)
+            tr_uvw = w.uvw[idx] * np.where(rng.random((n_train, 1)) < 0.5, -1.0, 1.0)
+            tgt = O.pixel_response(L, dL, w.ra0, w.dec0, tr_uvw)
+            t_gen += time.perf_counter() - t0
+            x_max = float(np.max(np.abs(tr_uvw * O.level_pixel_size(L)))) * 1.0001
+            mlp = wt.Mlp(L, w.ra0, w.dec0, depth=dL, x_max=x_max, seed=7 + L)
+            tu, tt = d(tr_uvw), d(np.stack([tgt.real, tgt.imag], axis=1).astype(np.float32))
+            del tr_uvw, tgt
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mlp.train(tu, tt, steps=2 * (n_train // 8192), batch=8192, lr=3e-3)
+            torch.cuda.synchronize()
+            t_train += time.perf_counter() - t0
+            del tu, tt
+            r_net = mlp.eval(d(su)).cpu().numpy()
+            errs.append(float(np.sqrt(np.mean(np.abs(r_net - O.pixel_response(L, dL, w.ra0, w.dec0, su)) ** 2))))
+            nets.append(mlp)
+        g_fine = np.abs(gam[offs[j0 - 1]:offs[J - 1]]).ravel()
+        for frac in (0.1, 0.5):
+            tau = float(np.quantile(g_fine, 1.0 - frac))
+            kept_nodes = int(np.sum(np.any(np.abs(gam[offs[j0 - 1]:offs[J - 1]]) >= tau, axis=1)))
+            terms = int(info["per_level"][j0 - 1]) + 4 * kept_nodes
+            rate_x, v_x = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw,
+                                                                      response=wt.WT_RESPONSE_EXACT, depth=d0,
+                                                                      out=out))
+            rate_s, v_s = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw, out=out))
+            rate_l, v_l = timed(lambda: wt.wt_predict_vis_thresholded(tree, j0, tau, uvw,
+                                                                      response=wt.WT_RESPONSE_LEARNED, mlps=nets,
+                                                                      out=out))
+            res["thresholded_j0_%d_keep_%d_percent" % (j0, round(100 * frac))] = {
+                "tau": tau, "kept_coefficients": int(np.sum(g_fine >= tau)), "terms_per_vis": terms,
+                "exact_response": {"vis_per_s": rate_x, "rms_err_vs_true": rms(v_x, v_true),
+                                   "note": "float64 responses, %d .. %d sub-pixels per level"
+                                           % (4 ** (d0 - (J - j0)), 4 ** d0)},
+                "learned": {"vis_per_s": rate_l, "rms_err_vs_true": rms(v_l, v_true),
+                            "max_rel_err_vs_exact_response_form": float(np.max(np.abs(v_l - v_x)) / S),
+                            "response_rms_err_vs_exact_per_level": errs,
+                            "networks": "one per level %d .. %d, %d oracle responses each (%.1f s to generate, "
+                                        "%.2f s to train all)" % (j0, J, n_train, t_gen, t_train)},
+                "centre_snapped": {"vis_per_s": rate_s, "rms_err_vs_true": rms(v_s, v_true)}}
+        for mlp in nets:
+            mlp.close()
     tree.close()
     return res
 

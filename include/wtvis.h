@@ -329,7 +329,8 @@ int wt_dirty_image(const double* uvw, const void* vis, int64_t n_vis, int n, dou
  * for w_planes planes uniformly spaced in |w| over [0, w_max] and
  * interpolated linearly in |w|. A visibility whose kernel support would
  * leave the grid is left out (and not counted in W); |w| above w_max takes
- * the last planes' extrapolation.
+ * the last plane's kernel (a w_max below the batch's largest |w| degrades
+ * the image, it does not fail).
  *   w_planes  2 .. 1024
  *   w_max     the largest |w| to plan for; 0: the batch's own, found on the
  *             device (this synchronises `stream`)

@@ -654,11 +654,20 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
     r["subtract_c64_64Mi_GBps"] = 24 * big / t / 1e9
     r["subtract_c64_64Mi_frac_of_hbm"] = 24 * big / t / 1e9 / HBM_PEAK_GBPS
     del a, b
-    # the learned response's inference alone, one sample per visibility
+    # the learned response's inference alone, one sample per visibility, on
+    # 16 copies of the batch (16 M samples, the learned workload's size: a
+    # single medium batch is a 60 us launch, dominated by its ramp)
     mlp = wt.Mlp(w.J, w.ra0, w.dec0, depth=3, x_max=1e30, seed=1)
-    t_mlp = _time_call(lambda: mlp.eval(uvw, out=out32), stream, flush)
+    uvw16 = uvw.repeat(16, 1)
+    r_out = torch.empty(uvw16.shape[0], dtype=torch.complex64, device=uvw.device)
+    t_mlp = _time_call(lambda: mlp.eval(uvw16, out=r_out), stream, flush)
+    t_mlp1 = _time_call(lambda: mlp.eval(uvw, out=out32), stream, flush)
     mlp.close()
-    r["mlp_eval_samples_per_s"] = n / t_mlp
+    n_mlp = uvw16.shape[0]
+    del uvw16, r_out
+    r["mlp_eval_samples_per_s"] = n_mlp / t_mlp
+    r["mlp_eval_samples"] = n_mlp
+    r["mlp_eval_1M_samples_per_s"] = n / t_mlp1
     # rooflines of the side kernels: the algorithmic work per unit (see the
     # constants) against the measured pipe peaks, and each form's own
     # operation count as pipe_busy
@@ -678,7 +687,7 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
                 "pipe_busy": {"frac": terms * ops_per_term / 1e12 / peaks["fp32_top_s"], "ops_per_term": ops_per_term,
                               "unit": "the form's float32 FMA-pipe element ops per term, of the measured rate"}}
 
-    mlp_tflops = n * 8832 / t_mlp / 1e12
+    mlp_tflops = n_mlp * 8832 / t_mlp / 1e12
     roof = {
         "dft_mixed_fast": dft_roof(r["dft_mixed_fast_vis_per_s"], OPS_DFT_FAST),
         "dft_mixed": dft_roof(r["dft_mixed_vis_per_s"], OPS_DFT),
@@ -692,10 +701,11 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
         "subtract_c64_64Mi": {"bound": "hbm", "frac": r["subtract_c64_64Mi_frac_of_hbm"],
                               "peak_gbps": HBM_PEAK_GBPS, "peak_source": PEAKS_SOURCE},
         "mlp_eval": {"bound": "sfu",
-                     "frac": n * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_tanh_top_s"],
+                     "frac": n_mlp * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_tanh_top_s"],
                      "unit": "hardware tanh of the two SiLU layers (%d per sample) of the measured tanh rate"
                              % MLP_TANH_PER_SAMPLE,
-                     "of_sine_rate": n * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_top_s"],
+                     "of_sine_rate": n_mlp * MLP_TANH_PER_SAMPLE / t_mlp / 1e12 / peaks["sfu_top_s"],
+                     "samples": n_mlp,
                      "tensor": {"achieved_tflops": mlp_tflops, "frac": mlp_tflops / BF16_PEAK_TFLOPS,
                                 "peak_tflops": BF16_PEAK_TFLOPS, "peak_source": PEAKS_SOURCE,
                                 "flops_per_sample": 8832}},
@@ -1220,6 +1230,9 @@ def forms_once(args):
     mlp = wt.Mlp(w.J, w.ra0, w.dec0, depth=3, x_max=1e30, seed=1)
     r_out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
     runs.append(("mlp_eval", lambda: mlp.eval(uvw, out=r_out)))
+    uvw16 = uvw.repeat(16, 1)
+    r_out16 = torch.empty(uvw16.shape[0], dtype=torch.complex64, device=dev)
+    runs.append(("mlp_eval_16x", lambda: mlp.eval(uvw16, out=r_out16)))
     # batched: 8 channels of the medium workload's components at 1.0 .. 1.8 GHz
     freqs = list(np.linspace(1.0e9, 1.8e9, 8))
     btrees = [wt.wt_build_tree(l, m, f, w.ra0, w.dec0, 10 + (c % 4)) for c in range(8)]

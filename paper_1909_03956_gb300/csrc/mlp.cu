@@ -62,6 +62,15 @@ __device__ __forceinline__ float silu_fast(float z)
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(hz));
     return fmaf(hz, t, hz);
 }
+// silu_fast on a pair (the same roundings per element).
+__device__ __forceinline__ float2 silu_fast2(float2 z)
+{
+    const float2 hz = mul2(make_float2(0.5f, 0.5f), z);
+    float2 t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t.x) : "f"(hz.x));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t.y) : "f"(hz.y));
+    return fma2(hz, t, hz);
+}
 __device__ __forceinline__ float dsilu_f(float z)
 {
     const float s = 1.0f / (1.0f + __expf(-z));
@@ -215,16 +224,22 @@ __global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const 
 {
     __shared__ __align__(1024) unsigned char sA[128 * kH * 2];
     __shared__ __align__(1024) unsigned char sB[kH * kH * 2];
-    __shared__ float sW1[kH * 3], sb1[kH], sb2[kH], sW3[2 * kH], sb3[2];
+    // the small layers' parameters as packed pairs: W1 column k of units
+    // (2q, 2q + 1), b1 and b2 of those units, and W3's two outputs of unit c
+    __shared__ float2 sW1p[3][kH / 2], sb1p[kH / 2], sb2p[kH / 2], sW3p[kH];
+    __shared__ float sb3[2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
-    for (int i = t; i < kH * 3; i += kApplyThreads) sW1[i] = p.params[oW1 + i];
-    for (int i = t; i < kH; i += kApplyThreads) {
-        sb1[i] = p.params[ob1 + i];
-        sb2[i] = p.params[ob2 + i];
+    for (int i = t; i < 3 * (kH / 2); i += kApplyThreads) {
+        const int k = i / (kH / 2), q = i % (kH / 2);
+        sW1p[k][q] = make_float2(p.params[oW1 + 3 * (2 * q) + k], p.params[oW1 + 3 * (2 * q + 1) + k]);
     }
-    for (int i = t; i < 2 * kH; i += kApplyThreads) sW3[i] = p.params[oW3 + i];
+    for (int q = t; q < kH / 2; q += kApplyThreads) {
+        sb1p[q] = make_float2(p.params[ob1 + 2 * q], p.params[ob1 + 2 * q + 1]);
+        sb2p[q] = make_float2(p.params[ob2 + 2 * q], p.params[ob2 + 2 * q + 1]);
+    }
+    for (int c = t; c < kH; c += kApplyThreads) sW3p[c] = make_float2(p.params[oW3 + c], p.params[oW3 + kH + c]);
     if (t < 2) sb3[t] = p.params[ob3 + t];
     for (int i = t; i < kH * kH / 2; i += kApplyThreads)   // W2 row n = output unit: K-major B
         *reinterpret_cast<uint32_t*>(sB + umma_off(i / 32, 2 * (i % 32))) = __ldg(&p.w2_bf16x2[i]);
@@ -275,18 +290,18 @@ __global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const 
                 nw = uvw[3 * s1 + 2];
             }
         }
-        // layer 1 into row t of A, one 16-byte core-matrix row (8 units) at a time
+        // layer 1 into row t of A, one 16-byte core-matrix row (8 units) at a
+        // time, two units per packed operation (the scalar order of the FMAs)
+        const float2 x0 = bcast2(x[0]), x1 = bcast2(x[1]), x2 = bcast2(x[2]);
 #pragma unroll
         for (int kg = 0; kg < 8; ++kg) {
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int c0 = 8 * kg + 2 * e, c1 = c0 + 1;
-                const float h0 =
-                    silu_fast(fmaf(sW1[3 * c0 + 2], x[2], fmaf(sW1[3 * c0 + 1], x[1], fmaf(sW1[3 * c0], x[0], sb1[c0]))));
-                const float h1 =
-                    silu_fast(fmaf(sW1[3 * c1 + 2], x[2], fmaf(sW1[3 * c1 + 1], x[1], fmaf(sW1[3 * c1], x[0], sb1[c1]))));
-                w[e] = pack_bf16x2(h0, h1);
+                const int q = 4 * kg + e;                              // units 2q, 2q + 1
+                const float2 z = fma2(sW1p[2][q], x2, fma2(sW1p[1][q], x1, fma2(sW1p[0][q], x0, sb1p[q])));
+                const float2 h = silu_fast2(z);
+                w[e] = pack_bf16x2(h.x, h.y);
             }
             *reinterpret_cast<uint4*>(sA + umma_off(t, 8 * kg)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -320,20 +335,22 @@ __global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const 
         tc_fence_after();
         // the accumulator row in two halves of 32 columns, each folded into
         // layer 3 at once (the same order of operations as one pass)
-        float rr = sb3[0], ri = sb3[1];
+        float2 ro = make_float2(sb3[0], sb3[1]);                       // (real, imaginary) output
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             uint32_t r[32];
             tmem_ld32(row_addr + 32 * half, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int cc = 0; cc < 32; ++cc) {
-                const int c = 32 * half + cc;
-                const float h = silu_fast(__uint_as_float(r[cc]) + sb2[c]);
-                rr = fmaf(sW3[c], h, rr);
-                ri = fmaf(sW3[kH + c], h, ri);
+            for (int cc = 0; cc < 32; cc += 2) {
+                const int c = 32 * half + cc;                          // units c, c + 1
+                const float2 h = silu_fast2(add2(make_float2(__uint_as_float(r[cc]), __uint_as_float(r[cc + 1])),
+                                                 sb2p[c / 2]));
+                ro = fma2(sW3p[c], bcast2(h.x), ro);
+                ro = fma2(sW3p[c + 1], bcast2(h.y), ro);
             }
         }
+        float rr = ro.x, ri = ro.y;
         if (live) {
             if (fmaxf(fabsf(x[0]), fmaxf(fabsf(x[1]), fabsf(x[2]))) > x_max) {
                 const double2 e = response_exact_one(bu, bv, bw, offs, n_off);

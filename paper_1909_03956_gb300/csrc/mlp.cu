@@ -224,22 +224,25 @@ __global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const 
 {
     __shared__ __align__(1024) unsigned char sA[128 * kH * 2];
     __shared__ __align__(1024) unsigned char sB[kH * kH * 2];
-    // the small layers' parameters as packed pairs: W1 column k of units
-    // (2q, 2q + 1), b1 and b2 of those units, and W3's two outputs of unit c
-    __shared__ float2 sW1p[3][kH / 2], sb1p[kH / 2], sb2p[kH / 2], sW3p[kH];
+    // the small layers' parameters, laid out for one 16-byte load per two
+    // packed pairs: for units (2q, 2q + 1) sL1a[q] = W1 columns 0 and 1,
+    // sL1b[q] = W1 column 2 and b1; for units (c, c + 1) sW3q[c / 2] = W3's
+    // two outputs of unit c, then of unit c + 1; sb2q[j] = b2 of units 4j .. 4j + 3
+    __shared__ float4 sL1a[kH / 2], sL1b[kH / 2], sW3q[kH / 2], sb2q[kH / 4];
     __shared__ float sb3[2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x;
-    for (int i = t; i < 3 * (kH / 2); i += kApplyThreads) {
-        const int k = i / (kH / 2), q = i % (kH / 2);
-        sW1p[k][q] = make_float2(p.params[oW1 + 3 * (2 * q) + k], p.params[oW1 + 3 * (2 * q + 1) + k]);
-    }
     for (int q = t; q < kH / 2; q += kApplyThreads) {
-        sb1p[q] = make_float2(p.params[ob1 + 2 * q], p.params[ob1 + 2 * q + 1]);
-        sb2p[q] = make_float2(p.params[ob2 + 2 * q], p.params[ob2 + 2 * q + 1]);
+        const float* w1a = p.params + oW1 + 3 * (2 * q);   // W1 row of unit 2q, then of unit 2q + 1
+        sL1a[q] = make_float4(w1a[0], w1a[3], w1a[1], w1a[4]);
+        sL1b[q] = make_float4(w1a[2], w1a[5], p.params[ob1 + 2 * q], p.params[ob1 + 2 * q + 1]);
+        sW3q[q] = make_float4(p.params[oW3 + 2 * q], p.params[oW3 + kH + 2 * q], p.params[oW3 + 2 * q + 1],
+                              p.params[oW3 + kH + 2 * q + 1]);
     }
-    for (int c = t; c < kH; c += kApplyThreads) sW3p[c] = make_float2(p.params[oW3 + c], p.params[oW3 + kH + c]);
+    for (int j = t; j < kH / 4; j += kApplyThreads)
+        sb2q[j] = make_float4(p.params[ob2 + 4 * j], p.params[ob2 + 4 * j + 1], p.params[ob2 + 4 * j + 2],
+                              p.params[ob2 + 4 * j + 3]);
     if (t < 2) sb3[t] = p.params[ob3 + t];
     for (int i = t; i < kH * kH / 2; i += kApplyThreads)   // W2 row n = output unit: K-major B
         *reinterpret_cast<uint32_t*>(sB + umma_off(i / 32, 2 * (i % 32))) = __ldg(&p.w2_bf16x2[i]);
@@ -299,7 +302,10 @@ __global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const 
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int q = 4 * kg + e;                              // units 2q, 2q + 1
-                const float2 z = fma2(sW1p[2][q], x2, fma2(sW1p[1][q], x1, fma2(sW1p[0][q], x0, sb1p[q])));
+                const float4 a = sL1a[q], b = sL1b[q];
+                const float2 z = fma2(make_float2(b.x, b.y), x2,
+                                      fma2(make_float2(a.z, a.w), x1,
+                                           fma2(make_float2(a.x, a.y), x0, make_float2(b.z, b.w))));
                 const float2 h = silu_fast2(z);
                 w[e] = pack_bf16x2(h.x, h.y);
             }
@@ -342,12 +348,18 @@ __global__ void __launch_bounds__(kApplyThreads, 8) k_mlp_apply(MlpDev p, const 
             tmem_ld32(row_addr + 32 * half, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 2) {
-                const int c = 32 * half + cc;                          // units c, c + 1
-                const float2 h = silu_fast2(add2(make_float2(__uint_as_float(r[cc]), __uint_as_float(r[cc + 1])),
-                                                 sb2p[c / 2]));
-                ro = fma2(sW3p[c], bcast2(h.x), ro);
-                ro = fma2(sW3p[c + 1], bcast2(h.y), ro);
+            for (int cc = 0; cc < 32; cc += 4) {
+                const int c = 32 * half + cc;                          // units c .. c + 3
+                const float4 b2 = sb2q[c / 4];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {                          // units c + 2e, c + 2e + 1
+                    const float2 h = silu_fast2(
+                        add2(make_float2(__uint_as_float(r[cc + 2 * e]), __uint_as_float(r[cc + 2 * e + 1])),
+                             e ? make_float2(b2.z, b2.w) : make_float2(b2.x, b2.y)));
+                    const float4 w3 = sW3q[c / 2 + e];
+                    ro = fma2(make_float2(w3.x, w3.y), bcast2(h.x), ro);
+                    ro = fma2(make_float2(w3.z, w3.w), bcast2(h.y), ro);
+                }
             }
         }
         float rr = ro.x, ri = ro.y;

@@ -83,11 +83,11 @@ struct BodyD {
 };
 
 // Mixed forms on packed float32 pairs: a thread owns two visibilities
-// (n and n + NT of its tile), and components are taken two at a time. The
-// phases of the two visibilities against one component form one pair of
-// double-floats; each visibility's (cos, sin) comes out as its own pair; the
-// two components' terms of a visibility are added plainly, then into its
-// Kahan sum (one rounding more per two terms than one at a time).
+// (n and n + NT of its tile). The phases of the two visibilities against one
+// component form one pair of double-floats; each visibility's (cos, sin)
+// comes out as its own pair. The components are taken kSumBlock at a time:
+// their terms added by FMAs into a partial per visibility, the partial then
+// into its Kahan sum (blockwise compensated summation).
 // GRID: the phases with their heads on the grids of Cg (phase_turns_grid2),
 // else with error-free sums (phase_turns_df2).
 template <bool FAST, bool GRID>
@@ -96,32 +96,35 @@ struct BodyF2 {
     float2 Cg;
     float2 acc[2], comp[2];
 
-    __device__ __forceinline__ void terms(const CompF& c, float2& e0, float2& e1) const
+    // p0 += flux (cos, sin) of visibility 0, p1 of visibility 1
+    __device__ __forceinline__ void add_term(const CompF& c, float2& p0, float2& p1) const
     {
-        float2 h, tl;
+        float2 h, tl, e0, e1;
         if constexpr (GRID) phase_turns_grid2(U, V, W, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, Cg, h, tl);
         else phase_turns_df2(U, V, W, F2{c.lh, c.ll}, F2{c.mh, c.ml}, F2{c.nh, c.nl}, h, tl);
         sincos_mixed2<FAST>(h, tl, e0, e1);
+        const float2 f = bcast2(c.flux);
+        p0 = fma2(f, e0, p0);
+        p1 = fma2(f, e1, p1);
     }
 
-    __device__ __forceinline__ void at(const CompF* cb, int r, int n)
+    // One block of components from record r on; returns how many it took
+    // (kSumBlock, or what is left of a list's last chunk).
+    __device__ __forceinline__ int at(const CompF* cb, int r, int n)
     {
-        if (r & 1) return;                         // taken with its even neighbour
-        const CompF& a = cb[r];
-        float2 a0, a1;
-        terms(a, a0, a1);
-        const float2 fa = bcast2(a.flux);
-        float2 x0 = mul2(fa, a0), x1 = mul2(fa, a1);
-        if (r + 1 < n) {                           // chunks hold an even count: only a list's last
-            const CompF& b = cb[r + 1];            // component can be alone
-            float2 b0, b1;
-            terms(b, b0, b1);
-            const float2 fb = bcast2(b.flux);
-            x0 = fma2(fb, b0, x0);
-            x1 = fma2(fb, b1, x1);
+        float2 p0 = make_float2(0.f, 0.f), p1 = p0;
+        int taken;
+        if (r + kSumBlock <= n) {
+#pragma unroll 2
+            for (int j = 0; j < kSumBlock; ++j) add_term(cb[r + j], p0, p1);
+            taken = kSumBlock;
+        } else {
+            for (int j = r; j < n; ++j) add_term(cb[j], p0, p1);
+            taken = n - r;
         }
-        kahan_add2(acc[0], comp[0], x0);
-        kahan_add2(acc[1], comp[1], x1);
+        kahan_add2(acc[0], comp[0], p0);
+        kahan_add2(acc[1], comp[1], p1);
+        return taken;
     }
 };
 

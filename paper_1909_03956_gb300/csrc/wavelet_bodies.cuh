@@ -221,10 +221,10 @@ struct Eq17F {
 
 // Eq. 16 in the mixed forms on packed pairs: a thread's visibilities taken
 // two at a time (their phases against one leaf as one pair of double-floats,
-// each visibility's (cos, sin) its own pair) and the leaf records two at a
-// time (the second's term added plainly to the first's, then into the
-// Kahan sum, one rounding more per two terms); an odd last visibility of
-// the thread alone. GRID: the phases with their heads on each visibility's
+// each visibility's (cos, sin) its own pair), an odd last visibility of the
+// thread alone; the leaf records kSumBlock at a time (their terms added by
+// FMAs into a partial per visibility, the partial then into its Kahan sum:
+// blockwise compensated summation). GRID: the phases with their heads on each visibility's
 // grid (constants Cg / Cs, set by the caller; phase_turns_grid2), else with
 // error-free sums (phase_turns_df2).
 template <int VPT, bool FAST, bool GRID>
@@ -260,8 +260,9 @@ struct Eq16F2 {
 
     __device__ __forceinline__ float2 result(int k) const { return sub2(acc[k], comp[k]); }
 
-    // One leaf's terms: e[k] = Phi exp(i 2 pi phase) of visibility k.
-    __device__ __forceinline__ void terms(const RecF& r, float2 (&e)[VPT]) const
+    // One leaf's terms into the partials: p[k] += Phi exp(i 2 pi phase) of
+    // visibility k.
+    __device__ __forceinline__ void add_terms(const RecF& r, float2 (&x)[VPT]) const
     {
         const F2 su{r.a, r.b}, sv{r.c, r.d}, sw{r.e, r.f};
         const float2 fl = bcast2(r.g);
@@ -271,31 +272,37 @@ struct Eq16F2 {
             if constexpr (GRID) phase_turns_grid2(U[p], V[p], W[p], su, sv, sw, Cg[p], h, tl);
             else phase_turns_df2(U[p], V[p], W[p], su, sv, sw, h, tl);
             sincos_mixed2<FAST>(h, tl, e0, e1);
-            e[2 * p] = mul2(fl, e0);
-            e[2 * p + 1] = mul2(fl, e1);
+            x[2 * p] = fma2(fl, e0, x[2 * p]);
+            x[2 * p + 1] = fma2(fl, e1, x[2 * p + 1]);
         }
         if constexpr (ODD) {
             float th, tl, sn, cs;
             if constexpr (GRID) phase_turns_grid(us, vs, ws, su, sv, sw, Cs, th, tl);
             else phase_turns_df(us, vs, ws, su, sv, sw, th, tl);
             sincos_mixed<FAST>(th, tl, sn, cs);
-            e[VPT - 1] = mul2(fl, make_float2(cs, sn));
+            x[VPT - 1] = fma2(fl, make_float2(cs, sn), x[VPT - 1]);
         }
     }
 
-    __device__ __forceinline__ void at(const RecF* cb, int r, int n)
+    // One block of leaves from record r on; returns how many it took
+    // (kSumBlock, or what is left of a list's last chunk).
+    __device__ __forceinline__ int at(const RecF* cb, int r, int n)
     {
-        if (r & 1) return;                             // taken with its even neighbour
         float2 x[VPT];
-        terms(cb[r], x);
-        if (r + 1 < n) {                               // chunks hold an even count: only a list's
-            float2 y[VPT];                             // last leaf can be alone
-            terms(cb[r + 1], y);
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) x[k] = add2(x[k], y[k]);
+        for (int k = 0; k < VPT; ++k) x[k] = make_float2(0.f, 0.f);
+        int taken;
+        if (r + kSumBlock <= n) {
+#pragma unroll 2
+            for (int j = 0; j < kSumBlock; ++j) add_terms(cb[r + j], x);
+            taken = kSumBlock;
+        } else {
+            for (int j = r; j < n; ++j) add_terms(cb[j], x);
+            taken = n - r;
         }
 #pragma unroll
         for (int k = 0; k < VPT; ++k) kahan_add2(acc[k], comp[k], x[k]);
+        return taken;
     }
 };
 

@@ -475,6 +475,13 @@ __device__ __forceinline__ void sincos_mixed2(float2 h, float2 tl, float2& e0, f
     else sincos_turns_f32x2(h, tl, e0, e1);
 }
 
+// Blockwise compensated summation of the term-per-component sums (the
+// direct sum, Eq. 12, and Eq. 16): the terms of up to kSumBlock consecutive
+// records are added by plain FMAs into a partial sum (at most kSumBlock
+// roundings, a relative error of at most 8 u of the block's sum of |terms|),
+// and each partial enters the Kahan sum once.
+constexpr int kSumBlock = 8;
+
 // Kahan-compensated sum of pairs (each element as kahan_add).
 __device__ __forceinline__ void kahan_add2(float2& sum, float2& comp, float2 x)
 {

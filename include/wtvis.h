@@ -71,12 +71,20 @@ typedef enum {
     WT_MIXED_FAST = 3, /* as WT_MIXED, but sin/cos of the reduced phase from the
                          special-function unit: at most ~7e-7 of a term's flux in
                          error per term (measured against the oracle); complex64 */
-    WT_FP64_DF = 4    /* float64-class accuracy on the float32 pipe: phase, sin/cos
+    WT_FP64_DF = 4,   /* float64-class accuracy on the float32 pipe: phase, sin/cos
                          (table method) and every sum in double-float arithmetic
                          (48-bit significands: a term's phase error is a few times
                          2^-48 |B.s| turns, 32x float64's); complex128 output;
                          wt_predict_vis with WT_SUM_EQ17_REGROUPED or
                          WT_SUM_EQ16 */
+    WT_MIXED_TC = 5   /* dft_predict_vis only: WT_MIXED_FAST's sin/cos and sums,
+                         with the phase contraction u l + v m + w (n - 1) on the
+                         tensor cores from exact 11-bit float16 slices of the
+                         baselines and coordinates (three FP32 accumulators,
+                         recombined modulo 1 in float32; phase error below
+                         2^-29 turns); tiles of 128 visibilities beyond
+                         2^14 turns per coordinate fall back to WT_MIXED_FAST's
+                         exact pass; complex64 */
 } wt_mode;
 
 typedef enum {
@@ -239,7 +247,8 @@ int wt_predict_vis_batched(const wt_tree* trees, const double* freq_hz, int n_ch
  *   l, m, flux  device float64 [n_comp]
  *   uvw         device float64 [n_vis][3]
  *   vis_out     device complex128 (WT_FP64, WT_FP64_DF) or complex64
- *               (WT_MIXED, WT_MIXED_FAST) [n_vis]
+ *               (WT_MIXED, WT_MIXED_FAST, WT_MIXED_TC) [n_vis]
+ *   mode        WT_FP64, WT_FP64_DF, WT_MIXED, WT_MIXED_FAST or WT_MIXED_TC
  * ------------------------------------------------------------------------- */
 int dft_predict_vis(const double* l, const double* m, const double* flux, int64_t n_comp,
                     const double* uvw, int64_t n_vis, void* vis_out, int mode, int sign,

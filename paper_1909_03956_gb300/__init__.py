@@ -30,7 +30,7 @@ import numpy as np
 
 WT_OK, WT_ERR_ARG, WT_ERR_RANGE, WT_ERR_CUDA, WT_ERR_NOMEM, WT_ERR_TIMEOUT, WT_ERR_CORRUPT, WT_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7
-WT_FP64, WT_MIXED, WT_LEARNED, WT_MIXED_FAST, WT_FP64_DF = 0, 1, 2, 3, 4
+WT_FP64, WT_MIXED, WT_LEARNED, WT_MIXED_FAST, WT_FP64_DF, WT_MIXED_TC = 0, 1, 2, 3, 4, 5
 WT_SUM_EQ17, WT_SUM_EQ16, WT_SUM_EQ17_REGROUPED = 0, 1, 2
 WT_PREDICT_TREE, WT_PREDICT_DIRECT = 0, 1
 WT_RESPONSE_SNAPPED, WT_RESPONSE_LEARNED, WT_RESPONSE_EXACT = 0, 1, 2

@@ -18,6 +18,13 @@
 #include "wt_internal.cuh"
 
 namespace wt {
+
+// dft_tc.cu: the tensor-core form (WT_MIXED_TC)
+size_t dft_tc_scratch_bytes(int64_t n_comp);
+int dft_tc_launch(const double* l, const double* m, const double* flux, int64_t n_comp, const void* recs,
+                  const uint32_t* bound, void* tc, const double* uvw, int64_t n_vis, float2* vis, int sign,
+                  int* status, cudaStream_t s);
+
 namespace {
 
 constexpr int kChunk = 512;
@@ -314,6 +321,25 @@ int dft_launch_packed(const void* scratch, const uint32_t* bound, int64_t n_comp
     return WT_OK;
 }
 
+// The exact pass of the mixed fast direct sum over 128-visibility tiles
+// (64 threads, two visibilities each): only the tiles whose first
+// visibility carries kDeferredMark are evaluated (the tensor-core form's
+// tiles beyond its range).
+int dft_exact_pass_128(const void* recs, const uint32_t* bound, int64_t n_comp, const double* uvw, int64_t n_vis,
+                       float2* vis, int sign, int* status, cudaStream_t s)
+{
+    constexpr int NT = 64;
+    const size_t smem = static_cast<size_t>(stager_bytes<CompF>(kChunk));
+    auto ke = k_dft_mixed<NT, true, false>;
+    dim3 grid;
+    int rc = grid_for(ke, NT, 2 * NT, smem, n_vis, grid);
+    if (rc) return rc;
+    ke<<<grid, NT, smem, s>>>(static_cast<const CompF*>(recs), n_comp, bound, uvw, n_vis, vis,
+                              static_cast<float>(sign), status);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
 // Pack the components into `scratch` and, for the float forms, zero and
 // reduce their coordinate bounds at `bound` (16 bytes, 16-byte aligned).
 int dft_pack(const double* l, const double* m, const double* flux, int64_t n_comp, void* scratch, uint32_t* bound,
@@ -335,9 +361,11 @@ int predict_dft(const double* l, const double* m, const double* flux, int64_t n_
 {
     if (n_vis == 0) return WT_OK;
     // 32-byte records (a 16-byte multiple, as the bulk copies need), then
-    // the 16-byte block of coordinate bounds
-    const size_t rec_bytes = static_cast<size_t>(n_comp > 0 ? n_comp : 1) * 32;
-    const size_t bytes = rec_bytes + 256;
+    // the 16-byte block of coordinate bounds; the tensor-core form's slices
+    // after them
+    const bool tc = mode == WT_MIXED_TC;
+    const size_t rec_bytes = ((static_cast<size_t>(n_comp > 0 ? n_comp : 1) * 32 + 255) / 256) * 256;
+    const size_t bytes = rec_bytes + 256 + (tc ? dft_tc_scratch_bytes(n_comp) : 0);
     void* scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
     if (e != cudaSuccess) {
@@ -351,8 +379,14 @@ int predict_dft(const double* l, const double* m, const double* flux, int64_t n_
         cudaFreeAsync(scratch, s);
         return set_error(WT_ERR_CUDA, "dft_predict_vis: no device status word");
     }
-    int rc = dft_pack(l, m, flux, n_comp, scratch, bound, mode, status, s);
-    if (rc == WT_OK) rc = dft_launch_packed(scratch, bound, n_comp, uvw, n_vis, vis, mode, sign, status, s);
+    int rc = dft_pack(l, m, flux, n_comp, scratch, bound, tc ? WT_MIXED_FAST : mode, status, s);
+    if (rc == WT_OK) {
+        if (tc)
+            rc = dft_tc_launch(l, m, flux, n_comp, scratch, bound, static_cast<unsigned char*>(scratch) + rec_bytes + 256,
+                               uvw, n_vis, static_cast<float2*>(vis), sign, status, s);
+        else
+            rc = dft_launch_packed(scratch, bound, n_comp, uvw, n_vis, vis, mode, sign, status, s);
+    }
     cudaError_t ef = cudaFreeAsync(scratch, s);
     if (rc != WT_OK) return rc;
     if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync");

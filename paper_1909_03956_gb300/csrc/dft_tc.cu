@@ -1,0 +1,425 @@
+// dft_tc.cu -- the direct sum (Sec. 3.3, Eq. 12) with its phase contraction
+// on the 5th-generation tensor cores (mode WT_MIXED_TC).
+//
+// The phase of visibility n against component m is a contraction over the
+// three coordinates, t = u l + v m + w (n - 1) turns: a matrix product of the
+// n_vis x 3 baselines with the 3 x n_comp component coordinates. Only t
+// modulo 1 matters, to about 2^-30 turns, while |t| reaches 2^14 turns, so
+// float32 products cannot carry it. Here every coordinate is cut into exact
+// 11-bit integer slices (float16 holds integers up to 2048 exactly), the
+// products of slices are summed on the tensor cores (exact: each product is
+// an integer below 2^20 and each sum stays below 2^24), and the three FP32
+// accumulators are recombined modulo 1 in float32 with exact steps only.
+//
+// Slicing. For coordinate c, q_c is fixed per call by the components' bound
+// (|s_c| < 1024 2^q_c). A component coordinate s = sum_j b_j 2^(q_c - 11 j),
+// j = 0..3, with b_j = rint of the remainder (|b_j| <= 1024); a baseline
+// coordinate x = sum_i a_i 2^(-q_c - 11 i), i = 0..4 (|a_0| <= 16 is the
+// tile's condition, see below; |a_i| <= 1024). The product of slices a_i b_j
+// carries the scale 2^(-11 (i + j)), so i + j = 0 is an integer and drops
+// out modulo 1, and the rest is, per (visibility, component),
+//   acc1 = sum_c (a0 b1 + a1 b0)                               (scale 2^-11)
+//   acc2 = sum_c (a0 b2 + a1 b1 + a2 b0)                       (scale 2^-22)
+//   acc3 = sum_c (a0 b3 + a1 b2 + a2 b1 + a3 b0)
+//        + 2^-11 sum_c (a1 b3 + a2 b2 + a3 b1 + a4 b0)         (scale 2^-33)
+// acc1 and acc2 are sums of at most 9 integer products below 2^20 x 1.01:
+// exact in FP32 whatever the order of addition. acc3 is a small tail.
+// Dropped: the slices' truncations (below 2^-30 turns for |a_0| <= 16) and
+// i + j = 5 (below 2^-31 turns).
+//
+// Recombination (float32, exact until the last two roundings):
+//   f1 = acc1 2^-11 - rint(acc1 2^-11)        (|acc1 2^-11| < 2^12: exact)
+//   h  = acc2 2^-22 + f1                      (a multiple of 2^-22 below 2: exact)
+//   t  = (h - rint(h)) + acc3 2^-33           (one rounding)
+// rint by the 1.5 2^23 constant; sin/cos of 2 pi t from the special-function
+// unit as in WT_MIXED_FAST.
+//
+// Layout. A tile is 128 visibilities (the MMA's M); each row of the A
+// operand holds a visibility's 64 float16 slice products' left factors, in
+// four K = 16 blocks (one MMA each): block 0 -> acc1, block 1 -> acc2,
+// blocks 2 and 3 -> acc3. The components' B operand is built once per call
+// by k_tc_slice_components in the same no-swizzle K-major layout, chunks of
+// NC components (the MMA's N), and streamed through shared memory by bulk
+// copies, two stages of 16 KB. Per chunk one thread issues the four MMAs
+// into one of two tensor-memory buffers (3 NC columns each) and commits to
+// an mbarrier; while the tensor cores fill the next buffer, every thread
+// reads its own row of the current one (tcgen05.ld), forms the terms
+// C_m (cos, sin) and adds them, eight at a time, to its Kahan sum.
+//
+// A tile whose baselines exceed the condition (|a_0| <= 16, i.e. phases
+// below 2^14 turns per coordinate) or are not finite is marked and left to
+// the exact pass of the double-float direct sum (dft.cu).
+#include <cuda_fp16.h>
+
+#include "tcgen05.cuh"
+#include "wt_internal.cuh"
+
+namespace wt {
+
+// dft.cu: the exact pass of the mixed direct sum over 128-visibility tiles
+// marked by mark_deferred.
+int dft_exact_pass_128(const void* recs, const uint32_t* bound, int64_t n_comp, const double* uvw, int64_t n_vis,
+                       float2* vis, int sign, int* status, cudaStream_t s);
+
+namespace {
+
+constexpr int kTcRows = 128;                // visibilities per tile (M of the MMA)
+constexpr int kTcNC = 32;                   // components per chunk (N of the MMA)
+constexpr int kTcStageBytes = 16384;        // B operand per stage
+constexpr int kTcG = kTcStageBytes / (kTcNC * 128);   // chunks per stage
+constexpr int kTcStageComps = kTcG * kTcNC;
+constexpr int kTcAcc = 3 * kTcNC;           // tensor-memory columns per buffer
+constexpr uint32_t kTcTmemCols = 256;       // two buffers, rounded to a power of two
+constexpr int kTcEmptyQ = -200;             // q of a coordinate that is zero for every component
+constexpr float kTcMaxA0 = 16.0f;           // |a_0| bound of a tile on the tensor cores
+static_assert(2 * kTcAcc <= static_cast<int>(kTcTmemCols), "tensor memory of the two buffers");
+static_assert(kTcG >= 1 && kTcG * kTcNC * 128 == kTcStageBytes, "stage layout");
+
+constexpr uint32_t kTcIdesc = idesc_f16(false, kTcRows, kTcNC);
+
+// q with |s| < 1024 2^q for every component coordinate s, from the bound of
+// the float32 heads (raised by 2^-20 to cover their rounding).
+__device__ __forceinline__ int tc_exponent(uint32_t bound_bits)
+{
+    const float b = __uint_as_float(bound_bits);
+    if (!(b > 0.0f)) return kTcEmptyQ;
+    return ilogb(static_cast<double>(b) * (1.0 + 0x1p-20)) - 9;
+}
+
+// n slices of y (float64): d_k = rint of the remainder, the remainder then
+// scaled by 2^11. Every step is exact.
+template <int N>
+__device__ __forceinline__ void tc_slices(double y, float (&d)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const double r = rint(y);
+        d[k] = static_cast<float>(r);
+        y = (y - r) * 2048.0;
+    }
+}
+
+__device__ __forceinline__ uint32_t half2_bits(float lo, float hi)
+{
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Row r of a 64-column float16 operand from v[64], in the umma_off layout
+// at base (8 stores of 16 bytes).
+__device__ __forceinline__ void tc_store_row(unsigned char* base, int r, const float (&v)[64])
+{
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const uint4 q = make_uint4(half2_bits(v[8 * g], v[8 * g + 1]), half2_bits(v[8 * g + 2], v[8 * g + 3]),
+                                   half2_bits(v[8 * g + 4], v[8 * g + 5]), half2_bits(v[8 * g + 6], v[8 * g + 7]));
+        *reinterpret_cast<uint4*>(base + umma_off(r, 8 * g)) = q;
+    }
+}
+
+// The B operand: component i (of n_pad, zero beyond n) as row i % NC of
+// chunk i / NC (chunks of NC x 128 bytes, contiguous), and its flux as
+// float32. The coordinates are formed as k_pack_components forms them (a
+// component that fails its range check there adds nothing here either).
+__global__ void k_tc_slice_components(const double* __restrict__ l, const double* __restrict__ m,
+                                      const double* __restrict__ flux, int64_t n, int64_t n_pad,
+                                      const uint32_t* __restrict__ bound, unsigned char* __restrict__ bsl,
+                                      float* __restrict__ bfl)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    float f = 0.0f;
+    if (i < n) {
+        const double li = l[i], mi = m[i], fi = flux[i];
+        const double r2 = li * li + mi * mi;
+        if (r2 < 1.0 && isfinite(li) && isfinite(mi) && isfinite(fi)) {
+            s[0] = li;
+            s[1] = mi;
+            s[2] = -r2 / (1.0 + sqrt(1.0 - r2));
+            f = static_cast<float>(fi);
+        }
+    }
+    float b[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tc_slices<4>(scalbn(s[c], -tc_exponent(bound[c])), b[c]);
+    float v[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = b[c][1];            // block 0 (acc1): a0 b1, a1 b0
+        v[3 + c] = b[c][0];
+        v[16 + c] = b[c][2];       // block 1 (acc2): a0 b2, a1 b1, a2 b0
+        v[19 + c] = b[c][1];
+        v[22 + c] = b[c][0];
+        v[32 + c] = b[c][3];       // block 2 (acc3): a0 b3, a1 b2, a2 b1, a3 b0, 2^-11 a4 b0
+        v[35 + c] = b[c][2];
+        v[38 + c] = b[c][1];
+        v[41 + c] = b[c][0];
+        v[44 + c] = b[c][0];
+        v[48 + c] = b[c][3];       // block 3 (acc3): 2^-11 (a1 b3, a2 b2, a3 b1)
+        v[51 + c] = b[c][2];
+        v[54 + c] = b[c][1];
+    }
+    tc_store_row(bsl + (i / kTcNC) * (kTcNC * 128), static_cast<int>(i % kTcNC), v);
+    bfl[i] = f;
+}
+
+// Plain arrive on an mbarrier (one of its expected arrivals).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// The direct sum of one tile of 128 visibilities per CTA (see the top of
+// the file), warp-specialised: warps 0-3 own a visibility per thread (TMEM
+// lane = row = thread) and form the terms; warp 4 (one lane) streams the B
+// operand and issues the MMAs. Two tensor-memory buffers: the producer fills
+// buffer i & 1 with chunk i once the epilogue warps have read chunk i - 2
+// out of it (mbarrier `empty`, one arrival per warp, given as soon as a
+// warp's tcgen05.ld of the three accumulators completes), and commits to
+// `full`. The B operand comes in stages of kTcG chunks, two slots; the slot
+// of stage s - 1 is refilled with stage s + 1 once the MMAs that read it
+// have completed (tcgen05.commit to `sdone` after a stage's last chunk).
+// Fluxes are read from global memory (all lanes one address, L1-resident).
+// Every wait is bounded; a wait that runs out records WT_ERR_TIMEOUT, the
+// producer then waits once more (bounded) for its copies and MMAs in flight,
+// and the CTA frees its tensor memory and leaves.
+constexpr int kTcThreads = 160;
+
+__global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __restrict__ bsl,
+                                                      const float* __restrict__ bfl, int64_t n_chunks,
+                                                      int64_t n_stages, const uint32_t* __restrict__ bound,
+                                                      const double* __restrict__ uvw, int64_t n_vis,
+                                                      float2* __restrict__ vis, float sgn, int* status)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_ld[2], bar_sdone[2];
+    __shared__ uint32_t tmem_base;
+    unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + kTcRows * 128;
+
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane_id = t & 31;
+    const bool epi = warp < 4;
+    const int64_t tile = blockIdx.x;
+    const int64_t n = tile * kTcRows + t;
+    const bool live = epi && n < n_vis;
+    const double sg = static_cast<double>(sgn);       // the sign folded into the baseline (exact)
+    bool fits = true;
+    if (epi) {
+        double x[3] = {0.0, 0.0, 0.0};
+        if (live) {
+            x[0] = sg * uvw[3 * n];
+            x[1] = sg * uvw[3 * n + 1];
+            x[2] = sg * uvw[3 * n + 2];
+        }
+        float a[3][5];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double y = scalbn(x[c], tc_exponent(bound[c]));
+            fits = fits && fabs(y) <= static_cast<double>(kTcMaxA0);   // false for a NaN
+            tc_slices<5>(fits ? y : 0.0, a[c]);
+        }
+        float v[64];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = 0.0f;
+        constexpr float s11 = 0x1p-11f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = a[c][0];
+            v[3 + c] = a[c][1];
+            v[16 + c] = a[c][0];
+            v[19 + c] = a[c][1];
+            v[22 + c] = a[c][2];
+            v[32 + c] = a[c][0];
+            v[35 + c] = a[c][1];
+            v[38 + c] = a[c][2];
+            v[41 + c] = a[c][3];
+            v[44 + c] = a[c][4] * s11;
+            v[48 + c] = a[c][1] * s11;
+            v[51 + c] = a[c][2] * s11;
+            v[54 + c] = a[c][3] * s11;
+        }
+        tc_store_row(sA, t, v);
+    }
+    if (!__syncthreads_and(fits ? 1 : 0)) {
+        mark_deferred(vis + tile * kTcRows);          // left to the exact pass
+        return;
+    }
+    if (t == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_full[b], 1);
+            mbar_init(&bar_empty[b], 4);
+            mbar_init(&bar_ld[b], 1);
+            mbar_init(&bar_sdone[b], 1);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, kTcTmemCols);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A's generic writes before the MMAs read it
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = tmem_base;
+
+    if (warp == 4) {
+        // ------------------------------------------------------------ producer
+        if (lane_id == 0 && n_chunks > 0) {
+            const uint32_t a_addr = smem_addr(sA), b_addr = smem_addr(sB);
+            int64_t st_issued = 0, mma_issued = 0;
+            auto issue_stage = [&](int64_t s) {
+                const int slot = static_cast<int>(s & 1);
+                mbar_arrive_expect_tx(&bar_ld[slot], kTcStageBytes);
+                bulk_copy_g2s(sB + slot * kTcStageBytes, bsl + s * kTcStageBytes, kTcStageBytes, &bar_ld[slot]);
+                st_issued = s + 1;
+            };
+            issue_stage(0);
+            if (n_stages > 1) issue_stage(1);
+            bool ok = true;
+            for (int64_t i = 0; i < n_chunks && ok; ++i) {
+                const int b = static_cast<int>(i & 1);
+                const int64_t s = i / kTcG;
+                const int w = static_cast<int>(i % kTcG);
+                if (i >= 2) ok = mbar_wait_parity(&bar_empty[b], static_cast<uint32_t>(((i >> 1) - 1) & 1));
+                if (ok && w == 0) ok = mbar_wait_parity(&bar_ld[s & 1], static_cast<uint32_t>((s >> 1) & 1));
+                if (ok && w == 1 && s >= 1 && s + 1 < n_stages) {
+                    // stage s - 1's MMAs are done: its slot takes stage s + 1
+                    ok = mbar_wait_parity(&bar_sdone[(s - 1) & 1], static_cast<uint32_t>(((s - 1) >> 1) & 1));
+                    if (ok) issue_stage(s + 1);
+                }
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t bb = b_addr + static_cast<uint32_t>(s & 1) * kTcStageBytes + w * (kTcNC * 128);
+                const uint32_t col = tm + static_cast<uint32_t>(b) * kTcAcc;
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) {
+                    const uint32_t d = col + (kb == 0 ? 0u : kb == 1 ? kTcNC : 2u * kTcNC);
+                    tc_mma_f16(d, umma_desc(a_addr + kb * 256), umma_desc(bb + kb * 256), kTcIdesc, kb == 3);
+                }
+                tc_commit(&bar_full[b]);
+                if (w == kTcG - 1 || i + 1 == n_chunks) tc_commit(&bar_sdone[s & 1]);
+                mma_issued = i + 1;
+            }
+            if (!ok) {
+                record_status(status, WT_ERR_TIMEOUT);
+                // once more, bounded, for what is in flight: the last two
+                // chunks' MMAs and the stages issued (a completed phase
+                // passes at once)
+                for (int64_t c = mma_issued >= 2 ? mma_issued - 2 : 0; c < mma_issued; ++c)
+                    mbar_wait_parity(&bar_full[c & 1], static_cast<uint32_t>((c >> 1) & 1));
+                for (int64_t s = st_issued >= 2 ? st_issued - 2 : 0; s < st_issued; ++s)
+                    mbar_wait_parity(&bar_ld[s & 1], static_cast<uint32_t>((s >> 1) & 1));
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const uint32_t lane = tm + (static_cast<uint32_t>(warp * 32) << 16);
+        const float2 M2 = bcast2(12582912.0f);        // 1.5 2^23: x + M2 - M2 = rint(x) for |x| < 2^22
+        const float2 s11 = bcast2(0x1p-11f), s22 = bcast2(0x1p-22f);
+        const float2 twopi = bcast2(6.28318530717958648f), s33 = bcast2(6.28318530717958648f * 0x1p-33f);
+        float2 acc = make_float2(0.f, 0.f), cmp = make_float2(0.f, 0.f);
+        bool ok = true;
+        for (int64_t i = 0; i < n_chunks; ++i) {
+            const int b = static_cast<int>(i & 1);
+            ok = __all_sync(0xffffffffu, mbar_wait_parity(&bar_full[b], static_cast<uint32_t>((i >> 1) & 1)));
+            if (!ok) break;
+            tc_fence_after();
+            uint32_t r1[32], r2[32], r3[32];
+            const uint32_t col = lane + static_cast<uint32_t>(b) * kTcAcc;
+            tmem_ld32(col, r1);
+            tmem_ld32(col + kTcNC, r2);
+            tmem_ld32(col + 2 * kTcNC, r3);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane_id == 0) mbar_arrive(&bar_empty[b]);   // the buffer may be refilled
+            const float4* fl = reinterpret_cast<const float4*>(bfl + i * kTcNC);
+#pragma unroll
+            for (int g = 0; g < kTcNC / 8; ++g) {
+                const float4 fa = __ldg(fl + 2 * g), fb = __ldg(fl + 2 * g + 1);
+                const float fx[8] = {fa.x, fa.y, fa.z, fa.w, fb.x, fb.y, fb.z, fb.w};
+                float2 p = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    const int k = 8 * g + j;
+                    const float2 A1 = make_float2(__uint_as_float(r1[k]), __uint_as_float(r1[k + 1]));
+                    const float2 A2 = make_float2(__uint_as_float(r2[k]), __uint_as_float(r2[k + 1]));
+                    const float2 A3 = make_float2(__uint_as_float(r3[k]), __uint_as_float(r3[k + 1]));
+                    const float2 y = fma2(A1, s11, M2);
+                    const float2 f1 = fma2(A1, s11, sub2(M2, y));         // acc1 2^-11 mod 1, exact
+                    const float2 h = fma2(A2, s22, f1);                   // exact
+                    const float2 hp = add2(h, sub2(M2, add2(h, M2)));     // h - rint(h), exact
+                    const float2 xa = fma2(A3, s33, mul2(hp, twopi));     // 2 pi t
+                    float s0, c0, s1, c1;
+                    __sincosf(xa.x, &s0, &c0);
+                    __sincosf(xa.y, &s1, &c1);
+                    p = fma2(bcast2(fx[j]), make_float2(c0, s0), p);
+                    p = fma2(bcast2(fx[j + 1]), make_float2(c1, s1), p);
+                }
+                kahan_add2(acc, cmp, p);
+            }
+        }
+        if (!ok && lane_id == 0) record_status(status, WT_ERR_TIMEOUT);
+        __syncwarp();
+        if (ok && live) vis[n] = sub2(acc, cmp);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_free(tm, kTcTmemCols);
+}
+
+}  // namespace
+
+// Bytes of the tensor-core form's component operand after the packed
+// records: the float16 slices and the float32 fluxes of n_comp components
+// padded to whole stages.
+size_t dft_tc_scratch_bytes(int64_t n_comp)
+{
+    const int64_t stages = (n_comp + kTcStageComps - 1) / kTcStageComps;
+    return static_cast<size_t>(stages) * (kTcStageBytes + kTcStageComps * 4);
+}
+
+// The tensor-core direct sum on components already packed (recs, bound:
+// k_pack_components in the mixed layout) with `tc` (dft_tc_scratch_bytes,
+// 256-byte aligned) for the slices; then the exact pass over the tiles left
+// to it.
+int dft_tc_launch(const double* l, const double* m, const double* flux, int64_t n_comp, const void* recs,
+                  const uint32_t* bound, void* tc, const double* uvw, int64_t n_vis, float2* vis, int sign,
+                  int* status, cudaStream_t s)
+{
+    if (n_vis == 0) return WT_OK;
+    const int64_t stages = (n_comp + kTcStageComps - 1) / kTcStageComps;
+    const int64_t n_pad = stages * kTcStageComps;
+    unsigned char* bsl = static_cast<unsigned char*>(tc);
+    float* bfl = reinterpret_cast<float*>(bsl + stages * kTcStageBytes);
+    if (n_pad > 0) {
+        const int tb = 256;
+        k_tc_slice_components<<<static_cast<unsigned>((n_pad + tb - 1) / tb), tb, 0, s>>>(l, m, flux, n_comp, n_pad,
+                                                                                         bound, bsl, bfl);
+        WT_CUDA_TRY(cudaGetLastError());
+    }
+    // at most two CTAs per SM: their tensor memory (2 x 256 columns) is all
+    // of an SM's, so a third would wait in tcgen05.alloc
+    const size_t need = 1024 + kTcRows * 128 + 2 * kTcStageBytes;
+    size_t smem = need;
+    int per_sm = 0;
+    for (;;) {
+        WT_CUDA_TRY(cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_tc, kTcThreads, smem));
+        if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "dft_predict_vis: tensor-core kernel does not fit on an SM");
+        if (per_sm * kTcTmemCols <= 512) break;
+        smem += 8192;
+    }
+    const int64_t tiles = (n_vis + kTcRows - 1) / kTcRows;
+    if (tiles > 0x7fffffff) return set_error(WT_ERR_RANGE, "dft_predict_vis: too many visibilities for one launch");
+    k_dft_tc<<<static_cast<unsigned>(tiles), kTcThreads, smem, s>>>(bsl, bfl, stages * kTcG, stages, bound, uvw, n_vis,
+                                                                vis, static_cast<float>(sign), status);
+    WT_CUDA_TRY(cudaGetLastError());
+    return dft_exact_pass_128(recs, bound, n_comp, uvw, n_vis, vis, sign, status, s);
+}
+
+}  // namespace wt

@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "sphere.cuh"
+#include "tcgen05.cuh"
 #include "wt_internal.cuh"
 
 namespace wt {
@@ -164,46 +165,9 @@ struct MlpDev {
 constexpr int kApplyThreads = 128;
 constexpr uint32_t kTmemCols = 64;   // the 128 x 64 FP32 accumulator
 
-// Byte offset of element (r, k) of an [r][64] bf16 operand in the
-// no-swizzle K-major layout of the tensor cores: core matrices of 8 rows x
-// 16 bytes, core (r/8, k/8) at (r/8) 1024 + (k/8) 128, row r%8 at 16 bytes,
-// element k%8 at 2 bytes.
-__device__ __forceinline__ uint32_t umma_off(int r, int k)
-{
-    return static_cast<uint32_t>((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor of such an operand: start address, the
-// leading byte offset (stride between core matrices along K, 128), the
-// stride byte offset (between 8-row groups, 1024), descriptor version 1,
-// base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
-{
-    return static_cast<uint64_t>((saddr >> 4) & 0x3fff) | (static_cast<uint64_t>(128 >> 4) << 16) |
-           (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46);
-}
-
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, BF16 A
-// and B, both K-major, N = 64 (bits 17-22: N/8), M = 128 (bits 24-28: M/16).
-constexpr uint32_t kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 consecutive accumulator columns of this thread's TMEM lane (its warp's
-// quarter of the 128 lanes, lane = row = sample).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-}
+// and B, both K-major, M = 128, N = 64.
+constexpr uint32_t kMlpIdesc = idesc_f16(true, 128, 64);
 
 // Inference of the 3 -> 64 -> 64 -> 2 network on the 5th-generation tensor
 // cores. Per tile of 128 samples: every thread computes its sample's first

@@ -460,7 +460,7 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
     if (n_comp < 0 || n_vis < 0) return set_error(WT_ERR_ARG, "%s: negative size", fn);
     if (n_comp > (int64_t(1) << 30)) return set_error(WT_ERR_RANGE, "%s: n_comp too large", fn);
     if (sign != 1 && sign != -1) return set_error(WT_ERR_ARG, "%s: sign must be +1 or -1", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST && mode != WT_FP64_DF)
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST && mode != WT_FP64_DF && mode != WT_MIXED_TC)
         return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
     const size_t nb = static_cast<size_t>(n_comp) * 8;
     const size_t ob = static_cast<size_t>(n_vis) * ((mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8);

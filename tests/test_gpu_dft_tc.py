@@ -1,0 +1,124 @@
+"""The direct sum (Eq. 12) with its phase contraction on the tensor cores
+(WT_MIXED_TC): exact float16 slices of the baselines and of the component
+coordinates, summed by tcgen05.mma into three FP32 accumulators and
+recombined modulo 1 in float32. Held to the mixed forms' bar (1e-6 of
+sum |C|) against the oracle's Eq. 12 on the synthetic workloads, across
+stage and chunk boundaries, ragged tiles, both signs, the degenerate skies,
+and tiles beyond the tensor-core range (left to the exact pass).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+wt = pytest.importorskip("paper_1909_03956_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOLMIX = 1e-6
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def predict(l, m, f, uvw, mode=wt.WT_MIXED_TC, sign=1):
+    return wt.dft_predict_vis(dev(l), dev(m), dev(f), dev(uvw), mode=mode, sign=sign).cpu().numpy()
+
+
+def rel_err(l, m, f, uvw, sign=1):
+    v = predict(l, m, f, uvw, sign=sign)
+    return float(np.max(np.abs(v - O.dft(l, m, f, uvw, sign))) / np.abs(f).sum())
+
+
+def sky(n, half_width_rad, rng):
+    return (rng.uniform(-half_width_rad, half_width_rad, n), rng.uniform(-half_width_rad, half_width_rad, n),
+            10.0 ** rng.uniform(-3, 0, n))
+
+
+def test_small_workload_every_visibility_both_signs():
+    w = synth.small()
+    assert rel_err(w.l, w.m, w.flux, w.uvw) <= TOLMIX
+    assert rel_err(w.l, w.m, w.flux, w.uvw, sign=-1) <= TOLMIX
+
+
+def test_medium_workload_sample():
+    # 5 000 clustered components (40 stages of 128) against a strided sample
+    # of the medium array's visibilities, ragged at both ends
+    w = synth.medium()
+    uvw = w.uvw[::97][:12345]
+    assert rel_err(w.l, w.m, w.flux, uvw) <= TOLMIX
+
+
+@pytest.mark.parametrize("n_comp", [1, 31, 32, 33, 127, 128, 129, 257, 1000])
+def test_chunk_and_stage_boundaries(n_comp):
+    rng = np.random.default_rng(900 + n_comp)
+    l, m, f = sky(n_comp, 0.03, rng)
+    uvw = rng.uniform(-4e4, 4e4, (1000, 3))   # 7 full tiles and a ragged one
+    assert rel_err(l, m, f, uvw) <= TOLMIX
+
+
+def test_matches_the_fast_mixed_form():
+    # same terms, same sin/cos unit: the two forms differ by their phases'
+    # last roundings only
+    rng = np.random.default_rng(910)
+    l, m, f = sky(3000, 0.02, rng)
+    uvw = rng.uniform(-3e4, 3e4, (5000, 3))
+    a = predict(l, m, f, uvw)
+    b = predict(l, m, f, uvw, mode=wt.WT_MIXED_FAST)
+    assert np.max(np.abs(a - b)) / f.sum() <= TOLMIX
+
+
+def test_single_component_worst_case():
+    # one component: no averaging over terms, the per-term bound must hold
+    rng = np.random.default_rng(911)
+    l, m, f = np.array([0.0123]), np.array([-0.0071]), np.array([1.0])
+    for scale in (3e3, 3e5):
+        uvw = rng.uniform(-scale, scale, (20000, 3))
+        assert rel_err(l, m, f, uvw) <= TOLMIX
+        assert rel_err(l, m, f, uvw, sign=-1) <= TOLMIX
+
+
+def test_degenerate_skies():
+    rng = np.random.default_rng(912)
+    uvw = rng.uniform(-5e4, 5e4, (700, 3))
+    # every component at the phase centre: each coordinate's bound is 0 and
+    # V = sum of the fluxes on every baseline
+    f = 10.0 ** rng.uniform(-3, 0, 40)
+    z = np.zeros(40)
+    v = predict(z, z, f, uvw)
+    assert np.max(np.abs(v - f.sum())) / f.sum() <= TOLMIX
+    # components on the l axis only (m and n - 1 bounds from l alone)
+    l = rng.uniform(-0.01, 0.01, 40)
+    assert rel_err(l, z, f, uvw) <= TOLMIX
+    # zero baselines: V = sum of the fluxes
+    l, m, f = sky(60, 0.05, rng)
+    v = predict(l, m, f, np.zeros((300, 3)))
+    assert np.max(np.abs(v - f.sum())) / f.sum() <= TOLMIX
+    # no components: every visibility 0
+    e = np.zeros(0)
+    v = predict(e, e, e, uvw)
+    assert np.array_equal(v, np.zeros(len(uvw), dtype=v.dtype))
+
+
+def test_tiles_beyond_the_tensor_core_range():
+    # long baselines in one visibility of every 500: the 128-visibility tiles
+    # that hold one exceed 2^14 turns per coordinate and take the exact pass
+    rng = np.random.default_rng(913)
+    l, m, f = sky(200, 0.3, rng)
+    uvw = rng.uniform(-2e3, 2e3, (6000, 3))
+    uvw[::500] = rng.uniform(5e4, 8e4, (len(uvw[::500]), 3)) * rng.choice([-1.0, 1.0], (len(uvw[::500]), 3))
+    assert rel_err(l, m, f, uvw) <= TOLMIX
+    assert rel_err(l, m, f, uvw, sign=-1) <= TOLMIX
+
+
+def test_repeatable_and_status_clear():
+    rng = np.random.default_rng(914)
+    l, m, f = sky(500, 0.02, rng)
+    uvw = rng.uniform(-3e4, 3e4, (2000, 3))
+    a = predict(l, m, f, uvw)
+    b = predict(l, m, f, uvw)
+    assert np.array_equal(a, b)
+    wt.wt_device_status()   # raises on a recorded device-side error

@@ -572,6 +572,13 @@ OPS_DF_NODE = 4 + 36 + 22
 OPS_DFT_FAST = OPS_PHASE_GRID + 3 + 2 + 4
 OPS_DFT = OPS_PHASE_GRID + 15 + 2 + 4
 OPS_DFT_FP64 = 21
+# Direct sum with the phase on the tensor cores (k_dft_tc), FMA-pipe element
+# ops per (visibility, component) in the epilogue: the accumulators'
+# recombination modulo 1 7, the angle 2, the SFU's scaling 1, the flux times
+# (cos, sin) 2, a Kahan add of a pair per eight terms 1 -> 13. Tensor cores:
+# four MMAs of K = 16 per (visibility, component), 128 flops.
+OPS_DFT_TC = 13
+TC_FLOPS_DFT_TERM = 128
 # Algorithmic work per (visibility, component) of the direct sum: the phase
 # (3 multiplies, 2 adds), its reduction (rounding and subtraction), the
 # complex multiply-add by a real flux (4): 11 flops, plus one sin and one cos.
@@ -631,7 +638,8 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
                                    ("wavelet_mixed_fast_eq17", wt.WT_MIXED_FAST, wt.WT_SUM_EQ17, out32),
                                    ("wavelet_mixed_fast_eq17_regrouped", wt.WT_MIXED_FAST, wt.WT_SUM_EQ17_REGROUPED,
                                     out32),
-                                   ("wavelet_mixed_fast_eq16", wt.WT_MIXED_FAST, wt.WT_SUM_EQ16, out32)]:
+                                   ("wavelet_mixed_fast_eq16", wt.WT_MIXED_FAST, wt.WT_SUM_EQ16, out32),
+                                   ("wavelet_mixed_tc_eq16", wt.WT_MIXED_TC, wt.WT_SUM_EQ16, out32)]:
         t = _time_call(lambda: wt.wt_predict_vis(tree, uvw, mode=mode, which=which, out=out), stream, flush)
         r[name + "_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_FP64, out=out64), stream, flush, reps=1)
@@ -642,6 +650,11 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
     r["dft_mixed_vis_per_s"] = n / t
     t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED_FAST, out=out32), stream, flush)
     r["dft_mixed_fast_vis_per_s"] = n / t
+    # the phase contraction on the tensor cores; its error against the
+    # double-float form still in out64 (float64-class, ~1e-13)
+    t = _time_call(lambda: wt.dft_predict_vis(l, m, fl, uvw, mode=wt.WT_MIXED_TC, out=out32), stream, flush)
+    r["dft_mixed_tc_vis_per_s"] = n / t
+    r["dft_mixed_tc_max_rel_err_vs_df"] = float((out32.to(torch.complex128) - out64).abs().max()) / float(fl.abs().sum())
     r["dft_terms"] = w.n_comp
     t = _time_call(lambda: wt.subtract_model(out32, out32, mode=wt.WT_MIXED, out=out32), stream, flush)
     r["subtract_c64_GBps"] = 24 * n / t / 1e9
@@ -690,6 +703,20 @@ def side_measurements(wt, torch, w, l, m, fl, uvw, tree, stream, flush, peaks):
     mlp_tflops = n_mlp * 8832 / t_mlp / 1e12
     roof = {
         "dft_mixed_fast": dft_roof(r["dft_mixed_fast_vis_per_s"], OPS_DFT_FAST),
+        "dft_mixed_tc": {"bound": "sfu",
+                         "frac": r["dft_mixed_tc_vis_per_s"] * nc * 2 / 1e12 / peaks["sfu_top_s"],
+                         "unit": "sin and cos of every term of the measured SFU rate (the phase is on the tensor "
+                                 "cores)",
+                         "alg_fp32_frac": r["dft_mixed_tc_vis_per_s"] * nc * ALG_FLOPS_DFT_TERM / 1e12
+                         / peaks["fp32_tflops"],
+                         "pipe_busy": {"frac": r["dft_mixed_tc_vis_per_s"] * nc * OPS_DFT_TC / 1e12
+                                       / peaks["fp32_top_s"], "ops_per_term": OPS_DFT_TC,
+                                       "unit": "the form's float32 FMA-pipe element ops per term, of the measured "
+                                               "rate"},
+                         "tensor": {"achieved_tflops": r["dft_mixed_tc_vis_per_s"] * nc * TC_FLOPS_DFT_TERM / 1e12,
+                                    "flops_per_term": TC_FLOPS_DFT_TERM,
+                                    "frac_of_bf16_peak": r["dft_mixed_tc_vis_per_s"] * nc * TC_FLOPS_DFT_TERM / 1e12
+                                    / BF16_PEAK_TFLOPS}},
         "dft_mixed": dft_roof(r["dft_mixed_vis_per_s"], OPS_DFT),
         "dft_fp64": dft_roof(r["dft_fp64_vis_per_s"], OPS_DFT_FP64, fp64=True),
         "dft_fp64_df": dft_roof(r["dft_fp64_df_vis_per_s"], OPS_DFT_DF),
@@ -1224,6 +1251,7 @@ def forms_once(args):
             ("wavelet_mixed", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_MIXED, out=o32)),
             ("wavelet_fp64", lambda: wt.wt_predict_vis(tree, uvw, mode=wt.WT_FP64, out=o64)),
             ("dft_mixed", lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=o32)),
+            ("dft_mixed_tc", lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED_TC, out=o32)),
             ("dft_fp64_131072", lambda: wt.dft_predict_vis(l, m, f, sub, mode=wt.WT_FP64, out=o64[:131072])),
             ("subtract_c64", lambda: wt.subtract_model(o32, o32, mode=wt.WT_MIXED, out=o32))]
     # the learned response's tensor-core inference on every visibility

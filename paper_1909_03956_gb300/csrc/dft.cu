@@ -32,10 +32,7 @@ constexpr int kChunk = 512;
 struct CompD {
     double l, m, nm1, flux;
 };
-struct CompF {
-    float lh, ll, mh, ml, nh, nl, flux, flux_lo;   // flux_lo: the double-float form's low half of C
-};
-static_assert(sizeof(CompD) == 32 && sizeof(CompF) == 32, "component record layout");
+static_assert(sizeof(CompD) == 32, "component record layout");
 
 // n - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)), free of cancellation.
 // bound (float records only; zeroed before the launch): the largest |l|,

@@ -64,12 +64,13 @@ int dft_exact_pass_128(const void* recs, const uint32_t* bound, int64_t n_comp, 
 namespace {
 
 constexpr int kTcRows = 128;                // visibilities per tile (M of the MMA)
-constexpr int kTcNC = 32;                   // components per chunk (N of the MMA)
+constexpr int kTcNC = 16;                   // components per chunk (N of the MMA)
 constexpr int kTcStageBytes = 16384;        // B operand per stage
 constexpr int kTcG = kTcStageBytes / (kTcNC * 128);   // chunks per stage
 constexpr int kTcStageComps = kTcG * kTcNC;
 constexpr int kTcAcc = 3 * kTcNC;           // tensor-memory columns per buffer
-constexpr uint32_t kTcTmemCols = 256;       // two buffers, rounded to a power of two
+// two buffers, rounded up to a power of two (at least 32 columns)
+constexpr uint32_t kTcTmemCols = 2 * kTcAcc <= 32 ? 32 : 2 * kTcAcc <= 64 ? 64 : 2 * kTcAcc <= 128 ? 128 : 2 * kTcAcc <= 256 ? 256 : 512;
 constexpr int kTcEmptyQ = -200;             // q of a coordinate that is zero for every component
 constexpr float kTcMaxA0 = 16.0f;           // |a_0| bound of a tile on the tensor cores
 static_assert(2 * kTcAcc <= static_cast<int>(kTcTmemCols), "tensor memory of the two buffers");
@@ -99,6 +100,29 @@ __device__ __forceinline__ void tc_slices(double y, float (&d)[N])
     }
 }
 
+// The five slices of a baseline coordinate from its fixed-point value Y =
+// rint(x 2^44) (|Y| <= 16 2^44): balanced base-2048 digits, least
+// significant first (d = Y mod 2048 in [-1024, 1024), then Y = (Y - d) / 2048
+// exactly), a[0] the rest (|a[0]| <= 16). The digits are the slices of x
+// after rounding it to 2^-44, the precision of its five float64 slices.
+// Integer steps and small-integer conversions by the 1.5 2^23 constant, so
+// that no float64 or conversion-unit work is needed.
+__device__ __forceinline__ float small_int_to_float(int d)
+{
+    return __int_as_float(0x4B400000 + d) - 12582912.0f;   // exact for |d| < 2^22
+}
+
+__device__ __forceinline__ void tc_slices5_int(long long Y, float (&a)[5])
+{
+#pragma unroll
+    for (int k = 4; k >= 1; --k) {
+        const int d = static_cast<int>((Y + 1024) & 2047) - 1024;
+        a[k] = small_int_to_float(d);
+        Y = (Y - d) >> 11;   // exact: Y - d is a multiple of 2048
+    }
+    a[0] = small_int_to_float(static_cast<int>(Y));
+}
+
 __device__ __forceinline__ uint32_t half2_bits(float lo, float hi)
 {
     const __half2 h = __floats2half2_rn(lo, hi);
@@ -117,29 +141,13 @@ __device__ __forceinline__ void tc_store_row(unsigned char* base, int r, const f
     }
 }
 
-// The B operand: component i (of n_pad, zero beyond n) as row i % NC of
-// chunk i / NC (chunks of NC x 128 bytes, contiguous), and its flux as
-// float32. The coordinates are formed as k_pack_components forms them (a
-// component that fails its range check there adds nothing here either).
-__global__ void k_tc_slice_components(const double* __restrict__ l, const double* __restrict__ m,
-                                      const double* __restrict__ flux, int64_t n, int64_t n_pad,
-                                      const uint32_t* __restrict__ bound, unsigned char* __restrict__ bsl,
-                                      float* __restrict__ bfl)
+// Row i of the B operand (component i as row i % NC of chunk i / NC;
+// chunks of NC x 128 bytes, contiguous) from its coordinates s (float64)
+// and the bounds' bits, and its flux as float32.
+__device__ __forceinline__ void tc_write_b_row(int64_t i, const double (&s)[3], float f,
+                                               const uint32_t* __restrict__ bound, unsigned char* __restrict__ bsl,
+                                               float* __restrict__ bfl)
 {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
-    double s[3] = {0.0, 0.0, 0.0};
-    float f = 0.0f;
-    if (i < n) {
-        const double li = l[i], mi = m[i], fi = flux[i];
-        const double r2 = li * li + mi * mi;
-        if (r2 < 1.0 && isfinite(li) && isfinite(mi) && isfinite(fi)) {
-            s[0] = li;
-            s[1] = mi;
-            s[2] = -r2 / (1.0 + sqrt(1.0 - r2));
-            f = static_cast<float>(fi);
-        }
-    }
     float b[3][4];
 #pragma unroll
     for (int c = 0; c < 3; ++c) tc_slices<4>(scalbn(s[c], -tc_exponent(bound[c])), b[c]);
@@ -166,6 +174,67 @@ __global__ void k_tc_slice_components(const double* __restrict__ l, const double
     bfl[i] = f;
 }
 
+// The B operand of the direct sum: component i of n_pad (zero beyond n).
+// The coordinates are formed as k_pack_components forms them (a component
+// that fails its range check there adds nothing here either).
+__global__ void k_tc_slice_components(const double* __restrict__ l, const double* __restrict__ m,
+                                      const double* __restrict__ flux, int64_t n, int64_t n_pad,
+                                      const uint32_t* __restrict__ bound, unsigned char* __restrict__ bsl,
+                                      float* __restrict__ bfl)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    float f = 0.0f;
+    if (i < n) {
+        const double li = l[i], mi = m[i], fi = flux[i];
+        const double r2 = li * li + mi * mi;
+        if (r2 < 1.0 && isfinite(li) && isfinite(mi) && isfinite(fi)) {
+            s[0] = li;
+            s[1] = mi;
+            s[2] = -r2 / (1.0 + sqrt(1.0 - r2));
+            f = static_cast<float>(fi);
+        }
+    }
+    tc_write_b_row(i, s, f, bound, bsl, bfl);
+}
+
+// The B operand of Eq. 16 over a tree's leaf records (RecF: the pixel
+// centre (s_u, s_v, s_w - 1) as double-float pairs, g = the merged flux
+// Phi_k; their number in hdr->n_leaves, their bounds in hdr->smax): leaf i
+// of cap_pad (zero beyond n_leaves). Also each leaf as a direct-sum record
+// (CompF) for the exact pass of the tiles beyond the tensor-core range.
+__global__ void k_tc_slice_leaves(const RecF* __restrict__ recs, const TreeHeader* __restrict__ hdr,
+                                  int64_t cap_pad, unsigned char* __restrict__ bsl, float* __restrict__ bfl,
+                                  CompF* __restrict__ exact)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= cap_pad) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    float f = 0.0f;
+    CompF e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < hdr->n_leaves) {
+        const RecF r = recs[i];
+        s[0] = static_cast<double>(r.a) + static_cast<double>(r.b);   // exact: a double-float pair
+        s[1] = static_cast<double>(r.c) + static_cast<double>(r.d);
+        s[2] = static_cast<double>(r.e) + static_cast<double>(r.f);
+        f = r.g;
+        e = CompF{r.a, r.b, r.c, r.d, r.e, r.f, r.g, 0.f};
+    }
+    tc_write_b_row(i, s, f, reinterpret_cast<const uint32_t*>(hdr->smax), bsl, bfl);
+    exact[i] = e;
+}
+
+// One accumulator's NC columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[kTcNC])
+{
+    if constexpr (kTcNC == 32) tmem_ld32(taddr, r);
+    else if constexpr (kTcNC == 16) tmem_ld16(taddr, r);
+    else {
+        static_assert(kTcNC == 16 || kTcNC == 32, "chunks of 16 or 32 components");
+    }
+}
+
 // Plain arrive on an mbarrier (one of its expected arrivals).
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -190,10 +259,17 @@ constexpr int kTcThreads = 160;
 
 __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __restrict__ bsl,
                                                       const float* __restrict__ bfl, int64_t n_chunks,
-                                                      int64_t n_stages, const uint32_t* __restrict__ bound,
+                                                      int64_t n_stages, const int64_t* __restrict__ n_dev,
+                                                      const uint32_t* __restrict__ bound,
                                                       const double* __restrict__ uvw, int64_t n_vis,
                                                       float2* __restrict__ vis, float sgn, int* status)
 {
+    if (n_dev) {   // the count on the device (a tree's leaves): the chunks it needs, at most those allocated
+        const int64_t nd = *n_dev;
+        const int64_t nc = nd > 0 ? (nd + kTcNC - 1) / kTcNC : 0;
+        if (nc < n_chunks) n_chunks = nc;
+        n_stages = (n_chunks + kTcG - 1) / kTcG;
+    }
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_ld[2], bar_sdone[2];
     __shared__ uint32_t tmem_base;
@@ -219,9 +295,10 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
         float a[3][5];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double y = scalbn(x[c], tc_exponent(bound[c]));
-            fits = fits && fabs(y) <= static_cast<double>(kTcMaxA0);   // false for a NaN
-            tc_slices<5>(fits ? y : 0.0, a[c]);
+            // y = x 2^q in units of 2^-44: one exact scaling, one rounding
+            const double y = x[c] * scalbn(1.0, tc_exponent(bound[c]) + 44);
+            fits = fits && fabs(y) <= static_cast<double>(kTcMaxA0) * 0x1p44;   // false for a NaN
+            tc_slices5_int(fits ? __double2ll_rn(y) : 0ll, a[c]);
         }
         float v[64];
 #pragma unroll
@@ -327,11 +404,11 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
             ok = __all_sync(0xffffffffu, mbar_wait_parity(&bar_full[b], static_cast<uint32_t>((i >> 1) & 1)));
             if (!ok) break;
             tc_fence_after();
-            uint32_t r1[32], r2[32], r3[32];
+            uint32_t r1[kTcNC], r2[kTcNC], r3[kTcNC];
             const uint32_t col = lane + static_cast<uint32_t>(b) * kTcAcc;
-            tmem_ld32(col, r1);
-            tmem_ld32(col + kTcNC, r2);
-            tmem_ld32(col + 2 * kTcNC, r3);
+            tmem_ld_cols(col, r1);
+            tmem_ld_cols(col + kTcNC, r2);
+            tmem_ld_cols(col + 2 * kTcNC, r3);
             tmem_wait_ld();
             tc_fence_before();
             __syncwarp();
@@ -383,6 +460,37 @@ size_t dft_tc_scratch_bytes(int64_t n_comp)
     return static_cast<size_t>(stages) * (kTcStageBytes + kTcStageComps * 4);
 }
 
+namespace {
+
+// Launch k_dft_tc over the tiles of n_vis visibilities: B operand bsl / bfl
+// of `stages` stages, n_chunks chunks of it used (or those *n_dev items
+// need, when n_dev is given).
+int tc_main_launch(const unsigned char* bsl, const float* bfl, int64_t n_chunks, int64_t stages, const int64_t* n_dev,
+                   const uint32_t* bound, const double* uvw, int64_t n_vis, float2* vis, int sign, int* status,
+                   cudaStream_t s, const char* fn)
+{
+    // no more CTAs per SM than their tensor memory allows (a CTA beyond
+    // that would wait in tcgen05.alloc): four of 128 columns
+    const size_t need = 1024 + kTcRows * 128 + 2 * kTcStageBytes;
+    size_t smem = need;
+    int per_sm = 0;
+    for (;;) {
+        WT_CUDA_TRY(cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_tc, kTcThreads, smem));
+        if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "%s: tensor-core kernel does not fit on an SM", fn);
+        if (per_sm * kTcTmemCols <= 512) break;
+        smem += 8192;
+    }
+    const int64_t tiles = (n_vis + kTcRows - 1) / kTcRows;
+    if (tiles > 0x7fffffff) return set_error(WT_ERR_RANGE, "%s: too many visibilities for one launch", fn);
+    k_dft_tc<<<static_cast<unsigned>(tiles), kTcThreads, smem, s>>>(bsl, bfl, n_chunks, stages, n_dev, bound, uvw,
+                                                                   n_vis, vis, static_cast<float>(sign), status);
+    WT_CUDA_TRY(cudaGetLastError());
+    return WT_OK;
+}
+
+}  // namespace
+
 // The tensor-core direct sum on components already packed (recs, bound:
 // k_pack_components in the mixed layout) with `tc` (dft_tc_scratch_bytes,
 // 256-byte aligned) for the slices; then the exact pass over the tiles left
@@ -402,24 +510,52 @@ int dft_tc_launch(const double* l, const double* m, const double* flux, int64_t 
                                                                                          bound, bsl, bfl);
         WT_CUDA_TRY(cudaGetLastError());
     }
-    // at most two CTAs per SM: their tensor memory (2 x 256 columns) is all
-    // of an SM's, so a third would wait in tcgen05.alloc
-    const size_t need = 1024 + kTcRows * 128 + 2 * kTcStageBytes;
-    size_t smem = need;
-    int per_sm = 0;
-    for (;;) {
-        WT_CUDA_TRY(cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_tc, kTcThreads, smem));
-        if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "dft_predict_vis: tensor-core kernel does not fit on an SM");
-        if (per_sm * kTcTmemCols <= 512) break;
-        smem += 8192;
-    }
-    const int64_t tiles = (n_vis + kTcRows - 1) / kTcRows;
-    if (tiles > 0x7fffffff) return set_error(WT_ERR_RANGE, "dft_predict_vis: too many visibilities for one launch");
-    k_dft_tc<<<static_cast<unsigned>(tiles), kTcThreads, smem, s>>>(bsl, bfl, stages * kTcG, stages, bound, uvw, n_vis,
-                                                                vis, static_cast<float>(sign), status);
-    WT_CUDA_TRY(cudaGetLastError());
+    int rc = tc_main_launch(bsl, bfl, (n_comp + kTcNC - 1) / kTcNC, stages, nullptr, bound, uvw, n_vis, vis, sign,
+                            status, s, "dft_predict_vis");
+    if (rc) return rc;
     return dft_exact_pass_128(recs, bound, n_comp, uvw, n_vis, vis, sign, status, s);
+}
+
+// Eq. 16 in the tensor-core form over leaf records (RecF, at most cap of
+// them, their count and bounds in the device header hdr): V = sum_k Phi_k
+// exp(sign i 2 pi B.(c_k - P)), the direct sum over the leaves' pixel
+// centres with their merged fluxes. The scratch (the B operand and the
+// exact pass's records) is allocated and released on the stream.
+int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, const double* uvw, int64_t n_vis,
+                   float2* vis, int sign, int* status, cudaStream_t s, const char* fn)
+{
+    if (n_vis == 0) return WT_OK;
+    const int64_t stages = (cap + kTcStageComps - 1) / kTcStageComps;
+    const int64_t cap_pad = stages * kTcStageComps;
+    const size_t exact_bytes = static_cast<size_t>(cap_pad > 0 ? cap_pad : 1) * sizeof(CompF);
+    const size_t bytes = ((exact_bytes + 255) / 256) * 256 + dft_tc_scratch_bytes(cap_pad);
+    unsigned char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WT_ERR_NOMEM, "%s: scratch allocation of %zu bytes failed: %s", fn, bytes,
+                         cudaGetErrorString(e));
+    }
+    CompF* exact = reinterpret_cast<CompF*>(scratch);
+    unsigned char* bsl = scratch + ((exact_bytes + 255) / 256) * 256;
+    float* bfl = reinterpret_cast<float*>(bsl + stages * kTcStageBytes);
+    int rc = WT_OK;
+    if (cap_pad > 0) {
+        const int tb = 256;
+        k_tc_slice_leaves<<<static_cast<unsigned>((cap_pad + tb - 1) / tb), tb, 0, s>>>(recs, hdr, cap_pad, bsl, bfl,
+                                                                                       exact);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(WT_ERR_CUDA, "%s: leaf slicing launch", fn);
+    }
+    const uint32_t* bound = reinterpret_cast<const uint32_t*>(hdr->smax);   // device address of the bounds
+    if (rc == WT_OK)
+        rc = tc_main_launch(bsl, bfl, stages * kTcG, stages, &hdr->n_leaves, bound, uvw, n_vis, vis, sign, status, s,
+                            fn);
+    // the exact pass over every capacity record (those beyond the count are zero)
+    if (rc == WT_OK) rc = dft_exact_pass_128(exact, bound, cap_pad, uvw, n_vis, vis, sign, status, s);
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (rc != WT_OK) return rc;
+    if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync");
+    return WT_OK;
 }
 
 }  // namespace wt

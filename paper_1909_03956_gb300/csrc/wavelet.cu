@@ -531,6 +531,14 @@ int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int 
                     cudaStream_t s)
 {
     if (n_vis == 0) return WT_OK;
+    if (mode == WT_MIXED_TC) {   // Eq. 16 as a direct sum over the leaves, the phase on the tensor cores
+        if (which != WT_SUM_EQ16)
+            return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis: WT_MIXED_TC is Eq. 16 only (WT_SUM_EQ16)");
+        int* status = device_status_word();
+        if (!status) return set_error(WT_ERR_CUDA, "wt_predict_vis: no device status word");
+        return eq16_tc_launch(t->d.leaff, t->d.hdr, t->cap_leaves, uvw, n_vis, static_cast<float2*>(vis), sign, status,
+                              s, "wt_predict_vis");
+    }
     WaveletJob jb;
     jb.recd = t->d.recd;
     jb.recf = t->d.recf;

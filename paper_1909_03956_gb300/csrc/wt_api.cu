@@ -442,7 +442,7 @@ int wt_predict_vis(wt_tree t, const double* uvw, int64_t n_vis, void* vis_out, i
         return set_error(WT_ERR_ARG, "%s: bad sum selector", fn);
     if (mode == WT_LEARNED)
         return set_error(WT_ERR_UNSUPPORTED, "%s: the learned response has its own entry point", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST && mode != WT_FP64_DF)
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_MIXED_FAST && mode != WT_FP64_DF && mode != WT_MIXED_TC)
         return set_error(WT_ERR_ARG, "%s: bad mode %d", fn, mode);
     if (mode == WT_FP64_DF && which == WT_SUM_EQ17)
         return set_error(WT_ERR_UNSUPPORTED, "%s: WT_FP64_DF evaluates the regrouped Eq. 17 and Eq. 16 only", fn);

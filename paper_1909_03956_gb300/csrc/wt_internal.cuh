@@ -500,6 +500,14 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
     sum = t;
 }
 
+// Component record of the direct sum's float forms (32 bytes): l, m and
+// n - 1 as double-float pairs, C's high half (flux) and low half (flux_lo,
+// the double-float form's).
+struct CompF {
+    float lh, ll, mh, ml, nh, nl, flux, flux_lo;
+};
+static_assert(sizeof(CompF) == 32, "component record layout");
+
 // ---------------------------------------------------------------- tree handle
 // Node records for the predictors, in post-order, pre-decoded at build time.
 // A thread keeps one column of a shared-memory "stack" of 4 (J - 1) rows:
@@ -720,6 +728,9 @@ void batch_forget_tree(wt_tree t);
 int check_device_buffer(const void* p, size_t bytes, const char* fn, const char* name, size_t align);
 // Alignment of a visibility buffer of `mode` (complex128 or complex64).
 inline size_t vis_align(int mode) { return (mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8; }
+// dft_tc.cu: Eq. 16 over leaf records with the phase on the tensor cores
+int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, const double* uvw, int64_t n_vis,
+                   float2* vis, int sign, int* status, cudaStream_t s, const char* fn);
 // dft.cu
 int predict_dft(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
                 int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s);

@@ -122,3 +122,63 @@ def test_repeatable_and_status_clear():
     b = predict(l, m, f, uvw)
     assert np.array_equal(a, b)
     wt.wt_device_status()   # raises on a recorded device-side error
+
+
+# ---------------------------------------------------------------- Eq. 16
+
+def eq16_err(w, J, uvw, sign=1):
+    """Eq. 16 in the tensor-core form against the oracle's Eq. 16 (the leaves'
+    pixel centres with their merged fluxes), relative to sum |C|."""
+    t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, J)
+    try:
+        v = wt.wt_predict_vis(t, dev(uvw), mode=wt.WT_MIXED_TC, which=wt.WT_SUM_EQ16, sign=sign).cpu().numpy()
+    finally:
+        t.close()
+    ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J).vis_eq16(uvw, sign)
+    return float(np.max(np.abs(v - ref)) / np.abs(w.flux).sum())
+
+
+@pytest.mark.parametrize("J", [1, 6, 12, 18])
+def test_eq16_small_workload(J):
+    w = synth.small()
+    assert eq16_err(w, J, w.uvw) <= TOLMIX
+    assert eq16_err(w, J, w.uvw[:999], sign=-1) <= TOLMIX
+
+
+def test_eq16_medium_workload():
+    # 1 115 leaves at J = 12 (9 stages of 128, the last one ragged)
+    w = synth.medium(n_t=6)
+    assert eq16_err(w, 12, w.uvw[::3]) <= TOLMIX
+
+
+def test_eq16_matches_the_fast_form_and_other_sums_are_refused():
+    w = synth.medium(n_t=4)
+    t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, 12)
+    try:
+        u = dev(w.uvw)
+        a = wt.wt_predict_vis(t, u, mode=wt.WT_MIXED_TC, which=wt.WT_SUM_EQ16).cpu().numpy()
+        b = wt.wt_predict_vis(t, u, mode=wt.WT_MIXED_FAST, which=wt.WT_SUM_EQ16).cpu().numpy()
+        assert np.max(np.abs(a - b)) / np.abs(w.flux).sum() <= TOLMIX
+        for which in (wt.WT_SUM_EQ17, wt.WT_SUM_EQ17_REGROUPED):
+            with pytest.raises(wt.WtError) as e:
+                wt.wt_predict_vis(t, u, mode=wt.WT_MIXED_TC, which=which)
+            assert e.value.status == wt.WT_ERR_UNSUPPORTED
+    finally:
+        t.close()
+
+
+def test_eq16_empty_tree_and_long_baselines():
+    rng = np.random.default_rng(915)
+    e = np.zeros(0)
+    t = wt.wt_build_tree(dev(e), dev(e), dev(e), synth.RA0, synth.DEC0, 10)
+    try:
+        v = wt.wt_predict_vis(t, dev(rng.uniform(-1e4, 1e4, (300, 3))), mode=wt.WT_MIXED_TC,
+                              which=wt.WT_SUM_EQ16).cpu().numpy()
+        assert np.array_equal(v, np.zeros(300, dtype=v.dtype))
+    finally:
+        t.close()
+    # a wide field and baselines beyond the tensor-core range in some tiles
+    w = synth.small()
+    uvw = w.uvw.copy()
+    uvw[::300] *= 400.0
+    assert eq16_err(w, 14, uvw) <= TOLMIX

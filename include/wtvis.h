@@ -472,7 +472,10 @@ int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis
  * nodes stand for their pixels, each with its pixel's flux
  * F_k = A_level lambda_level,k (Eq. 9: the merged flux below the node):
  *   V = R(B) sum_k F_k exp(sign i 2 pi B.(c_k - P))
- * (c_k the pixel centres, the sum in the fast mixed form), with
+ * (c_k the pixel centres, the sum in the fast mixed form, or, for a level
+ * of at least WT_TRUNCATED_TC_MIN_NODES nodes, in WT_MIXED_TC: the same
+ * terms with the phases on the tensor cores, faster there; the call then
+ * waits once for the tree's build stream to read the level's size), with
  *   response = WT_RESPONSE_SNAPPED: R = 1, each pixel's flux at its centre
  *              (Eq. 16 read at the truncation level);
  *              WT_RESPONSE_LEARNED: R = the network m of that level (exact
@@ -485,6 +488,7 @@ int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis
  * for that level and the tree's phase centre; depth (EXACT) 0..8. Output
  * device complex64 [n_vis]. Allocates scratch on `stream` and releases it.
  * ------------------------------------------------------------------------- */
+#define WT_TRUNCATED_TC_MIN_NODES 256
 #define WT_RESPONSE_SNAPPED 0
 #define WT_RESPONSE_LEARNED 1
 #define WT_RESPONSE_EXACT 2

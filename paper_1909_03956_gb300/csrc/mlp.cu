@@ -906,7 +906,13 @@ int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int d
     k_level_records<<<static_cast<unsigned>(blocks), 256, 0, s>>>(t->d.key, t->d.lambda, t->d.hdr, level, R, recs,
                                                                   view, cap);
     rc = (cudaGetLastError() == cudaSuccess) ? WT_OK : set_error(WT_ERR_CUDA, "%s: level records launch", fn);
-    if (rc == WT_OK) {
+    // the level's size (the tree's header on the host): a large level's sum
+    // runs with its phases on the tensor cores
+    int64_t level_nodes = -1;
+    if (rc == WT_OK && tree_sync_header(t) == WT_OK) level_nodes = t->host_hdr->per_level[level];
+    if (rc == WT_OK && level_nodes >= WT_TRUNCATED_TC_MIN_NODES) {
+        rc = eq16_tc_launch(recs, view, cap, uvw, n_vis, static_cast<float2*>(vis_out), sign, status, s, fn);
+    } else if (rc == WT_OK) {
         // Eq. 16 over the level's pixel centres, in the fast mixed form
         WaveletJob jb{};
         jb.recf_leaf = recs;

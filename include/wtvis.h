@@ -514,7 +514,10 @@ int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int d
  * of J - j0 + 1, levels j0 .. J; WT_RESPONSE_LEARNED); or the exact response
  * of the phase-centre pixel with depth - (L - j0) levels of sub-pixels (one
  * common finest level j0 + depth; J - j0 <= depth <= 8; WT_RESPONSE_EXACT).
- * As in wt_predict_vis_truncated all pixels of a level share one response.
+ * As in wt_predict_vis_truncated all pixels of a level share one response,
+ * and level j0's sum runs on the tensor cores when that level has at least
+ * WT_TRUNCATED_TC_MIN_NODES nodes (the finer levels' sums, whose sizes the
+ * device decides, in the fast mixed form).
  * Output device complex64 [n_vis]; the selection runs on the device
  * (deterministic). Allocates scratch on `stream` and releases it.
  * ------------------------------------------------------------------------- */

@@ -1028,20 +1028,28 @@ int wt_predict_vis_thresholded(wt_tree t, int j0, double tau, int response, cons
     int64_t b2 = (n_vis + 255) / 256;
     const int64_t bcap = static_cast<int64_t>(num_sms()) * 8;
     if (b2 > bcap) b2 = bcap;
+    // the size of level j0 (the tree's header on the host): a large one sums
+    // with its phases on the tensor cores, as in the truncated predictor
+    int64_t j0_nodes = -1;
+    if (rc == WT_OK && tree_sync_header(t) == WT_OK) j0_nodes = t->host_hdr->per_level[j0];
     for (int L = j0; L <= J && rc == WT_OK; ++L) {
         float2* target = (L == j0) ? static_cast<float2*>(vis_out) : tmp;
-        WaveletJob jb{};
-        jb.recf_leaf = recs + seg.off[L];
-        jb.hdr = views + (L - j0);
-        jb.uvw = uvw;
-        jb.n_vis = n_vis;
-        jb.vis = target;
-        jb.mode = WT_MIXED_FAST;
-        jb.sign = sign;
-        jb.which = WT_SUM_EQ16;
-        jb.J = J;
-        jb.status = status;
-        rc = launch_wavelet(jb, default_wavelet_variant(WT_MIXED_FAST, WT_SUM_EQ16, J), s);
+        if (L == j0 && j0_nodes >= WT_TRUNCATED_TC_MIN_NODES) {
+            rc = eq16_tc_launch(recs + seg.off[L], views, capl, uvw, n_vis, target, sign, status, s, fn);
+        } else {
+            WaveletJob jb{};
+            jb.recf_leaf = recs + seg.off[L];
+            jb.hdr = views + (L - j0);
+            jb.uvw = uvw;
+            jb.n_vis = n_vis;
+            jb.vis = target;
+            jb.mode = WT_MIXED_FAST;
+            jb.sign = sign;
+            jb.which = WT_SUM_EQ16;
+            jb.J = J;
+            jb.status = status;
+            rc = launch_wavelet(jb, default_wavelet_variant(WT_MIXED_FAST, WT_SUM_EQ16, J), s);
+        }
         if (rc == WT_OK && response == WT_RESPONSE_LEARNED)
             rc = launch_apply(mlps[L - j0], uvw, n_vis, target, sign, true, s);
         if (rc == WT_OK && response == WT_RESPONSE_EXACT) {

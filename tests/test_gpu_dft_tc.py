@@ -182,3 +182,31 @@ def test_eq16_empty_tree_and_long_baselines():
     uvw = w.uvw.copy()
     uvw[::300] *= 400.0
     assert eq16_err(w, 14, uvw) <= TOLMIX
+
+
+# ------------------------------------------------- truncated and thresholded
+
+def test_large_level_of_truncation_and_thresholding():
+    # level 11 of the medium sky's J = 12 tree has 409 nodes, above
+    # WT_TRUNCATED_TC_MIN_NODES: the truncated and the thresholded (j0 = 11)
+    # predictors sum it on the tensor cores
+    from oracle import threshold as T
+    J, j0 = 12, 11
+    w = synth.medium(n_t=3)
+    uvw = w.uvw[::7][:2000]
+    t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, J)
+    try:
+        assert t.info()["per_level"][j0 - 1] >= wt.WT_TRUNCATED_TC_MIN_NODES
+        tol = TOLMIX * np.abs(w.flux).sum()
+        tr = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, J)
+        got = wt.wt_predict_vis_truncated(t, j0, dev(uvw)).cpu().numpy()
+        assert np.max(np.abs(got - tr.vis_truncated(j0, uvw, kind="snapped"))) <= tol
+        base, G, S = T.full_response_terms(tr.export(), J, j0, uvw, w.ra0, w.dec0, d_leaf=1, reading="snapped")
+        tau = float(np.median(np.abs(G)))
+        th = wt.wt_predict_vis_thresholded(t, j0, tau, dev(uvw), response=wt.WT_RESPONSE_SNAPPED).cpu().numpy()
+        assert np.max(np.abs(th - T.thresholded_vis_tau(base, G, S, tau))) <= tol
+        # nothing kept below j0: the truncated tree, bit for bit
+        none = wt.wt_predict_vis_thresholded(t, j0, np.inf, dev(uvw), response=wt.WT_RESPONSE_SNAPPED).cpu().numpy()
+        assert np.array_equal(none, got)
+    finally:
+        t.close()

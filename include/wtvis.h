@@ -275,7 +275,9 @@ int dft_predict_vis(const double* l, const double* m, const double* flux, int64_
  *     that device (after cudaDeviceReset, say); make that first call before
  *     any stream capture.
  *   - mode: WT_FP64 or WT_FP64_DF (complex128 out), WT_MIXED or
- *     WT_MIXED_FAST (complex64 out), as for dft_predict_vis.
+ *     WT_MIXED_FAST (complex64 out), as for dft_predict_vis; WT_MIXED_TC,
+ *     whose operand for the tensor cores needs more room than the fixed
+ *     array, returns WT_ERR_ARG.
  *   - All calls on a device share the array and it keeps the last call's
  *     records. Calls whose work overlaps on the GPU (e.g. on two streams with
  *     no ordering between them) race on it and give wrong results; order
@@ -381,7 +383,9 @@ int wt_hogbom(float* image, const float* psf, int n, float gain, float threshold
  * after n_major cycles or a cycle that finds no component, and leaves the
  * dirty image of the final residual visibilities in image_resid.
  *   vis_obs     device complex64 [n_vis]
- *   mode        WT_MIXED or WT_MIXED_FAST (the prediction's form)
+ *   mode        WT_MIXED or WT_MIXED_FAST (the prediction's form), or
+ *               WT_MIXED_TC with WT_PREDICT_DIRECT (the direct sum with its
+ *               phases on the tensor cores)
  *   w_planes    0: the images as wt_dirty_image (nearest cell, no w term);
  *               2 .. 1024: as wt_dirty_image_w with that many w-planes over
  *               the batch's largest |w| (found once: one more stream

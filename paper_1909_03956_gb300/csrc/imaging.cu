@@ -1150,8 +1150,10 @@ extern "C" int wt_clean(const double* uvw, const void* vis_obs, int64_t n_vis, i
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
     if (predictor != WT_PREDICT_TREE && predictor != WT_PREDICT_DIRECT)
         return set_error(WT_ERR_ARG, "%s: bad predictor %d", fn, predictor);
-    if (mode != WT_MIXED && mode != WT_MIXED_FAST)
-        return set_error(WT_ERR_ARG, "%s: mode must be WT_MIXED or WT_MIXED_FAST (complex64 visibilities)", fn);
+    if (mode != WT_MIXED && mode != WT_MIXED_FAST && !(mode == WT_MIXED_TC && predictor == WT_PREDICT_DIRECT))
+        return set_error(WT_ERR_ARG,
+                         "%s: mode must be WT_MIXED or WT_MIXED_FAST (complex64 visibilities), or WT_MIXED_TC with "
+                         "the direct-sum predictor", fn);
     if (minor_iter < 0 || n_major < 0 || static_cast<int64_t>(minor_iter) * n_major > (1 << 24))
         return set_error(WT_ERR_ARG, "%s: minor_iter x n_major outside 0..2^24", fn);
     if (!(gain > 0.0f) || !(gain <= 1.0f)) return set_error(WT_ERR_RANGE, "%s: gain must be in (0, 1]", fn);

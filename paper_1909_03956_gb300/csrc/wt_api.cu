@@ -478,7 +478,8 @@ int subtract_model(const void* vis_obs, const void* vis_model, void* vis_resid, 
 {
     const char* fn = "subtract_model";
     if (n_vis < 0) return set_error(WT_ERR_ARG, "%s: n_vis < 0", fn);
-    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_LEARNED && mode != WT_MIXED_FAST && mode != WT_FP64_DF)
+    if (mode != WT_FP64 && mode != WT_MIXED && mode != WT_LEARNED && mode != WT_MIXED_FAST && mode != WT_FP64_DF &&
+        mode != WT_MIXED_TC)
         return set_error(WT_ERR_ARG, "%s: bad mode", fn);
     if (mode == WT_FP64_DF) mode = WT_FP64;   // both complex128
     const size_t b = static_cast<size_t>(n_vis) * (mode == WT_FP64 ? 16 : 8);

@@ -64,3 +64,20 @@ def test_host_argument_checks_of_the_imaging_and_cross_reference_entries():
     assert L.wt_selftest_grid_barrier(0, None) == wt.WT_ERR_ARG
     # the double-float mode is known to the mode checks (a null tree is the error here)
     assert L.wt_predict_vis(None, None, 0, None, wt.WT_FP64_DF, 1, 2, None) == wt.WT_ERR_ARG
+
+
+def test_host_checks_of_the_tensor_core_mode():
+    L = wt.load()
+    assert wt.WT_MIXED_TC == 5
+    # an unknown mode is rejected before any device call; WT_MIXED_TC passes
+    # the mode check and, with nothing to read, stops at the missing device
+    # (or, on a machine with one, has nothing to do)
+    assert L.dft_predict_vis(None, None, None, 0, None, 0, None, 6, 1, None) == wt.WT_ERR_ARG
+    assert L.dft_predict_vis(None, None, None, 0, None, 0, None, wt.WT_MIXED_TC, 1, None) in (wt.WT_ERR_CUDA,
+                                                                                              wt.WT_OK)
+    # the no-allocation direct sum refuses it: its fixed array holds no tensor-core operand
+    assert L.dft_predict_vis_noalloc(None, None, None, 0, None, 0, None, wt.WT_MIXED_TC, 1, None,
+                                     None) == wt.WT_ERR_ARG
+    assert "bad mode" in L.wt_last_error().decode()
+    # a negative size is still the first thing checked
+    assert L.subtract_model(None, None, None, -1, wt.WT_MIXED_TC, None) == wt.WT_ERR_ARG

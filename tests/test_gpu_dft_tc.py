@@ -210,3 +210,32 @@ def test_large_level_of_truncation_and_thresholding():
         assert np.array_equal(none, got)
     finally:
         t.close()
+
+
+# ---------------------------------------------------------------- major cycle
+
+def test_clean_with_the_tensor_core_direct_sum_matches_the_oracle():
+    # one major cycle of wt_clean with the direct-sum predictor in WT_MIXED_TC
+    # (and its subtraction, complex64) against the imaging oracle's cycle
+    from oracle import imaging as I
+    n = 64
+    w = synth.small()
+    uvw = w.uvw * np.array([1.0, 1.0, 0.0])
+    dl = 0.45 / np.max(np.abs(uvw[:, :2]))
+    src = [(n // 2 + 6, n // 2 - 4, 1.0), (n // 2 - 9, n // 2 + 5, 0.6)]
+    l = np.array([(x - n // 2) * dl for x, y, _ in src])
+    m = np.array([(y - n // 2) * dl for x, y, _ in src])
+    f = np.array([s[2] for s in src])
+    obs = O.dft(l, m, f, uvw)
+    pix, flux, resid, img = wt.wt_clean(dev(uvw), dev(obs.astype(np.complex64)), n, dl, synth.RA0, synth.DEC0, 12,
+                                        predictor=wt.WT_PREDICT_DIRECT, mode=wt.WT_MIXED_TC, gain=0.2,
+                                        minor_iter=20, n_major=1)
+    pix_o, flux_o, resid_o, img_o = I.major_cycles(uvw, obs, n, dl, 0.2, 20, 0.0, 1,
+                                                   lambda a, b, c, d: O.dft(a, b, c, d))
+    assert np.array_equal(pix.cpu().numpy(), pix_o.astype(np.int32))
+    assert np.allclose(flux.cpu().numpy(), flux_o, rtol=1e-4)
+    assert np.max(np.abs(resid.cpu().numpy() - resid_o)) <= 1e-4 * np.max(np.abs(obs))
+    # the tree predictor has no tensor-core form of its regrouped sum
+    with pytest.raises(wt.WtError):
+        wt.wt_clean(dev(uvw), dev(obs.astype(np.complex64)), n, dl, synth.RA0, synth.DEC0, 12,
+                    predictor=wt.WT_PREDICT_TREE, mode=wt.WT_MIXED_TC, minor_iter=5, n_major=1)

@@ -920,6 +920,7 @@ def mixed_measurement(wt, torch, dev, stream, flush):
     errs = {n: [] for n, _, _ in forms}
     tws = {n: 0.0 for n, _, _ in forms}
     errs_d, td = [], 0.0
+    errs_tc, ttc = [], 0.0
     ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J)
     for fr in w.extra["freqs"]:
         uvw_np = w.extra["uvw_m"] * (fr / synth.C_LIGHT)
@@ -935,14 +936,20 @@ def mixed_measurement(wt, torch, dev, stream, flush):
             errs[name].append(float(np.max(np.abs(vw.cpu().numpy()[idx] - ref)) / S))
         wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd)
         td += _time_call(lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED, out=vd), stream, flush, reps=1)
-        errs_d.append(float(np.max(np.abs(vd.cpu().numpy()[idx] - O.dft(w.l, w.m, w.flux, uvw_np[idx]))) / S))
+        ref_d = O.dft(w.l, w.m, w.flux, uvw_np[idx])
+        errs_d.append(float(np.max(np.abs(vd.cpu().numpy()[idx] - ref_d)) / S))
+        # the direct sum with its phases on the tensor cores
+        wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED_TC, out=vd)
+        ttc += _time_call(lambda: wt.dft_predict_vis(l, m, f, uvw, mode=wt.WT_MIXED_TC, out=vd), stream, flush)
+        errs_tc.append(float(np.max(np.abs(vd.cpu().numpy()[idx] - ref_d)) / S))
     n_tot = 2 * out["n_vis_per_ch"]
     tree.close()
     for name, _, _ in forms:
         out[name + "_vis_per_s"] = n_tot / tws[name]
         out[name + "_max_rel_err"] = max(errs[name])
     out.update({"dft_mixed_vis_per_s": n_tot / td, "dft_mixed_vis_terms_per_s": n_tot * w.n_comp / td,
-                "dft_max_rel_err": max(errs_d)})
+                "dft_max_rel_err": max(errs_d), "dft_mixed_tc_vis_per_s": n_tot / ttc,
+                "dft_mixed_tc_vis_terms_per_s": n_tot * w.n_comp / ttc, "dft_mixed_tc_max_rel_err": max(errs_tc)})
     return out
 
 

@@ -5,7 +5,8 @@ outputs that the oracle computes one by one.
 Workloads: medium (1 008 000 visibilities, 5 000 components, J = 12, and
 J = 8, 14); isolated components (140, J = 20 and 25);
 mixed (2 032 000 visibilities at 1.3 GHz, 20 000 components, J = 12);
-learned-response array (15 993 600 visibilities, 50 000 components, J = 12);
+learned-response array and the large array (15 993 600 visibilities, 50 000
+components, J = 12; the large one's Eq. 16 and truncation on the tensor cores);
 batched (64 channels x 2 032 000 visibilities, uneven trees).
 """
 import numpy as np
@@ -78,7 +79,28 @@ def test_mixed_config_full_size_wavelet_and_direct():
     ref = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J).vis_eq17(uvw[idx])
     assert np.max(np.abs(vw[idx] - ref)) / S <= 1e-6
     assert np.max(np.abs(vr[idx] - ref)) / S <= 1e-6
-    assert np.max(np.abs(vd[idx] - O.dft(w.l, w.m, w.flux, uvw[idx]))) / S <= 1e-6
+    ref_d = O.dft(w.l, w.m, w.flux, uvw[idx])
+    assert np.max(np.abs(vd[idx] - ref_d)) / S <= 1e-6
+    # the direct sum with its phases on the tensor cores, as the bench times it
+    vt = wt.dft_predict_vis(dev(w.l), dev(w.m), dev(w.flux), dev(uvw), mode=wt.WT_MIXED_TC).cpu().numpy()
+    assert np.max(np.abs(vt[idx] - ref_d)) / S <= 1e-6
+
+
+def test_large_array_full_size_eq16_and_truncation_on_the_tensor_cores():
+    # 15 993 600 visibilities, 50 000 components, J = 12: Eq. 16 over the
+    # 1 663 leaves and the truncation at level 11 (522 nodes), both on the
+    # tensor cores, on a strided sample against the oracle
+    w = synth.large()
+    t = wt.wt_build_tree(dev(w.l), dev(w.m), dev(w.flux), w.ra0, w.dec0, w.J)
+    u = dev(w.uvw)
+    v16 = wt.wt_predict_vis(t, u, mode=wt.WT_MIXED_TC, which=wt.WT_SUM_EQ16).cpu().numpy()
+    v11 = wt.wt_predict_vis_truncated(t, 11, u).cpu().numpy()
+    t.close()
+    idx = _sample(w.n_vis, 200)
+    S = np.abs(w.flux).sum()
+    ot = O.Tree(w.l, w.m, w.flux, w.ra0, w.dec0, w.J)
+    assert np.max(np.abs(v16[idx] - ot.vis_eq16(w.uvw[idx]))) / S <= 1e-6
+    assert np.max(np.abs(v11[idx] - ot.vis_truncated(11, w.uvw[idx], kind="snapped"))) / S <= 1e-6
 
 
 @pytest.mark.parametrize("mode,which", [(wt.WT_MIXED, wt.WT_SUM_EQ17),

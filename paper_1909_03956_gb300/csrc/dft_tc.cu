@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     unsigned char* sA = smem;
     unsigned char* sB = smem + kTcRows * 128;
+    float* sF = reinterpret_cast<float*>(sB + 2 * kTcStageBytes);   // the stages' fluxes
 
     const int t = threadIdx.x;
     const int warp = t >> 5, lane_id = t & 31;
@@ -349,8 +350,9 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
             int64_t st_issued = 0, mma_issued = 0;
             auto issue_stage = [&](int64_t s) {
                 const int slot = static_cast<int>(s & 1);
-                mbar_arrive_expect_tx(&bar_ld[slot], kTcStageBytes);
+                mbar_arrive_expect_tx(&bar_ld[slot], kTcStageBytes + kTcStageComps * 4);
                 bulk_copy_g2s(sB + slot * kTcStageBytes, bsl + s * kTcStageBytes, kTcStageBytes, &bar_ld[slot]);
+                bulk_copy_g2s(sF + slot * kTcStageComps, bfl + s * kTcStageComps, kTcStageComps * 4, &bar_ld[slot]);
                 st_issued = s + 1;
             };
             issue_stage(0);
@@ -401,7 +403,13 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
         bool ok = true;
         for (int64_t i = 0; i < n_chunks; ++i) {
             const int b = static_cast<int>(i & 1);
-            ok = __all_sync(0xffffffffu, mbar_wait_parity(&bar_full[b], static_cast<uint32_t>((i >> 1) & 1)));
+            const int64_t st = i / kTcG;
+            bool got = true;
+            if (i % kTcG == 0)   // the stage's fluxes have landed (its phase stays complete until this
+                                 // warp has released the stage's last chunk)
+                got = mbar_wait_parity(&bar_ld[st & 1], static_cast<uint32_t>((st >> 1) & 1));
+            got = got && mbar_wait_parity(&bar_full[b], static_cast<uint32_t>((i >> 1) & 1));
+            ok = __all_sync(0xffffffffu, got);
             if (!ok) break;
             tc_fence_after();
             uint32_t r1[kTcNC], r2[kTcNC], r3[kTcNC];
@@ -409,15 +417,27 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
             tmem_ld_cols(col, r1);
             tmem_ld_cols(col + kTcNC, r2);
             tmem_ld_cols(col + 2 * kTcNC, r3);
+            // the chunk's fluxes into registers before its buffer and, with
+            // the stage's last chunk, the stage's slot are given back
+            float fx[kTcNC];
+            {
+                const float4* fl =
+                    reinterpret_cast<const float4*>(sF + (st & 1) * kTcStageComps + (i % kTcG) * kTcNC);
+#pragma unroll
+                for (int q = 0; q < kTcNC / 4; ++q) {
+                    const float4 f4 = fl[q];
+                    fx[4 * q] = f4.x;
+                    fx[4 * q + 1] = f4.y;
+                    fx[4 * q + 2] = f4.z;
+                    fx[4 * q + 3] = f4.w;
+                }
+            }
             tmem_wait_ld();
             tc_fence_before();
             __syncwarp();
             if (lane_id == 0) mbar_arrive(&bar_empty[b]);   // the buffer may be refilled
-            const float4* fl = reinterpret_cast<const float4*>(bfl + i * kTcNC);
 #pragma unroll
             for (int g = 0; g < kTcNC / 8; ++g) {
-                const float4 fa = __ldg(fl + 2 * g), fb = __ldg(fl + 2 * g + 1);
-                const float fx[8] = {fa.x, fa.y, fa.z, fa.w, fb.x, fb.y, fb.z, fb.w};
                 float2 p = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
@@ -433,8 +453,8 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
                     float s0, c0, s1, c1;
                     __sincosf(xa.x, &s0, &c0);
                     __sincosf(xa.y, &s1, &c1);
-                    p = fma2(bcast2(fx[j]), make_float2(c0, s0), p);
-                    p = fma2(bcast2(fx[j + 1]), make_float2(c1, s1), p);
+                    p = fma2(bcast2(fx[k]), make_float2(c0, s0), p);
+                    p = fma2(bcast2(fx[k + 1]), make_float2(c1, s1), p);
                 }
                 kahan_add2(acc, cmp, p);
             }
@@ -471,7 +491,7 @@ int tc_main_launch(const unsigned char* bsl, const float* bfl, int64_t n_chunks,
 {
     // no more CTAs per SM than their tensor memory allows (a CTA beyond
     // that would wait in tcgen05.alloc): four of 128 columns
-    const size_t need = 1024 + kTcRows * 128 + 2 * kTcStageBytes;
+    const size_t need = 1024 + kTcRows * 128 + 2 * kTcStageBytes + 2 * kTcStageComps * 4;
     size_t smem = need;
     int per_sm = 0;
     for (;;) {

@@ -68,7 +68,12 @@ constexpr int kTcNC = 16;                   // components per chunk (N of the MM
 constexpr int kTcStageBytes = 16384;        // B operand per stage
 constexpr int kTcG = kTcStageBytes / (kTcNC * 128);   // chunks per stage
 constexpr int kTcStageComps = kTcG * kTcNC;
-constexpr int kTcAcc = 3 * kTcNC;           // tensor-memory columns per buffer
+// Tiles of 128 visibilities per CTA (one row of each per epilogue thread).
+// Measured on the medium direct sum: one tile 1.64 T terms/s, two 1.45
+// (half the warps per SM at the same tensor memory); two were faster only
+// for a few hundred terms (their set-up shared), so one it is.
+constexpr int kTcTiles = 1;
+constexpr int kTcAcc = 3 * kTcNC * kTcTiles;   // tensor-memory columns per buffer
 // two buffers, rounded up to a power of two (at least 32 columns)
 constexpr uint32_t kTcTmemCols = 2 * kTcAcc <= 32 ? 32 : 2 * kTcAcc <= 64 ? 64 : 2 * kTcAcc <= 128 ? 128 : 2 * kTcAcc <= 256 ? 256 : 512;
 constexpr int kTcEmptyQ = -200;             // q of a coordinate that is zero for every component
@@ -241,21 +246,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// The direct sum of one tile of 128 visibilities per CTA (see the top of
-// the file), warp-specialised: warps 0-3 own a visibility per thread (TMEM
-// lane = row = thread) and form the terms; warp 4 (one lane) streams the B
-// operand and issues the MMAs. Two tensor-memory buffers: the producer fills
-// buffer i & 1 with chunk i once the epilogue warps have read chunk i - 2
-// out of it (mbarrier `empty`, one arrival per warp, given as soon as a
-// warp's tcgen05.ld of the three accumulators completes), and commits to
-// `full`. The B operand comes in stages of kTcG chunks, two slots; the slot
-// of stage s - 1 is refilled with stage s + 1 once the MMAs that read it
-// have completed (tcgen05.commit to `sdone` after a stage's last chunk).
-// Fluxes are read from global memory (all lanes one address, L1-resident).
-// Every wait is bounded; a wait that runs out records WT_ERR_TIMEOUT, the
-// producer then waits once more (bounded) for its copies and MMAs in flight,
-// and the CTA frees its tensor memory and leaves.
+// The direct sum of kTcTiles tiles of 128 visibilities per CTA (see the top
+// of the file), warp-specialised: warps 0-3 own kTcTiles visibilities per
+// thread (TMEM lane = row = thread, one row of every tile) and form the
+// terms; warp 4 (one lane) streams the B operand and issues the MMAs (four
+// per tile and chunk, against the same B chunk). Two tensor-memory buffers:
+// the producer fills buffer i & 1 with chunk i once the epilogue warps have
+// read chunk i - 2 out of it (mbarrier `empty`, one arrival per warp, given
+// as soon as a warp's tcgen05.ld of the accumulators completes and it has
+// copied the chunk's fluxes), and commits to `full`. The B operand and its
+// fluxes come in stages of kTcG chunks, two slots; the slot of stage s - 1
+// is refilled with stage s + 1 once the MMAs that read it have completed
+// (tcgen05.commit to `sdone` after a stage's last chunk) and the epilogue
+// has released the stage's last chunk. Every wait is bounded; a wait that
+// runs out records WT_ERR_TIMEOUT, the producer then waits once more
+// (bounded) for its copies and MMAs in flight, and the CTA frees its tensor
+// memory and leaves.
 constexpr int kTcThreads = 160;
+constexpr int kTcCtaVis = kTcRows * kTcTiles;      // visibilities per CTA
 
 __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __restrict__ bsl,
                                                       const float* __restrict__ bfl, int64_t n_chunks,
@@ -274,57 +282,67 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
     __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_ld[2], bar_sdone[2];
     __shared__ uint32_t tmem_base;
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + kTcRows * 128;
+    unsigned char* sA = smem;                                         // kTcTiles x 128 rows x 128 bytes
+    unsigned char* sB = smem + kTcTiles * kTcRows * 128;
     float* sF = reinterpret_cast<float*>(sB + 2 * kTcStageBytes);   // the stages' fluxes
 
     const int t = threadIdx.x;
     const int warp = t >> 5, lane_id = t & 31;
     const bool epi = warp < 4;
     const int64_t tile = blockIdx.x;
-    const int64_t n = tile * kTcRows + t;
-    const bool live = epi && n < n_vis;
     const double sg = static_cast<double>(sgn);       // the sign folded into the baseline (exact)
     bool fits = true;
     if (epi) {
-        double x[3] = {0.0, 0.0, 0.0};
-        if (live) {
-            x[0] = sg * uvw[3 * n];
-            x[1] = sg * uvw[3 * n + 1];
-            x[2] = sg * uvw[3 * n + 2];
-        }
-        float a[3][5];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            // y = x 2^q in units of 2^-44: one exact scaling, one rounding
-            const double y = x[c] * scalbn(1.0, tc_exponent(bound[c]) + 44);
-            fits = fits && fabs(y) <= static_cast<double>(kTcMaxA0) * 0x1p44;   // false for a NaN
-            tc_slices5_int(fits ? __double2ll_rn(y) : 0ll, a[c]);
-        }
-        float v[64];
+        for (int q = 0; q < kTcTiles; ++q) {
+            const int64_t n = tile * kTcCtaVis + q * kTcRows + t;
+            double x[3] = {0.0, 0.0, 0.0};
+            if (n < n_vis) {
+                x[0] = sg * uvw[3 * n];
+                x[1] = sg * uvw[3 * n + 1];
+                x[2] = sg * uvw[3 * n + 2];
+            }
+            float a[3][5];
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = 0.0f;
-        constexpr float s11 = 0x1p-11f;
+            for (int c = 0; c < 3; ++c) {
+                // y = x 2^q in units of 2^-44: one exact scaling, one rounding
+                const double y = x[c] * scalbn(1.0, tc_exponent(bound[c]) + 44);
+                fits = fits && fabs(y) <= static_cast<double>(kTcMaxA0) * 0x1p44;   // false for a NaN
+                tc_slices5_int(fits ? __double2ll_rn(y) : 0ll, a[c]);
+            }
+            float v[64];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            v[c] = a[c][0];
-            v[3 + c] = a[c][1];
-            v[16 + c] = a[c][0];
-            v[19 + c] = a[c][1];
-            v[22 + c] = a[c][2];
-            v[32 + c] = a[c][0];
-            v[35 + c] = a[c][1];
-            v[38 + c] = a[c][2];
-            v[41 + c] = a[c][3];
-            v[44 + c] = a[c][4] * s11;
-            v[48 + c] = a[c][1] * s11;
-            v[51 + c] = a[c][2] * s11;
-            v[54 + c] = a[c][3] * s11;
+            for (int k = 0; k < 64; ++k) v[k] = 0.0f;
+            constexpr float s11 = 0x1p-11f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = a[c][0];
+                v[3 + c] = a[c][1];
+                v[16 + c] = a[c][0];
+                v[19 + c] = a[c][1];
+                v[22 + c] = a[c][2];
+                v[32 + c] = a[c][0];
+                v[35 + c] = a[c][1];
+                v[38 + c] = a[c][2];
+                v[41 + c] = a[c][3];
+                v[44 + c] = a[c][4] * s11;
+                v[48 + c] = a[c][1] * s11;
+                v[51 + c] = a[c][2] * s11;
+                v[54 + c] = a[c][3] * s11;
+            }
+            tc_store_row(sA + q * (kTcRows * 128), t, v);
         }
-        tc_store_row(sA, t, v);
     }
     if (!__syncthreads_and(fits ? 1 : 0)) {
-        mark_deferred(vis + tile * kTcRows);          // left to the exact pass
+        // left to the exact pass, which takes tiles of 128 visibilities
+        if (t == 0) {
+#pragma unroll
+            for (int q = 0; q < kTcTiles; ++q) {
+                const int64_t first = tile * kTcCtaVis + q * kTcRows;
+                if (first < n_vis)
+                    vis[first] = make_float2(__uint_as_float(kDeferredMark), __uint_as_float(kDeferredMark));
+            }
+        }
         return;
     }
     if (t == 0) {
@@ -374,9 +392,13 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
                 const uint32_t bb = b_addr + static_cast<uint32_t>(s & 1) * kTcStageBytes + w * (kTcNC * 128);
                 const uint32_t col = tm + static_cast<uint32_t>(b) * kTcAcc;
 #pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    const uint32_t d = col + (kb == 0 ? 0u : kb == 1 ? kTcNC : 2u * kTcNC);
-                    tc_mma_f16(d, umma_desc(a_addr + kb * 256), umma_desc(bb + kb * 256), kTcIdesc, kb == 3);
+                for (int q = 0; q < kTcTiles; ++q) {
+#pragma unroll
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const uint32_t d = col + q * (3 * kTcNC) + (kb == 0 ? 0u : kb == 1 ? kTcNC : 2u * kTcNC);
+                        tc_mma_f16(d, umma_desc(a_addr + q * (kTcRows * 128) + kb * 256), umma_desc(bb + kb * 256),
+                                   kTcIdesc, kb == 3);
+                    }
                 }
                 tc_commit(&bar_full[b]);
                 if (w == kTcG - 1 || i + 1 == n_chunks) tc_commit(&bar_sdone[s & 1]);
@@ -399,7 +421,9 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
         const float2 M2 = bcast2(12582912.0f);        // 1.5 2^23: x + M2 - M2 = rint(x) for |x| < 2^22
         const float2 s11 = bcast2(0x1p-11f), s22 = bcast2(0x1p-22f);
         const float2 twopi = bcast2(6.28318530717958648f), s33 = bcast2(6.28318530717958648f * 0x1p-33f);
-        float2 acc = make_float2(0.f, 0.f), cmp = make_float2(0.f, 0.f);
+        float2 acc[kTcTiles], cmp[kTcTiles];
+#pragma unroll
+        for (int q = 0; q < kTcTiles; ++q) acc[q] = cmp[q] = make_float2(0.f, 0.f);
         bool ok = true;
         for (int64_t i = 0; i < n_chunks; ++i) {
             const int b = static_cast<int>(i & 1);
@@ -412,11 +436,14 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
             ok = __all_sync(0xffffffffu, got);
             if (!ok) break;
             tc_fence_after();
-            uint32_t r1[kTcNC], r2[kTcNC], r3[kTcNC];
-            const uint32_t col = lane + static_cast<uint32_t>(b) * kTcAcc;
-            tmem_ld_cols(col, r1);
-            tmem_ld_cols(col + kTcNC, r2);
-            tmem_ld_cols(col + 2 * kTcNC, r3);
+            uint32_t r1[kTcTiles][kTcNC], r2[kTcTiles][kTcNC], r3[kTcTiles][kTcNC];
+#pragma unroll
+            for (int q = 0; q < kTcTiles; ++q) {
+                const uint32_t col = lane + static_cast<uint32_t>(b) * kTcAcc + q * (3 * kTcNC);
+                tmem_ld_cols(col, r1[q]);
+                tmem_ld_cols(col + kTcNC, r2[q]);
+                tmem_ld_cols(col + 2 * kTcNC, r3[q]);
+            }
             // the chunk's fluxes into registers before its buffer and, with
             // the stage's last chunk, the stage's slot are given back
             float fx[kTcNC];
@@ -424,12 +451,12 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
                 const float4* fl =
                     reinterpret_cast<const float4*>(sF + (st & 1) * kTcStageComps + (i % kTcG) * kTcNC);
 #pragma unroll
-                for (int q = 0; q < kTcNC / 4; ++q) {
-                    const float4 f4 = fl[q];
-                    fx[4 * q] = f4.x;
-                    fx[4 * q + 1] = f4.y;
-                    fx[4 * q + 2] = f4.z;
-                    fx[4 * q + 3] = f4.w;
+                for (int k = 0; k < kTcNC / 4; ++k) {
+                    const float4 f4 = fl[k];
+                    fx[4 * k] = f4.x;
+                    fx[4 * k + 1] = f4.y;
+                    fx[4 * k + 2] = f4.z;
+                    fx[4 * k + 3] = f4.w;
                 }
             }
             tmem_wait_ld();
@@ -438,30 +465,39 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
             if (lane_id == 0) mbar_arrive(&bar_empty[b]);   // the buffer may be refilled
 #pragma unroll
             for (int g = 0; g < kTcNC / 8; ++g) {
-                float2 p = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    const int k = 8 * g + j;
-                    const float2 A1 = make_float2(__uint_as_float(r1[k]), __uint_as_float(r1[k + 1]));
-                    const float2 A2 = make_float2(__uint_as_float(r2[k]), __uint_as_float(r2[k + 1]));
-                    const float2 A3 = make_float2(__uint_as_float(r3[k]), __uint_as_float(r3[k + 1]));
-                    const float2 y = fma2(A1, s11, M2);
-                    const float2 f1 = fma2(A1, s11, sub2(M2, y));         // acc1 2^-11 mod 1, exact
-                    const float2 h = fma2(A2, s22, f1);                   // exact
-                    const float2 hp = add2(h, sub2(M2, add2(h, M2)));     // h - rint(h), exact
-                    const float2 xa = fma2(A3, s33, mul2(hp, twopi));     // 2 pi t
-                    float s0, c0, s1, c1;
-                    __sincosf(xa.x, &s0, &c0);
-                    __sincosf(xa.y, &s1, &c1);
-                    p = fma2(bcast2(fx[k]), make_float2(c0, s0), p);
-                    p = fma2(bcast2(fx[k + 1]), make_float2(c1, s1), p);
+                for (int q = 0; q < kTcTiles; ++q) {
+                    float2 p = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) {
+                        const int k = 8 * g + j;
+                        const float2 A1 = make_float2(__uint_as_float(r1[q][k]), __uint_as_float(r1[q][k + 1]));
+                        const float2 A2 = make_float2(__uint_as_float(r2[q][k]), __uint_as_float(r2[q][k + 1]));
+                        const float2 A3 = make_float2(__uint_as_float(r3[q][k]), __uint_as_float(r3[q][k + 1]));
+                        const float2 y = fma2(A1, s11, M2);
+                        const float2 f1 = fma2(A1, s11, sub2(M2, y));         // acc1 2^-11 mod 1, exact
+                        const float2 h = fma2(A2, s22, f1);                   // exact
+                        const float2 hp = add2(h, sub2(M2, add2(h, M2)));     // h - rint(h), exact
+                        const float2 xa = fma2(A3, s33, mul2(hp, twopi));     // 2 pi t
+                        float s0, c0, s1, c1;
+                        __sincosf(xa.x, &s0, &c0);
+                        __sincosf(xa.y, &s1, &c1);
+                        p = fma2(bcast2(fx[k]), make_float2(c0, s0), p);
+                        p = fma2(bcast2(fx[k + 1]), make_float2(c1, s1), p);
+                    }
+                    kahan_add2(acc[q], cmp[q], p);
                 }
-                kahan_add2(acc, cmp, p);
             }
         }
         if (!ok && lane_id == 0) record_status(status, WT_ERR_TIMEOUT);
         __syncwarp();
-        if (ok && live) vis[n] = sub2(acc, cmp);
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q < kTcTiles; ++q) {
+                const int64_t n = tile * kTcCtaVis + q * kTcRows + t;
+                if (n < n_vis) vis[n] = sub2(acc[q], cmp[q]);
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -491,7 +527,7 @@ int tc_main_launch(const unsigned char* bsl, const float* bfl, int64_t n_chunks,
 {
     // no more CTAs per SM than their tensor memory allows (a CTA beyond
     // that would wait in tcgen05.alloc): four of 128 columns
-    const size_t need = 1024 + kTcRows * 128 + 2 * kTcStageBytes + 2 * kTcStageComps * 4;
+    const size_t need = 1024 + kTcTiles * kTcRows * 128 + 2 * kTcStageBytes + 2 * kTcStageComps * 4;
     size_t smem = need;
     int per_sm = 0;
     for (;;) {
@@ -501,7 +537,7 @@ int tc_main_launch(const unsigned char* bsl, const float* bfl, int64_t n_chunks,
         if (per_sm * kTcTmemCols <= 512) break;
         smem += 8192;
     }
-    const int64_t tiles = (n_vis + kTcRows - 1) / kTcRows;
+    const int64_t tiles = (n_vis + kTcCtaVis - 1) / kTcCtaVis;
     if (tiles > 0x7fffffff) return set_error(WT_ERR_RANGE, "%s: too many visibilities for one launch", fn);
     k_dft_tc<<<static_cast<unsigned>(tiles), kTcThreads, smem, s>>>(bsl, bfl, n_chunks, stages, n_dev, bound, uvw,
                                                                    n_vis, vis, static_cast<float>(sign), status);

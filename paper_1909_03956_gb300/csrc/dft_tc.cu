@@ -40,11 +40,14 @@
 // blocks 2 and 3 -> acc3. The components' B operand is built once per call
 // by k_tc_slice_components in the same no-swizzle K-major layout, chunks of
 // NC components (the MMA's N), and streamed through shared memory by bulk
-// copies, two stages of 16 KB. Per chunk one thread issues the four MMAs
-// into one of two tensor-memory buffers (3 NC columns each) and commits to
-// an mbarrier; while the tensor cores fill the next buffer, every thread
-// reads its own row of the current one (tcgen05.ld), forms the terms
-// C_m (cos, sin) and adds them, eight at a time, to its Kahan sum.
+// copies, two stages of 16 KB (with the components' fluxes). Per chunk one
+// thread of a producer warp issues the four MMAs into one of two
+// tensor-memory buffers (3 NC columns each) and commits to an mbarrier;
+// while the tensor cores fill the next buffer, every epilogue thread reads
+// its own row of the current one (tcgen05.ld), forms the terms
+// C_m (cos, sin) and adds them, eight at a time, to its Kahan sum. The same
+// kernel sums Eq. 16 over a tree's leaves (k_tc_slice_leaves builds the
+// operand from the leaf records, the count read on the device).
 //
 // A tile whose baselines exceed the condition (|a_0| <= 16, i.e. phases
 // below 2^14 turns per coordinate) or are not finite is marked and left to

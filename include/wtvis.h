@@ -11,8 +11,9 @@
  *     celestial sphere and keeps the nonzero scaling/wavelet coefficients in
  *     a tree; wt_predict_vis evaluates, per visibility, the plane wave's
  *     coefficients on that tree and the multiresolution sum.
- * subtract_model forms the residual visibilities (Sec. 2.2, major-cycle
- * step 2).
+ * The direct sum, and Eq. 16 over the tree's leaves, can form their phases
+ * on the tensor cores (WT_MIXED_TC). subtract_model forms the residual
+ * visibilities (Sec. 2.2, major-cycle step 2).
  *
  * Conventions (all entry points):
  *   - Pointers are DEVICE pointers unless the comment says host. The caller
@@ -25,8 +26,8 @@
  *   - Components are (l, m, flux): float64 direction cosines relative to the
  *     phase centre (Sec. 2.2; l east, m north) and float64 fluxes.
  *   - Visibilities are interleaved complex: complex128 ([re, im] float64
- *     pairs) in WT_FP64 mode, complex64 ([re, im] float32 pairs) in the
- *     other modes.
+ *     pairs) in the WT_FP64 and WT_FP64_DF modes, complex64 ([re, im]
+ *     float32 pairs) in the others (WT_MIXED, WT_MIXED_FAST, WT_MIXED_TC).
  *   - sign = +1 evaluates exp(+i 2 pi B.(s - P)) as printed in Eqs. 1, 12
  *     and 14; sign = -1 the conjugate convention.
  *   - stream is a cudaStream_t (NULL = legacy default stream). Every call is

@@ -78,14 +78,16 @@ typedef enum {
                          2^-48 |B.s| turns, 32x float64's); complex128 output;
                          wt_predict_vis with WT_SUM_EQ17_REGROUPED or
                          WT_SUM_EQ16 */
-    WT_MIXED_TC = 5   /* dft_predict_vis only: WT_MIXED_FAST's sin/cos and sums,
-                         with the phase contraction u l + v m + w (n - 1) on the
-                         tensor cores from exact 11-bit float16 slices of the
-                         baselines and coordinates (three FP32 accumulators,
-                         recombined modulo 1 in float32; phase error below
-                         2^-29 turns); tiles of 128 visibilities beyond
-                         2^14 turns per coordinate fall back to WT_MIXED_FAST's
-                         exact pass; complex64 */
+    WT_MIXED_TC = 5   /* dft_predict_vis, and wt_predict_vis with WT_SUM_EQ16
+                         (a direct sum over the leaves): WT_MIXED_FAST's sin/cos
+                         and sums, with the phase contraction
+                         u l + v m + w (n - 1) on the tensor cores from exact
+                         11-bit float16 slices of the baselines and coordinates
+                         (three FP32 accumulators, recombined modulo 1 in
+                         float32; phase error below 2^-29 turns); tiles of 128
+                         visibilities beyond 2^14 turns per coordinate fall
+                         back to WT_MIXED_FAST's exact pass; faster than
+                         WT_MIXED_FAST from about 150 terms on; complex64 */
 } wt_mode;
 
 typedef enum {
@@ -493,7 +495,7 @@ int wt_predict_vis_learned(wt_tree t, wt_mlp m, const double* uvw, int64_t n_vis
  * for that level and the tree's phase centre; depth (EXACT) 0..8. Output
  * device complex64 [n_vis]. Allocates scratch on `stream` and releases it.
  * ------------------------------------------------------------------------- */
-#define WT_TRUNCATED_TC_MIN_NODES 256
+#define WT_TRUNCATED_TC_MIN_NODES 160
 #define WT_RESPONSE_SNAPPED 0
 #define WT_RESPONSE_LEARNED 1
 #define WT_RESPONSE_EXACT 2

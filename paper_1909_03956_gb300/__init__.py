@@ -53,7 +53,7 @@ EXPORTS = [
 ]
 MLP_N_PARAMS = 4546
 WT_NOALLOC_MAX_COMPONENTS = 65536
-WT_TRUNCATED_TC_MIN_NODES = 256
+WT_TRUNCATED_TC_MIN_NODES = 160
 
 
 class WtError(RuntimeError):

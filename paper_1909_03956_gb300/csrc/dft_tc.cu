@@ -71,17 +71,24 @@ constexpr int kTcNC = 16;                   // components per chunk (N of the MM
 constexpr int kTcStageBytes = 16384;        // B operand per stage
 constexpr int kTcG = kTcStageBytes / (kTcNC * 128);   // chunks per stage
 constexpr int kTcStageComps = kTcG * kTcNC;
-// Tiles of 128 visibilities per CTA (one row of each per epilogue thread).
-// Measured on the medium direct sum: one tile 1.64 T terms/s, two 1.45
-// (half the warps per SM at the same tensor memory); two were faster only
-// for a few hundred terms (their set-up shared), so one it is.
-constexpr int kTcTiles = 1;
-constexpr int kTcAcc = 3 * kTcNC * kTcTiles;   // tensor-memory columns per buffer
+// Tiles of 128 visibilities per CTA (one row of each per epilogue thread):
+// a launch takes one, or two for a few hundred terms at most
+// (kTcTwoTileMaxChunks chunks). Measured on the medium direct sum: one tile
+// 1.64 T terms/s, two 1.45 (half the warps per SM at the same tensor
+// memory); over 179 leaves (Eq. 16, the large workload at J = 10) two tiles
+// took 2.38 ms against 2.82 for one (their set-up shared).
+constexpr int kTcTwoTileMaxChunks = 16;
+// tensor-memory columns per buffer (three accumulators of kTcNC per tile)
+constexpr int tc_acc_cols(int tiles) { return 3 * kTcNC * tiles; }
 // two buffers, rounded up to a power of two (at least 32 columns)
-constexpr uint32_t kTcTmemCols = 2 * kTcAcc <= 32 ? 32 : 2 * kTcAcc <= 64 ? 64 : 2 * kTcAcc <= 128 ? 128 : 2 * kTcAcc <= 256 ? 256 : 512;
+constexpr uint32_t tc_tmem_cols(int tiles)
+{
+    return 2 * tc_acc_cols(tiles) <= 32 ? 32 : 2 * tc_acc_cols(tiles) <= 64 ? 64 : 2 * tc_acc_cols(tiles) <= 128 ? 128
+         : 2 * tc_acc_cols(tiles) <= 256 ? 256 : 512;
+}
 constexpr int kTcEmptyQ = -200;             // q of a coordinate that is zero for every component
 constexpr float kTcMaxA0 = 16.0f;           // |a_0| bound of a tile on the tensor cores
-static_assert(2 * kTcAcc <= static_cast<int>(kTcTmemCols), "tensor memory of the two buffers");
+static_assert(2 * tc_acc_cols(2) <= static_cast<int>(tc_tmem_cols(2)), "tensor memory of the two buffers");
 static_assert(kTcG >= 1 && kTcG * kTcNC * 128 == kTcStageBytes, "stage layout");
 
 constexpr uint32_t kTcIdesc = idesc_f16(false, kTcRows, kTcNC);
@@ -266,8 +273,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 // (bounded) for its copies and MMAs in flight, and the CTA frees its tensor
 // memory and leaves.
 constexpr int kTcThreads = 160;
-constexpr int kTcCtaVis = kTcRows * kTcTiles;      // visibilities per CTA
 
+template <int kTcTiles>
 __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __restrict__ bsl,
                                                       const float* __restrict__ bfl, int64_t n_chunks,
                                                       int64_t n_stages, const int64_t* __restrict__ n_dev,
@@ -275,6 +282,9 @@ __global__ void __launch_bounds__(kTcThreads) k_dft_tc(const unsigned char* __re
                                                       const double* __restrict__ uvw, int64_t n_vis,
                                                       float2* __restrict__ vis, float sgn, int* status)
 {
+    constexpr int kTcCtaVis = kTcRows * kTcTiles;                 // visibilities per CTA
+    constexpr int kTcAcc = tc_acc_cols(kTcTiles);
+    constexpr uint32_t kTcTmemCols = tc_tmem_cols(kTcTiles);
     if (n_dev) {   // the count on the device (a tree's leaves): the chunks it needs, at most those allocated
         const int64_t nd = *n_dev;
         const int64_t nc = nd > 0 ? (nd + kTcNC - 1) / kTcNC : 0;
@@ -521,31 +531,44 @@ size_t dft_tc_scratch_bytes(int64_t n_comp)
 
 namespace {
 
-// Launch k_dft_tc over the tiles of n_vis visibilities: B operand bsl / bfl
-// of `stages` stages, n_chunks chunks of it used (or those *n_dev items
-// need, when n_dev is given).
-int tc_main_launch(const unsigned char* bsl, const float* bfl, int64_t n_chunks, int64_t stages, const int64_t* n_dev,
-                   const uint32_t* bound, const double* uvw, int64_t n_vis, float2* vis, int sign, int* status,
-                   cudaStream_t s, const char* fn)
+template <int TILES>
+int tc_launch_tiles(const unsigned char* bsl, const float* bfl, int64_t n_chunks, int64_t stages,
+                    const int64_t* n_dev, const uint32_t* bound, const double* uvw, int64_t n_vis, float2* vis,
+                    int sign, int* status, cudaStream_t s, const char* fn)
 {
+    auto kernel = k_dft_tc<TILES>;
     // no more CTAs per SM than their tensor memory allows (a CTA beyond
-    // that would wait in tcgen05.alloc): four of 128 columns
-    const size_t need = 1024 + kTcTiles * kTcRows * 128 + 2 * kTcStageBytes + 2 * kTcStageComps * 4;
+    // that would wait in tcgen05.alloc)
+    const size_t need = 1024 + TILES * kTcRows * 128 + 2 * kTcStageBytes + 2 * kTcStageComps * 4;
     size_t smem = need;
     int per_sm = 0;
     for (;;) {
-        WT_CUDA_TRY(cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dft_tc, kTcThreads, smem));
+        WT_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        WT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTcThreads, smem));
         if (per_sm < 1) return set_error(WT_ERR_UNSUPPORTED, "%s: tensor-core kernel does not fit on an SM", fn);
-        if (per_sm * kTcTmemCols <= 512) break;
+        if (per_sm * tc_tmem_cols(TILES) <= 512) break;
         smem += 8192;
     }
-    const int64_t tiles = (n_vis + kTcCtaVis - 1) / kTcCtaVis;
+    const int64_t cta_vis = static_cast<int64_t>(kTcRows) * TILES;
+    const int64_t tiles = (n_vis + cta_vis - 1) / cta_vis;
     if (tiles > 0x7fffffff) return set_error(WT_ERR_RANGE, "%s: too many visibilities for one launch", fn);
-    k_dft_tc<<<static_cast<unsigned>(tiles), kTcThreads, smem, s>>>(bsl, bfl, n_chunks, stages, n_dev, bound, uvw,
-                                                                   n_vis, vis, static_cast<float>(sign), status);
+    kernel<<<static_cast<unsigned>(tiles), kTcThreads, smem, s>>>(bsl, bfl, n_chunks, stages, n_dev, bound, uvw, n_vis,
+                                                                  vis, static_cast<float>(sign), status);
     WT_CUDA_TRY(cudaGetLastError());
     return WT_OK;
+}
+
+// Launch k_dft_tc over the tiles of n_vis visibilities: B operand bsl / bfl
+// of `stages` stages, n_chunks chunks of it used (or those *n_dev items
+// need, when n_dev is given); chunks_hint, the chunks the host expects,
+// picks two tiles per CTA for a few hundred terms.
+int tc_main_launch(const unsigned char* bsl, const float* bfl, int64_t n_chunks, int64_t stages, const int64_t* n_dev,
+                   int64_t chunks_hint, const uint32_t* bound, const double* uvw, int64_t n_vis, float2* vis,
+                   int sign, int* status, cudaStream_t s, const char* fn)
+{
+    if (chunks_hint <= kTcTwoTileMaxChunks)
+        return tc_launch_tiles<2>(bsl, bfl, n_chunks, stages, n_dev, bound, uvw, n_vis, vis, sign, status, s, fn);
+    return tc_launch_tiles<1>(bsl, bfl, n_chunks, stages, n_dev, bound, uvw, n_vis, vis, sign, status, s, fn);
 }
 
 }  // namespace
@@ -569,8 +592,9 @@ int dft_tc_launch(const double* l, const double* m, const double* flux, int64_t 
                                                                                          bound, bsl, bfl);
         WT_CUDA_TRY(cudaGetLastError());
     }
-    int rc = tc_main_launch(bsl, bfl, (n_comp + kTcNC - 1) / kTcNC, stages, nullptr, bound, uvw, n_vis, vis, sign,
-                            status, s, "dft_predict_vis");
+    const int64_t chunks = (n_comp + kTcNC - 1) / kTcNC;
+    int rc = tc_main_launch(bsl, bfl, chunks, stages, nullptr, chunks, bound, uvw, n_vis, vis, sign, status, s,
+                            "dft_predict_vis");
     if (rc) return rc;
     return dft_exact_pass_128(recs, bound, n_comp, uvw, n_vis, vis, sign, status, s);
 }
@@ -578,11 +602,13 @@ int dft_tc_launch(const double* l, const double* m, const double* flux, int64_t 
 // Eq. 16 in the tensor-core form over leaf records (RecF, at most cap of
 // them, their count and bounds in the device header hdr): V = sum_k Phi_k
 // exp(sign i 2 pi B.(c_k - P)), the direct sum over the leaves' pixel
-// centres with their merged fluxes. The scratch (the B operand and the
+// centres with their merged fluxes; n_hint, their number as the host knows
+// it (or -1), picks the launch shape. The scratch (the B operand and the
 // exact pass's records) is allocated and released on the stream.
-int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, const double* uvw, int64_t n_vis,
-                   float2* vis, int sign, int* status, cudaStream_t s, const char* fn)
+int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, int64_t n_hint, const double* uvw,
+                   int64_t n_vis, float2* vis, int sign, int* status, cudaStream_t s, const char* fn)
 {
+    if (n_hint < 0) n_hint = cap;
     if (n_vis == 0) return WT_OK;
     const int64_t stages = (cap + kTcStageComps - 1) / kTcStageComps;
     const int64_t cap_pad = stages * kTcStageComps;
@@ -607,8 +633,8 @@ int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, const d
     }
     const uint32_t* bound = reinterpret_cast<const uint32_t*>(hdr->smax);   // device address of the bounds
     if (rc == WT_OK)
-        rc = tc_main_launch(bsl, bfl, stages * kTcG, stages, &hdr->n_leaves, bound, uvw, n_vis, vis, sign, status, s,
-                            fn);
+        rc = tc_main_launch(bsl, bfl, stages * kTcG, stages, &hdr->n_leaves, (n_hint + kTcNC - 1) / kTcNC, bound, uvw,
+                            n_vis, vis, sign, status, s, fn);
     // the exact pass over every capacity record (those beyond the count are zero)
     if (rc == WT_OK) rc = dft_exact_pass_128(exact, bound, cap_pad, uvw, n_vis, vis, sign, status, s);
     cudaError_t ef = cudaFreeAsync(scratch, s);

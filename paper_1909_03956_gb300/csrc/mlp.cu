@@ -911,7 +911,8 @@ int wt_predict_vis_truncated(wt_tree t, int level, int response, wt_mlp m, int d
     int64_t level_nodes = -1;
     if (rc == WT_OK && tree_sync_header(t) == WT_OK) level_nodes = t->host_hdr->per_level[level];
     if (rc == WT_OK && level_nodes >= WT_TRUNCATED_TC_MIN_NODES) {
-        rc = eq16_tc_launch(recs, view, cap, uvw, n_vis, static_cast<float2*>(vis_out), sign, status, s, fn);
+        rc = eq16_tc_launch(recs, view, cap, level_nodes, uvw, n_vis, static_cast<float2*>(vis_out), sign, status, s,
+                            fn);
     } else if (rc == WT_OK) {
         // Eq. 16 over the level's pixel centres, in the fast mixed form
         WaveletJob jb{};
@@ -1035,7 +1036,7 @@ int wt_predict_vis_thresholded(wt_tree t, int j0, double tau, int response, cons
     for (int L = j0; L <= J && rc == WT_OK; ++L) {
         float2* target = (L == j0) ? static_cast<float2*>(vis_out) : tmp;
         if (L == j0 && j0_nodes >= WT_TRUNCATED_TC_MIN_NODES) {
-            rc = eq16_tc_launch(recs + seg.off[L], views, capl, uvw, n_vis, target, sign, status, s, fn);
+            rc = eq16_tc_launch(recs + seg.off[L], views, capl, j0_nodes, uvw, n_vis, target, sign, status, s, fn);
         } else {
             WaveletJob jb{};
             jb.recf_leaf = recs + seg.off[L];

@@ -536,8 +536,9 @@ int predict_wavelet(wt_tree t, const double* uvw, int64_t n_vis, void* vis, int 
             return set_error(WT_ERR_UNSUPPORTED, "wt_predict_vis: WT_MIXED_TC is Eq. 16 only (WT_SUM_EQ16)");
         int* status = device_status_word();
         if (!status) return set_error(WT_ERR_CUDA, "wt_predict_vis: no device status word");
-        return eq16_tc_launch(t->d.leaff, t->d.hdr, t->cap_leaves, uvw, n_vis, static_cast<float2*>(vis), sign, status,
-                              s, "wt_predict_vis");
+        const int64_t hint = tree_sync_header(t) == WT_OK ? t->host_hdr->n_leaves : -1;
+        return eq16_tc_launch(t->d.leaff, t->d.hdr, t->cap_leaves, hint, uvw, n_vis, static_cast<float2*>(vis), sign,
+                              status, s, "wt_predict_vis");
     }
     WaveletJob jb;
     jb.recd = t->d.recd;

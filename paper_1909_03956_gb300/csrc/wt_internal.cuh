@@ -729,8 +729,8 @@ int check_device_buffer(const void* p, size_t bytes, const char* fn, const char*
 // Alignment of a visibility buffer of `mode` (complex128 or complex64).
 inline size_t vis_align(int mode) { return (mode == WT_FP64 || mode == WT_FP64_DF) ? 16 : 8; }
 // dft_tc.cu: Eq. 16 over leaf records with the phase on the tensor cores
-int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, const double* uvw, int64_t n_vis,
-                   float2* vis, int sign, int* status, cudaStream_t s, const char* fn);
+int eq16_tc_launch(const RecF* recs, const TreeHeader* hdr, int64_t cap, int64_t n_hint, const double* uvw,
+                   int64_t n_vis, float2* vis, int sign, int* status, cudaStream_t s, const char* fn);
 // dft.cu
 int predict_dft(const double* l, const double* m, const double* flux, int64_t n_comp, const double* uvw,
                 int64_t n_vis, void* vis, int mode, int sign, cudaStream_t s);
